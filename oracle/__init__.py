@@ -1,0 +1,335 @@
+"""FP64 CPU oracle for the LoopSmart global registration hot path.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package. The
+product path (``paper_1801_01572_gb300``) never imports it, and the two share no
+code: the oracle is plain C (``lsr_oracle.c``) compiled with gcc, wrapped here
+with ctypes and numpy.
+
+Every function follows a passage of the paper (Sec. IV, Algorithm 1, eq. (1),
+eq. (3)-(5)) or the FPFH definition the paper cites (Rusu et al., ICRA 2009);
+the C file states the passage and the reading taken where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lsr_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liblsr_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+D = 33
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(C.Structure):
+    _fields_ = [("r_normal", C.c_double), ("r_feature", C.c_double), ("eps_inlier", C.c_double),
+                ("tau", C.c_double), ("cos_normal", C.c_double), ("min_inlier_ratio", C.c_double),
+                ("mu_scale", C.c_double), ("n_hypotheses", C.c_int64), ("refine_iters", C.c_int32),
+                ("pad_", C.c_int32), ("seed", C.c_uint64), ("pair_id", C.c_uint64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("T", C.c_double * 16), ("T_hyp", C.c_double * 16), ("inliers", C.c_int64),
+                ("survivors", C.c_int64), ("best_h", C.c_int64), ("hyp_inliers", C.c_int64),
+                ("n_normal_ok", C.c_int64), ("fitness", C.c_double), ("hyp_fitness", C.c_double),
+                ("status", C.c_int32), ("refine_iters_done", C.c_int32)]
+
+
+DEFAULTS = dict(r_normal=0.05, r_feature=0.125, eps_inlier=0.0375, tau=0.9,
+                cos_normal=float(np.cos(np.deg2rad(30.0))), min_inlier_ratio=0.05, mu_scale=1.0,
+                n_hypotheses=4_000_000, refine_iters=50, seed=0, pair_id=0)
+
+
+def _P(a, dt):
+    return a.ctypes.data_as(C.POINTER(dt)) if a is not None else None
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            dp, ip, up8, u64p = C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_uint8), C.POINTER(C.c_uint64)
+            i64, dbl = C.c_int64, C.c_double
+            sig = {
+                "orc_set_threads": (None, [C.c_int]),
+                "orc_get_threads": (C.c_int, []),
+                "orc_radius_count_brute": (None, [dp, i64, dp, i64, dbl, ip]),
+                "orc_radius_count_grid": (None, [dp, i64, dp, i64, dbl, ip]),
+                "orc_eig3": (None, [dp, dp, dp]),
+                "orc_normals": (None, [dp, i64, dp, dbl, ip, i64, dp, dp, ip, dp]),
+                "orc_pair_features": (C.c_int, [dp, dp, dp, dp, dp]),
+                "orc_spfh": (None, [dp, dp, i64, dbl, ip, i64, dbl, dp, ip, ip]),
+                "orc_fpfh": (None, [dp, dp, dp, i64, dbl, ip, i64, dp]),
+                "orc_match": (None, [dp, i64, dp, i64, i64, ip, i64, ip, dp, dp]),
+                "orc_philox4x64_10": (None, [u64p, u64p, u64p]),
+                "orc_sample_indices": (None, [C.c_uint64, C.c_uint64, i64, i64, i64, ip]),
+                "orc_hypotheses": (None, [dp, i64, dp, i64, ip, up8, up8, i64, C.c_uint64, C.c_uint64, dbl, up8]),
+                "orc_kabsch": (None, [dp, dp, i64, dp, dp]),
+                "orc_nn_within_grid": (None, [dp, i64, dp, i64, dbl, ip, dp]),
+                "orc_nn_within_brute": (None, [dp, i64, dp, i64, dbl, ip, dp]),
+                "orc_consensus": (None, [dp, i64, dp, i64, dp, dp, i64, dbl, dbl, ip, dp, ip]),
+                "orc_exp_so3": (None, [dp, dp]),
+                "orc_apply_xi": (None, [dp, dp, dp]),
+                "orc_refine": (C.c_int, [dp, i64, dp, i64, dp, dbl, dbl, C.c_int, dbl, dp]),
+                "orc_objective": (C.c_double, [dp, i64, dp, i64, dp, dp, dbl, dbl, dp, dp, dp, ip]),
+                "orc_register": (C.c_int, [dp, i64, dp, i64, dp, dp, C.POINTER(Params), C.POINTER(Result), dp, dp, ip]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _f64(a, shape_last=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape_last is not None:
+        a = a.reshape(-1, shape_last)
+    return a
+
+
+def _idx(qidx):
+    if qidx is None:
+        return None, 0
+    q = np.ascontiguousarray(np.asarray(qidx, dtype=np.int64))
+    return q, len(q)
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+# ------------------------------------------------------------------ neighbours
+def radius_count_brute(P, X, r):
+    P, X = _f64(P, 3), _f64(X, 3)
+    out = np.zeros(len(X), np.int64)
+    lib().orc_radius_count_brute(_P(P, C.c_double), len(P), _P(X, C.c_double), len(X), r, _P(out, C.c_int64))
+    return out
+
+
+def radius_count_grid(P, X, r):
+    P, X = _f64(P, 3), _f64(X, 3)
+    out = np.zeros(len(X), np.int64)
+    lib().orc_radius_count_grid(_P(P, C.c_double), len(P), _P(X, C.c_double), len(X), r, _P(out, C.c_int64))
+    return out
+
+
+def nn_within(Q, X, r, brute=False):
+    Q, X = _f64(Q, 3), _f64(X, 3)
+    nn = np.zeros(len(X), np.int64)
+    d2 = np.zeros(len(X), np.float64)
+    f = lib().orc_nn_within_brute if brute else lib().orc_nn_within_grid
+    f(_P(Q, C.c_double), len(Q), _P(X, C.c_double), len(X), r, _P(nn, C.c_int64), _P(d2, C.c_double))
+    return nn, d2
+
+
+def eig3(A):
+    A = _f64(A).reshape(9)
+    w = np.zeros(3)
+    V = np.zeros(9)
+    lib().orc_eig3(_P(A, C.c_double), _P(w, C.c_double), _P(V, C.c_double))
+    return w, V.reshape(3, 3)
+
+
+# ------------------------------------------------------------------ normals
+def normals(P, vp=(0.0, 0.0, 0.0), r=0.05, qidx=None):
+    """Returns (normals nq x 3, curvature nq, count nq, diag nq x 3)."""
+    P = _f64(P, 3)
+    vp = _f64(vp).reshape(3)
+    q, nq = _idx(qidx)
+    m = nq if q is not None else len(P)
+    nrm, curv = np.zeros((m, 3)), np.zeros(m)
+    cnt, diag = np.zeros(m, np.int64), np.zeros((m, 3))
+    lib().orc_normals(_P(P, C.c_double), len(P), _P(vp, C.c_double), r, _P(q, C.c_int64), nq,
+                      _P(nrm, C.c_double), _P(curv, C.c_double), _P(cnt, C.c_int64), _P(diag, C.c_double))
+    return nrm, curv, cnt, diag
+
+
+# ------------------------------------------------------------------ FPFH
+def pair_features(ps, ns, pt, nt):
+    a = [_f64(v).reshape(3) for v in (ps, ns, pt, nt)]
+    f = np.zeros(3)
+    ok = lib().orc_pair_features(*[_P(v, C.c_double) for v in a], _P(f, C.c_double))
+    return bool(ok), f
+
+
+def spfh(P, N, r=0.125, qidx=None, delta=1e-4):
+    """Returns (spfh nq x 33, k nq, nclose nq)."""
+    P, N = _f64(P, 3), _f64(N, 3)
+    q, nq = _idx(qidx)
+    m = nq if q is not None else len(P)
+    S = np.zeros((m, D))
+    k, nc = np.zeros(m, np.int64), np.zeros(m, np.int64)
+    lib().orc_spfh(_P(P, C.c_double), _P(N, C.c_double), len(P), r, _P(q, C.c_int64), nq, delta,
+                   _P(S, C.c_double), _P(k, C.c_int64), _P(nc, C.c_int64))
+    return S, k, nc
+
+
+def fpfh(P, N, S, r=0.125, qidx=None):
+    P, N, S = _f64(P, 3), _f64(N, 3), _f64(S, D)
+    q, nq = _idx(qidx)
+    m = nq if q is not None else len(P)
+    F = np.zeros((m, D))
+    lib().orc_fpfh(_P(P, C.c_double), _P(N, C.c_double), _P(S, C.c_double), len(P), r, _P(q, C.c_int64), nq,
+                   _P(F, C.c_double))
+    return F
+
+
+# ------------------------------------------------------------------ matching
+def match(A, B, qidx=None):
+    """Brute-force NN of each row of A among the rows of B: (nn, d1, d2)."""
+    A = _f64(A)
+    B = _f64(B)
+    dim = A.shape[1]
+    q, nq = _idx(qidx)
+    m = nq if q is not None else len(A)
+    nn, d1, d2 = np.zeros(m, np.int64), np.zeros(m), np.zeros(m)
+    lib().orc_match(_P(A, C.c_double), len(A), _P(B, C.c_double), len(B), dim, _P(q, C.c_int64), nq,
+                    _P(nn, C.c_int64), _P(d1, C.c_double), _P(d2, C.c_double))
+    return nn, d1, d2
+
+
+# ------------------------------------------------------------------ RNG + hypotheses
+def philox4x64_10(ctr, key):
+    c = np.ascontiguousarray(np.asarray(ctr, np.uint64).reshape(4))
+    k = np.ascontiguousarray(np.asarray(key, np.uint64).reshape(2))
+    out = np.zeros(4, np.uint64)
+    lib().orc_philox4x64_10(_P(c, C.c_uint64), _P(k, C.c_uint64), _P(out, C.c_uint64))
+    return out
+
+
+def sample_indices(seed, pair, h0, nh, n):
+    out = np.zeros((nh, 4), np.int64)
+    lib().orc_sample_indices(C.c_uint64(seed), C.c_uint64(pair), h0, nh, n, _P(out, C.c_int64))
+    return out
+
+
+def hypotheses(P, Q, nn, validP, validQ, H, seed, pair, tau=0.9):
+    """Per-hypothesis flag: 0 rejected, 1 survives, 2 ambiguous."""
+    P, Q = _f64(P, 3), _f64(Q, 3)
+    nn = np.ascontiguousarray(np.asarray(nn, np.int64))
+    vP = np.ascontiguousarray(np.asarray(validP, np.uint8))
+    vQ = np.ascontiguousarray(np.asarray(validQ, np.uint8))
+    flag = np.zeros(H, np.uint8)
+    lib().orc_hypotheses(_P(P, C.c_double), len(P), _P(Q, C.c_double), len(Q), _P(nn, C.c_int64),
+                         _P(vP, C.c_uint8), _P(vQ, C.c_uint8), H, C.c_uint64(seed), C.c_uint64(pair), tau,
+                         _P(flag, C.c_uint8))
+    return flag
+
+
+# ------------------------------------------------------------------ pose
+def kabsch(p, q):
+    p, q = _f64(p, 3), _f64(q, 3)
+    R, t = np.zeros(9), np.zeros(3)
+    lib().orc_kabsch(_P(p, C.c_double), _P(q, C.c_double), len(p), _P(R, C.c_double), _P(t, C.c_double))
+    return R.reshape(3, 3), t
+
+
+def consensus(P, Q, Rs, ts, eps, band=0.0):
+    """Inlier count, sum of squared inlier distances, and near-eps count per pose."""
+    P, Q = _f64(P, 3), _f64(Q, 3)
+    Rs = _f64(Rs).reshape(-1, 9)
+    ts = _f64(ts).reshape(-1, 3)
+    nh = len(Rs)
+    cnt, amb = np.zeros(nh, np.int64), np.zeros(nh, np.int64)
+    sd = np.zeros(nh)
+    lib().orc_consensus(_P(P, C.c_double), len(P), _P(Q, C.c_double), len(Q), _P(Rs, C.c_double),
+                        _P(ts, C.c_double), nh, eps, band, _P(cnt, C.c_int64), _P(sd, C.c_double), _P(amb, C.c_int64))
+    return cnt, sd, amb
+
+
+def exp_so3(w):
+    w = _f64(w).reshape(3)
+    R = np.zeros(9)
+    lib().orc_exp_so3(_P(w, C.c_double), _P(R, C.c_double))
+    return R.reshape(3, 3)
+
+
+def apply_xi(xi, T):
+    xi = _f64(xi).reshape(6)
+    T = _f64(T).reshape(16)
+    out = np.zeros(16)
+    lib().orc_apply_xi(_P(xi, C.c_double), _P(T, C.c_double), _P(out, C.c_double))
+    return out.reshape(4, 4)
+
+
+def refine(P, Q, T, eps_r, mu, iters=30, tol=1e-10):
+    P, Q = _f64(P, 3), _f64(Q, 3)
+    T = _f64(T).reshape(16)
+    out = np.zeros(16)
+    n = lib().orc_refine(_P(P, C.c_double), len(P), _P(Q, C.c_double), len(Q), _P(T, C.c_double), eps_r, mu,
+                         iters, tol, _P(out, C.c_double))
+    return out.reshape(4, 4), int(n)
+
+
+def objective(P, Q, xi, T0, eps, mu, grad=True):
+    """E and (if grad) dE/dP, dE/dQ, dE/dxi, plus the NN index of each point."""
+    P, Q = _f64(P, 3), _f64(Q, 3)
+    xi = _f64(xi).reshape(6)
+    T0 = _f64(T0).reshape(16)
+    nn = np.zeros(len(P), np.int64)
+    if grad:
+        dP, dQ, dxi = np.zeros((len(P), 3)), np.zeros((len(Q), 3)), np.zeros(6)
+    else:
+        dP = dQ = dxi = None
+    E = lib().orc_objective(_P(P, C.c_double), len(P), _P(Q, C.c_double), len(Q), _P(xi, C.c_double),
+                            _P(T0, C.c_double), eps, mu, _P(dP, C.c_double), _P(dQ, C.c_double),
+                            _P(dxi, C.c_double), _P(nn, C.c_int64))
+    return float(E), dP, dQ, dxi, nn
+
+
+def make_params(**kw) -> Params:
+    d = dict(DEFAULTS)
+    d.update(kw)
+    p = Params()
+    for k, v in d.items():
+        setattr(p, k, v)
+    return p
+
+
+def register(P, Q, vpP=(0, 0, 0), vpQ=(0, 0, 0), debug=False, **kw):
+    """Algorithm 1 end to end, then the robust refinement. Returns a dict."""
+    P, Q = _f64(P, 3), _f64(Q, 3)
+    vpP = _f64(vpP).reshape(3)
+    vpQ = _f64(vpQ).reshape(3)
+    prm = make_params(**kw)
+    res = Result()
+    fP = np.zeros((len(P), D)) if debug else None
+    fQ = np.zeros((len(Q), D)) if debug else None
+    nn = np.zeros(len(P), np.int64) if debug else None
+    rc = lib().orc_register(_P(P, C.c_double), len(P), _P(Q, C.c_double), len(Q), _P(vpP, C.c_double),
+                            _P(vpQ, C.c_double), C.byref(prm), C.byref(res), _P(fP, C.c_double),
+                            _P(fQ, C.c_double), _P(nn, C.c_int64))
+    out = dict(rc=rc, T=np.array(res.T).reshape(4, 4), T_hyp=np.array(res.T_hyp).reshape(4, 4),
+               inliers=res.inliers, fitness=res.fitness, status=res.status, survivors=res.survivors,
+               best_h=res.best_h, hyp_inliers=res.hyp_inliers, hyp_fitness=res.hyp_fitness,
+               n_normal_ok=res.n_normal_ok, refine_iters=res.refine_iters_done)
+    if debug:
+        out.update(FP=fP, FQ=fQ, nn=nn)
+    return out
