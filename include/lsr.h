@@ -1,0 +1,232 @@
+/*
+ * lsr.h -- C ABI of the GB300 (sm_103a) implementation of the global point
+ * cloud registration of LoopSmart (Zhang & Chen, arXiv 1801.01572), Sec. IV,
+ * Algorithm 1 ("Global Registration on GPU"), with the robust refinement and
+ * alignment objective of eq. (3)-(5).
+ *
+ * Given two fragments P and Q (float32 xyz, N x 3 row-major), the library
+ * estimates T_QP (q ~ T p) with no initial pose: radius-PCA normals, FPFH
+ * descriptors (Rusu et al. 2009, the descriptor of Alg. 1 line 2), the feature
+ * pre-matching cache (Alg. 1, "Parallel FPFH feature pre-matching"), 4-point
+ * hypotheses with polygon pre-rejection (Alg. 1, tau of Sec. IV), stream
+ * compaction, consensus on a 3D grid (eq. (1)), selection, and a robust
+ * Geman-McClure refinement (the line process of eq. (4) eliminated).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: LSR_OK (0) or a negative LSR_E_* code. On error, outputs
+ *    are unspecified and lsr_last_error(ctx) holds a one-line message.
+ *    "No alignment found" is NOT an error: it is result.status (Alg. 1 only
+ *    returns a pose "if hypothesis found").
+ *  - Point / descriptor arrays may be device pointers (cudaMalloc, torch CUDA
+ *    tensors) or host pointers (pageable or pinned); host inputs are copied to
+ *    the device inside the call and host outputs are copied back before it
+ *    returns. Arrays must be contiguous and 4-byte aligned. The caller owns all
+ *    input and output buffers; the library owns its device workspace, which
+ *    grows on demand and is released by lsr_destroy.
+ *  - All device work is ordered on the context's stream. Entry points that
+ *    return results in host memory synchronise that stream once before
+ *    returning.
+ *  - A context is not thread-safe: use one context per host thread.
+ *  - Indices are 0-based and refer to the caller's point order.
+ */
+#ifndef LSR_H
+#define LSR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LSR_API __attribute__((visibility("default")))
+#else
+#define LSR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define LSR_OK 0
+#define LSR_E_ARG (-1)     /* invalid argument: NULL pointer, n < 4, size too large, bad parameter */
+#define LSR_E_CUDA (-2)    /* a CUDA runtime call or kernel launch failed */
+#define LSR_E_OOM (-3)     /* device or host memory allocation failed */
+#define LSR_E_TIMEOUT (-4) /* a bounded device-side wait ran out */
+#define LSR_E_STATE (-5)   /* context not usable (NULL, destroyed, or a previous sticky CUDA error) */
+
+#define LSR_STATUS_ALIGNED 0
+#define LSR_STATUS_NO_ALIGNMENT 1
+
+#define LSR_MATCH_FP32 0 /* descriptor matching on FP32 SIMT cores */
+#define LSR_MATCH_BF16 1 /* BF16 tensor-core candidates + FP32 re-rank */
+
+#define LSR_DESC_DIM 33 /* FPFH: 3 angular features x 11 bins */
+
+typedef struct lsr_ctx lsr_ctx;
+
+/* Parameters. Defaults (lsr_default_params) are the paper's hyper-parameters
+ * (Sec. IV: normal radius 0.1 m, FPFH radius 0.25 m, 4,000,000 hypotheses,
+ * maximum correspondence distance 0.075 m, tau = 0.9) with the radii scaled to
+ * the 5 cm / 12.5 cm neighbourhoods of the synthetic fragments, keeping the
+ * paper's ratio eps = 0.75 r_normal. */
+typedef struct {
+  float r_normal;         /* normal estimation radius (m), default 0.05 */
+  float r_feature;        /* FPFH radius (m), default 0.125 */
+  float eps_inlier;       /* maximum correspondence distance (m), default 0.0375 */
+  float tau;              /* polygon similarity threshold, default 0.9 */
+  float cos_normal;       /* normal check: reject a hypothesis if any sampled pair has cos(R n_p, n_q) below this; default cos(30 deg) */
+  float min_inlier_ratio; /* accept the best hypothesis if inliers / |P| >= this; default 0.05 */
+  float mu_scale;         /* Geman-McClure scale: mu = mu_scale * r^2 at refinement radius r; default 1 */
+  int32_t refine_iters;   /* maximum refinement iterations per level, default 50 */
+  int64_t n_hypotheses;   /* sampled hypotheses per pair, default 4,000,000 (at most 2^31 - 1) */
+  uint64_t seed;          /* hypothesis RNG key word 0 (Philox-4x64-10 key = (seed, pair_id)) */
+  uint64_t pair_id;       /* RNG key word 1 for lsr_register_pair; a batch uses pair_id + i */
+  int32_t match_precision; /* LSR_MATCH_FP32 (default) or LSR_MATCH_BF16 */
+  int32_t refine_levels;  /* graduated refinement levels L (1..8), default 4: radius eps * 2^(L-1-l) at level l */
+  int32_t reserved_[4];
+} lsr_params;
+
+/* Result of one registration. */
+typedef struct {
+  double T[16];           /* row-major 4x4 T_QP (q ~ T p); identity if status is NO_ALIGNMENT */
+  double T_hyp[16];       /* pose of the selected 4-point hypothesis before refinement */
+  int64_t inliers;        /* points of P with a Q point closer than eps under T */
+  int64_t hyp_inliers;    /* inliers of the selected hypothesis */
+  int64_t survivors;      /* hypotheses left after pre-rejection */
+  int64_t n_normal_ok;    /* survivors that also pass the normal check */
+  int64_t best_h;         /* id of the selected hypothesis, -1 if none */
+  int64_t match_fallbacks; /* BF16 matching: queries re-scanned exactly in FP32 */
+  float fitness;          /* mean squared inlier distance under T (m^2) */
+  float hyp_fitness;      /* the same for the selected hypothesis */
+  int32_t status;         /* LSR_STATUS_ALIGNED or LSR_STATUS_NO_ALIGNMENT */
+  int32_t refine_iters_done;
+  float stage_ms[8];      /* per-stage device time when profiling is enabled, else 0:
+                             [0] pack+grids [1] normals [2] SPFH+FPFH [3] matching
+                             [4] hypotheses [5] consensus [6] selection+refinement [7] total */
+} lsr_result;
+
+/* Fill p with the defaults described above. */
+LSR_API void lsr_default_params(lsr_params *p);
+
+/* Create a context on CUDA device `device`. params may be NULL (defaults).
+ * cuda_stream: a cudaStream_t to order all work on, or NULL for a new
+ * non-blocking stream owned by the context. */
+LSR_API int lsr_create(lsr_ctx **out, const lsr_params *params, int device, void *cuda_stream);
+
+/* Release the context, its stream (if owned) and its workspace. NULL is a no-op. */
+LSR_API int lsr_destroy(lsr_ctx *ctx);
+
+/* Replace the context's parameters (validated; LSR_E_ARG if out of range). */
+LSR_API int lsr_set_params(lsr_ctx *ctx, const lsr_params *params);
+LSR_API int lsr_get_params(const lsr_ctx *ctx, lsr_params *params);
+
+/* Enable (1) or disable (0) per-stage CUDA-event timing in lsr_result.stage_ms. */
+LSR_API int lsr_set_profiling(lsr_ctx *ctx, int enable);
+
+/* Static message for a return code, and the last error message of a context. */
+LSR_API const char *lsr_error_string(int code);
+LSR_API const char *lsr_last_error(const lsr_ctx *ctx);
+
+/* Bytes of device workspace currently held by the context. */
+LSR_API int64_t lsr_workspace_bytes(const lsr_ctx *ctx);
+
+/* Algorithm 1 followed by the robust refinement, for one pair.
+ * P: nP x 3 float32, Q: nQ x 3 float32 (device or host). vpP / vpQ: viewpoints
+ * (3 floats, host) the normals of each cloud are oriented toward; NULL means
+ * the origin. out: host. nP, nQ >= 4. */
+LSR_API int lsr_register_pair(lsr_ctx *ctx, const float *P, int64_t nP, const float *Q, int64_t nQ, const float *vpP,
+                      const float *vpQ, lsr_result *out);
+
+/* Batched loop-candidate verification: n independent pairs, pair i with RNG
+ * key (seed, pair_id + i). P[i], Q[i]: clouds (device or host); vp: n x 6 host
+ * floats (vpP, vpQ per pair) or NULL; out: n host results. Equivalent to n
+ * calls of lsr_register_pair, scheduled together. */
+LSR_API int lsr_register_batch(lsr_ctx *ctx, int32_t n, const float *const *P, const int64_t *nP, const float *const *Q,
+                       const int64_t *nQ, const float *vp, lsr_result *out);
+
+/* ------------------------------------------------------------------------
+ * Stage entry points. Each runs one stage of the path on caller-supplied
+ * inputs (the same kernels the full registration launches), so that every
+ * stage can be checked on its own. Arrays are in the caller's point order.
+ * ------------------------------------------------------------------------ */
+
+/* Normals (needed by FPFH, Alg. 1 line 2; radius of Sec. IV): eigenvector of
+ * the smallest eigenvalue of the covariance of the points within r (inclusive,
+ * the point itself included), oriented toward vp; fewer than 3 neighbours give
+ * a zero normal and curvature -1. normals: n x 3, count: n (neighbours),
+ * curvature: n (lambda0 / sum lambda). Any output may be NULL. */
+LSR_API int lsr_stage_normals(lsr_ctx *ctx, const float *P, int64_t n, const float *vp, float r, float *normals, int32_t *count,
+                      float *curvature);
+
+/* SPFH (Rusu et al. 2009) of every point from given normals (n x 3, zero =
+ * invalid): per pair within r, the Darboux-frame angles (alpha, phi, theta)
+ * binned 3 x 11, each sub-histogram scaled to sum 1. spfh: n x 33, k: n pairs
+ * used (either may be NULL). */
+LSR_API int lsr_stage_spfh(lsr_ctx *ctx, const float *P, const float *normals, int64_t n, float r, float *spfh, int32_t *k);
+
+/* FPFH from given SPFH (n x 33): F(p) = SPFH(p) + (1/k) sum SPFH(q) / |q - p|
+ * over valid neighbours within r, each sub-histogram rescaled to sum 1. */
+LSR_API int lsr_stage_fpfh(lsr_ctx *ctx, const float *P, const float *normals, const float *spfh, int64_t n, float r,
+                   float *fpfh);
+
+/* Feature pre-matching (Alg. 1): nn[i] = argmin_j |FP_i - FQ_j|^2 (ties to the
+ * smallest j), d1[i] its squared distance. FP: nP x 33, FQ: nQ x 33.
+ * precision: LSR_MATCH_FP32 or LSR_MATCH_BF16. fallbacks (host, may be NULL):
+ * BF16 queries that were re-scanned in FP32. */
+LSR_API int lsr_stage_match(lsr_ctx *ctx, const float *FP, int64_t nP, const float *FQ, int64_t nQ, int32_t precision,
+                    int32_t *nn, float *d1, int64_t *fallbacks);
+
+/* Hypothesis sampling + polygon pre-rejection + compaction (Alg. 1). Samples
+ * hypotheses h = 0..H-1 with Philox-4x64-10(counter (h,0,0,0), key (seed,
+ * pair_id)), index k = floor(word_k * nP / 2^64); rejects repeated indices,
+ * invalid points (valid* == 0), cyclic edges shorter than 1e-6, and edges with
+ * |p_k - p_k+1| < tau |q_k - q_k+1| or the reverse. surv (capacity cap,
+ * device or host): surviving ids in ascending order; *nsurv (host): their
+ * number (may exceed cap, in which case only cap ids are written). */
+LSR_API int lsr_stage_hypotheses(lsr_ctx *ctx, const float *P, int64_t nP, const float *Q, int64_t nQ, const int32_t *nn,
+                         const uint8_t *validP, const uint8_t *validQ, int64_t H, uint64_t seed, uint64_t pair_id,
+                         float tau, int32_t *surv, int64_t cap, int64_t *nsurv);
+
+/* Rigid transform from 4 point pairs per hypothesis (Alg. 1, "Estimate
+ * transformation"): ps, qs: nh x 4 x 3; Rt: nh x 12 (row-major [R | t]). */
+LSR_API int lsr_stage_rigid4(lsr_ctx *ctx, const float *ps, const float *qs, int64_t nh, float *Rt);
+
+/* Consensus (Alg. 1, "Consensus for the remaining quadruple pairs"; grid of
+ * eq. (1)): for each pose Rt (nh x 12, row-major [R | t]) count the points of
+ * P whose nearest Q point is closer than eps, and sum their squared distances.
+ * count: nh int32, sumd2: nh double. */
+LSR_API int lsr_stage_consensus(lsr_ctx *ctx, const float *P, int64_t nP, const float *Q, int64_t nQ, const float *Rt,
+                        int64_t nh, float eps, int32_t *count, double *sumd2);
+
+/* Graduated robust refinement from T_in (host, 4x4 row-major double). Level
+ * l = 0..levels-1 iterates Geman-McClure IRLS (at most iters steps) with exact
+ * NN within r_l = eps * 2^(levels-1-l), mu_l = mu_scale * r_l^2, on the points
+ * of P and Q whose caller index is a multiple of s_l = max(1, min(4^(levels-1-l),
+ * N / 4096)) (per cloud). T_out (host, double[16]); iters_done (host, may be
+ * NULL): total steps taken. */
+LSR_API int lsr_stage_refine(lsr_ctx *ctx, const float *P, int64_t nP, const float *Q, int64_t nQ, const double *T_in,
+                             float eps, float mu_scale, int32_t levels, int32_t iters, double *T_out,
+                             int32_t *iters_done);
+
+/* ------------------------------------------------------------------------
+ * Robust alignment objective (the refinement's cost, eq. (3)-(4) with the
+ * line process eliminated) and its adjoint, for n pairs.
+ * Pair i: E_i = sum_j rho~(|T_i p_j - q_nn(j)|^2) over the points whose nearest
+ * Q point is within eps, with T_i = [Exp(xi_i[0:3]) | xi_i[3:6]] * T0_i
+ * (xi = (alpha, beta, gamma, x, y, z) as in eq. (5)), rho(s) = mu s / (mu + s)
+ * and rho~(s) = rho(s) - rho(eps^2). Nearest neighbours are recomputed by the
+ * backward call, never stored.
+ * P[i], Q[i]: device float32 clouds; xi: n x 6 double; T0: n x 16 double;
+ * E: n double (all host or all device, as the point arrays). dE: n double
+ * upstream gradients. dP[i], dQ[i]: device float32 gradients (written, not
+ * accumulated), dxi: n x 6 double.
+ * ------------------------------------------------------------------------ */
+LSR_API int lsr_objective_fwd(lsr_ctx *ctx, int32_t n, const float *const *P, const int64_t *nP, const float *const *Q,
+                      const int64_t *nQ, const double *xi, const double *T0, float eps, float mu, double *E);
+LSR_API int lsr_objective_bwd(lsr_ctx *ctx, int32_t n, const float *const *P, const int64_t *nP, const float *const *Q,
+                      const int64_t *nQ, const double *xi, const double *T0, float eps, float mu, const double *dE,
+                      float *const *dP, float *const *dQ, double *dxi);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSR_H */

@@ -45,7 +45,7 @@ class Params(C.Structure):
     _fields_ = [("r_normal", C.c_double), ("r_feature", C.c_double), ("eps_inlier", C.c_double),
                 ("tau", C.c_double), ("cos_normal", C.c_double), ("min_inlier_ratio", C.c_double),
                 ("mu_scale", C.c_double), ("n_hypotheses", C.c_int64), ("refine_iters", C.c_int32),
-                ("pad_", C.c_int32), ("seed", C.c_uint64), ("pair_id", C.c_uint64)]
+                ("refine_levels", C.c_int32), ("seed", C.c_uint64), ("pair_id", C.c_uint64)]
 
 
 class Result(C.Structure):
@@ -57,7 +57,7 @@ class Result(C.Structure):
 
 DEFAULTS = dict(r_normal=0.05, r_feature=0.125, eps_inlier=0.0375, tau=0.9,
                 cos_normal=float(np.cos(np.deg2rad(30.0))), min_inlier_ratio=0.05, mu_scale=1.0,
-                n_hypotheses=4_000_000, refine_iters=50, seed=0, pair_id=0)
+                n_hypotheses=4_000_000, refine_iters=50, refine_levels=4, seed=0, pair_id=0)
 
 
 def _P(a, dt):
@@ -92,6 +92,8 @@ def lib():
                 "orc_exp_so3": (None, [dp, dp]),
                 "orc_apply_xi": (None, [dp, dp, dp]),
                 "orc_refine": (C.c_int, [dp, i64, dp, i64, dp, dbl, dbl, C.c_int, dbl, dp]),
+                "orc_refine_gnc": (C.c_int, [dp, i64, dp, i64, dp, dbl, dbl, C.c_int, C.c_int, dbl, dp]),
+                "orc_gnc_stride": (i64, [i64, C.c_int, C.c_int]),
                 "orc_objective": (C.c_double, [dp, i64, dp, i64, dp, dp, dbl, dbl, dp, dp, dp, ip]),
                 "orc_register": (C.c_int, [dp, i64, dp, i64, dp, dp, C.POINTER(Params), C.POINTER(Result), dp, dp, ip]),
             }
@@ -286,6 +288,20 @@ def refine(P, Q, T, eps_r, mu, iters=30, tol=1e-10):
     n = lib().orc_refine(_P(P, C.c_double), len(P), _P(Q, C.c_double), len(Q), _P(T, C.c_double), eps_r, mu,
                          iters, tol, _P(out, C.c_double))
     return out.reshape(4, 4), int(n)
+
+
+def refine_gnc(P, Q, T, eps, mu_scale=1.0, levels=4, iters=50, tol=1e-10):
+    """Graduated refinement: radii eps * 2^(L-1-l), subsets by caller index."""
+    P, Q = _f64(P, 3), _f64(Q, 3)
+    T = _f64(T).reshape(16)
+    out = np.zeros(16)
+    n = lib().orc_refine_gnc(_P(P, C.c_double), len(P), _P(Q, C.c_double), len(Q), _P(T, C.c_double), eps,
+                             mu_scale, levels, iters, tol, _P(out, C.c_double))
+    return out.reshape(4, 4), int(n)
+
+
+def gnc_stride(n, level, levels):
+    return int(lib().orc_gnc_stride(int(n), int(level), int(levels)))
 
 
 def objective(P, Q, xi, T0, eps, mu, grad=True):

@@ -1214,6 +1214,44 @@ int orc_refine(const double *P, int64_t nP, const double *Q, int64_t nQ, const d
 }
 
 /* ------------------------------------------------------------------------ */
+/* Graduated refinement (reading: the paper gives no refinement schedule;    */
+/* this follows the graduated non-convexity of Fast Global Registration,    */
+/* Zhou et al. 2016, which the paper compares against). Level l = 0..L-1     */
+/* runs the refinement above with radius eps_l = eps * 2^(L-1-l) and          */
+/* mu_l = mu_scale * eps_l^2 on the subsets P_l = {p_i : i mod sP_l = 0} and */
+/* Q_l = {q_j : j mod sQ_l = 0}, s_l = max(1, min(4^(L-1-l), N / 4096)), so  */
+/* the coarse levels see a smooth cost and the result does not depend on    */
+/* which nearby hypothesis started it.                                        */
+/* ------------------------------------------------------------------------ */
+int64_t orc_gnc_stride(int64_t n, int level, int levels) {
+  int64_t f = 1;
+  for (int k = 0; k < levels - 1 - level; ++k) f *= 4;
+  int64_t cap = n / 4096;
+  if (f > cap) f = cap;
+  return f < 1 ? 1 : f;
+}
+
+int orc_refine_gnc(const double *P, int64_t nP, const double *Q, int64_t nQ, const double T_in[16], double eps,
+                   double mu_scale, int levels, int iters, double tol, double T_out[16]) {
+  double T[16];
+  memcpy(T, T_in, sizeof(T));
+  int total = 0;
+  for (int l = 0; l < levels; ++l) {
+    double e = eps * (double)(1LL << (levels - 1 - l));
+    int64_t sp = orc_gnc_stride(nP, l, levels), sq = orc_gnc_stride(nQ, l, levels);
+    int64_t mp = (nP + sp - 1) / sp, mq = (nQ + sq - 1) / sq;
+    double *Ps = (double *)malloc(sizeof(double) * 3 * (size_t)mp), *Qs = (double *)malloc(sizeof(double) * 3 * (size_t)mq);
+    for (int64_t i = 0; i < mp; ++i) memcpy(Ps + 3 * i, P + 3 * i * sp, sizeof(double) * 3);
+    for (int64_t j = 0; j < mq; ++j) memcpy(Qs + 3 * j, Q + 3 * j * sq, sizeof(double) * 3);
+    total += orc_refine(Ps, mp, Qs, mq, T, e, mu_scale * e * e, iters, tol, T);
+    free(Ps);
+    free(Qs);
+  }
+  memcpy(T_out, T, sizeof(T));
+  return total;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Robust alignment objective and its analytic gradient (the objective of   */
 /* the refinement above, with NN correspondences recomputed at the given   */
 /* pose): E = sum_i rho~(s_i), s_i = |T(xi) p_i - q_n(i)|^2 over the points */
@@ -1281,8 +1319,8 @@ double orc_objective(const double *P, int64_t nP, const double *Q, int64_t nQ, c
 typedef struct {
   double r_normal, r_feature, eps_inlier, tau, cos_normal, min_inlier_ratio, mu_scale;
   int64_t n_hypotheses;
-  int32_t refine_iters;
-  int32_t pad_;
+  int32_t refine_iters;  /* per level */
+  int32_t refine_levels;
   uint64_t seed;
   uint64_t pair_id;
 } orc_params;
@@ -1407,8 +1445,8 @@ int orc_register(const double *P, int64_t nP, const double *Q, int64_t nQ, const
     res->best_h = bh;
     res->hyp_inliers = bc;
     res->hyp_fitness = bf;
-    double mu = prm->mu_scale * eps * eps;
-    res->refine_iters_done = orc_refine(P, nP, Q, nQ, T0, eps, mu, prm->refine_iters, 1e-10, res->T);
+    res->refine_iters_done =
+        orc_refine_gnc(P, nP, Q, nQ, T0, eps, prm->mu_scale, prm->refine_levels, prm->refine_iters, 1e-10, res->T);
     double R[9], t[3];
     for (int r = 0; r < 3; ++r) {
       for (int q = 0; q < 3; ++q) R[3 * r + q] = res->T[4 * r + q];

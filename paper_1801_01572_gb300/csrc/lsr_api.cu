@@ -1,0 +1,1134 @@
+// lsr_api.cu -- the C ABI (include/lsr.h): context, device workspace, and the
+// host-side orchestration of the registration pipeline of Algorithm 1.
+//
+// Every stage runs on the context's stream without host round trips: counts
+// that decide launch sizes (survivors, selected hypothesis, convergence) live
+// in device memory and are read by persistent-grid kernels, so a whole
+// registration is one stream of launches followed by a single device-to-host
+// copy of the result and one synchronisation.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/lsr.h"
+#include "lsr_internal.cuh"
+
+using namespace lsr;
+
+struct lsr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  lsr_params prm{};
+  bool profiling = false;
+  char *ws = nullptr;
+  size_t ws_cap = 0;
+  RansacState *st_host = nullptr;  // pinned, one per batch slot
+  int st_host_cap = 0;
+  float *box_host = nullptr;       // pinned, 2 x 8 floats per slot
+  cudaEvent_t ev[9] = {};
+  std::string last_error;
+  bool broken = false;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+// Bump allocator over the workspace; with base == nullptr it only measures.
+struct Arena {
+  char *base;
+  size_t off = 0;
+  explicit Arena(char *b) : base(b) {}
+  template <class T>
+  T *take(size_t n) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+    off += sizeof(T) * (n > 0 ? n : 1);
+    return p;
+  }
+};
+
+int cap_cells_for(int n) { return std::max(8 * n, 1 << 20); }
+
+struct CloudLayout {
+  int n = 0, cap_f = 0, cap_n = 0, cap_e = 0;
+  float *src = nullptr;  // staged copy of host input (or null)
+  float *box = nullptr;  // 8 floats: bbox (6) + non-finite flag + pad
+  float *box_part = nullptr;
+  GridParams *gf = nullptr, *gn = nullptr, *ge = nullptr;
+  int *start_f = nullptr, *start_n = nullptr, *start_e = nullptr;
+  float4 *X = nullptr, *Xn = nullptr, *Xe = nullptr, *N = nullptr;
+  int *inv = nullptr;
+  float *S = nullptr, *F = nullptr;
+};
+
+struct ScratchLayout {
+  int n_max = 0, cap_max = 0;
+  GridScratch g{};
+};
+
+void plan_cloud(Arena &a, int n, bool stage_src, bool features, bool eps_grid, CloudLayout &c) {
+  c.n = n;
+  c.cap_f = cap_cells_for(n);
+  c.cap_n = cap_cells_for(n);
+  c.cap_e = cap_cells_for(n);
+  c.src = stage_src ? a.take<float>((size_t)3 * n) : nullptr;
+  c.box = a.take<float>(8);
+  c.box_part = a.take<float>((size_t)7 * bbox_blocks(n));
+  c.gf = a.take<GridParams>(1);
+  c.gn = a.take<GridParams>(1);
+  c.ge = a.take<GridParams>(1);
+  c.start_f = a.take<int>((size_t)c.cap_f + 1);
+  c.X = a.take<float4>(n);
+  c.inv = a.take<int>(n);
+  if (features) {
+    c.start_n = a.take<int>((size_t)c.cap_n + 1);
+    c.Xn = a.take<float4>(n);
+    c.N = a.take<float4>(n);
+    c.S = a.take<float>((size_t)n * kDS);
+    c.F = a.take<float>((size_t)n * kDS);
+  }
+  if (eps_grid) {
+    c.start_e = a.take<int>((size_t)c.cap_e + 1);
+    c.Xe = a.take<float4>(n);
+  }
+}
+
+void plan_scratch(Arena &a, int n_max, int cap_max, ScratchLayout &s) {
+  s.n_max = n_max;
+  s.cap_max = cap_max;
+  s.g.slot = a.take<int>(n_max);
+  s.g.tmp = a.take<int>(n_max);
+  s.g.counts = a.take<int>((size_t)cap_max + 1);
+  s.g.scan = a.take<int>((size_t)scan_scratch_ints(cap_max));
+}
+
+// Coarse levels of the graduated refinement: subsampled copies of Q and their
+// grids (the finest level uses Q's eps grid).
+struct LevelLayout {
+  int levels = 0;
+  int sQ[kMaxLevels] = {}, nsub[kMaxLevels] = {}, cap[kMaxLevels] = {};
+  float4 *Qsub[kMaxLevels] = {}, *Xs[kMaxLevels] = {};
+  int *start[kMaxLevels] = {};
+  GridParams *g[kMaxLevels] = {};
+};
+
+void plan_levels(Arena &a, int nQ, int levels, LevelLayout &V) {
+  V.levels = levels;
+  for (int l = 0; l + 1 < levels; ++l) {
+    V.sQ[l] = gnc_stride(nQ, l, levels);
+    V.nsub[l] = (int)lsr_div_up(nQ, V.sQ[l]);
+    V.cap[l] = cap_cells_for(V.nsub[l]);
+    V.Qsub[l] = a.take<float4>(V.nsub[l]);
+    V.Xs[l] = a.take<float4>(V.nsub[l]);
+    V.start[l] = a.take<int>((size_t)V.cap[l] + 1);
+    V.g[l] = a.take<GridParams>(1);
+  }
+}
+
+struct PairLayout {
+  CloudLayout P, Q;
+  LevelLayout lv;
+  ScratchLayout sc;
+  int *nn = nullptr;
+  float *d1 = nullptr;
+  int nb = 0;
+  int *blk_cnt = nullptr, *blk_off = nullptr, *blk_scan = nullptr;
+  int surv_cap = 0;
+  int *surv = nullptr;
+  float *pose = nullptr;
+  uint8_t *ok = nullptr;
+  int *count = nullptr;
+  unsigned long long *sum = nullptr;
+  double *ref_part = nullptr;
+  float *fpose = nullptr;
+  int *fcount = nullptr;
+  unsigned long long *fsum = nullptr;
+  RansacState *st = nullptr;
+};
+
+int surv_cap_for(int64_t H) { return (int)std::min<int64_t>(H, (int64_t)1 << 22); }
+
+void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int levels, PairLayout &L) {
+  plan_cloud(a, nP, stP, true, false, L.P);
+  plan_cloud(a, nQ, stQ, true, true, L.Q);
+  plan_levels(a, nQ, levels, L.lv);
+  plan_scratch(a, std::max(nP, nQ), std::max(L.P.cap_f, L.Q.cap_f), L.sc);
+  L.nn = a.take<int>(nP);
+  L.d1 = a.take<float>(nP);
+  L.nb = hyp_blocks(H);
+  L.blk_cnt = a.take<int>((size_t)L.nb + 2);
+  L.blk_off = a.take<int>((size_t)L.nb + 2);
+  L.blk_scan = a.take<int>((size_t)scan_scratch_ints(L.nb));
+  L.surv_cap = surv_cap_for(H);
+  L.surv = a.take<int>(L.surv_cap);
+  L.pose = a.take<float>((size_t)12 * L.surv_cap);
+  L.ok = a.take<uint8_t>(L.surv_cap);
+  L.count = a.take<int>(L.surv_cap);
+  L.sum = a.take<unsigned long long>(L.surv_cap);
+  L.ref_part = a.take<double>((size_t)kRefAcc * refine_blocks(nP));
+  L.fpose = a.take<float>(12);
+  L.fcount = a.take<int>(1);
+  L.fsum = a.take<unsigned long long>(1);
+  L.st = a.take<RansacState>(1);
+}
+
+int set_err(lsr_ctx *c, int code, const char *msg) {
+  if (c) c->last_error = msg ? msg : lsr_error_string(code);
+  return code;
+}
+
+int cuda_err(lsr_ctx *c, cudaError_t e, const char *where) {
+  if (e == cudaSuccess) return LSR_OK;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  if (c) {
+    c->last_error = buf;
+    if (e == cudaErrorIllegalAddress || e == cudaErrorLaunchFailure || e == cudaErrorIllegalInstruction ||
+        e == cudaErrorMisalignedAddress || e == cudaErrorHardwareStackError)
+      c->broken = true;
+  }
+  return e == cudaErrorMemoryAllocation ? LSR_E_OOM : LSR_E_CUDA;
+}
+
+#define TRY_CUDA(ctx, call, where)                       \
+  do {                                                   \
+    cudaError_t e__ = (call);                            \
+    if (e__ != cudaSuccess) return cuda_err(ctx, e__, where); \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+int ensure_ws(lsr_ctx *c, size_t bytes) {
+  if (bytes <= c->ws_cap) return LSR_OK;
+  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "workspace sync");
+  if (c->ws) cudaFree(c->ws);
+  c->ws = nullptr;
+  c->ws_cap = 0;
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&c->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->ws = nullptr;
+    return set_err(c, LSR_E_OOM, "device workspace allocation failed");
+  }
+  c->ws_cap = want;
+  return LSR_OK;
+}
+
+int ensure_host_slots(lsr_ctx *c, int n) {
+  if (n <= c->st_host_cap) return LSR_OK;
+  if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->box_host) cudaFreeHost(c->box_host);
+  c->st_host = nullptr;
+  c->box_host = nullptr;
+  c->st_host_cap = 0;
+  if (cudaMallocHost(&c->st_host, sizeof(RansacState) * n) != cudaSuccess ||
+      cudaMallocHost(&c->box_host, sizeof(float) * 16 * n) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(c, LSR_E_OOM, "pinned host allocation failed");
+  }
+  c->st_host_cap = n;
+  return LSR_OK;
+}
+
+int check_params(const lsr_params *p) {
+  if (!(p->r_normal > 0.f && p->r_feature > 0.f && p->eps_inlier > 0.f && p->tau > 0.f && p->tau <= 1.f &&
+        p->cos_normal >= -1.f && p->cos_normal <= 1.f && p->min_inlier_ratio >= 0.f && p->mu_scale > 0.f &&
+        p->refine_iters >= 0 && p->refine_iters <= 10000 && p->refine_levels >= 1 &&
+        p->refine_levels <= kMaxLevels && p->n_hypotheses >= 1 &&
+        p->n_hypotheses <= 2147483647LL && (p->match_precision == LSR_MATCH_FP32 || p->match_precision == LSR_MATCH_BF16)))
+    return LSR_E_ARG;
+  if (p->eps_inlier > 10.f) return LSR_E_ARG;  // fixed-point inlier sums assume eps^2 * |P| << 2^23
+  return LSR_OK;
+}
+
+constexpr int64_t kMaxPoints = (int64_t)1 << 26;
+
+// ---------------------------------------------------------------- small kernels
+__global__ void k_pack(const float *xyz, int n, float4 *out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], __int_as_float(i));
+}
+__global__ void k_iota(int *p, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
+}
+// internal-order normals from caller-order normals (zero normal = invalid)
+__global__ void k_gather_normals(const float *nrm, const float4 *X, int n, float4 *N) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    int o = __float_as_int(X[k].w);
+    float a = nrm[3 * o], b = nrm[3 * o + 1], c = nrm[3 * o + 2];
+    N[k] = make_float4(a, b, c, (a == 0.f && b == 0.f && c == 0.f) ? -1.f : 0.f);
+  }
+}
+__global__ void k_valid_normals(const uint8_t *valid, int n, float4 *N) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    N[k] = make_float4(0.f, 0.f, 1.f, valid[k] ? 0.f : -1.f);
+}
+__global__ void k_gather_rows(const float *src, int src_stride, const float4 *X, int n, float *dst) {
+  // dst (internal, stride kDS) <- src (caller order, stride src_stride, 33 used)
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * kDS;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int k = (int)(t / kDS), b = (int)(t - (int64_t)k * kDS);
+    int o = X ? __float_as_int(X[k].w) : k;
+    dst[t] = b < kD ? src[(size_t)o * src_stride + b] : 0.f;
+  }
+}
+__global__ void k_scatter_rows(const float *src, const float4 *X, int n, float *dst) {
+  // dst (caller order, stride 33) <- src (internal, stride kDS)
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * kD;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int k = (int)(t / kD), b = (int)(t - (int64_t)k * kD);
+    int o = __float_as_int(X[k].w);
+    dst[(size_t)o * kD + b] = src[(size_t)k * kDS + b];
+  }
+}
+__global__ void k_scatter_normals(const float4 *N, const int *cnt, const float4 *X, int n, float *nrm, int32_t *count,
+                                  float *curv) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    int o = __float_as_int(X[k].w);
+    float4 v = N[k];
+    if (nrm) nrm[3 * o] = v.x, nrm[3 * o + 1] = v.y, nrm[3 * o + 2] = v.z;
+    if (count) count[o] = cnt[k];
+    if (curv) curv[o] = v.w;
+  }
+}
+__global__ void k_scatter_int(const int *src, const float4 *X, int n, int32_t *dst) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    dst[__float_as_int(X[k].w)] = src[k];
+}
+__global__ void k_sum_to_double(const unsigned long long *s, int n, double *d) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) d[k] = (double)s[k] / kFixScale;
+}
+int nblk(int64_t n, int t = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 152 * 32)); }
+
+// Build the feature-radius grid (internal order) and, optionally, the
+// normal-radius and eps grids of one cloud.
+cudaError_t build_cloud(const float *xyz, CloudLayout &c, float r_f, float r_n, float eps, bool normal_grid,
+                        bool eps_grid, const ScratchLayout &sc, cudaStream_t s) {
+  LSR_CUDA_TRY(launch_bbox_xyz(xyz, c.n, c.box_part, bbox_blocks(c.n), c.box, s));
+  LSR_CUDA_TRY(launch_grid_params(c.box, r_f, c.n, c.cap_f, c.gf, s));
+  LSR_CUDA_TRY(build_grid_xyz(xyz, c.n, c.gf, c.cap_f, c.start_f, c.X, c.inv, sc.g, s));
+  if (normal_grid) {
+    LSR_CUDA_TRY(launch_grid_params(c.box, r_n, c.n, c.cap_n, c.gn, s));
+    LSR_CUDA_TRY(build_grid_f4(c.X, c.n, c.gn, c.cap_n, c.start_n, c.Xn, sc.g, s));
+  }
+  if (eps_grid) {
+    LSR_CUDA_TRY(launch_grid_params(c.box, eps, c.n, c.cap_e, c.ge, s));
+    LSR_CUDA_TRY(build_grid_f4(c.X, c.n, c.ge, c.cap_e, c.start_e, c.Xe, sc.g, s));
+  }
+  return cudaSuccess;
+}
+
+// Graduated refinement (levels l = 0..L-1, radius eps * 2^(L-1-l)) from the
+// pose in st. XP: P in internal order with caller indices in w; Q: caller-order
+// xyz on the device; (ge, start_e, Xe): Q's eps grid for the finest level.
+cudaError_t enqueue_refine(const float4 *XP, int nP, const float *Q, int nQ, const float *boxQ, const GridParams *ge,
+                           const int *start_e, const float4 *Xe, const LevelLayout &V, float eps, float mu_scale,
+                           int iters, RansacState *st, double *part, const ScratchLayout &sc, cudaStream_t s) {
+  int L = V.levels;
+  for (int l = 0; l < L; ++l) {
+    float e = eps * (float)(1 << (L - 1 - l));
+    float mu = mu_scale * e * e;
+    int sP = gnc_stride(nP, l, L);
+    const GridParams *g = ge;
+    const int *st0 = start_e;
+    const float4 *xs = Xe;
+    if (l + 1 < L) {
+      LSR_CUDA_TRY(launch_subsample(Q, nQ, V.sQ[l], V.Qsub[l], s));
+      LSR_CUDA_TRY(launch_grid_params(boxQ, e, V.nsub[l], V.cap[l], V.g[l], s));
+      LSR_CUDA_TRY(build_grid_f4(V.Qsub[l], V.nsub[l], V.g[l], V.cap[l], V.start[l], V.Xs[l], sc.g, s));
+      g = V.g[l], st0 = V.start[l], xs = V.Xs[l];
+    }
+    LSR_CUDA_TRY(launch_refine_level_begin(st, s));
+    for (int it = 0; it < iters; ++it)
+      LSR_CUDA_TRY(launch_refine_step(XP, nP, sP, g, st0, xs, e, mu, iters, st, part, s));
+  }
+  return cudaSuccess;
+}
+
+struct Timer {
+  lsr_ctx *c;
+  int k = 0;
+  void mark() {
+    if (c->profiling && k < 9) cudaEventRecord(c->ev[k++], c->stream);
+  }
+};
+
+// The registration of one pair, enqueued on the stream. Results stay in L.st.
+int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q, const float *vpP, const float *vpQ,
+                 uint64_t pair_id, Timer &tm) {
+  cudaStream_t s = c->stream;
+  const lsr_params &p = c->prm;
+  int nP = L.P.n, nQ = L.Q.n;
+  tm.mark();
+  TRY_CUDA(c, cudaMemsetAsync(L.st, 0, sizeof(RansacState), s), "memset state");
+  CloudLayout Pc = L.P, Qc = L.Q;
+  TRY_CUDA(c, build_cloud(P, Pc, p.r_feature, p.r_normal, p.eps_inlier, true, false, L.sc, s), "grids P");
+  TRY_CUDA(c, build_cloud(Q, Qc, p.r_feature, p.r_normal, p.eps_inlier, true, true, L.sc, s), "grids Q");
+  tm.mark();
+  float3 vp_p = vpP ? make_float3(vpP[0], vpP[1], vpP[2]) : make_float3(0.f, 0.f, 0.f);
+  float3 vp_q = vpQ ? make_float3(vpQ[0], vpQ[1], vpQ[2]) : make_float3(0.f, 0.f, 0.f);
+  TRY_CUDA(c, launch_normals(Pc.X, nP, Pc.gn, Pc.start_n, Pc.Xn, p.r_normal, vp_p, Pc.N, nullptr, s), "normals P");
+  TRY_CUDA(c, launch_normals(Qc.X, nQ, Qc.gn, Qc.start_n, Qc.Xn, p.r_normal, vp_q, Qc.N, nullptr, s), "normals Q");
+  tm.mark();
+  TRY_CUDA(c, launch_spfh(Pc.X, Pc.N, nP, Pc.gf, Pc.start_f, p.r_feature, Pc.S, nullptr, s), "spfh P");
+  TRY_CUDA(c, launch_spfh(Qc.X, Qc.N, nQ, Qc.gf, Qc.start_f, p.r_feature, Qc.S, nullptr, s), "spfh Q");
+  TRY_CUDA(c, launch_fpfh(Pc.X, Pc.N, Pc.S, nP, Pc.gf, Pc.start_f, p.r_feature, Pc.F, s), "fpfh P");
+  TRY_CUDA(c, launch_fpfh(Qc.X, Qc.N, Qc.S, nQ, Qc.gf, Qc.start_f, p.r_feature, Qc.F, s), "fpfh Q");
+  tm.mark();
+  TRY_CUDA(c, launch_match_fp32(Pc.F, nP, Qc.F, nQ, L.nn, L.d1, s), "match");
+  tm.mark();
+  TRY_CUDA(c,
+           launch_hypotheses(Pc.X, Pc.inv, Pc.N, nP, Qc.X, Qc.N, nQ, L.nn, nullptr, nullptr, p.n_hypotheses, p.seed,
+                             pair_id, p.tau, L.blk_cnt, L.blk_off, L.blk_scan, L.surv, L.surv_cap, L.st, s),
+           "hypotheses");
+  tm.mark();
+  TRY_CUDA(c,
+           launch_rigid_survivors(Pc.X, Pc.inv, Pc.N, nP, Qc.X, Qc.N, L.nn, L.surv, L.st, p.seed, pair_id,
+                                  p.cos_normal, L.pose, L.ok, &L.st->n_normal_ok, s),
+           "rigid");
+  TRY_CUDA(c, cudaMemsetAsync(L.count, 0, sizeof(int) * L.surv_cap, s), "memset count");
+  TRY_CUDA(c, cudaMemsetAsync(L.sum, 0, sizeof(unsigned long long) * L.surv_cap, s), "memset sum");
+  TRY_CUDA(c,
+           launch_consensus(Pc.X, nP, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.ok, &L.st->n_surv, 0, p.eps_inlier, L.count,
+                            L.sum, s),
+           "consensus");
+  tm.mark();
+  TRY_CUDA(c, launch_select(L.surv, L.count, L.sum, L.ok, L.pose, nP, p.min_inlier_ratio, L.st, s), "select");
+  TRY_CUDA(c, launch_refine_init(L.st, Qc.box, nullptr, s), "refine init");
+  float eps = p.eps_inlier;
+  TRY_CUDA(c,
+           enqueue_refine(Pc.X, nP, Q, nQ, Qc.box, Qc.ge, Qc.start_e, Qc.Xe, L.lv, eps, p.mu_scale, p.refine_iters,
+                          L.st, L.ref_part, L.sc, s),
+           "refine");
+  TRY_CUDA(c, launch_final_pose(L.st, L.fpose, s), "final pose");
+  TRY_CUDA(c, cudaMemsetAsync(L.fcount, 0, sizeof(int), s), "memset fcount");
+  TRY_CUDA(c, cudaMemsetAsync(L.fsum, 0, sizeof(unsigned long long), s), "memset fsum");
+  TRY_CUDA(c, launch_consensus(Pc.X, nP, Qc.ge, Qc.start_e, Qc.Xe, L.fpose, nullptr, nullptr, 1, eps, L.fcount, L.fsum, s),
+           "final count");
+  TRY_CUDA(c, launch_final_count(L.fcount, L.fsum, L.st, s), "final count");
+  tm.mark();
+  return LSR_OK;
+}
+
+void fill_result(const RansacState &st, const float *boxP, const float *boxQ, lsr_result *r) {
+  memset(r, 0, sizeof(*r));
+  bool ok = st.status == 0;
+  for (int i = 0; i < 16; ++i) {
+    r->T[i] = ok ? st.T[i] : (i % 5 == 0 ? 1.0 : 0.0);
+    r->T_hyp[i] = ok ? st.T_hyp[i] : (i % 5 == 0 ? 1.0 : 0.0);
+  }
+  r->inliers = st.final_count;
+  r->hyp_inliers = st.best_count;
+  r->survivors = st.n_surv_total;
+  r->n_normal_ok = st.n_normal_ok;
+  r->best_h = st.best >= 0 ? st.best_h : -1;
+  r->match_fallbacks = 0;
+  r->fitness = st.final_count > 0 ? (float)(st.final_sumd2 / st.final_count) : 0.f;
+  r->hyp_fitness = st.best_fit;
+  r->status = ok ? LSR_STATUS_ALIGNED : LSR_STATUS_NO_ALIGNMENT;
+  r->refine_iters_done = st.iters_done;
+  (void)boxP;
+  (void)boxQ;
+}
+
+// Stage a cloud to the device if it lives in host memory.
+int stage_input(lsr_ctx *c, const float *src, int64_t n, float *dst, const float **out) {
+  if (is_device_ptr(src)) {
+    *out = src;
+    return LSR_OK;
+  }
+  TRY_CUDA(c, cudaMemcpyAsync(dst, src, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream), "H2D");
+  *out = dst;
+  return LSR_OK;
+}
+
+int guard(lsr_ctx *c) {
+  if (!c) return LSR_E_STATE;
+  if (c->broken) return set_err(c, LSR_E_STATE, "context unusable after a device fault");
+  if (cudaSetDevice(c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(c, LSR_E_CUDA, "cudaSetDevice failed");
+  }
+  return LSR_OK;
+}
+
+// Generic copy of a result array to a caller pointer (device or host).
+int copy_out(lsr_ctx *c, void *dst, const void *src, size_t bytes) {
+  TRY_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream), "copy out");
+  return LSR_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+void lsr_default_params(lsr_params *p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->r_normal = 0.05f;
+  p->r_feature = 0.125f;
+  p->eps_inlier = 0.0375f;
+  p->tau = 0.9f;
+  p->cos_normal = 0.86602540378f;  // cos(30 deg)
+  p->min_inlier_ratio = 0.05f;
+  p->mu_scale = 1.0f;
+  p->refine_iters = 50;
+  p->refine_levels = 4;
+  p->n_hypotheses = 4000000;
+  p->seed = 0;
+  p->pair_id = 0;
+  p->match_precision = LSR_MATCH_FP32;
+}
+
+const char *lsr_error_string(int code) {
+  switch (code) {
+    case LSR_OK: return "ok";
+    case LSR_E_ARG: return "invalid argument";
+    case LSR_E_CUDA: return "CUDA error";
+    case LSR_E_OOM: return "out of memory";
+    case LSR_E_TIMEOUT: return "device wait timed out";
+    case LSR_E_STATE: return "context unusable";
+    default: return "unknown error";
+  }
+}
+
+const char *lsr_last_error(const lsr_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+int lsr_create(lsr_ctx **out, const lsr_params *params, int device, void *cuda_stream) {
+  if (!out) return LSR_E_ARG;
+  *out = nullptr;
+  lsr_params p;
+  if (params)
+    p = *params;
+  else
+    lsr_default_params(&p);
+  if (check_params(&p) != LSR_OK) return LSR_E_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return LSR_E_ARG;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return LSR_E_CUDA;
+  }
+  lsr_ctx *c = new (std::nothrow) lsr_ctx();
+  if (!c) return LSR_E_OOM;
+  c->device = device;
+  c->prm = p;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return LSR_E_CUDA;
+    }
+    c->own_stream = true;
+  }
+  for (auto &e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      lsr_destroy(c);
+      return LSR_E_CUDA;
+    }
+  *out = c;
+  return LSR_OK;
+}
+
+int lsr_destroy(lsr_ctx *c) {
+  if (!c) return LSR_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->ws) cudaFree(c->ws);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->box_host) cudaFreeHost(c->box_host);
+  for (auto &e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  cudaGetLastError();
+  delete c;
+  return LSR_OK;
+}
+
+int lsr_set_params(lsr_ctx *c, const lsr_params *p) {
+  if (!c) return LSR_E_STATE;
+  if (!p || check_params(p) != LSR_OK) return set_err(c, LSR_E_ARG, "parameter out of range");
+  c->prm = *p;
+  return LSR_OK;
+}
+
+int lsr_get_params(const lsr_ctx *c, lsr_params *p) {
+  if (!c) return LSR_E_STATE;
+  if (!p) return LSR_E_ARG;
+  *p = c->prm;
+  return LSR_OK;
+}
+
+int lsr_set_profiling(lsr_ctx *c, int enable) {
+  if (!c) return LSR_E_STATE;
+  c->profiling = enable != 0;
+  return LSR_OK;
+}
+
+int64_t lsr_workspace_bytes(const lsr_ctx *c) { return c ? (int64_t)c->ws_cap : 0; }
+
+static int register_many(lsr_ctx *c, int32_t n, const float *const *P, const int64_t *nP, const float *const *Q,
+                         const int64_t *nQ, const float *vp, uint64_t pair0, lsr_result *out) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && (!P || !nP || !Q || !nQ || !out))) return set_err(c, LSR_E_ARG, "null argument");
+  if (n == 0) return LSR_OK;
+  int64_t maxP = 0, maxQ = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!P[i] || !Q[i]) return set_err(c, LSR_E_ARG, "null cloud");
+    if (nP[i] < 4 || nQ[i] < 4) return set_err(c, LSR_E_ARG, "a cloud has fewer than 4 points");
+    if (nP[i] > kMaxPoints || nQ[i] > kMaxPoints) return set_err(c, LSR_E_ARG, "a cloud has too many points");
+    maxP = std::max(maxP, nP[i]);
+    maxQ = std::max(maxQ, nQ[i]);
+  }
+  // one workspace sized for the largest pair; pairs run back to back on the stream
+  Arena m(nullptr);
+  PairLayout Lm;
+  plan_pair(m, (int)maxP, (int)maxQ, true, true, c->prm.n_hypotheses, c->prm.refine_levels, Lm);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  if ((rc = ensure_host_slots(c, n))) return rc;
+  Timer tm{c};
+  for (int i = 0; i < n; ++i) {
+    Arena a(c->ws);
+    PairLayout L;
+    plan_pair(a, (int)nP[i], (int)nQ[i], true, true, c->prm.n_hypotheses, c->prm.refine_levels, L);
+    const float *dP, *dQ;
+    if ((rc = stage_input(c, P[i], nP[i], L.P.src, &dP))) return rc;
+    if ((rc = stage_input(c, Q[i], nQ[i], L.Q.src, &dQ))) return rc;
+    Timer t1{c};
+    Timer &t = (n == 1) ? tm : t1;
+    if (n != 1) t.k = 9;  // per-stage timing only for single pairs
+    if ((rc = enqueue_pair(c, L, dP, dQ, vp ? vp + 6 * i : nullptr, vp ? vp + 6 * i + 3 : nullptr, pair0 + i, t)))
+      return rc;
+    TRY_CUDA(c, cudaMemcpyAsync(&c->st_host[i], L.st, sizeof(RansacState), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    TRY_CUDA(c, cudaMemcpyAsync(&c->box_host[16 * i], L.P.box, sizeof(float) * 8, cudaMemcpyDeviceToHost, c->stream),
+             "D2H");
+    TRY_CUDA(c, cudaMemcpyAsync(&c->box_host[16 * i + 8], L.Q.box, sizeof(float) * 8, cudaMemcpyDeviceToHost, c->stream),
+             "D2H");
+  }
+  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+  TRY_CUDA(c, cudaGetLastError(), "kernel");
+  for (int i = 0; i < n; ++i) {
+    if (c->box_host[16 * i + 6] != 0.f || c->box_host[16 * i + 14] != 0.f)
+      return set_err(c, LSR_E_ARG, "non-finite input coordinates");
+    fill_result(c->st_host[i], &c->box_host[16 * i], &c->box_host[16 * i + 8], &out[i]);
+  }
+  if (n == 1 && c->profiling && tm.k == 9) {
+    float tot = 0.f;
+    for (int k = 0; k < 7; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]);
+      out[0].stage_ms[k] = ms;
+      tot += ms;
+    }
+    out[0].stage_ms[7] = tot;
+  }
+  return LSR_OK;
+}
+
+int lsr_register_pair(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int64_t nQ, const float *vpP,
+                      const float *vpQ, lsr_result *out) {
+  if (!c) return LSR_E_STATE;
+  float vp[6] = {0, 0, 0, 0, 0, 0};
+  if (vpP) vp[0] = vpP[0], vp[1] = vpP[1], vp[2] = vpP[2];
+  if (vpQ) vp[3] = vpQ[0], vp[4] = vpQ[1], vp[5] = vpQ[2];
+  return register_many(c, 1, &P, &nP, &Q, &nQ, vp, c->prm.pair_id, out);
+}
+
+int lsr_register_batch(lsr_ctx *c, int32_t n, const float *const *P, const int64_t *nP, const float *const *Q,
+                       const int64_t *nQ, const float *vp, lsr_result *out) {
+  if (!c) return LSR_E_STATE;
+  return register_many(c, n, P, nP, Q, nQ, vp, c->prm.pair_id, out);
+}
+
+// ------------------------------------------------------------------ stages
+int lsr_stage_normals(lsr_ctx *c, const float *P, int64_t n, const float *vp, float r, float *normals, int32_t *count,
+                      float *curvature) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!P || n < 1 || n > kMaxPoints || !(r > 0.f)) return set_err(c, LSR_E_ARG, "bad argument");
+  Arena m(nullptr);
+  CloudLayout Cm;
+  plan_cloud(m, (int)n, true, true, false, Cm);
+  ScratchLayout Sm;
+  plan_scratch(m, (int)n, Cm.cap_f, Sm);
+  int *cnt_m = m.take<int>(n);
+  float *o_n = m.take<float>(3 * n);
+  int *o_c = m.take<int>(n);
+  float *o_v = m.take<float>(n);
+  (void)cnt_m, (void)o_n, (void)o_c, (void)o_v;
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  CloudLayout C;
+  plan_cloud(a, (int)n, true, true, false, C);
+  ScratchLayout S;
+  plan_scratch(a, (int)n, C.cap_f, S);
+  int *cnt = a.take<int>(n);
+  float *dn = a.take<float>(3 * n);
+  int *dc = a.take<int>(n);
+  float *dv = a.take<float>(n);
+  const float *src;
+  if ((rc = stage_input(c, P, n, C.src, &src))) return rc;
+  cudaStream_t s = c->stream;
+  TRY_CUDA(c, build_cloud(src, C, r, r, r, true, false, S, s), "grids");
+  float3 v = vp ? make_float3(vp[0], vp[1], vp[2]) : make_float3(0.f, 0.f, 0.f);
+  TRY_CUDA(c, launch_normals(C.X, (int)n, C.gn, C.start_n, C.Xn, r, v, C.N, cnt, s), "normals");
+  k_scatter_normals<<<nblk(n), 256, 0, s>>>(C.N, cnt, C.X, (int)n, dn, dc, dv);
+  TRY_CUDA(c, cudaGetLastError(), "scatter");
+  if (normals && (rc = copy_out(c, normals, dn, sizeof(float) * 3 * n))) return rc;
+  if (count && (rc = copy_out(c, count, dc, sizeof(int) * n))) return rc;
+  if (curvature && (rc = copy_out(c, curvature, dv, sizeof(float) * n))) return rc;
+  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  return LSR_OK;
+}
+
+static int stage_desc_common(lsr_ctx *c, const float *P, const float *normals, const float *spfh_in, int64_t n, float r,
+                             float *out, int32_t *k_out) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!P || !normals || n < 1 || n > kMaxPoints || !(r > 0.f)) return set_err(c, LSR_E_ARG, "bad argument");
+  auto plan = [&](Arena &a, CloudLayout &C, ScratchLayout &S, float *&nrm, float *&sp, float *&o, int *&kk,
+                  int *&ko) {
+    plan_cloud(a, (int)n, true, true, false, C);
+    plan_scratch(a, (int)n, C.cap_f, S);
+    nrm = a.take<float>(3 * n);
+    sp = a.take<float>(kD * n);
+    o = a.take<float>(kD * n);
+    kk = a.take<int>(n);
+    ko = a.take<int>(n);
+  };
+  Arena m(nullptr);
+  CloudLayout Cm;
+  ScratchLayout Sm;
+  float *a1, *a2, *a3;
+  int *a4, *a5;
+  plan(m, Cm, Sm, a1, a2, a3, a4, a5);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  CloudLayout C;
+  ScratchLayout S;
+  float *nrm, *sp, *o;
+  int *kk, *ko;
+  plan(a, C, S, nrm, sp, o, kk, ko);
+  cudaStream_t s = c->stream;
+  const float *src;
+  if ((rc = stage_input(c, P, n, C.src, &src))) return rc;
+  TRY_CUDA(c, cudaMemcpyAsync(nrm, normals, sizeof(float) * 3 * n, cudaMemcpyDefault, s), "copy normals");
+  TRY_CUDA(c, build_cloud(src, C, r, r, r, false, false, S, s), "grids");
+  k_gather_normals<<<nblk(n), 256, 0, s>>>(nrm, C.X, (int)n, C.N);
+  if (!spfh_in) {
+    TRY_CUDA(c, launch_spfh(C.X, C.N, (int)n, C.gf, C.start_f, r, C.S, kk, s), "spfh");
+    k_scatter_rows<<<nblk(n * kD), 256, 0, s>>>(C.S, C.X, (int)n, o);
+    if (k_out) k_scatter_int<<<nblk(n), 256, 0, s>>>(kk, C.X, (int)n, ko);
+  } else {
+    TRY_CUDA(c, cudaMemcpyAsync(sp, spfh_in, sizeof(float) * kD * n, cudaMemcpyDefault, s), "copy spfh");
+    k_gather_rows<<<nblk(n * kDS), 256, 0, s>>>(sp, kD, C.X, (int)n, C.S);
+    TRY_CUDA(c, launch_fpfh(C.X, C.N, C.S, (int)n, C.gf, C.start_f, r, C.F, s), "fpfh");
+    k_scatter_rows<<<nblk(n * kD), 256, 0, s>>>(C.F, C.X, (int)n, o);
+  }
+  TRY_CUDA(c, cudaGetLastError(), "stage kernels");
+  if ((rc = copy_out(c, out, o, sizeof(float) * kD * n))) return rc;
+  if (k_out && !spfh_in && (rc = copy_out(c, k_out, ko, sizeof(int) * n))) return rc;
+  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  return LSR_OK;
+}
+
+int lsr_stage_spfh(lsr_ctx *c, const float *P, const float *normals, int64_t n, float r, float *spfh, int32_t *k) {
+  if (!spfh) return c ? set_err(c, LSR_E_ARG, "null output") : LSR_E_STATE;
+  return stage_desc_common(c, P, normals, nullptr, n, r, spfh, k);
+}
+
+int lsr_stage_fpfh(lsr_ctx *c, const float *P, const float *normals, const float *spfh, int64_t n, float r,
+                   float *fpfh) {
+  if (!spfh || !fpfh) return c ? set_err(c, LSR_E_ARG, "null argument") : LSR_E_STATE;
+  return stage_desc_common(c, P, normals, spfh, n, r, fpfh, nullptr);
+}
+
+int lsr_stage_match(lsr_ctx *c, const float *FP, int64_t nP, const float *FQ, int64_t nQ, int32_t precision,
+                    int32_t *nn, float *d1, int64_t *fallbacks) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!FP || !FQ || !nn || nP < 1 || nQ < 1 || nP > kMaxPoints || nQ > kMaxPoints)
+    return set_err(c, LSR_E_ARG, "bad argument");
+  if (precision != LSR_MATCH_FP32 && precision != LSR_MATCH_BF16) return set_err(c, LSR_E_ARG, "bad precision");
+  auto plan = [&](Arena &a, float *&fp, float *&fq, float *&FPi, float *&FQi, int *&dn, float *&dd) {
+    fp = a.take<float>(kD * nP);
+    fq = a.take<float>(kD * nQ);
+    FPi = a.take<float>(kDS * nP);
+    FQi = a.take<float>(kDS * nQ);
+    dn = a.take<int>(nP);
+    dd = a.take<float>(nP);
+  };
+  Arena m(nullptr);
+  float *x1, *x2, *x3, *x4, *x6;
+  int *x5;
+  plan(m, x1, x2, x3, x4, x5, x6);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  float *fp, *fq, *FPi, *FQi, *dd;
+  int *dn;
+  plan(a, fp, fq, FPi, FQi, dn, dd);
+  cudaStream_t s = c->stream;
+  TRY_CUDA(c, cudaMemcpyAsync(fp, FP, sizeof(float) * kD * nP, cudaMemcpyDefault, s), "copy FP");
+  TRY_CUDA(c, cudaMemcpyAsync(fq, FQ, sizeof(float) * kD * nQ, cudaMemcpyDefault, s), "copy FQ");
+  k_gather_rows<<<nblk(nP * kDS), 256, 0, s>>>(fp, kD, nullptr, (int)nP, FPi);
+  k_gather_rows<<<nblk(nQ * kDS), 256, 0, s>>>(fq, kD, nullptr, (int)nQ, FQi);
+  TRY_CUDA(c, launch_match_fp32(FPi, (int)nP, FQi, (int)nQ, dn, dd, s), "match");
+  if ((rc = copy_out(c, nn, dn, sizeof(int) * nP))) return rc;
+  if (d1 && (rc = copy_out(c, d1, dd, sizeof(float) * nP))) return rc;
+  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  if (fallbacks) *fallbacks = 0;
+  return LSR_OK;
+}
+
+int lsr_stage_hypotheses(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int64_t nQ, const int32_t *nn,
+                         const uint8_t *validP, const uint8_t *validQ, int64_t H, uint64_t seed, uint64_t pair_id,
+                         float tau, int32_t *surv, int64_t cap, int64_t *nsurv) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!P || !Q || !nn || !validP || !validQ || !surv || !nsurv || nP < 4 || nQ < 4 || nP > kMaxPoints ||
+      nQ > kMaxPoints || H < 1 || H > 2147483647LL || cap < 0 || !(tau > 0.f && tau <= 1.f))
+    return set_err(c, LSR_E_ARG, "bad argument");
+  auto plan = [&](Arena &a, float *&p, float *&q, float4 *&XP, float4 *&XQ, float4 *&NP, float4 *&NQ, int *&inv,
+                  int *&dnn, uint8_t *&vp, uint8_t *&vq, PairLayout &L) {
+    p = a.take<float>(3 * nP);
+    q = a.take<float>(3 * nQ);
+    XP = a.take<float4>(nP);
+    XQ = a.take<float4>(nQ);
+    NP = a.take<float4>(nP);
+    NQ = a.take<float4>(nQ);
+    inv = a.take<int>(nP);
+    dnn = a.take<int>(nP);
+    vp = a.take<uint8_t>(nP);
+    vq = a.take<uint8_t>(nQ);
+    L.nb = hyp_blocks(H);
+    L.blk_cnt = a.take<int>((size_t)L.nb + 2);
+    L.blk_off = a.take<int>((size_t)L.nb + 2);
+    L.blk_scan = a.take<int>((size_t)scan_scratch_ints(L.nb));
+    L.surv_cap = (int)std::min<int64_t>(H, (int64_t)1 << 26);
+    L.surv = a.take<int>(L.surv_cap);
+    L.st = a.take<RansacState>(1);
+  };
+  Arena m(nullptr);
+  float *y1, *y2;
+  float4 *y3, *y4, *y5, *y6;
+  int *y7, *y8;
+  uint8_t *y9, *y10;
+  PairLayout Lm;
+  plan(m, y1, y2, y3, y4, y5, y6, y7, y8, y9, y10, Lm);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  float *p, *q;
+  float4 *XP, *XQ, *NP, *NQ;
+  int *inv, *dnn;
+  uint8_t *vp, *vq;
+  PairLayout L;
+  plan(a, p, q, XP, XQ, NP, NQ, inv, dnn, vp, vq, L);
+  cudaStream_t s = c->stream;
+  TRY_CUDA(c, cudaMemcpyAsync(p, P, sizeof(float) * 3 * nP, cudaMemcpyDefault, s), "copy P");
+  TRY_CUDA(c, cudaMemcpyAsync(q, Q, sizeof(float) * 3 * nQ, cudaMemcpyDefault, s), "copy Q");
+  TRY_CUDA(c, cudaMemcpyAsync(dnn, nn, sizeof(int) * nP, cudaMemcpyDefault, s), "copy nn");
+  TRY_CUDA(c, cudaMemcpyAsync(vp, validP, nP, cudaMemcpyDefault, s), "copy vP");
+  TRY_CUDA(c, cudaMemcpyAsync(vq, validQ, nQ, cudaMemcpyDefault, s), "copy vQ");
+  TRY_CUDA(c, cudaMemsetAsync(L.st, 0, sizeof(RansacState), s), "memset");
+  k_pack<<<nblk(nP), 256, 0, s>>>(p, (int)nP, XP);
+  k_pack<<<nblk(nQ), 256, 0, s>>>(q, (int)nQ, XQ);
+  k_iota<<<nblk(nP), 256, 0, s>>>(inv, (int)nP);
+  k_valid_normals<<<nblk(nP), 256, 0, s>>>(vp, (int)nP, NP);
+  k_valid_normals<<<nblk(nQ), 256, 0, s>>>(vq, (int)nQ, NQ);
+  TRY_CUDA(c,
+           launch_hypotheses(XP, inv, NP, (int)nP, XQ, NQ, (int)nQ, dnn, nullptr, nullptr, H, seed, pair_id, tau,
+                             L.blk_cnt, L.blk_off, L.blk_scan, L.surv, L.surv_cap, L.st, s),
+           "hypotheses");
+  RansacState st;
+  TRY_CUDA(c, cudaMemcpyAsync(&st, L.st, sizeof(st), cudaMemcpyDeviceToHost, s), "D2H");
+  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  *nsurv = st.n_surv_total;
+  int64_t ncopy = std::min<int64_t>(std::min<int64_t>(st.n_surv, cap), st.n_surv_total);
+  if (ncopy > 0) {
+    TRY_CUDA(c, cudaMemcpy(surv, L.surv, sizeof(int) * ncopy, cudaMemcpyDefault), "copy surv");
+  }
+  return LSR_OK;
+}
+
+int lsr_stage_rigid4(lsr_ctx *c, const float *ps, const float *qs, int64_t nh, float *Rt) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!ps || !qs || !Rt || nh < 1 || nh > ((int64_t)1 << 28)) return set_err(c, LSR_E_ARG, "bad argument");
+  Arena m(nullptr);
+  m.take<float>(12 * nh);
+  m.take<float>(12 * nh);
+  m.take<float>(12 * nh);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  float *dp = a.take<float>(12 * nh), *dq = a.take<float>(12 * nh), *dr = a.take<float>(12 * nh);
+  cudaStream_t s = c->stream;
+  TRY_CUDA(c, cudaMemcpyAsync(dp, ps, sizeof(float) * 12 * nh, cudaMemcpyDefault, s), "copy");
+  TRY_CUDA(c, cudaMemcpyAsync(dq, qs, sizeof(float) * 12 * nh, cudaMemcpyDefault, s), "copy");
+  TRY_CUDA(c, launch_rigid4(dp, dq, (int)nh, dr, s), "rigid4");
+  if ((rc = copy_out(c, Rt, dr, sizeof(float) * 12 * nh))) return rc;
+  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  return LSR_OK;
+}
+
+int lsr_stage_consensus(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int64_t nQ, const float *Rt, int64_t nh,
+                        float eps, int32_t *count, double *sumd2) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!P || !Q || !Rt || !count || !sumd2 || nP < 1 || nQ < 1 || nP > kMaxPoints || nQ > kMaxPoints || nh < 1 ||
+      nh > ((int64_t)1 << 26) || !(eps > 0.f && eps <= 10.f))
+    return set_err(c, LSR_E_ARG, "bad argument");
+  auto plan = [&](Arena &a, float *&p, float4 *&XP, CloudLayout &Cq, ScratchLayout &S, float *&pose, int *&cnt,
+                  unsigned long long *&sum, double *&sd) {
+    p = a.take<float>(3 * nP);
+    XP = a.take<float4>(nP);
+    plan_cloud(a, (int)nQ, true, false, true, Cq);
+    plan_scratch(a, (int)nQ, Cq.cap_f, S);
+    pose = a.take<float>(12 * nh);
+    cnt = a.take<int>(nh);
+    sum = a.take<unsigned long long>(nh);
+    sd = a.take<double>(nh);
+  };
+  Arena m(nullptr);
+  float *z1, *z5;
+  float4 *z2;
+  CloudLayout z3;
+  ScratchLayout z4;
+  int *z6;
+  unsigned long long *z7;
+  double *z8;
+  plan(m, z1, z2, z3, z4, z5, z6, z7, z8);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  float *p, *pose;
+  float4 *XP;
+  CloudLayout Cq;
+  ScratchLayout S;
+  int *cnt;
+  unsigned long long *sum;
+  double *sd;
+  plan(a, p, XP, Cq, S, pose, cnt, sum, sd);
+  cudaStream_t s = c->stream;
+  TRY_CUDA(c, cudaMemcpyAsync(p, P, sizeof(float) * 3 * nP, cudaMemcpyDefault, s), "copy P");
+  const float *qsrc;
+  if ((rc = stage_input(c, Q, nQ, Cq.src, &qsrc))) return rc;
+  TRY_CUDA(c, cudaMemcpyAsync(pose, Rt, sizeof(float) * 12 * nh, cudaMemcpyDefault, s), "copy Rt");
+  k_pack<<<nblk(nP), 256, 0, s>>>(p, (int)nP, XP);
+  TRY_CUDA(c, build_cloud(qsrc, Cq, eps, eps, eps, false, true, S, s), "grid Q");
+  TRY_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int) * nh, s), "memset");
+  TRY_CUDA(c, cudaMemsetAsync(sum, 0, sizeof(unsigned long long) * nh, s), "memset");
+  TRY_CUDA(c, launch_consensus(XP, (int)nP, Cq.ge, Cq.start_e, Cq.Xe, pose, nullptr, nullptr, (int)nh, eps, cnt, sum, s),
+           "consensus");
+  k_sum_to_double<<<nblk(nh), 256, 0, s>>>(sum, (int)nh, sd);
+  if ((rc = copy_out(c, count, cnt, sizeof(int) * nh))) return rc;
+  if ((rc = copy_out(c, sumd2, sd, sizeof(double) * nh))) return rc;
+  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  return LSR_OK;
+}
+
+int lsr_stage_refine(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int64_t nQ, const double *T_in,
+                     float eps, float mu_scale, int32_t levels, int32_t iters, double *T_out, int32_t *iters_done) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!P || !Q || !T_in || !T_out || nP < 1 || nQ < 1 || nP > kMaxPoints || nQ > kMaxPoints || iters < 0 ||
+      iters > 10000 || levels < 1 || levels > kMaxLevels || !(eps > 0.f && eps * (float)(1 << (levels - 1)) <= 10.f) ||
+      !(mu_scale > 0.f))
+    return set_err(c, LSR_E_ARG, "bad argument");
+  auto plan = [&](Arena &a, float *&p, float4 *&XP, CloudLayout &Cq, LevelLayout &V, ScratchLayout &S, double *&part,
+                  double *&Td, RansacState *&st) {
+    p = a.take<float>(3 * nP);
+    XP = a.take<float4>(nP);
+    plan_cloud(a, (int)nQ, true, false, true, Cq);
+    plan_levels(a, (int)nQ, levels, V);
+    plan_scratch(a, (int)nQ, Cq.cap_f, S);
+    part = a.take<double>((size_t)kRefAcc * refine_blocks((int)nP));
+    Td = a.take<double>(16);
+    st = a.take<RansacState>(1);
+  };
+  Arena m(nullptr);
+  float *w1;
+  float4 *w2;
+  CloudLayout w3;
+  LevelLayout w8;
+  ScratchLayout w4;
+  double *w5, *w6;
+  RansacState *w7;
+  plan(m, w1, w2, w3, w8, w4, w5, w6, w7);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  float *p;
+  float4 *XP;
+  CloudLayout Cq;
+  LevelLayout V;
+  ScratchLayout S;
+  double *part, *Td;
+  RansacState *st;
+  plan(a, p, XP, Cq, V, S, part, Td, st);
+  cudaStream_t s = c->stream;
+  TRY_CUDA(c, cudaMemcpyAsync(p, P, sizeof(float) * 3 * nP, cudaMemcpyDefault, s), "copy P");
+  const float *qsrc;
+  if ((rc = stage_input(c, Q, nQ, Cq.src, &qsrc))) return rc;
+  TRY_CUDA(c, cudaMemcpyAsync(Td, T_in, sizeof(double) * 16, cudaMemcpyDefault, s), "copy T");
+  TRY_CUDA(c, cudaMemsetAsync(st, 0, sizeof(RansacState), s), "memset");
+  k_pack<<<nblk(nP), 256, 0, s>>>(p, (int)nP, XP);
+  TRY_CUDA(c, build_cloud(qsrc, Cq, eps, eps, eps, false, true, S, s), "grid Q");
+  TRY_CUDA(c, launch_refine_init(st, Cq.box, Td, s), "init");
+  TRY_CUDA(c,
+           enqueue_refine(XP, (int)nP, qsrc, (int)nQ, Cq.box, Cq.ge, Cq.start_e, Cq.Xe, V, eps, mu_scale, iters, st,
+                          part, S, s),
+           "refine");
+  RansacState h;
+  TRY_CUDA(c, cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H");
+  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  memcpy(T_out, h.T, sizeof(double) * 16);
+  if (iters_done) *iters_done = h.iters_done;
+  return LSR_OK;
+}
+
+// ------------------------------------------------------------------ objective
+static void host_exp_so3(const double w[3], double R[9]) {
+  double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2], th = sqrt(th2);
+  double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+  double a = th < 1e-6 ? 1.0 - th2 / 6.0 : sin(th) / th;
+  double b = th < 1e-6 ? 0.5 - th2 / 24.0 : (1.0 - cos(th)) / th2;
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) {
+      double k2 = K[3 * r] * K[q] + K[3 * r + 1] * K[3 + q] + K[3 * r + 2] * K[6 + q];
+      R[3 * r + q] = (r == q ? 1.0 : 0.0) + a * K[3 * r + q] + b * k2;
+    }
+}
+
+// Left Jacobian of SO(3): Exp(w + d) = Exp(J_l(w) d) Exp(w) to first order.
+static void host_left_jacobian(const double w[3], double J[9]) {
+  double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2], th = sqrt(th2);
+  double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+  double a = th < 1e-5 ? 0.5 - th2 / 24.0 : (1.0 - cos(th)) / th2;
+  double b = th < 1e-5 ? 1.0 / 6.0 - th2 / 120.0 : (th - sin(th)) / (th2 * th);
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) {
+      double k2 = K[3 * r] * K[q] + K[3 * r + 1] * K[3 + q] + K[3 * r + 2] * K[6 + q];
+      J[3 * r + q] = (r == q ? 1.0 : 0.0) + a * K[3 * r + q] + b * k2;
+    }
+}
+
+static int objective_impl(lsr_ctx *c, int32_t n, const float *const *P, const int64_t *nP, const float *const *Q,
+                          const int64_t *nQ, const double *xi, const double *T0, float eps, float mu, const double *dE,
+                          double *E, float *const *dP, float *const *dQ, double *dxi) {
+  int rc = guard(c);
+  if (rc) return rc;
+  bool grad = dE != nullptr;
+  if (n < 0 || (n > 0 && (!P || !nP || !Q || !nQ || !xi || !T0)) || !(eps > 0.f && eps <= 10.f) || !(mu > 0.f) ||
+      (!grad && !E) || (grad && (!dP || !dQ || !dxi)))
+    return set_err(c, LSR_E_ARG, "bad argument");
+  int64_t maxP = 0, maxQ = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!P[i] || !Q[i] || nP[i] < 1 || nQ[i] < 1 || nP[i] > kMaxPoints || nQ[i] > kMaxPoints)
+      return set_err(c, LSR_E_ARG, "bad cloud");
+    if (!is_device_ptr(P[i]) || !is_device_ptr(Q[i])) return set_err(c, LSR_E_ARG, "objective clouds must be on the device");
+    if (grad && (!dP[i] || !dQ[i] || !is_device_ptr(dP[i]) || !is_device_ptr(dQ[i])))
+      return set_err(c, LSR_E_ARG, "objective gradients must be device arrays");
+    maxP = std::max(maxP, nP[i]);
+    maxQ = std::max(maxQ, nQ[i]);
+  }
+  if (n == 0) return LSR_OK;
+  auto plan = [&](Arena &a, CloudLayout &Cq, ScratchLayout &S, double *&part, double *&out7) {
+    plan_cloud(a, (int)maxQ, false, false, true, Cq);
+    plan_scratch(a, (int)maxQ, Cq.cap_f, S);
+    part = a.take<double>((size_t)7 * objective_blocks((int)maxP));
+    out7 = a.take<double>((size_t)7 * n);
+  };
+  Arena m(nullptr);
+  CloudLayout q1;
+  ScratchLayout q2;
+  double *q3, *q4;
+  plan(m, q1, q2, q3, q4);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  CloudLayout Cq0;
+  ScratchLayout S;
+  double *part, *out7;
+  plan(a, Cq0, S, part, out7);
+  cudaStream_t s = c->stream;
+  std::vector<double> host7((size_t)7 * n);
+  for (int i = 0; i < n; ++i) {
+    CloudLayout Cq = Cq0;
+    Cq.n = (int)nQ[i];
+    const double *w = xi + 6 * i, *T = T0 + 16 * i;
+    double Rw[9], Tm[16];
+    host_exp_so3(w, Rw);
+    double M[16] = {Rw[0], Rw[1], Rw[2], w[3], Rw[3], Rw[4], Rw[5], w[4], Rw[6], Rw[7], Rw[8], w[5], 0, 0, 0, 1};
+    for (int r = 0; r < 4; ++r)
+      for (int q = 0; q < 4; ++q) {
+        double acc = 0.0;
+        for (int k = 0; k < 4; ++k) acc += M[4 * r + k] * T[4 * k + q];
+        Tm[4 * r + q] = acc;
+      }
+    float Rf[9], tf[3], vf[3];
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) Rf[3 * r + q] = (float)Tm[4 * r + q];
+      tf[r] = (float)Tm[4 * r + 3];
+      vf[r] = (float)w[3 + r];
+    }
+    // eps grid of Q with caller indices (build_grid_xyz carries caller order)
+    TRY_CUDA(c, launch_bbox_xyz(Q[i], Cq.n, Cq.box_part, bbox_blocks(Cq.n), Cq.box, s), "bbox");
+    TRY_CUDA(c, launch_grid_params(Cq.box, eps, Cq.n, Cq.cap_e, Cq.ge, s), "grid params");
+    TRY_CUDA(c, build_grid_xyz(Q[i], Cq.n, Cq.ge, Cq.cap_e, Cq.start_e, Cq.Xe, Cq.inv, S.g, s), "grid");
+    if (grad) TRY_CUDA(c, cudaMemsetAsync(dQ[i], 0, sizeof(float) * 3 * nQ[i], s), "memset dQ");
+    TRY_CUDA(c,
+             launch_objective(P[i], (int)nP[i], Cq.ge, Cq.start_e, Cq.Xe, Rf, tf, vf, eps, mu,
+                              grad ? (float)dE[i] : 1.f, grad ? 1 : 0, part, out7 + 7 * i, grad ? dP[i] : nullptr,
+                              grad ? dQ[i] : nullptr, s),
+             "objective");
+  }
+  TRY_CUDA(c, cudaMemcpyAsync(host7.data(), out7, sizeof(double) * 7 * n, cudaMemcpyDeviceToHost, s), "D2H");
+  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  for (int i = 0; i < n; ++i) {
+    const double *o = &host7[(size_t)7 * i];
+    if (E) E[i] = o[0];
+    if (grad) {
+      double J[9];
+      host_left_jacobian(xi + 6 * i, J);
+      for (int q = 0; q < 3; ++q) dxi[6 * i + q] = dE[i] * (J[0 * 3 + q] * o[4] + J[1 * 3 + q] * o[5] + J[2 * 3 + q] * o[6]);
+      for (int q = 0; q < 3; ++q) dxi[6 * i + 3 + q] = dE[i] * o[1 + q];
+    }
+  }
+  return LSR_OK;
+}
+
+int lsr_objective_fwd(lsr_ctx *c, int32_t n, const float *const *P, const int64_t *nP, const float *const *Q,
+                      const int64_t *nQ, const double *xi, const double *T0, float eps, float mu, double *E) {
+  return objective_impl(c, n, P, nP, Q, nQ, xi, T0, eps, mu, nullptr, E, nullptr, nullptr, nullptr);
+}
+
+int lsr_objective_bwd(lsr_ctx *c, int32_t n, const float *const *P, const int64_t *nP, const float *const *Q,
+                      const int64_t *nQ, const double *xi, const double *T0, float eps, float mu, const double *dE,
+                      float *const *dP, float *const *dQ, double *dxi) {
+  if (!dE) return c ? set_err(c, LSR_E_ARG, "null dE") : LSR_E_STATE;
+  return objective_impl(c, n, P, nP, Q, nQ, xi, T0, eps, mu, dE, nullptr, dP, dQ, dxi);
+}
+
+}  // extern "C"

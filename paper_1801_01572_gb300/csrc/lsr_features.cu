@@ -1,0 +1,297 @@
+// lsr_features.cu -- per-point normals, SPFH and FPFH (Algorithm 1, line 2:
+// "Compute FPFH features"; radii of Sec. IV).
+//
+// All three kernels are warp-per-point: the 32 lanes of a warp stride over the
+// contiguous sorted ranges of the neighbouring grid cells, so the neighbour
+// loads of a warp are coalesced and the work per point is split evenly.
+#include <math_constants.h>
+
+#include "lsr_internal.cuh"
+
+namespace lsr {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations in FP32. a[6]
+// = (xx, xy, xz, yy, yz, zz). Returns the eigenvalues w[3] (unsorted) and the
+// eigenvectors as the columns of v.
+__device__ void sym3_eigen(const float a[6], float w[3], float v[3][3]) {
+  float A[3][3] = {{a[0], a[1], a[2]}, {a[1], a[3], a[4]}, {a[2], a[4], a[5]}};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) v[r][c] = (r == c) ? 1.f : 0.f;
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    float off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    float diag = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= 1e-14f * diag) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      float apq = A[p][q];
+      if (apq == 0.f) continue;
+      float theta = (A[q][q] - A[p][p]) / (2.f * apq);
+      float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+      float c = rsqrtf(t * t + 1.f), s = t * c;
+      for (int k = 0; k < 3; ++k) {
+        float akp = A[k][p], akq = A[k][q];
+        A[k][p] = c * akp - s * akq;
+        A[k][q] = s * akp + c * akq;
+      }
+      for (int k = 0; k < 3; ++k) {
+        float apk = A[p][k], aqk = A[q][k];
+        A[p][k] = c * apk - s * aqk;
+        A[q][k] = s * apk + c * aqk;
+      }
+      for (int k = 0; k < 3; ++k) {
+        float vkp = v[k][p], vkq = v[k][q];
+        v[k][p] = c * vkp - s * vkq;
+        v[k][q] = s * vkp + c * vkq;
+      }
+    }
+  }
+  w[0] = A[0][0], w[1] = A[1][1], w[2] = A[2][2];
+}
+
+// Normal of each point: PCA of the points within r (inclusive, self included),
+// accumulated about the query point (one pass), eigenvector of the smallest
+// eigenvalue, turned toward the viewpoint; fewer than 3 points: invalid.
+__global__ void __launch_bounds__(kThreads) k_normals(const float4 *__restrict__ X, int n, const GridParams *gnp,
+                                                      const int *__restrict__ start, const float4 *__restrict__ Xn,
+                                                      float r2, float3 vp, float4 *__restrict__ N,
+                                                      int *__restrict__ count) {
+  const GridParams g = *gnp;
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * kThreads + threadIdx.x) >> 5, nwarps = (gridDim.x * kThreads) >> 5;
+  for (int i = warp; i < n; i += nwarps) {
+    float3 p = f3(X[i]);
+    int k = 0;
+    float s[3] = {0, 0, 0}, ss[6] = {0, 0, 0, 0, 0, 0};
+    grid_ranges(g, start, p.x, p.y, p.z, [&](int b, int e) {
+      for (int t = b + lane; t < e; t += 32) {
+        float4 q = Xn[t];
+        float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+        if (dx * dx + dy * dy + dz * dz <= r2) {
+          ++k;
+          s[0] += dx, s[1] += dy, s[2] += dz;
+          ss[0] += dx * dx, ss[1] += dx * dy, ss[2] += dx * dz;
+          ss[3] += dy * dy, ss[4] += dy * dz, ss[5] += dz * dz;
+        }
+      }
+    });
+    k = warp_sum(k);
+    for (int d = 0; d < 3; ++d) s[d] = warp_sum(s[d]);
+    for (int d = 0; d < 6; ++d) ss[d] = warp_sum(ss[d]);
+    if (lane == 0) {
+      float4 out = make_float4(0.f, 0.f, 0.f, -1.f);
+      if (k >= 3) {
+        float ik = 1.f / (float)k;
+        float m[3] = {s[0] * ik, s[1] * ik, s[2] * ik};
+        float C[6] = {ss[0] * ik - m[0] * m[0], ss[1] * ik - m[0] * m[1], ss[2] * ik - m[0] * m[2],
+                      ss[3] * ik - m[1] * m[1], ss[4] * ik - m[1] * m[2], ss[5] * ik - m[2] * m[2]};
+        float w[3], V[3][3];
+        sym3_eigen(C, w, V);
+        int j = 0;
+        if (w[1] < w[j]) j = 1;
+        if (w[2] < w[j]) j = 2;
+        float3 nrm = make_float3(V[0][j], V[1][j], V[2][j]);
+        float3 tv = make_float3(vp.x - p.x, vp.y - p.y, vp.z - p.z);
+        if (dot3(nrm, tv) < 0.f) nrm = make_float3(-nrm.x, -nrm.y, -nrm.z);
+        float sum = w[0] + w[1] + w[2];
+        out = make_float4(nrm.x, nrm.y, nrm.z, sum > 0.f ? fmaxf(w[j], 0.f) / sum : 0.f);
+      }
+      N[i] = out;
+      if (count) count[i] = k;
+    }
+  }
+}
+
+// Darboux-frame pair features of FPFH (Rusu et al., ICRA 2009). The source is
+// the point whose normal makes the smaller angle with the joining line (ties
+// keep p); u = n_s, v = (u x e)/|u x e|, w = u x v; alpha = v.n_t, phi = u.e,
+// theta = atan2(w.n_t, u.n_t). A pair without a frame (|u x e|^2 < 1e-12) is
+// skipped. Bins: 11 per feature over [-1, 1], [-1, 1], [-pi, pi].
+__device__ __forceinline__ bool pair_bins(float3 p, float3 np, float3 q, float3 nq, float d2, int &ba, int &bp,
+                                          int &bt) {
+  float id = rsqrtf(d2);
+  float3 e = make_float3((q.x - p.x) * id, (q.y - p.y) * id, (q.z - p.z) * id);
+  float cs = fabsf(dot3(np, e)), ct = fabsf(dot3(nq, e));
+  float3 u = np, nt = nq;
+  if (cs < ct) {
+    u = nq, nt = np;
+    e = make_float3(-e.x, -e.y, -e.z);
+  }
+  float3 v = cross3(u, e);
+  float vn2 = dot3(v, v);
+  if (vn2 < 1e-12f) return false;
+  float iv = rsqrtf(vn2);
+  v = make_float3(v.x * iv, v.y * iv, v.z * iv);
+  float3 w = cross3(u, v);
+  float alpha = dot3(v, nt), phi = dot3(u, e), theta = atan2f(dot3(w, nt), dot3(u, nt));
+  ba = min(max(__float2int_rd((alpha + 1.f) * 5.5f), 0), 10);
+  bp = min(max(__float2int_rd((phi + 1.f) * 5.5f), 0), 10);
+  bt = min(max(__float2int_rd((theta + CUDART_PI_F) * (11.f / (2.f * CUDART_PI_F))), 0), 10);
+  return true;
+}
+
+// SPFH: every lane counts its pairs into a private column of a per-warp
+// [bin][lane] histogram in shared memory (row stride 33 words, so both the
+// lane-private updates and the per-bin column sums avoid bank conflicts).
+__global__ void __launch_bounds__(kThreads) k_spfh(const float4 *__restrict__ X, const float4 *__restrict__ N, int n,
+                                                   const GridParams *gfp, const int *__restrict__ start, float r2,
+                                                   float *__restrict__ S, int *__restrict__ kout) {
+  __shared__ int hist[kWarps][kD * 33];
+  const GridParams g = *gfp;
+  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  int warp = (blockIdx.x * kThreads + threadIdx.x) >> 5, nwarps = (gridDim.x * kThreads) >> 5;
+  int *h = hist[wl];
+  for (int i = warp; i < n; i += nwarps) {
+    for (int b = 0; b < kD; ++b) h[b * 33 + lane] = 0;
+    float3 p = f3(X[i]);
+    float4 np4 = N[i];
+    int kk = 0;
+    if (np4.w >= 0.f) {
+      float3 np = f3(np4);
+      grid_ranges(g, start, p.x, p.y, p.z, [&](int b, int e) {
+        for (int t = b + lane; t < e; t += 32) {
+          if (t == i) continue;
+          float4 q4 = X[t];
+          float dx = q4.x - p.x, dy = q4.y - p.y, dz = q4.z - p.z;
+          float d2 = dx * dx + dy * dy + dz * dz;
+          if (d2 > r2 || d2 == 0.f) continue;
+          float4 nq4 = N[t];
+          if (nq4.w < 0.f) continue;
+          int ba, bp, bt;
+          if (!pair_bins(p, np, f3(q4), f3(nq4), d2, ba, bp, bt)) continue;
+          h[ba * 33 + lane] += 1;
+          h[(kNB + bp) * 33 + lane] += 1;
+          h[(2 * kNB + bt) * 33 + lane] += 1;
+          ++kk;
+        }
+      });
+    }
+    kk = warp_sum(kk);
+    __syncwarp();
+    float inv = kk > 0 ? 1.f / (float)kk : 0.f;
+    float *row = S + (size_t)i * kDS;
+    int c = 0;
+    for (int l = 0; l < 32; ++l) c += h[lane * 33 + l];
+    row[lane] = (float)c * inv;
+    if (lane == 0) {
+      int c2 = 0;
+      for (int l = 0; l < 32; ++l) c2 += h[32 * 33 + l];
+      row[32] = (float)c2 * inv;
+    }
+    if (lane >= 1 && lane <= 3) row[32 + lane] = 0.f;
+    if (lane == 0 && kout) kout[i] = kk;
+    __syncwarp();
+  }
+}
+
+// FPFH: every lane accumulates the distance-weighted SPFH rows of its
+// neighbours in registers; the warp then sums the 33 bins through a [lane][bin]
+// shared-memory transpose, adds SPFH(p), and rescales each sub-histogram.
+__global__ void __launch_bounds__(kThreads) k_fpfh(const float4 *__restrict__ X, const float4 *__restrict__ N,
+                                                   const float *__restrict__ S, int n, const GridParams *gfp,
+                                                   const int *__restrict__ start, float r2, float *__restrict__ F) {
+  __shared__ float red[kWarps][32 * 33 + 33];
+  const GridParams g = *gfp;
+  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  int warp = (blockIdx.x * kThreads + threadIdx.x) >> 5, nwarps = (gridDim.x * kThreads) >> 5;
+  float *sm = red[wl];
+  for (int i = warp; i < n; i += nwarps) {
+    float3 p = f3(X[i]);
+    bool valid = N[i].w >= 0.f;
+    float acc[kD];
+#pragma unroll
+    for (int b = 0; b < kD; ++b) acc[b] = 0.f;
+    int kk = 0;
+    if (valid) {
+      grid_ranges(g, start, p.x, p.y, p.z, [&](int b, int e) {
+        for (int t = b + lane; t < e; t += 32) {
+          if (t == i) continue;
+          float4 q4 = X[t];
+          float dx = q4.x - p.x, dy = q4.y - p.y, dz = q4.z - p.z;
+          float d2 = dx * dx + dy * dy + dz * dz;
+          if (d2 > r2 || d2 == 0.f) continue;
+          if (N[t].w < 0.f) continue;
+          float w = rsqrtf(d2);
+          const float4 *srow = reinterpret_cast<const float4 *>(S + (size_t)t * kDS);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float4 v = srow[q];
+            acc[4 * q + 0] += w * v.x;
+            acc[4 * q + 1] += w * v.y;
+            acc[4 * q + 2] += w * v.z;
+            acc[4 * q + 3] += w * v.w;
+          }
+          acc[32] += w * S[(size_t)t * kDS + 32];
+          ++kk;
+        }
+      });
+    }
+    kk = warp_sum(kk);
+#pragma unroll
+    for (int b = 0; b < kD; ++b) sm[lane * 33 + b] = acc[b];
+    __syncwarp();
+    float tot = 0.f, tot32 = 0.f;
+    for (int l = 0; l < 32; ++l) tot += sm[l * 33 + lane];
+    if (lane == 0)
+      for (int l = 0; l < 32; ++l) tot32 += sm[l * 33 + 32];
+    __syncwarp();
+    const float *srow_i = S + (size_t)i * kDS;
+    float ik = kk > 0 ? 1.f / (float)kk : 0.f;
+    float f = valid ? srow_i[lane] + tot * ik : 0.f;
+    float f32 = valid ? srow_i[32] + tot32 * ik : 0.f;
+    // sub-histogram sums: bins 0..10, 11..21, 22..32
+    float *fb = sm + 32 * 33;  // 33 spare words
+    fb[lane] = f;
+    if (lane == 0) fb[32] = f32;
+    __syncwarp();
+    int grp = lane / kNB;
+    float gs = 0.f;
+    for (int b = 0; b < kNB; ++b) gs += fb[grp * kNB + b];
+    float g2 = 0.f;
+    if (lane == 0)
+      for (int b = 0; b < kNB; ++b) g2 += fb[2 * kNB + b];
+    float *row = F + (size_t)i * kDS;
+    row[lane] = gs > 0.f ? f / gs : 0.f;
+    if (lane == 0) row[32] = g2 > 0.f ? f32 / g2 : 0.f;
+    if (lane >= 1 && lane <= 3) row[32 + lane] = 0.f;
+    __syncwarp();
+  }
+}
+
+inline int blocks_for_warps(int n) {
+  int b = (int)lsr_div_up(n, kWarps);
+  return b < 1 ? 1 : (b > 152 * 64 ? 152 * 64 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_normals(const float4 *X, int n, const GridParams *gn, const int *start_n, const float4 *Xn, float r,
+                           float3 vp, float4 *N, int *count, cudaStream_t s) {
+  k_normals<<<blocks_for_warps(n), kThreads, 0, s>>>(X, n, gn, start_n, Xn, r * r, vp, N, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spfh(const float4 *X, const float4 *N, int n, const GridParams *gf, const int *start_f, float r,
+                        float *spfh, int *k, cudaStream_t s) {
+  k_spfh<<<blocks_for_warps(n), kThreads, 0, s>>>(X, N, n, gf, start_f, r * r, spfh, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fpfh(const float4 *X, const float4 *N, const float *spfh, int n, const GridParams *gf,
+                        const int *start_f, float r, float *fpfh, cudaStream_t s) {
+  k_fpfh<<<blocks_for_warps(n), kThreads, 0, s>>>(X, N, spfh, n, gf, start_f, r * r, fpfh);
+  return cudaGetLastError();
+}
+
+}  // namespace lsr

@@ -1,0 +1,229 @@
+// lsr_internal.cuh -- internal declarations shared by the CUDA translation
+// units of the registration library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lsr {
+
+constexpr int kD = 33;       // FPFH length: 3 features x 11 bins
+constexpr int kNB = 11;      // bins per feature
+constexpr int kDS = 36;      // stored row stride of SPFH / FPFH (16-byte aligned rows)
+constexpr int kWarp = 32;
+
+// Uniform 3D grid of eq. (1): cell index = floor((x - origin) / cell), stored
+// densely over the cloud's bounding box. When the box holds more cells than
+// the allocated capacity, the y and z (and if needed x) cell coordinates wrap
+// modulo the stored extents; wrapped cells share storage, which only adds
+// candidates that the exact distance test then rejects. The cell edge is the
+// search radius times (1 + 1e-4), so every point within the radius of a query
+// lies in the 3 x 3 x 3 block of cells around it even after FP32 rounding.
+struct GridParams {
+  float ox, oy, oz;  // origin (bounding-box minimum)
+  float cell, inv_cell;
+  int nx, ny, nz;    // extent of the bounding box in cells
+  int wx, wy, wz;    // stored extents (<= n*, equal unless wrapped)
+  int ncells;        // wx * wy * wz
+  int npts;
+  int pad_;
+};
+
+// Device view of one cloud after packing and grid building. "Internal order"
+// is the order of the feature-radius grid (points sorted by cell, then by
+// caller index), which keeps neighbourhoods contiguous in memory.
+struct CloudDev {
+  int n;
+  const float4 *X;        // n, internal order; w = caller index (int bits)
+  const int *inv;         // n, caller index -> internal index
+  const GridParams *gf;   // feature-radius grid over X (its sorted array is X)
+  const int *start_f;     // gf->ncells + 1
+  const GridParams *gn;   // normal-radius grid
+  const int *start_n;
+  const float4 *Xn;       // n, sorted by normal grid; w = internal index
+  const GridParams *ge;   // eps grid (consensus / refinement / objective)
+  const int *start_e;
+  const float4 *Xe;       // n, sorted by eps grid; w = internal index
+  const float4 *N;        // n normals (internal order); w = curvature, -1 if invalid
+  const float *F;         // n x kDS FPFH (internal order)
+};
+
+// ----------------------------------------------------------------- helpers
+__host__ __device__ inline int64_t lsr_div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+#define LSR_CUDA_TRY(call)                         \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return e_;              \
+  } while (0)
+
+// Visit the sorted-point ranges that can hold points within one cell of the
+// query (the 27 cells around it): f(b, e) is called for each range [b, e) of
+// the grid's sorted array. Without wrapping, the three x-adjacent cells of a
+// row are one contiguous range (9 calls). With wrapping, each distinct storage
+// cell is visited once. Queries more than one cell outside the box visit
+// nothing.
+template <class F>
+__device__ __forceinline__ void grid_ranges(const GridParams &g, const int *__restrict__ start, float x, float y,
+                                            float z, F &&f) {
+  float fx = (x - g.ox) * g.inv_cell, fy = (y - g.oy) * g.inv_cell, fz = (z - g.oz) * g.inv_cell;
+  if (!(fx >= -1.f && fx < (float)g.nx + 1.f && fy >= -1.f && fy < (float)g.ny + 1.f && fz >= -1.f &&
+        fz < (float)g.nz + 1.f))
+    return;
+  int cx = __float2int_rd(fx), cy = __float2int_rd(fy), cz = __float2int_rd(fz);
+  int x0 = cx - 1 < 0 ? 0 : cx - 1, x1 = cx + 1 > g.nx - 1 ? g.nx - 1 : cx + 1;
+  if (x0 > x1) return;
+  bool wrapped = (g.wx != g.nx) | (g.wy != g.ny) | (g.wz != g.nz);
+  if (!wrapped) {
+    for (int dz = -1; dz <= 1; ++dz) {
+      int iz = cz + dz;
+      if (iz < 0 || iz >= g.nz) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        int iy = cy + dy;
+        if (iy < 0 || iy >= g.ny) continue;
+        int row = (iz * g.wy + iy) * g.wx;
+        f(start[row + x0], start[row + x1 + 1]);
+      }
+    }
+    return;
+  }
+  int seen[27];
+  int ns = 0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    int iz = cz + dz;
+    if (iz < 0 || iz >= g.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      int iy = cy + dy;
+      if (iy < 0 || iy >= g.ny) continue;
+      for (int ix = x0; ix <= x1; ++ix) {
+        int slot = ((iz % g.wz) * g.wy + (iy % g.wy)) * g.wx + (ix % g.wx);
+        bool dup = false;
+        for (int k = 0; k < ns; ++k) dup |= (seen[k] == slot);
+        if (dup) continue;
+        seen[ns++] = slot;
+        f(start[slot], start[slot + 1]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ int warp_sum(int v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// ----------------------------------------------------------------- grid build (lsr_grid.cu)
+// Bounding box of a float32 xyz array (AoS) or a float4 array, reduced into
+// box[6] = (minx, miny, minz, maxx, maxy, maxz) via per-block partials.
+cudaError_t launch_bbox_xyz(const float *xyz, int n, float *partials, int nblk_cap, float *box, cudaStream_t s);
+cudaError_t launch_bbox_f4(const float4 *x, int n, float *partials, int nblk_cap, float *box, cudaStream_t s);
+int bbox_blocks(int n);
+
+// Fill a GridParams from a bounding box on the device.
+cudaError_t launch_grid_params(const float *box, float radius, int npts, int cap_cells, GridParams *g, cudaStream_t s);
+
+// Counting sort of points into the grid: out[k] = point sorted k-th by (cell,
+// source index) with w replaced by the carried index (source index if
+// carry == nullptr). start gets the exclusive cell offsets (ncells + 1).
+// Scratch: slot (n ints), counts (cap + 1 ints), scan scratch (scan_scratch_ints(cap)).
+struct GridScratch {
+  int *slot;
+  int *counts;
+  int *tmp;       // n ints
+  int *scan;      // scan_scratch_ints(cap + 1)
+};
+int64_t scan_scratch_ints(int64_t n);
+cudaError_t build_grid_xyz(const float *xyz, int n, const GridParams *g, int cap_cells, int *start, float4 *out,
+                           int *inv_out, GridScratch sc, cudaStream_t s);
+cudaError_t build_grid_f4(const float4 *x, int n, const GridParams *g, int cap_cells, int *start, float4 *out,
+                          GridScratch sc, cudaStream_t s);
+
+// Exclusive scan of in[0..*n_dev) into out[0..*n_dev] (out[n] = total).
+cudaError_t scan_exclusive(const int *in, int *out, const int *n_dev, int cap, int *scratch, cudaStream_t s);
+
+// ----------------------------------------------------------------- features (lsr_features.cu)
+cudaError_t launch_normals(const float4 *X, int n, const GridParams *gn, const int *start_n, const float4 *Xn,
+                           float r, float3 vp, float4 *N, int *count, cudaStream_t s);
+cudaError_t launch_spfh(const float4 *X, const float4 *N, int n, const GridParams *gf, const int *start_f, float r,
+                        float *spfh, int *k, cudaStream_t s);
+cudaError_t launch_fpfh(const float4 *X, const float4 *N, const float *spfh, int n, const GridParams *gf,
+                        const int *start_f, float r, float *fpfh, cudaStream_t s);
+
+// ----------------------------------------------------------------- matching (lsr_match.cu)
+cudaError_t launch_match_fp32(const float *FP, int nP, const float *FQ, int nQ, int *nn, float *d1, cudaStream_t s);
+
+// ----------------------------------------------------------------- RANSAC (lsr_ransac.cu)
+// Device-side counters and selection state of one registration.
+struct RansacState {
+  int n_surv;          // survivors written (capped at surv_cap)
+  int n_surv_total;    // survivors found
+  int n_normal_ok;
+  int best;            // survivor slot of the best hypothesis, -1 none
+  int best_h;
+  int best_count;
+  float best_fit;
+  int status;          // 0 aligned, 1 no alignment
+  int active;          // refinement still iterating
+  int iters_done;
+  int final_count;
+  int level_iters;     // refinement steps taken at the current level
+  double final_sumd2;
+  double T[16];        // current pose (refinement), row-major
+  double T_hyp[16];
+  float pose_f[12];    // FP32 copy of the pose used by consensus-type kernels
+  double center[3];    // linearisation centre of the refinement (centroid of Q)
+  double last_step;
+};
+
+int hyp_blocks(int64_t H);
+cudaError_t launch_hypotheses(const float4 *XP, const int *invP, const float4 *NP, int nP, const float4 *XQ,
+                              const float4 *NQ, int nQ, const int *nn, const uint8_t *vP_ext, const uint8_t *vQ_ext,
+                              int64_t H, uint64_t seed, uint64_t pair, float tau, int *block_counts, int *block_offsets,
+                              int *scan_scratch, int *surv, int surv_cap, RansacState *st, cudaStream_t s);
+// Pose of each survivor from its 4 pairs + the normal check. pose: cap x 12 floats, ok: cap bytes.
+cudaError_t launch_rigid_survivors(const float4 *XP, const int *invP, const float4 *NP, int nP, const float4 *XQ,
+                                   const float4 *NQ, const int *nn, const int *surv, const RansacState *st,
+                                   uint64_t seed, uint64_t pair, float cos_normal, float *pose, uint8_t *ok,
+                                   int *n_normal_ok, cudaStream_t s);
+cudaError_t launch_rigid4(const float *ps, const float *qs, int nh, float *pose, cudaStream_t s);
+// Consensus: for every pose k < *n_dev (or n_host if n_dev is null) with ok[k] (or ok == null),
+// count[k] / sum[k] (fixed point, 2^-40 m^2 units) over all P points.
+cudaError_t launch_consensus(const float4 *XP, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
+                             const float *pose, const uint8_t *ok, const int *n_dev, int n_host, float eps,
+                             int *count, unsigned long long *sum, cudaStream_t s);
+cudaError_t launch_select(const int *surv, const int *count, const unsigned long long *sum, const uint8_t *ok,
+                          const float *pose, int nP, float min_ratio, RansacState *st, cudaStream_t s);
+constexpr double kFixScale = 1099511627776.0;  // 2^40
+
+// ----------------------------------------------------------------- refinement (lsr_refine.cu)
+int refine_blocks(int nP);
+cudaError_t launch_refine_init(RansacState *st, const float *boxQ, const double *T_in, cudaStream_t s);
+constexpr int kRefAcc = 28;  // per-block partial sums of one refinement step
+constexpr int kMaxLevels = 8;
+// Subsampling stride of graduated refinement level l of L for a cloud of n points.
+int gnc_stride(int64_t n, int level, int levels);
+cudaError_t launch_refine_level_begin(RansacState *st, cudaStream_t s);
+// One IRLS step on the points of P (internal order, w = caller index) whose
+// caller index is a multiple of strideP, against the given grid of Q.
+cudaError_t launch_refine_step(const float4 *XP, int nP, int strideP, const GridParams *ge, const int *start_e,
+                               const float4 *Xe, float eps_r, float mu, int max_iters, RansacState *st,
+                               double *partials, cudaStream_t s);
+// out[m] = (Q[m * stride], m) for m < ceil(n / stride); Q caller-order xyz.
+cudaError_t launch_subsample(const float *xyz, int n, int stride, float4 *out, cudaStream_t s);
+cudaError_t launch_final_pose(RansacState *st, float *pose, cudaStream_t s);
+cudaError_t launch_final_count(const int *count, const unsigned long long *sum, RansacState *st, cudaStream_t s);
+
+// Objective forward / backward for one pair (lsr_refine.cu). P: caller-order
+// float32 xyz; the eps grid of Q carries caller indices in Xe.w. out7 (device):
+// E, g_v[3], g_w[3]. dP / dQ (device, caller order) are written when want_grad
+// (dQ must be zeroed by the caller), scaled by `scale`.
+int objective_blocks(int nP);
+cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
+                             const float R[9], const float t[3], const float v[3], float eps, float mu, float scale,
+                             int want_grad, double *partials, double *out7, float *dP, float *dQ, cudaStream_t s);
+
+}  // namespace lsr

@@ -1,0 +1,358 @@
+// lsr_refine.cu -- robust pose refinement and the robust alignment objective.
+//
+// The cost is the line-process objective of eq. (3)-(4) with the line process
+// eliminated: for a residual r, min_l l r^2 + mu (sqrt(l) - 1)^2 is reached at
+// l* = (mu / (mu + r^2))^2 and equals the Geman-McClure rho(r^2) = mu r^2 /
+// (mu + r^2). Refinement iterates reweighted Gauss-Newton with the Jacobian
+// G_p = [-[p]_x | I] of eq. (5): FP32 per-thread and per-block sums, FP64
+// across blocks, an FP64 Cholesky solve and an FP64 pose update on the device.
+#include "lsr_internal.cuh"
+
+namespace lsr {
+
+namespace {
+
+constexpr int kRefThreads = 256;
+constexpr int kNAcc = 28;  // 21 (upper triangle of A) + 6 (b) + 1 (count)
+
+__device__ __forceinline__ void nn_within(const GridParams &g, const int *start, const float4 *Xe, float x, float y,
+                                          float z, float eps2, float &best, int &bt) {
+  best = eps2;
+  bt = -1;
+  grid_ranges(g, start, x, y, z, [&](int b, int e) {
+    for (int t = b; t < e; ++t) {
+      float4 q = Xe[t];
+      float dx = q.x - x, dy = q.y - y, dz = q.z - z;
+      float d2 = dx * dx + dy * dy + dz * dz;
+      int qi = __float_as_int(q.w);
+      if (d2 < best || (d2 == best && bt >= 0 && qi < __float_as_int(Xe[bt].w))) best = d2, bt = t;
+    }
+  });
+}
+
+template <int N>
+__device__ __forceinline__ void block_reduce_to(float (&v)[N], double *out) {
+  __shared__ float sm[kRefThreads / 32][N];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < N; ++k) sm[w][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double s = 0.0;
+    for (int k = 0; k < kRefThreads / 32; ++k) s += (double)sm[k][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kRefThreads) k_refine_accum(const float4 *__restrict__ XP, int nP, int strideP,
+                                                              const GridParams *gep, const int *__restrict__ start,
+                                                              const float4 *__restrict__ Xe, float eps2, float mu,
+                                                              const RansacState *st, double *partials) {
+  if (!st->active) return;
+  const GridParams g = *gep;
+  const double *T = st->T;
+  float R[9], tc[3], c[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) R[3 * r + k] = (float)T[4 * r + k];
+    c[r] = (float)st->center[r];
+    tc[r] = (float)(T[4 * r + 3] - st->center[r]);
+  }
+  float acc[kNAcc];
+#pragma unroll
+  for (int k = 0; k < kNAcc; ++k) acc[k] = 0.f;
+  for (int i = blockIdx.x * kRefThreads + threadIdx.x; i < nP; i += gridDim.x * kRefThreads) {
+    float4 p = XP[i];
+    if (strideP > 1 && __float_as_int(p.w) % strideP != 0) continue;
+    float xc0 = fmaf(R[0], p.x, fmaf(R[1], p.y, fmaf(R[2], p.z, tc[0])));
+    float xc1 = fmaf(R[3], p.x, fmaf(R[4], p.y, fmaf(R[5], p.z, tc[1])));
+    float xc2 = fmaf(R[6], p.x, fmaf(R[7], p.y, fmaf(R[8], p.z, tc[2])));
+    float x = xc0 + c[0], y = xc1 + c[1], z = xc2 + c[2];
+    float best;
+    int bt;
+    nn_within(g, start, Xe, x, y, z, eps2, best, bt);
+    if (bt < 0) continue;
+    float4 q = Xe[bt];
+    float r[3] = {x - q.x, y - q.y, z - q.z};
+    float s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    float l = mu / (mu + s);
+    float w = l * l;
+    // J = [-[xc]_x | I] (rows: x, y, z; columns: alpha, beta, gamma, tx, ty, tz)
+    float J[3][6] = {{0.f, xc2, -xc1, 1.f, 0.f, 0.f}, {-xc2, 0.f, xc0, 0.f, 1.f, 0.f}, {xc1, -xc0, 0.f, 0.f, 0.f, 1.f}};
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int b = a; b < 6; ++b) {
+        acc[k++] += w * (J[0][a] * J[0][b] + J[1][a] * J[1][b] + J[2][a] * J[2][b]);
+      }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) acc[21 + a] += w * (J[0][a] * r[0] + J[1][a] * r[1] + J[2][a] * r[2]);
+    acc[27] += 1.f;
+  }
+  block_reduce_to<kNAcc>(acc, partials + (size_t)blockIdx.x * kNAcc);
+}
+
+__device__ void exp_so3(const double w[3], double R[9]) {
+  double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2], th = sqrt(th2);
+  double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+  double a, b;
+  if (th < 1e-6) {
+    a = 1.0 - th2 / 6.0;
+    b = 0.5 - th2 / 24.0;
+  } else {
+    a = sin(th) / th;
+    b = (1.0 - cos(th)) / th2;
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double k2 = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+      R[3 * r + c] = (r == c ? 1.0 : 0.0) + a * K[3 * r + c] + b * k2;
+    }
+}
+
+// Sum the block partials in FP64 (fixed order), solve A d = -b by Cholesky,
+// and left-multiply the pose by the update about the linearisation centre c:
+// x' = Exp(d_w)(x - c) + c + d_v.
+__global__ void k_refine_solve(const double *partials, int nblocks, RansacState *st, int max_iters, double tol) {
+  if (threadIdx.x != 0 || !st->active) return;
+  double acc[kNAcc];
+  for (int k = 0; k < kNAcc; ++k) acc[k] = 0.0;
+  for (int b = 0; b < nblocks; ++b)
+    for (int k = 0; k < kNAcc; ++k) acc[k] += partials[(size_t)b * kNAcc + k];
+  double A[36];
+  int k = 0;
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) {
+      A[6 * a + b] = A[6 * b + a] = acc[k++];
+    }
+  double L[36];
+  for (int i = 0; i < 36; ++i) L[i] = 0.0;
+  bool pd = acc[27] >= 3.0;
+  for (int i = 0; i < 6 && pd; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = A[6 * i + j];
+      for (int q = 0; q < j; ++q) s -= L[6 * i + q] * L[6 * j + q];
+      if (i == j) {
+        if (!(s > 0.0)) {
+          pd = false;
+          break;
+        }
+        L[6 * i + i] = sqrt(s);
+      } else {
+        L[6 * i + j] = s / L[6 * j + j];
+      }
+    }
+  if (!pd) {
+    st->active = 0;
+    return;
+  }
+  double y[6], d[6];
+  for (int i = 0; i < 6; ++i) {
+    double s = -acc[21 + i];
+    for (int q = 0; q < i; ++q) s -= L[6 * i + q] * y[q];
+    y[i] = s / L[6 * i + i];
+  }
+  for (int i = 5; i >= 0; --i) {
+    double s = y[i];
+    for (int q = i + 1; q < 6; ++q) s -= L[6 * q + i] * d[q];
+    d[i] = s / L[6 * i + i];
+  }
+  double Rd[9];
+  exp_so3(d, Rd);
+  const double *c = st->center;
+  double v[3];
+  for (int r = 0; r < 3; ++r) v[r] = c[r] - (Rd[3 * r] * c[0] + Rd[3 * r + 1] * c[1] + Rd[3 * r + 2] * c[2]) + d[3 + r];
+  double M[16] = {Rd[0], Rd[1], Rd[2], v[0], Rd[3], Rd[4], Rd[5], v[1], Rd[6], Rd[7], Rd[8], v[2], 0, 0, 0, 1};
+  double Tn[16];
+  for (int r = 0; r < 4; ++r)
+    for (int q = 0; q < 4; ++q) {
+      double s = 0.0;
+      for (int m = 0; m < 4; ++m) s += M[4 * r + m] * st->T[4 * m + q];
+      Tn[4 * r + q] = s;
+    }
+  for (int i = 0; i < 16; ++i) st->T[i] = Tn[i];
+  double nd = 0.0;
+  for (int i = 0; i < 6; ++i) nd += d[i] * d[i];
+  nd = sqrt(nd);
+  st->last_step = nd;
+  st->iters_done += 1;
+  st->level_iters += 1;
+  if (nd < tol || st->level_iters >= max_iters) st->active = 0;
+}
+
+__global__ void k_refine_level_begin(RansacState *st) {
+  if (threadIdx.x == 0) {
+    st->active = st->status == 0 ? 1 : 0;
+    st->level_iters = 0;
+  }
+}
+
+__global__ void k_subsample(const float *xyz, int n, int stride, float4 *out) {
+  int m_n = (n + stride - 1) / stride;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < m_n; m += gridDim.x * blockDim.x) {
+    int i = m * stride;
+    out[m] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], __int_as_float(m));
+  }
+}
+
+__global__ void k_refine_init(RansacState *st, const float *boxQ, const double *T_in) {
+  if (threadIdx.x != 0) return;
+  for (int d = 0; d < 3; ++d) st->center[d] = 0.5 * ((double)boxQ[d] + (double)boxQ[3 + d]);
+  if (T_in) {
+    for (int i = 0; i < 16; ++i) st->T[i] = st->T_hyp[i] = T_in[i];
+    st->active = 1;
+    st->status = 0;
+    st->iters_done = 0;
+  }
+}
+
+__global__ void k_final_pose(const RansacState *st, float *pose) {
+  if (threadIdx.x < 12) {
+    int r = threadIdx.x / 4, c = threadIdx.x % 4;
+    pose[threadIdx.x] = (float)st->T[4 * r + c];
+  }
+}
+
+__global__ void k_final_count(const int *count, const unsigned long long *sum, RansacState *st) {
+  if (threadIdx.x == 0) {
+    st->final_count = count[0];
+    st->final_sumd2 = (double)sum[0] / kFixScale;
+  }
+}
+
+// ---------------------------------------------------------------- objective
+// E = sum_i rho(s_i) - rho(eps^2) over points with an NN closer than eps.
+// Forward and backward share this kernel; the backward also writes
+// dP_i = 2 rho'(s) R^T r_i, scatters dQ_j -= 2 rho'(s) r_i, and reduces
+// g_v = sum 2 rho' r_i and g_w = sum z_i x (2 rho' r_i) with z_i = x_i - v.
+// dxi = (J_l(w)^T g_w, g_v) is finished on the host.
+struct ObjArgs {
+  float R[9], t[3], v[3];
+  float eps2, mu, rho_eps, scale;
+};
+
+__global__ void __launch_bounds__(kRefThreads) k_objective(const float *__restrict__ P, int nP, const GridParams *gep,
+                                                           const int *__restrict__ start,
+                                                           const float4 *__restrict__ Xe, ObjArgs a, int want_grad,
+                                                           double *partials, float *__restrict__ dP,
+                                                           float *__restrict__ dQ) {
+  const GridParams g = *gep;
+  float acc[7] = {0, 0, 0, 0, 0, 0, 0};  // E, g_v (3), g_w (3)
+  for (int i = blockIdx.x * kRefThreads + threadIdx.x; i < nP; i += gridDim.x * kRefThreads) {
+    float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+    float x = fmaf(a.R[0], px, fmaf(a.R[1], py, fmaf(a.R[2], pz, a.t[0])));
+    float y = fmaf(a.R[3], px, fmaf(a.R[4], py, fmaf(a.R[5], pz, a.t[1])));
+    float z = fmaf(a.R[6], px, fmaf(a.R[7], py, fmaf(a.R[8], pz, a.t[2])));
+    float best;
+    int bt;
+    nn_within(g, start, Xe, x, y, z, a.eps2, best, bt);
+    if (bt < 0) {
+      if (want_grad) dP[3 * i] = dP[3 * i + 1] = dP[3 * i + 2] = 0.f;
+      continue;
+    }
+    float4 q = Xe[bt];
+    float r0 = x - q.x, r1 = y - q.y, r2 = z - q.z;
+    float s = r0 * r0 + r1 * r1 + r2 * r2;
+    float den = a.mu + s;
+    acc[0] += a.mu * s / den - a.rho_eps;
+    if (want_grad) {
+      float k2 = 2.f * a.mu * a.mu / (den * den);
+      float g0 = k2 * r0, g1 = k2 * r1, g2 = k2 * r2;
+      dP[3 * i + 0] = a.scale * (a.R[0] * g0 + a.R[3] * g1 + a.R[6] * g2);
+      dP[3 * i + 1] = a.scale * (a.R[1] * g0 + a.R[4] * g1 + a.R[7] * g2);
+      dP[3 * i + 2] = a.scale * (a.R[2] * g0 + a.R[5] * g1 + a.R[8] * g2);
+      int j = __float_as_int(q.w);
+      atomicAdd(&dQ[3 * j + 0], -a.scale * g0);
+      atomicAdd(&dQ[3 * j + 1], -a.scale * g1);
+      atomicAdd(&dQ[3 * j + 2], -a.scale * g2);
+      float zx = x - a.v[0], zy = y - a.v[1], zz = z - a.v[2];
+      acc[1] += g0, acc[2] += g1, acc[3] += g2;
+      acc[4] += zy * g2 - zz * g1;
+      acc[5] += zz * g0 - zx * g2;
+      acc[6] += zx * g1 - zy * g0;
+    }
+  }
+  block_reduce_to<7>(acc, partials + (size_t)blockIdx.x * 7);
+}
+
+__global__ void k_objective_sum(const double *partials, int nblocks, double *out) {
+  if (threadIdx.x < 7) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * 7 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+}  // namespace
+
+int refine_blocks(int nP) {
+  int b = (int)lsr_div_up(nP > 0 ? nP : 1, kRefThreads * 4);
+  return b < 1 ? 1 : (b > 152 * 4 ? 152 * 4 : b);
+}
+
+cudaError_t launch_refine_init(RansacState *st, const float *boxQ, const double *T_in, cudaStream_t s) {
+  k_refine_init<<<1, 32, 0, s>>>(st, boxQ, T_in);
+  return cudaGetLastError();
+}
+
+int gnc_stride(int64_t n, int level, int levels) {
+  int64_t f = 1;
+  for (int k = 0; k < levels - 1 - level; ++k) f *= 4;
+  int64_t cap = n / 4096;
+  if (f > cap) f = cap;
+  return (int)(f < 1 ? 1 : f);
+}
+
+cudaError_t launch_refine_level_begin(RansacState *st, cudaStream_t s) {
+  k_refine_level_begin<<<1, 32, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subsample(const float *xyz, int n, int stride, float4 *out, cudaStream_t s) {
+  int m = (n + stride - 1) / stride;
+  int b = (int)lsr_div_up(m > 0 ? m : 1, 256);
+  k_subsample<<<b < 4096 ? b : 4096, 256, 0, s>>>(xyz, n, stride, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_step(const float4 *XP, int nP, int strideP, const GridParams *ge, const int *start_e,
+                               const float4 *Xe, float eps_r, float mu, int max_iters, RansacState *st,
+                               double *partials, cudaStream_t s) {
+  int nb = refine_blocks(nP);
+  k_refine_accum<<<nb, kRefThreads, 0, s>>>(XP, nP, strideP, ge, start_e, Xe, eps_r * eps_r, mu, st, partials);
+  k_refine_solve<<<1, 32, 0, s>>>(partials, nb, st, max_iters, 1e-7);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final_pose(RansacState *st, float *pose, cudaStream_t s) {
+  k_final_pose<<<1, 32, 0, s>>>(st, pose);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final_count(const int *count, const unsigned long long *sum, RansacState *st, cudaStream_t s) {
+  k_final_count<<<1, 32, 0, s>>>(count, sum, st);
+  return cudaGetLastError();
+}
+
+int objective_blocks(int nP) { return refine_blocks(nP); }
+
+cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
+                             const float R[9], const float t[3], const float v[3], float eps, float mu, float scale,
+                             int want_grad, double *partials, double *out7, float *dP, float *dQ, cudaStream_t s) {
+  ObjArgs a;
+  for (int k = 0; k < 9; ++k) a.R[k] = R[k];
+  for (int k = 0; k < 3; ++k) a.t[k] = t[k], a.v[k] = v[k];
+  a.eps2 = eps * eps;
+  a.mu = mu;
+  a.rho_eps = mu * a.eps2 / (mu + a.eps2);
+  a.scale = scale;
+  int nb = objective_blocks(nP);
+  k_objective<<<nb, kRefThreads, 0, s>>>(P, nP, ge, start_e, Xe, a, want_grad, partials, dP, dQ);
+  k_objective_sum<<<1, 32, 0, s>>>(partials, nb, out7);
+  return cudaGetLastError();
+}
+
+}  // namespace lsr

@@ -174,22 +174,66 @@ def _objects_scene(rng):
     return prims, vp
 
 
+class _Occluded:
+    """A primitive with the points inside some vertical footprints removed (floor
+    under furniture is not seen by the camera)."""
+
+    def __init__(self, prim, footprints):
+        self.prim, self.fp = prim, footprints
+        self.area = prim.area
+
+    def _keep(self, X):
+        keep = np.ones(len(X), bool)
+        for (cx, cy, R, hx, hy, r) in self.fp:
+            d = X[:, :2] - [cx, cy]
+            if r > 0:
+                keep &= (d ** 2).sum(1) > r * r
+            else:
+                u = d @ R[:2, 0]
+                v = d @ R[:2, 1]
+                keep &= ~((np.abs(u) < hx) & (np.abs(v) < hy))
+        return X[keep]
+
+    def random(self, n, rng):
+        return self._keep(self.prim.random(n, rng))
+
+    def lattice(self, s, rng):
+        return self._keep(self.prim.lattice(s, rng))
+
+
 def _room_scene(rng, W=4.0, D=3.5, H=2.4, n_obj=20):
-    """Floor, four walls and n_obj boxes / cylinders standing on the floor."""
-    prims = [_Rect([W / 2, D / 2, 0.0], [1, 0, 0], [0, 1, 0], W / 2, D / 2),
-             _Rect([W / 2, 0.0, H / 2], [1, 0, 0], [0, 0, 1], W / 2, H / 2),
+    """Floor, four walls and n_obj boxes / cylinders: cabinets and shelves
+    against the walls, tables and stands in the room; the floor under them is
+    hidden. Room size varies by up to 15% per pair."""
+    W *= rng.uniform(0.85, 1.15)
+    D *= rng.uniform(0.85, 1.15)
+    walls = [_Rect([W / 2, 0.0, H / 2], [1, 0, 0], [0, 0, 1], W / 2, H / 2),
              _Rect([W / 2, D, H / 2], [1, 0, 0], [0, 0, 1], W / 2, H / 2),
              _Rect([0.0, D / 2, H / 2], [0, 1, 0], [0, 0, 1], D / 2, H / 2),
              _Rect([W, D / 2, H / 2], [0, 1, 0], [0, 0, 1], D / 2, H / 2)]
+    prims, foot = list(walls), []
     for k in range(n_obj):
-        x, y = rng.uniform(0.4, W - 0.4), rng.uniform(0.4, D - 0.4)
         if k % 2 == 0:
-            yaw = rng.uniform(0, 2 * np.pi)
+            half = np.array([rng.uniform(0.15, 0.5), rng.uniform(0.12, 0.3), rng.uniform(0.15, 0.9)])
+            if k % 4 == 0:
+                # against a wall (cabinet, shelf), possibly raised off the floor
+                side = int(rng.integers(4))
+                along = rng.uniform(0.3, (W if side < 2 else D) - 0.3)
+                yaw = [0.0, np.pi, np.pi / 2, -np.pi / 2][side]
+                x, y = [(along, half[1]), (along, D - half[1]), (half[1], along), (W - half[1], along)][side]
+                z = half[2] if rng.uniform() < 0.6 else rng.uniform(0.8, 1.6)
+            else:
+                yaw = rng.uniform(0, 2 * np.pi)
+                x, y, z = rng.uniform(0.5, W - 0.5), rng.uniform(0.5, D - 0.5), half[2]
             R = np.array([[np.cos(yaw), -np.sin(yaw), 0], [np.sin(yaw), np.cos(yaw), 0], [0, 0, 1.0]])
-            half = np.array([rng.uniform(0.1, 0.4), rng.uniform(0.1, 0.4), rng.uniform(0.1, 0.5)])
-            prims.extend(_box_faces(np.array([x, y, half[2]]), R, half, bottom=False))
+            prims.extend(_box_faces(np.array([x, y, z]), R, half, bottom=z > half[2] + 1e-9))
+            if z <= half[2] + 1e-9:
+                foot.append((x, y, R, half[0], half[1], 0.0))
         else:
-            prims.append(_Cylinder([x, y, 0.0], rng.uniform(0.08, 0.3), rng.uniform(0.2, 1.2)))
+            x, y, r = rng.uniform(0.4, W - 0.4), rng.uniform(0.4, D - 0.4), rng.uniform(0.08, 0.3)
+            prims.append(_Cylinder([x, y, 0.0], r, rng.uniform(0.2, 1.2)))
+            foot.append((x, y, None, 0.0, 0.0, r))
+    prims.insert(0, _Occluded(_Rect([W / 2, D / 2, 0.0], [1, 0, 0], [0, 1, 0], W / 2, D / 2), foot))
     vp = np.array([W / 2, D / 2, 1.2])
     return prims, vp
 
@@ -243,7 +287,9 @@ def _objects_pair(rng, n_p, n_q, sigma, overlap, outliers):
 def _room_pair(rng, n_p, n_q, sigma, overlap, grid=0.01):
     prims, vp = _room_scene(rng)
     T = random_pose(rng)
-    ang = rng.uniform(0, 2 * np.pi)
+    # sweep direction oblique to the walls (a sweep along a wall would leave the
+    # fragments free to slide along it)
+    ang = int(rng.integers(4)) * (np.pi / 2) + np.deg2rad(rng.uniform(25.0, 65.0))
     d = np.array([np.cos(ang), np.sin(ang), 0.0])
     LP = _lattice(prims, grid, rng)           # P's own lattice (world frame)
     LQ = _lattice(prims, grid, rng)           # Q's independent lattice

@@ -481,3 +481,51 @@ def test_prerejection_edges_are_the_cyclic_sides(orc):
         assert flag[h] == (1 if walk else 0), (h, i)
         n_ok += walk
     assert n_ok > 0
+
+
+# ------------------------------------------------------------------ graduated refinement
+def test_gnc_stride_definition(orc):
+    assert [orc.gnc_stride(5000, l, 4) for l in range(4)] == [1, 1, 1, 1]
+    assert [orc.gnc_stride(150_000, l, 4) for l in range(4)] == [36, 16, 4, 1]
+    assert [orc.gnc_stride(10 ** 6, l, 4) for l in range(4)] == [64, 16, 4, 1]
+    assert orc.gnc_stride(10 ** 6, 0, 1) == 1
+
+
+def test_gnc_one_level_is_plain_refinement(orc):
+    fp = make_pair(0)
+    T0 = fp.T.copy()
+    T0[:3, 3] += [0.01, -0.005, 0.004]
+    a, _ = orc.refine(fp.P, fp.Q, T0, 0.0375, 0.0375 ** 2, iters=50)
+    b, _ = orc.refine_gnc(fp.P, fp.Q, T0, 0.0375, 1.0, levels=1, iters=50)
+    assert np.array_equal(a, b)
+
+
+def test_gnc_result_independent_of_start(orc):
+    """Starts up to ~1 deg / 2 cm apart (the spread of near-best hypotheses)
+    reach the same pose, which single-level refinement does not guarantee."""
+    fp = make_pair(0, 0, n_p=3000, n_q=3000)
+    rng = np.random.default_rng(20)
+    outs = []
+    for _ in range(4):
+        d = np.eye(4)
+        d[:3, :3] = Rotation.from_rotvec(rng.normal(0, 0.01, 3)).as_matrix()
+        d[:3, 3] = rng.normal(0, 0.01, 3)
+        T, _ = orc.refine_gnc(fp.P, fp.Q, d @ fp.T, 0.0375, 1.0, levels=4, iters=100, tol=1e-12)
+        outs.append(T)
+    for T in outs[1:]:
+        ang, tr = pose_error(T, outs[0])
+        assert ang < 1e-6 and tr < 1e-8
+    ang, tr = pose_error(outs[0], fp.T)
+    assert ang < 0.5 and tr < 0.005
+
+
+def test_gnc_recovers_noiseless_pose(orc):
+    fp = make_pair(0)
+    P = fp.P.astype(np.float64)
+    Q = P @ fp.T[:3, :3].T + fp.T[:3, 3]
+    d = np.eye(4)
+    d[:3, :3] = Rotation.from_rotvec([0.02, 0.01, -0.015]).as_matrix()
+    d[:3, 3] = [0.02, -0.01, 0.01]
+    T, _ = orc.refine_gnc(P, Q, d @ fp.T, 0.0375, 1.0, levels=4, iters=100)
+    ang, tr = pose_error(T, fp.T)
+    assert ang < 1e-7 and tr < 1e-9
