@@ -80,7 +80,7 @@ typedef struct {
   uint64_t seed;          /* hypothesis RNG key word 0 (Philox-4x64-10 key = (seed, pair_id)) */
   uint64_t pair_id;       /* RNG key word 1 for lsr_register_pair; a batch uses pair_id + i */
   int32_t match_precision; /* LSR_MATCH_FP32 (default) or LSR_MATCH_BF16 */
-  int32_t refine_levels;  /* graduated refinement levels L (1..8), default 4: radius eps * 2^(L-1-l) at level l */
+  int32_t refine_levels;  /* graduated refinement levels L (1..8), default 3: radius eps * 2^(L-1-l) at level l */
   int32_t reserved_[4];
 } lsr_params;
 

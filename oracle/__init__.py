@@ -57,7 +57,7 @@ class Result(C.Structure):
 
 DEFAULTS = dict(r_normal=0.05, r_feature=0.125, eps_inlier=0.0375, tau=0.9,
                 cos_normal=float(np.cos(np.deg2rad(30.0))), min_inlier_ratio=0.05, mu_scale=1.0,
-                n_hypotheses=4_000_000, refine_iters=50, refine_levels=4, seed=0, pair_id=0)
+                n_hypotheses=4_000_000, refine_iters=50, refine_levels=3, seed=0, pair_id=0)
 
 
 def _P(a, dt):
@@ -290,7 +290,7 @@ def refine(P, Q, T, eps_r, mu, iters=30, tol=1e-10):
     return out.reshape(4, 4), int(n)
 
 
-def refine_gnc(P, Q, T, eps, mu_scale=1.0, levels=4, iters=50, tol=1e-10):
+def refine_gnc(P, Q, T, eps, mu_scale=1.0, levels=3, iters=50, tol=1e-10):
     """Graduated refinement: radii eps * 2^(L-1-l), subsets by caller index."""
     P, Q = _f64(P, 3), _f64(Q, 3)
     T = _f64(T).reshape(16)

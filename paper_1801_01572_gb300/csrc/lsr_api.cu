@@ -60,7 +60,7 @@ struct CloudLayout {
   int n = 0, cap_f = 0, cap_n = 0, cap_e = 0;
   float *src = nullptr;  // staged copy of host input (or null)
   float *box = nullptr;  // 8 floats: bbox (6) + non-finite flag + pad
-  float *box_part = nullptr;
+  double *box_part = nullptr;
   GridParams *gf = nullptr, *gn = nullptr, *ge = nullptr;
   int *start_f = nullptr, *start_n = nullptr, *start_e = nullptr;
   float4 *X = nullptr, *Xn = nullptr, *Xe = nullptr, *N = nullptr;
@@ -79,8 +79,8 @@ void plan_cloud(Arena &a, int n, bool stage_src, bool features, bool eps_grid, C
   c.cap_n = cap_cells_for(n);
   c.cap_e = cap_cells_for(n);
   c.src = stage_src ? a.take<float>((size_t)3 * n) : nullptr;
-  c.box = a.take<float>(8);
-  c.box_part = a.take<float>((size_t)7 * bbox_blocks(n));
+  c.box = a.take<float>(kBox);
+  c.box_part = a.take<double>((size_t)kBoxPart * bbox_blocks(n));
   c.gf = a.take<GridParams>(1);
   c.gn = a.take<GridParams>(1);
   c.ge = a.take<GridParams>(1);
@@ -114,13 +114,19 @@ void plan_scratch(Arena &a, int n_max, int cap_max, ScratchLayout &s) {
 struct LevelLayout {
   int levels = 0;
   int sQ[kMaxLevels] = {}, nsub[kMaxLevels] = {}, cap[kMaxLevels] = {};
-  float4 *Qsub[kMaxLevels] = {}, *Xs[kMaxLevels] = {};
+  int sP[kMaxLevels] = {}, nsubP[kMaxLevels] = {};
+  float4 *Qsub[kMaxLevels] = {}, *Xs[kMaxLevels] = {}, *Psub[kMaxLevels] = {};
   int *start[kMaxLevels] = {};
   GridParams *g[kMaxLevels] = {};
 };
 
-void plan_levels(Arena &a, int nQ, int levels, LevelLayout &V) {
+void plan_levels(Arena &a, int nP, int nQ, int levels, LevelLayout &V) {
   V.levels = levels;
+  for (int l = 0; l < levels; ++l) {
+    V.sP[l] = gnc_stride(nP, l, levels);
+    V.nsubP[l] = (int)lsr_div_up(nP, V.sP[l]);
+    if (V.sP[l] > 1) V.Psub[l] = a.take<float4>(V.nsubP[l]);
+  }
   for (int l = 0; l + 1 < levels; ++l) {
     V.sQ[l] = gnc_stride(nQ, l, levels);
     V.nsub[l] = (int)lsr_div_up(nQ, V.sQ[l]);
@@ -158,7 +164,7 @@ int surv_cap_for(int64_t H) { return (int)std::min<int64_t>(H, (int64_t)1 << 22)
 void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int levels, PairLayout &L) {
   plan_cloud(a, nP, stP, true, false, L.P);
   plan_cloud(a, nQ, stQ, true, true, L.Q);
-  plan_levels(a, nQ, levels, L.lv);
+  plan_levels(a, nP, nQ, levels, L.lv);
   plan_scratch(a, std::max(nP, nQ), std::max(L.P.cap_f, L.Q.cap_f), L.sc);
   L.nn = a.take<int>(nP);
   L.d1 = a.take<float>(nP);
@@ -239,7 +245,7 @@ int ensure_host_slots(lsr_ctx *c, int n) {
   c->box_host = nullptr;
   c->st_host_cap = 0;
   if (cudaMallocHost(&c->st_host, sizeof(RansacState) * n) != cudaSuccess ||
-      cudaMallocHost(&c->box_host, sizeof(float) * 16 * n) != cudaSuccess) {
+      cudaMallocHost(&c->box_host, sizeof(float) * 2 * kBox * n) != cudaSuccess) {
     cudaGetLastError();
     return set_err(c, LSR_E_OOM, "pinned host allocation failed");
   }
@@ -338,14 +344,21 @@ cudaError_t build_cloud(const float *xyz, CloudLayout &c, float r_f, float r_n, 
 // Graduated refinement (levels l = 0..L-1, radius eps * 2^(L-1-l)) from the
 // pose in st. XP: P in internal order with caller indices in w; Q: caller-order
 // xyz on the device; (ge, start_e, Xe): Q's eps grid for the finest level.
-cudaError_t enqueue_refine(const float4 *XP, int nP, const float *Q, int nQ, const float *boxQ, const GridParams *ge,
-                           const int *start_e, const float4 *Xe, const LevelLayout &V, float eps, float mu_scale,
-                           int iters, RansacState *st, double *part, const ScratchLayout &sc, cudaStream_t s) {
+cudaError_t enqueue_refine(const float4 *XP, const float *P, int nP, const float *Q, int nQ, const float *boxQ,
+                           const GridParams *ge, const int *start_e, const float4 *Xe, const LevelLayout &V, float eps,
+                           float mu_scale, int iters, RansacState *st, double *part, const ScratchLayout &sc,
+                           cudaStream_t s) {
   int L = V.levels;
   for (int l = 0; l < L; ++l) {
     float e = eps * (float)(1 << (L - 1 - l));
     float mu = mu_scale * e * e;
-    int sP = gnc_stride(nP, l, L);
+    // P at this level: every sP-th caller point, compacted (or all of X)
+    const float4 *xp = XP;
+    int np = nP;
+    if (V.sP[l] > 1) {
+      LSR_CUDA_TRY(launch_subsample(P, nP, V.sP[l], V.Psub[l], s));
+      xp = V.Psub[l], np = V.nsubP[l];
+    }
     const GridParams *g = ge;
     const int *st0 = start_e;
     const float4 *xs = Xe;
@@ -357,7 +370,7 @@ cudaError_t enqueue_refine(const float4 *XP, int nP, const float *Q, int nQ, con
     }
     LSR_CUDA_TRY(launch_refine_level_begin(st, s));
     for (int it = 0; it < iters; ++it)
-      LSR_CUDA_TRY(launch_refine_step(XP, nP, sP, g, st0, xs, e, mu, iters, st, part, s));
+      LSR_CUDA_TRY(launch_refine_step(xp, np, 1, g, st0, xs, e, mu, iters, st, part, s));
   }
   return cudaSuccess;
 }
@@ -411,10 +424,10 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
            "consensus");
   tm.mark();
   TRY_CUDA(c, launch_select(L.surv, L.count, L.sum, L.ok, L.pose, nP, p.min_inlier_ratio, L.st, s), "select");
-  TRY_CUDA(c, launch_refine_init(L.st, Qc.box, nullptr, s), "refine init");
+  TRY_CUDA(c, launch_refine_init(L.st, Pc.box, nullptr, s), "refine init");
   float eps = p.eps_inlier;
   TRY_CUDA(c,
-           enqueue_refine(Pc.X, nP, Q, nQ, Qc.box, Qc.ge, Qc.start_e, Qc.Xe, L.lv, eps, p.mu_scale, p.refine_iters,
+           enqueue_refine(Pc.X, P, nP, Q, nQ, Qc.box, Qc.ge, Qc.start_e, Qc.Xe, L.lv, eps, p.mu_scale, p.refine_iters,
                           L.st, L.ref_part, L.sc, s),
            "refine");
   TRY_CUDA(c, launch_final_pose(L.st, L.fpose, s), "final pose");
@@ -491,7 +504,7 @@ void lsr_default_params(lsr_params *p) {
   p->min_inlier_ratio = 0.05f;
   p->mu_scale = 1.0f;
   p->refine_iters = 50;
-  p->refine_levels = 4;
+  p->refine_levels = 3;
   p->n_hypotheses = 4000000;
   p->seed = 0;
   p->pair_id = 0;
@@ -625,19 +638,19 @@ static int register_many(lsr_ctx *c, int32_t n, const float *const *P, const int
     if ((rc = enqueue_pair(c, L, dP, dQ, vp ? vp + 6 * i : nullptr, vp ? vp + 6 * i + 3 : nullptr, pair0 + i, t)))
       return rc;
     TRY_CUDA(c, cudaMemcpyAsync(&c->st_host[i], L.st, sizeof(RansacState), cudaMemcpyDeviceToHost, c->stream), "D2H");
-    TRY_CUDA(c, cudaMemcpyAsync(&c->box_host[16 * i], L.P.box, sizeof(float) * 8, cudaMemcpyDeviceToHost, c->stream),
+    TRY_CUDA(c, cudaMemcpyAsync(&c->box_host[2 * kBox * i], L.P.box, sizeof(float) * kBox, cudaMemcpyDeviceToHost, c->stream),
              "D2H");
-    TRY_CUDA(c, cudaMemcpyAsync(&c->box_host[16 * i + 8], L.Q.box, sizeof(float) * 8, cudaMemcpyDeviceToHost, c->stream),
+    TRY_CUDA(c, cudaMemcpyAsync(&c->box_host[2 * kBox * i + kBox], L.Q.box, sizeof(float) * kBox, cudaMemcpyDeviceToHost, c->stream),
              "D2H");
   }
   TRY_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
   TRY_CUDA(c, cudaGetLastError(), "kernel");
   for (int i = 0; i < n; ++i) {
-    if (c->box_host[16 * i + 6] != 0.f || c->box_host[16 * i + 14] != 0.f)
+    if (c->box_host[2 * kBox * i + 6] != 0.f || c->box_host[2 * kBox * i + kBox + 6] != 0.f)
       return set_err(c, LSR_E_ARG, "non-finite input coordinates");
-    fill_result(c->st_host[i], &c->box_host[16 * i], &c->box_host[16 * i + 8], &out[i]);
+    fill_result(c->st_host[i], &c->box_host[2 * kBox * i], &c->box_host[2 * kBox * i + kBox], &out[i]);
   }
-  if (n == 1 && c->profiling && tm.k == 9) {
+  if (n == 1 && c->profiling && tm.k == 8) {  // 8 marks bound the 7 stages
     float tot = 0.f;
     for (int k = 0; k < 7; ++k) {
       float ms = 0.f;
@@ -958,12 +971,16 @@ int lsr_stage_refine(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int
       iters > 10000 || levels < 1 || levels > kMaxLevels || !(eps > 0.f && eps * (float)(1 << (levels - 1)) <= 10.f) ||
       !(mu_scale > 0.f))
     return set_err(c, LSR_E_ARG, "bad argument");
+  float *boxP = nullptr;
+  double *boxP_part = nullptr;
   auto plan = [&](Arena &a, float *&p, float4 *&XP, CloudLayout &Cq, LevelLayout &V, ScratchLayout &S, double *&part,
                   double *&Td, RansacState *&st) {
     p = a.take<float>(3 * nP);
     XP = a.take<float4>(nP);
+    boxP = a.take<float>(kBox);
+    boxP_part = a.take<double>((size_t)kBoxPart * bbox_blocks((int)nP));
     plan_cloud(a, (int)nQ, true, false, true, Cq);
-    plan_levels(a, (int)nQ, levels, V);
+    plan_levels(a, (int)nP, (int)nQ, levels, V);
     plan_scratch(a, (int)nQ, Cq.cap_f, S);
     part = a.take<double>((size_t)kRefAcc * refine_blocks((int)nP));
     Td = a.take<double>(16);
@@ -995,10 +1012,11 @@ int lsr_stage_refine(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int
   TRY_CUDA(c, cudaMemcpyAsync(Td, T_in, sizeof(double) * 16, cudaMemcpyDefault, s), "copy T");
   TRY_CUDA(c, cudaMemsetAsync(st, 0, sizeof(RansacState), s), "memset");
   k_pack<<<nblk(nP), 256, 0, s>>>(p, (int)nP, XP);
+  TRY_CUDA(c, launch_bbox_xyz(p, (int)nP, boxP_part, bbox_blocks((int)nP), boxP, s), "bbox P");
   TRY_CUDA(c, build_cloud(qsrc, Cq, eps, eps, eps, false, true, S, s), "grid Q");
-  TRY_CUDA(c, launch_refine_init(st, Cq.box, Td, s), "init");
+  TRY_CUDA(c, launch_refine_init(st, boxP, Td, s), "init");
   TRY_CUDA(c,
-           enqueue_refine(XP, (int)nP, qsrc, (int)nQ, Cq.box, Cq.ge, Cq.start_e, Cq.Xe, V, eps, mu_scale, iters, st,
+           enqueue_refine(XP, p, (int)nP, qsrc, (int)nQ, Cq.box, Cq.ge, Cq.start_e, Cq.Xe, V, eps, mu_scale, iters, st,
                           part, S, s),
            "refine");
   RansacState h;

@@ -21,10 +21,13 @@ __device__ __forceinline__ float3 load_xyz(const float *xyz, int i) {
   return make_float3(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]);
 }
 
+// Per block: min (3), max (3), non-finite flag, count and coordinate sums (3)
+// of the finite points, as kBoxPart doubles.
 template <bool kF4>
-__global__ void __launch_bounds__(kBoxThreads) k_bbox_partial(const void *src, int n, float *partials) {
+__global__ void __launch_bounds__(kBoxThreads) k_bbox_partial(const void *src, int n, double *partials) {
   float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-  float bad = 0.f;
+  float bad = 0.f, cnt = 0.f;
+  float sum[3] = {0.f, 0.f, 0.f};
   int base = blockIdx.x * kBoxThreads * kBoxItems;
   for (int k = 0; k < kBoxItems; ++k) {
     int i = base + k * kBoxThreads + threadIdx.x;
@@ -42,52 +45,70 @@ __global__ void __launch_bounds__(kBoxThreads) k_bbox_partial(const void *src, i
     }
     lo[0] = fminf(lo[0], p.x), lo[1] = fminf(lo[1], p.y), lo[2] = fminf(lo[2], p.z);
     hi[0] = fmaxf(hi[0], p.x), hi[1] = fmaxf(hi[1], p.y), hi[2] = fmaxf(hi[2], p.z);
+    sum[0] += p.x, sum[1] += p.y, sum[2] += p.z;
+    cnt += 1.f;
   }
   for (int off = 16; off > 0; off >>= 1) {
     for (int d = 0; d < 3; ++d) {
       lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
       hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], off));
+      sum[d] += __shfl_xor_sync(0xffffffffu, sum[d], off);
     }
     bad = fmaxf(bad, __shfl_xor_sync(0xffffffffu, bad, off));
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
   }
-  __shared__ float sm[kBoxThreads / 32][7];
+  __shared__ float sm[kBoxThreads / 32][kBoxPart];
   int w = threadIdx.x / 32, l = threadIdx.x % 32;
   if (l == 0) {
-    for (int d = 0; d < 3; ++d) sm[w][d] = lo[d], sm[w][3 + d] = hi[d];
+    for (int d = 0; d < 3; ++d) sm[w][d] = lo[d], sm[w][3 + d] = hi[d], sm[w][8 + d] = sum[d];
     sm[w][6] = bad;
+    sm[w][7] = cnt;
   }
   __syncthreads();
-  if (threadIdx.x < 7) {
-    float v = sm[0][threadIdx.x];
+  if (threadIdx.x < kBoxPart) {
+    int t = threadIdx.x;
+    double v = sm[0][t];
     for (int k = 1; k < kBoxThreads / 32; ++k) {
-      float u = sm[k][threadIdx.x];
-      v = threadIdx.x < 3 ? fminf(v, u) : fmaxf(v, u);
+      double u = sm[k][t];
+      v = t < 3 ? fmin(v, u) : (t < 7 ? fmax(v, u) : v + u);
     }
-    partials[7 * blockIdx.x + threadIdx.x] = v;
+    partials[(size_t)kBoxPart * blockIdx.x + t] = v;
   }
 }
 
-__global__ void k_bbox_final(const float *partials, int nblk, float *box) {
-  // one warp; fixed reduction order
+// box: min (3), max (3), non-finite flag, number of finite points, centroid (3).
+__global__ void k_bbox_final(const double *partials, int nblk, float *box) {
+  __shared__ double acc[kBoxPart];
   int t = threadIdx.x;
-  if (t < 7) {
-    float v = partials[t];
+  if (t < kBoxPart) {
+    double v = partials[t];
     for (int b = 1; b < nblk; ++b) {
-      float u = partials[7 * b + t];
-      v = t < 3 ? fminf(v, u) : fmaxf(v, u);
+      double u = partials[(size_t)kBoxPart * b + t];
+      v = t < 3 ? fmin(v, u) : (t < 7 ? fmax(v, u) : v + u);
     }
-    box[t] = v;  // box[6] = non-finite flag
+    acc[t] = v;
   }
+  __syncthreads();
+  if (t < 8) box[t] = (float)acc[t];
+  if (t >= 8 && t < 11) box[t] = acc[7] > 0.0 ? (float)(acc[t] / acc[7]) : 0.f;
+  if (t == 11) box[t] = 0.f;
 }
 
 __global__ void k_grid_params(const float *box, float radius, int npts, int cap, GridParams *g) {
   if (threadIdx.x != 0) return;
   GridParams q;
-  float cell = radius * 1.0001f;
+  float ext[3] = {box[3] - box[0], box[4] - box[1], box[5] - box[2]};
+  // Cell coordinates (x - origin) / cell are computed in FP32 with a relative
+  // error of a few units of 2^-24 of the box extent; the cell is enlarged by
+  // that margin (at least 1e-4) so that two points within the radius never
+  // land more than one cell apart.
+  float emax = fmaxf(fmaxf(ext[0], ext[1]), ext[2]);
+  if (!(emax >= 0.f) || !isfinite(emax)) emax = 0.f;
+  float delta = fmaxf(1e-4f, 8.f * 5.9604645e-8f * emax / radius);
+  float cell = radius * (1.f + delta);
   q.cell = cell;
   q.inv_cell = 1.0f / cell;
   q.ox = box[0], q.oy = box[1], q.oz = box[2];
-  float ext[3] = {box[3] - box[0], box[4] - box[1], box[5] - box[2]};
   int nn[3];
   for (int d = 0; d < 3; ++d) {
     float e = ext[d] * q.inv_cell;
@@ -276,7 +297,7 @@ inline int grid_blocks(int n, int threads = 256) {
 
 int bbox_blocks(int n) { return (int)lsr_div_up(n > 0 ? n : 1, kBoxThreads * kBoxItems); }
 
-cudaError_t launch_bbox_xyz(const float *xyz, int n, float *partials, int nblk_cap, float *box, cudaStream_t s) {
+cudaError_t launch_bbox_xyz(const float *xyz, int n, double *partials, int nblk_cap, float *box, cudaStream_t s) {
   int nb = bbox_blocks(n);
   if (nb > nblk_cap) return cudaErrorInvalidValue;
   k_bbox_partial<false><<<nb, kBoxThreads, 0, s>>>(xyz, n, partials);
@@ -284,7 +305,7 @@ cudaError_t launch_bbox_xyz(const float *xyz, int n, float *partials, int nblk_c
   return cudaGetLastError();
 }
 
-cudaError_t launch_bbox_f4(const float4 *x, int n, float *partials, int nblk_cap, float *box, cudaStream_t s) {
+cudaError_t launch_bbox_f4(const float4 *x, int n, double *partials, int nblk_cap, float *box, cudaStream_t s) {
   int nb = bbox_blocks(n);
   if (nb > nblk_cap) return cudaErrorInvalidValue;
   k_bbox_partial<true><<<nb, kBoxThreads, 0, s>>>(x, n, partials);

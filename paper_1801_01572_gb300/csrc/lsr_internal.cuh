@@ -17,8 +17,9 @@ constexpr int kWarp = 32;
 // the allocated capacity, the y and z (and if needed x) cell coordinates wrap
 // modulo the stored extents; wrapped cells share storage, which only adds
 // candidates that the exact distance test then rejects. The cell edge is the
-// search radius times (1 + 1e-4), so every point within the radius of a query
-// lies in the 3 x 3 x 3 block of cells around it even after FP32 rounding.
+// search radius times (1 + delta), delta >= 1e-4 growing with the box extent
+// to cover the FP32 rounding of the cell coordinates, so every point within
+// the radius of a query lies in the 3 x 3 x 3 block of cells around it.
 struct GridParams {
   float ox, oy, oz;  // origin (bounding-box minimum)
   float cell, inv_cell;
@@ -107,6 +108,43 @@ __device__ __forceinline__ void grid_ranges(const GridParams &g, const int *__re
   }
 }
 
+// Exact nearest neighbour within sqrt(eps2) of (x, y, z) by a group of G
+// lanes (G divides 32, the group's lanes are consecutive and all query the
+// same point): the lanes walk the concatenated candidate ranges with stride
+// G, so work spreads evenly across range boundaries, then combine (distance,
+// index) minima with shuffles. Ties go to the smaller carried index (w of the
+// grid's sorted points). Every lane returns the group's result; bt = -1 if no
+// point is within the radius.
+template <int G>
+__device__ __forceinline__ void group_nn(const GridParams &g, const int *__restrict__ start,
+                                         const float4 *__restrict__ Xe, float x, float y, float z, float eps2,
+                                         float &best, int &bt, int &bidx) {
+  int sub = threadIdx.x & (G - 1);
+  best = eps2;
+  bt = -1;
+  bidx = 0x7fffffff;
+  int next = sub, base = 0;
+  grid_ranges(g, start, x, y, z, [&](int b, int e) {
+    int len = e - b;
+    for (; next < base + len; next += G) {
+      int t = b + next - base;
+      float4 q = Xe[t];
+      float dx = q.x - x, dy = q.y - y, dz = q.z - z;
+      float d2 = dx * dx + dy * dy + dz * dz;
+      int qi = __float_as_int(q.w);
+      if (d2 < best || (d2 == best && qi < bidx)) best = d2, bt = t, bidx = qi;
+    }
+    base += len;
+  });
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) {
+    float ob = __shfl_xor_sync(0xffffffffu, best, off);
+    int ot = __shfl_xor_sync(0xffffffffu, bt, off);
+    int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+    if (ob < best || (ob == best && oi < bidx)) best = ob, bt = ot, bidx = oi;
+  }
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
@@ -117,10 +155,13 @@ __device__ __forceinline__ int warp_sum(int v) {
 }
 
 // ----------------------------------------------------------------- grid build (lsr_grid.cu)
-// Bounding box of a float32 xyz array (AoS) or a float4 array, reduced into
-// box[6] = (minx, miny, minz, maxx, maxy, maxz) via per-block partials.
-cudaError_t launch_bbox_xyz(const float *xyz, int n, float *partials, int nblk_cap, float *box, cudaStream_t s);
-cudaError_t launch_bbox_f4(const float4 *x, int n, float *partials, int nblk_cap, float *box, cudaStream_t s);
+// Bounding box and centroid of a float32 xyz array (AoS) or a float4 array,
+// reduced through kBoxPart doubles per block into box[kBox] = (min xyz, max
+// xyz, non-finite flag, finite count, centroid xyz, 0).
+constexpr int kBox = 12;
+constexpr int kBoxPart = 11;
+cudaError_t launch_bbox_xyz(const float *xyz, int n, double *partials, int nblk_cap, float *box, cudaStream_t s);
+cudaError_t launch_bbox_f4(const float4 *x, int n, double *partials, int nblk_cap, float *box, cudaStream_t s);
 int bbox_blocks(int n);
 
 // Fill a GridParams from a bounding box on the device.
@@ -171,6 +212,8 @@ struct RansacState {
   int iters_done;
   int final_count;
   int level_iters;     // refinement steps taken at the current level
+  unsigned ticket;     // blocks finished in the current refinement step
+  int pad_;
   double final_sumd2;
   double T[16];        // current pose (refinement), row-major
   double T_hyp[16];
@@ -201,8 +244,10 @@ constexpr double kFixScale = 1099511627776.0;  // 2^40
 
 // ----------------------------------------------------------------- refinement (lsr_refine.cu)
 int refine_blocks(int nP);
-cudaError_t launch_refine_init(RansacState *st, const float *boxQ, const double *T_in, cudaStream_t s);
-constexpr int kRefAcc = 28;  // per-block partial sums of one refinement step
+// Starting pose (T_in, or the selected hypothesis already in st) and the first
+// linearisation centre (the centroid of P, boxP[8..10], moved by that pose).
+cudaError_t launch_refine_init(RansacState *st, const float *boxP, const double *T_in, cudaStream_t s);
+constexpr int kRefAcc = 32;  // per-block partial sums of one refinement step
 constexpr int kMaxLevels = 8;
 // Subsampling stride of graduated refinement level l of L for a cloud of n points.
 int gnc_stride(int64_t n, int level, int levels);

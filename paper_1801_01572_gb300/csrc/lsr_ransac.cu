@@ -298,17 +298,41 @@ __global__ void k_rigid4(const float *ps, const float *qs, int nh, float *pose) 
 // distances are summed in 2^-40 fixed point so the totals do not depend on
 // the order of the atomic adds.
 constexpr int kConsThreads = 256;
-constexpr int kConsChunk = kConsThreads * 8;
+constexpr int kConsChunk = 2048;
+constexpr int kConsG = 8;  // lanes per query
+
+// Minimum squared distance below eps2 by a group of G lanes (no index needed).
+template <int G>
+__device__ __forceinline__ float group_min_d2(const GridParams &g, const int *__restrict__ start,
+                                              const float4 *__restrict__ Xe, float x, float y, float z, float eps2) {
+  int sub = threadIdx.x & (G - 1);
+  float best = eps2;
+  int next = sub, base = 0;
+  grid_ranges(g, start, x, y, z, [&](int b, int e) {
+    int len = e - b;
+    for (; next < base + len; next += G) {
+      float4 q = Xe[b + next - base];
+      float dx = q.x - x, dy = q.y - y, dz = q.z - z;
+      best = fminf(best, dx * dx + dy * dy + dz * dz);
+    }
+    base += len;
+  });
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, off));
+  return best;
+}
 
 __global__ void __launch_bounds__(kConsThreads) k_consensus(const float4 *__restrict__ XP, int nP, const GridParams *gep,
                                                             const int *__restrict__ start,
                                                             const float4 *__restrict__ Xe, const float *__restrict__ pose,
                                                             const uint8_t *__restrict__ ok, const int *n_dev, int n_host,
                                                             float eps2, int *count, unsigned long long *sum) {
+  constexpr int G = kConsG, GPB = kConsThreads / G;
   const GridParams g = *gep;
   int nh = n_dev ? *n_dev : n_host;
   int chunks = (nP + kConsChunk - 1) / kConsChunk;
   int64_t items = (int64_t)nh * chunks;
+  int grp = threadIdx.x / G, sub = threadIdx.x & (G - 1);
   __shared__ int s_cnt[kConsThreads / 32];
   __shared__ unsigned long long s_sum[kConsThreads / 32];
   for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
@@ -319,22 +343,17 @@ __global__ void __launch_bounds__(kConsThreads) k_consensus(const float4 *__rest
           r7 = T[9], r8 = T[10], t2 = T[11];
     int cnt = 0;
     unsigned long long acc = 0ull;
-    int i1 = (c + 1) * kConsChunk < nP ? (c + 1) * kConsChunk : nP;
-    for (int i = c * kConsChunk + threadIdx.x; i < i1; i += kConsThreads) {
-      float4 p = XP[i];
+    int i0 = c * kConsChunk, i1 = (c + 1) * kConsChunk < nP ? (c + 1) * kConsChunk : nP;
+    // block-uniform trip count: every lane reaches the group shuffles
+    for (int r = i0; r < i1; r += GPB) {
+      int i = r + grp;
+      bool valid = i < i1;
+      float4 p = valid ? XP[i] : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
       float x = fmaf(r0, p.x, fmaf(r1, p.y, fmaf(r2, p.z, t0)));
       float y = fmaf(r3, p.x, fmaf(r4, p.y, fmaf(r5, p.z, t1)));
       float z = fmaf(r6, p.x, fmaf(r7, p.y, fmaf(r8, p.z, t2)));
-      float best = eps2;
-      grid_ranges(g, start, x, y, z, [&](int b, int e) {
-        for (int t = b; t < e; ++t) {
-          float4 q = Xe[t];
-          float dx = q.x - x, dy = q.y - y, dz = q.z - z;
-          float d2 = dx * dx + dy * dy + dz * dz;
-          best = d2 < best ? d2 : best;
-        }
-      });
-      if (best < eps2) {
+      float best = group_min_d2<G>(g, start, Xe, x, y, z, eps2);
+      if (valid && sub == 0 && best < eps2) {
         ++cnt;
         acc += (unsigned long long)__double2ll_rn((double)best * kFixScale);
       }

@@ -4,8 +4,12 @@
 // eliminated: for a residual r, min_l l r^2 + mu (sqrt(l) - 1)^2 is reached at
 // l* = (mu / (mu + r^2))^2 and equals the Geman-McClure rho(r^2) = mu r^2 /
 // (mu + r^2). Refinement iterates reweighted Gauss-Newton with the Jacobian
-// G_p = [-[p]_x | I] of eq. (5): FP32 per-thread and per-block sums, FP64
-// across blocks, an FP64 Cholesky solve and an FP64 pose update on the device.
+// G_p = [-[p]_x | I] of eq. (5), taken about a linearisation centre c (the
+// weighted centroid of the current correspondences, so that FP32 stays exact
+// to the micrometre whatever the clouds' offset): FP32 per-thread and
+// per-block sums, then one launch-closing block sums the block partials in
+// FP64 in a fixed order, solves the 6x6 system by Cholesky and updates the
+// FP64 pose -- one kernel launch per iteration, no host round trip.
 #include "lsr_internal.cuh"
 
 namespace lsr {
@@ -13,22 +17,11 @@ namespace lsr {
 namespace {
 
 constexpr int kRefThreads = 256;
-constexpr int kNAcc = 28;  // 21 (upper triangle of A) + 6 (b) + 1 (count)
-
-__device__ __forceinline__ void nn_within(const GridParams &g, const int *start, const float4 *Xe, float x, float y,
-                                          float z, float eps2, float &best, int &bt) {
-  best = eps2;
-  bt = -1;
-  grid_ranges(g, start, x, y, z, [&](int b, int e) {
-    for (int t = b; t < e; ++t) {
-      float4 q = Xe[t];
-      float dx = q.x - x, dy = q.y - y, dz = q.z - z;
-      float d2 = dx * dx + dy * dy + dz * dz;
-      int qi = __float_as_int(q.w);
-      if (d2 < best || (d2 == best && bt >= 0 && qi < __float_as_int(Xe[bt].w))) best = d2, bt = t;
-    }
-  });
-}
+constexpr int kRefG = 16;  // lanes per nearest-neighbour query in refinement
+constexpr int kObjG = 8;   // lanes per query in the objective
+// 21 (upper triangle of A) + 6 (b) + count + sum w + sum w x (3)
+constexpr int kNAcc = kRefAcc;
+static_assert(kNAcc == 32, "refinement partial layout");
 
 template <int N>
 __device__ __forceinline__ void block_reduce_to(float (&v)[N], double *out) {
@@ -45,54 +38,6 @@ __device__ __forceinline__ void block_reduce_to(float (&v)[N], double *out) {
     for (int k = 0; k < kRefThreads / 32; ++k) s += (double)sm[k][threadIdx.x];
     out[threadIdx.x] = s;
   }
-}
-
-__global__ void __launch_bounds__(kRefThreads) k_refine_accum(const float4 *__restrict__ XP, int nP, int strideP,
-                                                              const GridParams *gep, const int *__restrict__ start,
-                                                              const float4 *__restrict__ Xe, float eps2, float mu,
-                                                              const RansacState *st, double *partials) {
-  if (!st->active) return;
-  const GridParams g = *gep;
-  const double *T = st->T;
-  float R[9], tc[3], c[3];
-  for (int r = 0; r < 3; ++r) {
-    for (int k = 0; k < 3; ++k) R[3 * r + k] = (float)T[4 * r + k];
-    c[r] = (float)st->center[r];
-    tc[r] = (float)(T[4 * r + 3] - st->center[r]);
-  }
-  float acc[kNAcc];
-#pragma unroll
-  for (int k = 0; k < kNAcc; ++k) acc[k] = 0.f;
-  for (int i = blockIdx.x * kRefThreads + threadIdx.x; i < nP; i += gridDim.x * kRefThreads) {
-    float4 p = XP[i];
-    if (strideP > 1 && __float_as_int(p.w) % strideP != 0) continue;
-    float xc0 = fmaf(R[0], p.x, fmaf(R[1], p.y, fmaf(R[2], p.z, tc[0])));
-    float xc1 = fmaf(R[3], p.x, fmaf(R[4], p.y, fmaf(R[5], p.z, tc[1])));
-    float xc2 = fmaf(R[6], p.x, fmaf(R[7], p.y, fmaf(R[8], p.z, tc[2])));
-    float x = xc0 + c[0], y = xc1 + c[1], z = xc2 + c[2];
-    float best;
-    int bt;
-    nn_within(g, start, Xe, x, y, z, eps2, best, bt);
-    if (bt < 0) continue;
-    float4 q = Xe[bt];
-    float r[3] = {x - q.x, y - q.y, z - q.z};
-    float s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-    float l = mu / (mu + s);
-    float w = l * l;
-    // J = [-[xc]_x | I] (rows: x, y, z; columns: alpha, beta, gamma, tx, ty, tz)
-    float J[3][6] = {{0.f, xc2, -xc1, 1.f, 0.f, 0.f}, {-xc2, 0.f, xc0, 0.f, 1.f, 0.f}, {xc1, -xc0, 0.f, 0.f, 0.f, 1.f}};
-    int k = 0;
-#pragma unroll
-    for (int a = 0; a < 6; ++a)
-#pragma unroll
-      for (int b = a; b < 6; ++b) {
-        acc[k++] += w * (J[0][a] * J[0][b] + J[1][a] * J[1][b] + J[2][a] * J[2][b]);
-      }
-#pragma unroll
-    for (int a = 0; a < 6; ++a) acc[21 + a] += w * (J[0][a] * r[0] + J[1][a] * r[1] + J[2][a] * r[2]);
-    acc[27] += 1.f;
-  }
-  block_reduce_to<kNAcc>(acc, partials + (size_t)blockIdx.x * kNAcc);
 }
 
 __device__ void exp_so3(const double w[3], double R[9]) {
@@ -113,15 +58,11 @@ __device__ void exp_so3(const double w[3], double R[9]) {
     }
 }
 
-// Sum the block partials in FP64 (fixed order), solve A d = -b by Cholesky,
-// and left-multiply the pose by the update about the linearisation centre c:
-// x' = Exp(d_w)(x - c) + c + d_v.
-__global__ void k_refine_solve(const double *partials, int nblocks, RansacState *st, int max_iters, double tol) {
-  if (threadIdx.x != 0 || !st->active) return;
-  double acc[kNAcc];
-  for (int k = 0; k < kNAcc; ++k) acc[k] = 0.0;
-  for (int b = 0; b < nblocks; ++b)
-    for (int k = 0; k < kNAcc; ++k) acc[k] += partials[(size_t)b * kNAcc + k];
+// Solve A d = -b (Cholesky, FP64) from the summed partials and left-multiply
+// the pose by the update about the centre c used for this step:
+// x' = Exp(d_w)(x - c) + c + d_v. The next step's centre is the weighted
+// centroid of this step's correspondences.
+__device__ void refine_solve(const double *acc, RansacState *st, int max_iters, double tol) {
   double A[36];
   int k = 0;
   for (int a = 0; a < 6; ++a)
@@ -174,6 +115,8 @@ __global__ void k_refine_solve(const double *partials, int nblocks, RansacState 
       Tn[4 * r + q] = s;
     }
   for (int i = 0; i < 16; ++i) st->T[i] = Tn[i];
+  if (acc[28] > 0.0)
+    for (int r = 0; r < 3; ++r) st->center[r] = acc[29 + r] / acc[28];
   double nd = 0.0;
   for (int i = 0; i < 6; ++i) nd += d[i] * d[i];
   nd = sqrt(nd);
@@ -183,10 +126,88 @@ __global__ void k_refine_solve(const double *partials, int nblocks, RansacState 
   if (nd < tol || st->level_iters >= max_iters) st->active = 0;
 }
 
+// One IRLS step. Every block accumulates its points; the last block to
+// finish (atomic ticket, no waiting) sums all block partials and solves.
+__global__ void __launch_bounds__(kRefThreads) k_refine_step(const float4 *__restrict__ XP, int nP, int strideP,
+                                                             const GridParams *gep, const int *__restrict__ start,
+                                                             const float4 *__restrict__ Xe, float eps2, float mu,
+                                                             RansacState *st, double *partials, int max_iters,
+                                                             double tol) {
+  __shared__ int s_last;
+  __shared__ double tot[kNAcc];
+  if (!st->active) return;
+  const GridParams g = *gep;
+  const double *T = st->T;
+  float R[9], tc[3], c[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) R[3 * r + k] = (float)T[4 * r + k];
+    c[r] = (float)st->center[r];
+    tc[r] = (float)(T[4 * r + 3] - st->center[r]);
+  }
+  float acc[kNAcc];
+#pragma unroll
+  for (int k = 0; k < kNAcc; ++k) acc[k] = 0.f;
+  constexpr int G = kRefG, GPB = kRefThreads / G;
+  int grp = threadIdx.x / G, sub = threadIdx.x & (G - 1);
+  // block-uniform trip count: every lane reaches the group shuffles
+  for (int r0 = blockIdx.x * GPB; r0 < nP; r0 += gridDim.x * GPB) {
+    int i = r0 + grp;
+    bool valid = i < nP;
+    float4 p = valid ? XP[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid && strideP > 1 && __float_as_int(p.w) % strideP != 0) valid = false;
+    if (!valid) p.x = __int_as_float(0x7fc00000);  // NaN: the query visits no cell
+    float xc0 = fmaf(R[0], p.x, fmaf(R[1], p.y, fmaf(R[2], p.z, tc[0])));
+    float xc1 = fmaf(R[3], p.x, fmaf(R[4], p.y, fmaf(R[5], p.z, tc[1])));
+    float xc2 = fmaf(R[6], p.x, fmaf(R[7], p.y, fmaf(R[8], p.z, tc[2])));
+    float x = xc0 + c[0], y = xc1 + c[1], z = xc2 + c[2];
+    float best;
+    int bt, bidx;
+    group_nn<G>(g, start, Xe, x, y, z, eps2, best, bt, bidx);
+    if (!valid || sub != 0 || bt < 0) continue;
+    float4 q = Xe[bt];
+    float r[3] = {x - q.x, y - q.y, z - q.z};
+    float s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    float l = mu / (mu + s);
+    float w = l * l;
+    // J = [-[xc]_x | I] (rows: x, y, z; columns: alpha, beta, gamma, tx, ty, tz)
+    float J[3][6] = {{0.f, xc2, -xc1, 1.f, 0.f, 0.f}, {-xc2, 0.f, xc0, 0.f, 1.f, 0.f}, {xc1, -xc0, 0.f, 0.f, 0.f, 1.f}};
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int b = a; b < 6; ++b) {
+        acc[k++] += w * (J[0][a] * J[0][b] + J[1][a] * J[1][b] + J[2][a] * J[2][b]);
+      }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) acc[21 + a] += w * (J[0][a] * r[0] + J[1][a] * r[1] + J[2][a] * r[2]);
+    acc[27] += 1.f;
+    acc[28] += w;
+    acc[29] += w * x, acc[30] += w * y, acc[31] += w * z;
+  }
+  block_reduce_to<kNAcc>(acc, partials + (size_t)blockIdx.x * kNAcc);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < kNAcc) {
+    double sum = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) sum += __ldcg(partials + (size_t)b * kNAcc + threadIdx.x);
+    tot[threadIdx.x] = sum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    refine_solve(tot, st, max_iters, tol);
+    st->ticket = 0u;
+  }
+}
+
 __global__ void k_refine_level_begin(RansacState *st) {
   if (threadIdx.x == 0) {
     st->active = st->status == 0 ? 1 : 0;
     st->level_iters = 0;
+    st->ticket = 0u;
   }
 }
 
@@ -198,15 +219,20 @@ __global__ void k_subsample(const float *xyz, int n, int stride, float4 *out) {
   }
 }
 
-__global__ void k_refine_init(RansacState *st, const float *boxQ, const double *T_in) {
+// Starting pose (T_in, or the selected hypothesis already in st) and the
+// first linearisation centre: the centroid of P moved by that pose.
+__global__ void k_refine_init(RansacState *st, const float *boxP, const double *T_in) {
   if (threadIdx.x != 0) return;
-  for (int d = 0; d < 3; ++d) st->center[d] = 0.5 * ((double)boxQ[d] + (double)boxQ[3 + d]);
   if (T_in) {
     for (int i = 0; i < 16; ++i) st->T[i] = st->T_hyp[i] = T_in[i];
     st->active = 1;
     st->status = 0;
     st->iters_done = 0;
   }
+  const double *T = st->T;
+  double m[3] = {boxP[8], boxP[9], boxP[10]};
+  for (int r = 0; r < 3; ++r) st->center[r] = T[4 * r] * m[0] + T[4 * r + 1] * m[1] + T[4 * r + 2] * m[2] + T[4 * r + 3];
+  st->ticket = 0u;
 }
 
 __global__ void k_final_pose(const RansacState *st, float *pose) {
@@ -241,14 +267,20 @@ __global__ void __launch_bounds__(kRefThreads) k_objective(const float *__restri
                                                            float *__restrict__ dQ) {
   const GridParams g = *gep;
   float acc[7] = {0, 0, 0, 0, 0, 0, 0};  // E, g_v (3), g_w (3)
-  for (int i = blockIdx.x * kRefThreads + threadIdx.x; i < nP; i += gridDim.x * kRefThreads) {
-    float px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+  constexpr int G = kObjG, GPB = kRefThreads / G;
+  int grp = threadIdx.x / G, sub = threadIdx.x & (G - 1);
+  for (int rb = blockIdx.x * GPB; rb < nP; rb += gridDim.x * GPB) {
+    int i = rb + grp;
+    bool valid = i < nP;
+    float px = valid ? P[3 * i] : __int_as_float(0x7fc00000), py = valid ? P[3 * i + 1] : 0.f,
+          pz = valid ? P[3 * i + 2] : 0.f;
     float x = fmaf(a.R[0], px, fmaf(a.R[1], py, fmaf(a.R[2], pz, a.t[0])));
     float y = fmaf(a.R[3], px, fmaf(a.R[4], py, fmaf(a.R[5], pz, a.t[1])));
     float z = fmaf(a.R[6], px, fmaf(a.R[7], py, fmaf(a.R[8], pz, a.t[2])));
     float best;
-    int bt;
-    nn_within(g, start, Xe, x, y, z, a.eps2, best, bt);
+    int bt, bidx;
+    group_nn<G>(g, start, Xe, x, y, z, a.eps2, best, bt, bidx);
+    if (!valid || sub != 0) continue;
     if (bt < 0) {
       if (want_grad) dP[3 * i] = dP[3 * i + 1] = dP[3 * i + 2] = 0.f;
       continue;
@@ -288,14 +320,11 @@ __global__ void k_objective_sum(const double *partials, int nblocks, double *out
 
 }  // namespace
 
+// One query per group of kRefG lanes per round; at most two blocks per SM so
+// that the launch-closing block sums few partials.
 int refine_blocks(int nP) {
-  int b = (int)lsr_div_up(nP > 0 ? nP : 1, kRefThreads * 4);
-  return b < 1 ? 1 : (b > 152 * 4 ? 152 * 4 : b);
-}
-
-cudaError_t launch_refine_init(RansacState *st, const float *boxQ, const double *T_in, cudaStream_t s) {
-  k_refine_init<<<1, 32, 0, s>>>(st, boxQ, T_in);
-  return cudaGetLastError();
+  int64_t b = lsr_div_up((int64_t)(nP > 0 ? nP : 1) * kRefG, kRefThreads);
+  return (int)(b < 1 ? 1 : (b > 152 * 2 ? 152 * 2 : b));
 }
 
 int gnc_stride(int64_t n, int level, int levels) {
@@ -304,6 +333,11 @@ int gnc_stride(int64_t n, int level, int levels) {
   int64_t cap = n / 4096;
   if (f > cap) f = cap;
   return (int)(f < 1 ? 1 : f);
+}
+
+cudaError_t launch_refine_init(RansacState *st, const float *boxP, const double *T_in, cudaStream_t s) {
+  k_refine_init<<<1, 32, 0, s>>>(st, boxP, T_in);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_refine_level_begin(RansacState *st, cudaStream_t s) {
@@ -321,9 +355,9 @@ cudaError_t launch_subsample(const float *xyz, int n, int stride, float4 *out, c
 cudaError_t launch_refine_step(const float4 *XP, int nP, int strideP, const GridParams *ge, const int *start_e,
                                const float4 *Xe, float eps_r, float mu, int max_iters, RansacState *st,
                                double *partials, cudaStream_t s) {
-  int nb = refine_blocks(nP);
-  k_refine_accum<<<nb, kRefThreads, 0, s>>>(XP, nP, strideP, ge, start_e, Xe, eps_r * eps_r, mu, st, partials);
-  k_refine_solve<<<1, 32, 0, s>>>(partials, nb, st, max_iters, 1e-7);
+  int nb = refine_blocks((int)lsr_div_up(nP, strideP));
+  k_refine_step<<<nb, kRefThreads, 0, s>>>(XP, nP, strideP, ge, start_e, Xe, eps_r * eps_r, mu, st, partials,
+                                           max_iters, 1e-6);
   return cudaGetLastError();
 }
 
@@ -337,7 +371,10 @@ cudaError_t launch_final_count(const int *count, const unsigned long long *sum, 
   return cudaGetLastError();
 }
 
-int objective_blocks(int nP) { return refine_blocks(nP); }
+int objective_blocks(int nP) {
+  int64_t b = lsr_div_up((int64_t)(nP > 0 ? nP : 1) * kObjG, kRefThreads);
+  return (int)(b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b));
+}
 
 cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
                              const float R[9], const float t[3], const float v[3], float eps, float mu, float scale,

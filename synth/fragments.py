@@ -201,10 +201,13 @@ class _Occluded:
         return self._keep(self.prim.lattice(s, rng))
 
 
-def _room_scene(rng, W=4.0, D=3.5, H=2.4, n_obj=20):
-    """Floor, four walls and n_obj boxes / cylinders: cabinets and shelves
-    against the walls, tables and stands in the room; the floor under them is
-    hidden. Room size varies by up to 15% per pair."""
+def _room_scene(rng, W=4.0, D=3.5, H=1.5, n_obj=20):
+    """Floor, four walls (the band up to H that a fragment's camera sees) and
+    n_obj boxes / cylinders: cabinets and shelves against the walls, tables and
+    stands in the room; the floor under them is hidden. Furniture is sized so
+    that less than half of a fragment lies on the floor and walls, as in the
+    cluttered indoor fragments the paper registers. Room size varies by up to
+    15% per pair."""
     W *= rng.uniform(0.85, 1.15)
     D *= rng.uniform(0.85, 1.15)
     walls = [_Rect([W / 2, 0.0, H / 2], [1, 0, 0], [0, 0, 1], W / 2, H / 2),
@@ -214,7 +217,7 @@ def _room_scene(rng, W=4.0, D=3.5, H=2.4, n_obj=20):
     prims, foot = list(walls), []
     for k in range(n_obj):
         if k % 2 == 0:
-            half = np.array([rng.uniform(0.15, 0.5), rng.uniform(0.12, 0.3), rng.uniform(0.15, 0.9)])
+            half = np.array([rng.uniform(0.2, 0.6), rng.uniform(0.15, 0.4), rng.uniform(0.2, 0.9)])
             if k % 4 == 0:
                 # against a wall (cabinet, shelf), possibly raised off the floor
                 side = int(rng.integers(4))
@@ -230,8 +233,8 @@ def _room_scene(rng, W=4.0, D=3.5, H=2.4, n_obj=20):
             if z <= half[2] + 1e-9:
                 foot.append((x, y, R, half[0], half[1], 0.0))
         else:
-            x, y, r = rng.uniform(0.4, W - 0.4), rng.uniform(0.4, D - 0.4), rng.uniform(0.08, 0.3)
-            prims.append(_Cylinder([x, y, 0.0], r, rng.uniform(0.2, 1.2)))
+            x, y, r = rng.uniform(0.4, W - 0.4), rng.uniform(0.4, D - 0.4), rng.uniform(0.1, 0.35)
+            prims.append(_Cylinder([x, y, 0.0], r, rng.uniform(0.3, 1.4)))
             foot.append((x, y, None, 0.0, 0.0, r))
     prims.insert(0, _Occluded(_Rect([W / 2, D / 2, 0.0], [1, 0, 0], [0, 1, 0], W / 2, D / 2), foot))
     vp = np.array([W / 2, D / 2, 1.2])

@@ -510,7 +510,7 @@ def test_gnc_result_independent_of_start(orc):
         d = np.eye(4)
         d[:3, :3] = Rotation.from_rotvec(rng.normal(0, 0.01, 3)).as_matrix()
         d[:3, 3] = rng.normal(0, 0.01, 3)
-        T, _ = orc.refine_gnc(fp.P, fp.Q, d @ fp.T, 0.0375, 1.0, levels=4, iters=100, tol=1e-12)
+        T, _ = orc.refine_gnc(fp.P, fp.Q, d @ fp.T, 0.0375, 1.0, levels=3, iters=100, tol=1e-12)
         outs.append(T)
     for T in outs[1:]:
         ang, tr = pose_error(T, outs[0])
@@ -526,6 +526,6 @@ def test_gnc_recovers_noiseless_pose(orc):
     d = np.eye(4)
     d[:3, :3] = Rotation.from_rotvec([0.02, 0.01, -0.015]).as_matrix()
     d[:3, 3] = [0.02, -0.01, 0.01]
-    T, _ = orc.refine_gnc(P, Q, d @ fp.T, 0.0375, 1.0, levels=4, iters=100)
+    T, _ = orc.refine_gnc(P, Q, d @ fp.T, 0.0375, 1.0, levels=3, iters=100)
     ang, tr = pose_error(T, fp.T)
     assert ang < 1e-7 and tr < 1e-9
