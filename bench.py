@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Throughput of the global registration hot path (Sec. IV, Algorithm 1, plus
+the robust refinement) on GB300.
+
+One step registers one fragment pair per GPU (pairs are independent, so N GPUs
+run N replicas on N different pairs: weak scaling, no collective). The default
+workload is the 150,000-point room pair on a 1 cm grid, FP32 end to end.
+Inputs are resident in HBM when the timed region starts and L2 is flushed
+(a 256 MB write) between steps, outside the timed events. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 0|1] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference for this path)
+on a bounded sample of the same workload, scaled to one pair.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fragment pairs/sec at ≤0.05°/≤0.5 mm vs plain FP32 path; HBM GB/s, TC util"
+WORKLOADS = {
+    0: "objects scene pair, 5,000 points per cloud, 70% overlap, 10% outliers, 4M hypotheses, FP32",
+    1: "indoor room pair on a 1 cm voxel grid, 150,000 points per cloud, 50% overlap, 4M hypotheses, FP32",
+}
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device, self.proc, self.lines = device, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, sm_max_nominal):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": sm_max_nominal, "reasons": ["not sampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_1801_01572_gb300 as lsr
+    from synth import make_pair
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    fp = make_pair(args.config, pair=rank)
+    nP, nQ = len(fp.P), len(fp.Q)
+    P = torch.from_numpy(fp.P).cuda()
+    Q = torch.from_numpy(fp.Q).cuda()
+    stream = torch.cuda.Stream()
+    ctx = lsr.Context(dev, stream=stream.cuda_stream)
+    ctx.set_profiling(True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        ctx.register_pair(P, Q, fp.vpP, fp.vpQ)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    pk, _ = peaks()
+    times, stages, last = [], np.zeros(8), None
+    with ClockSampler(dev) as clk:
+        l0 = lsr.launch_count()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = ctx.register_pair(P, Q, fp.vpP, fp.vpQ)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            stages += np.array(last.stage_ms)
+        launches = lsr.launch_count() - l0
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    stage_ms = stages / args.steps
+
+    # end to end through the public API from pinned host memory
+    Ph = torch.from_numpy(fp.P).pin_memory()
+    Qh = torch.from_numpy(fp.Q).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        ctx.register_pair(Ph, Qh, fp.vpP, fp.vpQ)
+    e2e_times = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.register_pair(Ph, Qh, fp.vpP, fp.vpQ)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = float(sum(e2e_times))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d, d2h = lsr.transfer_bytes(nP, nQ)
+    info = dict(fp=fp, nP=nP, nQ=nQ, last=last, stage_ms=stage_ms, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d,
+                d2h=d2h, launches=launches, clocks=clk.summary(pk.get("sm_max_mhz")), peaks=pk,
+                params=ctx.params)
+    ctx.close()
+    return info
+
+
+def roofline(info):
+    """Roofline of the kernel that dominates the step (from the stage timers)."""
+    pk, src = peaks()
+    st = info["stage_ms"]
+    nP, nQ, last = info["nP"], info["nQ"], info["last"]
+    names = ["grids", "normals", "features", "matching", "hypotheses", "consensus", "refinement"]
+    k = int(np.argmax(st[:7]))
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # FFMA TFLOP/s
+    if names[k] == "matching":
+        # brute-force FP32 NN: per (query, candidate) pair 33 subtract + 33 fused multiply-add
+        flops = float(nP) * float(nQ) * 33 * 3
+        ach = flops / (st[k] * 1e-3) / 1e12
+        return {"kernel": "k_match_fp32", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (FFMA issue peak)",
+                "work": "nP*nQ*33*3 flop"}
+    if names[k] == "consensus":
+        # per (hypothesis, point) query: the rigid transform (9 FMA) and the
+        # squared-distance test of the points within eps (counted at one candidate)
+        q = float(last.n_normal_ok) * nP
+        flops = q * (18 + 8)
+        ach = flops / (st[k] * 1e-3) / 1e12
+        return {"kernel": "k_consensus", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None, "queries": q,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz", "work": "queries*26 flop"}
+    # other stages: report HBM against the algorithmic bytes of the stage's inputs and outputs
+    bytes_ = float(nP + nQ) * (12 + 16 * 4 + 2 * 144)
+    ach = bytes_ / (st[k] * 1e-3) / 1e9
+    return {"kernel": names[k], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": src}
+
+
+# ---------------------------------------------------------------- oracle timing
+def cpu_sample(fp, n_ok: int, iters: int, H: int, budget: float = 1.0):
+    """Seconds the FP64 oracle needs for one pair, estimated from a bounded
+    sample of every stage (normals of all points; SPFH/FPFH, descriptor NN and
+    pre-rejection on fractions; consensus on a few poses; two refinement steps
+    per level), each scaled to the full stage. budget scales the sample size."""
+    import oracle
+    rng = np.random.default_rng(0)
+    P, Q = fp.P.astype(np.float64), fp.Q.astype(np.float64)
+    nP, nQ = len(P), len(Q)
+    t_total, parts = 0.0, {}
+
+    def tm(fn):
+        t0 = time.perf_counter()
+        out = fn()
+        return time.perf_counter() - t0, out
+
+    dt, (NP, _, _, _) = tm(lambda: oracle.normals(P, fp.vpP, 0.05))
+    parts["normals"] = dt * (nP + nQ) / nP
+    m = max(64, int(0.02 * budget * nP))
+    qi = np.sort(rng.choice(nP, m, replace=False))
+    dt, _ = tm(lambda: oracle.spfh(P, NP, 0.125, qidx=qi))
+    parts["spfh"] = dt * (nP + nQ) / m
+    dt, _ = tm(lambda: oracle.fpfh(P, NP, np.zeros((nP, 33)), 0.125, qidx=qi))
+    parts["fpfh"] = dt * (nP + nQ) / m
+    F = rng.uniform(size=(nP, 33))
+    mq = max(16, int(100 * budget))
+    dt, _ = tm(lambda: oracle.match(F, F[:nQ] if nQ <= nP else rng.uniform(size=(nQ, 33)),
+                                    qidx=rng.choice(nP, mq, replace=False)))
+    parts["matching"] = dt * nP / mq
+    hs = max(10_000, int(200_000 * budget))
+    nn = rng.integers(0, nQ, nP)
+    v = np.ones(max(nP, nQ), np.uint8)
+    dt, _ = tm(lambda: oracle.hypotheses(P, Q, nn, v[:nP], v[:nQ], hs, 1, 0, 0.9))
+    parts["hypotheses"] = dt * H / hs
+    npose = max(8, int(8 * budget))
+    from synth import random_pose
+    Rs, ts = [], []
+    for i in range(npose):
+        # most tested hypotheses are wrong; one pose in eight is the true one
+        T = fp.T if i % 8 == 0 else random_pose(rng) @ fp.T
+        Rs.append(T[:3, :3])
+        ts.append(T[:3, 3])
+    dt, _ = tm(lambda: oracle.consensus(P, Q, np.array(Rs), np.array(ts), 0.0375))
+    parts["consensus"] = dt * max(n_ok, 1) / npose
+    dt, _ = tm(lambda: oracle.refine(P, Q, fp.T, 0.0375, 0.0375 ** 2, iters=2, tol=0.0))
+    parts["refinement"] = dt / 2 * max(iters, 1)
+    t_total = sum(parts.values())
+    return t_total, parts
+
+
+def cpu_baseline_line(fp, n_ok, iters, H, budget=1.0):
+    import oracle
+    secs, parts = cpu_sample(fp, n_ok, iters, H, budget)
+    return {"value": 1.0 / secs, "unit": "pairs/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": ("FP64 C oracle (pthreads): normals of all points; SPFH/FPFH of %.0f%% of the points; "
+                       "descriptor NN of %d queries; pre-rejection of %d hypotheses; consensus of %d poses; "
+                       "2 refinement steps; each scaled to the full pair (%d normal-checked hypotheses, "
+                       "%d refinement steps as the GPU run)") % (2 * budget, max(16, int(100 * budget)),
+                                                               max(10_000, int(200_000 * budget)),
+                                                               max(8, int(8 * budget)), n_ok, iters),
+            "stage_s": {k: round(v, 3) for k, v in parts.items()}}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The oracle on bounded samples of the workload, one sample per step."""
+    if rank != 0:
+        return None
+    import oracle
+    from synth import make_pair
+    oracle.build()
+    fp = make_pair(args.config, pair=0)
+    n_ok = {0: 6900, 1: 8700}.get(args.config, 8000)  # normal-checked hypotheses of the workload
+    iters = 120
+    H = 4_000_000
+    budget = 2.0
+    for _ in range(args.warmup):
+        cpu_sample(fp, n_ok, iters, H, budget=0.25)
+    secs = []
+    for _ in range(args.steps):
+        s, parts = cpu_sample(fp, n_ok, iters, H, budget=budget)
+        secs.append(s)
+    value = len(secs) / sum(secs)
+    cores = oracle.threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": "per step: normals of all points, 4% of SPFH/FPFH, 200 descriptor-NN "
+                                       "queries, 400k hypotheses, 16 consensus poses (1 in 8 the true one), "
+                                       "2 refinement steps, each scaled to the full pair"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+# ---------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    rank = int(os.environ.get("RANK", 0))
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    info = run_ours(args, rank, world)
+    if rank == 0:
+        K = args.steps
+        value = world * K / (info["total_ms"] * 1e-3)
+        e2e = world * K / (info["e2e_ms"] * 1e-3)
+        last = info["last"]
+        prm = info["params"]
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": info["total_ms"] / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "points": [info["nP"], info["nQ"]],
+                       "hypotheses": int(prm.n_hypotheses), "match": "fp32", "refine_levels": int(prm.refine_levels),
+                       "l2": "flushed between steps by a 256 MB write outside the timed events",
+                       "parallelism": "replicas (one pair per GPU)" if world > 1 else "single GPU"},
+            "points_per_s": value * (info["nP"] + info["nQ"]),
+            "stage_ms": {n: round(float(v), 3) for n, v in zip(
+                ["grids", "normals", "features", "matching", "hypotheses", "consensus", "refinement", "total"],
+                info["stage_ms"])},
+            "result": {"inliers": last.inliers, "survivors": last.survivors, "normal_ok": last.n_normal_ok,
+                       "refine_iters": last.refine_iters},
+            "roofline": roofline(info),
+            "e2e": {"value": e2e, "unit": "pairs/s", "h2d_bytes_per_step": info["h2d"] * world,
+                    "d2h_bytes_per_step": info["d2h"] * world},
+            "gpu_launches": int(info["launches"]),
+            "clocks": info["clocks"],
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_line(info["fp"], last.n_normal_ok, last.refine_iters,
+                                                     int(prm.n_hypotheses), budget=12.0)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -128,6 +128,15 @@ LSR_API const char *lsr_last_error(const lsr_ctx *ctx);
 /* Bytes of device workspace currently held by the context. */
 LSR_API int64_t lsr_workspace_bytes(const lsr_ctx *ctx);
 
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts); the difference across a call counts that call's launches. */
+LSR_API uint64_t lsr_launch_count(void);
+
+/* Bytes a registration of host-resident clouds of nP and nQ points copies
+ * host to device (*h2d) and device to host (*d2h) inside lsr_register_pair.
+ * Either pointer may be NULL. */
+LSR_API int lsr_transfer_bytes(int64_t nP, int64_t nQ, int64_t *h2d, int64_t *d2h);
+
 /* Algorithm 1 followed by the robust refinement, for one pair.
  * P: nP x 3 float32, Q: nQ x 3 float32 (device or host). vpP / vpQ: viewpoints
  * (3 floats, host) the normals of each cloud are oriented toward; NULL means

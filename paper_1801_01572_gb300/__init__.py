@@ -9,7 +9,8 @@ from __future__ import annotations
 
 from .lsr import (DESC_DIM, LSR_E_ARG, LSR_E_CUDA, LSR_E_OOM, LSR_E_STATE, LSR_E_TIMEOUT, LSR_OK,  # noqa: F401
                   MATCH_BF16, MATCH_FP32, STATUS_ALIGNED, STATUS_NO_ALIGNMENT, ABI_FUNCTIONS, Context, LsrError,
-                  Params, Registration, context, default_params, lib, library_path, register_pair)
+                  Params, Registration, context, default_params, launch_count, lib, library_path, register_pair,
+                  transfer_bytes)
 
 
 def _torch():

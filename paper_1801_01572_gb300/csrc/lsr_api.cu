@@ -20,6 +20,10 @@
 
 using namespace lsr;
 
+namespace lsr {
+unsigned long long g_launches = 0;
+}
+
 struct lsr_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -66,6 +70,7 @@ struct CloudLayout {
   float4 *X = nullptr, *Xn = nullptr, *Xe = nullptr, *N = nullptr;
   int *inv = nullptr;
   float *S = nullptr, *F = nullptr;
+  unsigned *mask_e = nullptr;
 };
 
 struct ScratchLayout {
@@ -97,6 +102,7 @@ void plan_cloud(Arena &a, int n, bool stage_src, bool features, bool eps_grid, C
   if (eps_grid) {
     c.start_e = a.take<int>((size_t)c.cap_e + 1);
     c.Xe = a.take<float4>(n);
+    c.mask_e = a.take<unsigned>((size_t)nbmask_words(c.cap_e));
   }
 }
 
@@ -117,6 +123,7 @@ struct LevelLayout {
   int sP[kMaxLevels] = {}, nsubP[kMaxLevels] = {};
   float4 *Qsub[kMaxLevels] = {}, *Xs[kMaxLevels] = {}, *Psub[kMaxLevels] = {};
   int *start[kMaxLevels] = {};
+  unsigned *mask[kMaxLevels] = {};
   GridParams *g[kMaxLevels] = {};
 };
 
@@ -134,6 +141,7 @@ void plan_levels(Arena &a, int nP, int nQ, int levels, LevelLayout &V) {
     V.Qsub[l] = a.take<float4>(V.nsub[l]);
     V.Xs[l] = a.take<float4>(V.nsub[l]);
     V.start[l] = a.take<int>((size_t)V.cap[l] + 1);
+    V.mask[l] = a.take<unsigned>((size_t)nbmask_words(V.cap[l]));
     V.g[l] = a.take<GridParams>(1);
   }
 }
@@ -337,6 +345,7 @@ cudaError_t build_cloud(const float *xyz, CloudLayout &c, float r_f, float r_n, 
   if (eps_grid) {
     LSR_CUDA_TRY(launch_grid_params(c.box, eps, c.n, c.cap_e, c.ge, s));
     LSR_CUDA_TRY(build_grid_f4(c.X, c.n, c.ge, c.cap_e, c.start_e, c.Xe, sc.g, s));
+    LSR_CUDA_TRY(build_nbmask(c.ge, c.start_e, c.cap_e, c.mask_e, s));
   }
   return cudaSuccess;
 }
@@ -366,6 +375,7 @@ cudaError_t enqueue_refine(const float4 *XP, const float *P, int nP, const float
       LSR_CUDA_TRY(launch_subsample(Q, nQ, V.sQ[l], V.Qsub[l], s));
       LSR_CUDA_TRY(launch_grid_params(boxQ, e, V.nsub[l], V.cap[l], V.g[l], s));
       LSR_CUDA_TRY(build_grid_f4(V.Qsub[l], V.nsub[l], V.g[l], V.cap[l], V.start[l], V.Xs[l], sc.g, s));
+      LSR_CUDA_TRY(build_nbmask(V.g[l], V.start[l], V.cap[l], V.mask[l], s));
       g = V.g[l], st0 = V.start[l], xs = V.Xs[l];
     }
     LSR_CUDA_TRY(launch_refine_level_begin(st, s));
@@ -604,6 +614,15 @@ int lsr_set_profiling(lsr_ctx *c, int enable) {
 
 int64_t lsr_workspace_bytes(const lsr_ctx *c) { return c ? (int64_t)c->ws_cap : 0; }
 
+uint64_t lsr_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+int lsr_transfer_bytes(int64_t nP, int64_t nQ, int64_t *h2d, int64_t *d2h) {
+  if (nP < 0 || nQ < 0) return LSR_E_ARG;
+  if (h2d) *h2d = (int64_t)sizeof(float) * 3 * (nP + nQ);
+  if (d2h) *d2h = (int64_t)(sizeof(RansacState) + 2 * sizeof(float) * kBox);
+  return LSR_OK;
+}
+
 static int register_many(lsr_ctx *c, int32_t n, const float *const *P, const int64_t *nP, const float *const *Q,
                          const int64_t *nQ, const float *vp, uint64_t pair0, lsr_result *out) {
   int rc = guard(c);
@@ -710,7 +729,7 @@ int lsr_stage_normals(lsr_ctx *c, const float *P, int64_t n, const float *vp, fl
   TRY_CUDA(c, build_cloud(src, C, r, r, r, true, false, S, s), "grids");
   float3 v = vp ? make_float3(vp[0], vp[1], vp[2]) : make_float3(0.f, 0.f, 0.f);
   TRY_CUDA(c, launch_normals(C.X, (int)n, C.gn, C.start_n, C.Xn, r, v, C.N, cnt, s), "normals");
-  k_scatter_normals<<<nblk(n), 256, 0, s>>>(C.N, cnt, C.X, (int)n, dn, dc, dv);
+  LSR_LAUNCH(k_scatter_normals<<<nblk(n), 256, 0, s>>>(C.N, cnt, C.X, (int)n, dn, dc, dv));
   TRY_CUDA(c, cudaGetLastError(), "scatter");
   if (normals && (rc = copy_out(c, normals, dn, sizeof(float) * 3 * n))) return rc;
   if (count && (rc = copy_out(c, count, dc, sizeof(int) * n))) return rc;
@@ -752,16 +771,16 @@ static int stage_desc_common(lsr_ctx *c, const float *P, const float *normals, c
   if ((rc = stage_input(c, P, n, C.src, &src))) return rc;
   TRY_CUDA(c, cudaMemcpyAsync(nrm, normals, sizeof(float) * 3 * n, cudaMemcpyDefault, s), "copy normals");
   TRY_CUDA(c, build_cloud(src, C, r, r, r, false, false, S, s), "grids");
-  k_gather_normals<<<nblk(n), 256, 0, s>>>(nrm, C.X, (int)n, C.N);
+  LSR_LAUNCH(k_gather_normals<<<nblk(n), 256, 0, s>>>(nrm, C.X, (int)n, C.N));
   if (!spfh_in) {
     TRY_CUDA(c, launch_spfh(C.X, C.N, (int)n, C.gf, C.start_f, r, C.S, kk, s), "spfh");
-    k_scatter_rows<<<nblk(n * kD), 256, 0, s>>>(C.S, C.X, (int)n, o);
-    if (k_out) k_scatter_int<<<nblk(n), 256, 0, s>>>(kk, C.X, (int)n, ko);
+    LSR_LAUNCH(k_scatter_rows<<<nblk(n * kD), 256, 0, s>>>(C.S, C.X, (int)n, o));
+    if (k_out) LSR_LAUNCH(k_scatter_int<<<nblk(n), 256, 0, s>>>(kk, C.X, (int)n, ko));
   } else {
     TRY_CUDA(c, cudaMemcpyAsync(sp, spfh_in, sizeof(float) * kD * n, cudaMemcpyDefault, s), "copy spfh");
-    k_gather_rows<<<nblk(n * kDS), 256, 0, s>>>(sp, kD, C.X, (int)n, C.S);
+    LSR_LAUNCH(k_gather_rows<<<nblk(n * kDS), 256, 0, s>>>(sp, kD, C.X, (int)n, C.S));
     TRY_CUDA(c, launch_fpfh(C.X, C.N, C.S, (int)n, C.gf, C.start_f, r, C.F, s), "fpfh");
-    k_scatter_rows<<<nblk(n * kD), 256, 0, s>>>(C.F, C.X, (int)n, o);
+    LSR_LAUNCH(k_scatter_rows<<<nblk(n * kD), 256, 0, s>>>(C.F, C.X, (int)n, o));
   }
   TRY_CUDA(c, cudaGetLastError(), "stage kernels");
   if ((rc = copy_out(c, out, o, sizeof(float) * kD * n))) return rc;
@@ -808,8 +827,8 @@ int lsr_stage_match(lsr_ctx *c, const float *FP, int64_t nP, const float *FQ, in
   cudaStream_t s = c->stream;
   TRY_CUDA(c, cudaMemcpyAsync(fp, FP, sizeof(float) * kD * nP, cudaMemcpyDefault, s), "copy FP");
   TRY_CUDA(c, cudaMemcpyAsync(fq, FQ, sizeof(float) * kD * nQ, cudaMemcpyDefault, s), "copy FQ");
-  k_gather_rows<<<nblk(nP * kDS), 256, 0, s>>>(fp, kD, nullptr, (int)nP, FPi);
-  k_gather_rows<<<nblk(nQ * kDS), 256, 0, s>>>(fq, kD, nullptr, (int)nQ, FQi);
+  LSR_LAUNCH(k_gather_rows<<<nblk(nP * kDS), 256, 0, s>>>(fp, kD, nullptr, (int)nP, FPi));
+  LSR_LAUNCH(k_gather_rows<<<nblk(nQ * kDS), 256, 0, s>>>(fq, kD, nullptr, (int)nQ, FQi));
   TRY_CUDA(c, launch_match_fp32(FPi, (int)nP, FQi, (int)nQ, dn, dd, s), "match");
   if ((rc = copy_out(c, nn, dn, sizeof(int) * nP))) return rc;
   if (d1 && (rc = copy_out(c, d1, dd, sizeof(float) * nP))) return rc;
@@ -868,11 +887,11 @@ int lsr_stage_hypotheses(lsr_ctx *c, const float *P, int64_t nP, const float *Q,
   TRY_CUDA(c, cudaMemcpyAsync(vp, validP, nP, cudaMemcpyDefault, s), "copy vP");
   TRY_CUDA(c, cudaMemcpyAsync(vq, validQ, nQ, cudaMemcpyDefault, s), "copy vQ");
   TRY_CUDA(c, cudaMemsetAsync(L.st, 0, sizeof(RansacState), s), "memset");
-  k_pack<<<nblk(nP), 256, 0, s>>>(p, (int)nP, XP);
-  k_pack<<<nblk(nQ), 256, 0, s>>>(q, (int)nQ, XQ);
-  k_iota<<<nblk(nP), 256, 0, s>>>(inv, (int)nP);
-  k_valid_normals<<<nblk(nP), 256, 0, s>>>(vp, (int)nP, NP);
-  k_valid_normals<<<nblk(nQ), 256, 0, s>>>(vq, (int)nQ, NQ);
+  LSR_LAUNCH(k_pack<<<nblk(nP), 256, 0, s>>>(p, (int)nP, XP));
+  LSR_LAUNCH(k_pack<<<nblk(nQ), 256, 0, s>>>(q, (int)nQ, XQ));
+  LSR_LAUNCH(k_iota<<<nblk(nP), 256, 0, s>>>(inv, (int)nP));
+  LSR_LAUNCH(k_valid_normals<<<nblk(nP), 256, 0, s>>>(vp, (int)nP, NP));
+  LSR_LAUNCH(k_valid_normals<<<nblk(nQ), 256, 0, s>>>(vq, (int)nQ, NQ));
   TRY_CUDA(c,
            launch_hypotheses(XP, inv, NP, (int)nP, XQ, NQ, (int)nQ, dnn, nullptr, nullptr, H, seed, pair_id, tau,
                              L.blk_cnt, L.blk_off, L.blk_scan, L.surv, L.surv_cap, L.st, s),
@@ -950,13 +969,13 @@ int lsr_stage_consensus(lsr_ctx *c, const float *P, int64_t nP, const float *Q, 
   const float *qsrc;
   if ((rc = stage_input(c, Q, nQ, Cq.src, &qsrc))) return rc;
   TRY_CUDA(c, cudaMemcpyAsync(pose, Rt, sizeof(float) * 12 * nh, cudaMemcpyDefault, s), "copy Rt");
-  k_pack<<<nblk(nP), 256, 0, s>>>(p, (int)nP, XP);
+  LSR_LAUNCH(k_pack<<<nblk(nP), 256, 0, s>>>(p, (int)nP, XP));
   TRY_CUDA(c, build_cloud(qsrc, Cq, eps, eps, eps, false, true, S, s), "grid Q");
   TRY_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int) * nh, s), "memset");
   TRY_CUDA(c, cudaMemsetAsync(sum, 0, sizeof(unsigned long long) * nh, s), "memset");
   TRY_CUDA(c, launch_consensus(XP, (int)nP, Cq.ge, Cq.start_e, Cq.Xe, pose, nullptr, nullptr, (int)nh, eps, cnt, sum, s),
            "consensus");
-  k_sum_to_double<<<nblk(nh), 256, 0, s>>>(sum, (int)nh, sd);
+  LSR_LAUNCH(k_sum_to_double<<<nblk(nh), 256, 0, s>>>(sum, (int)nh, sd));
   if ((rc = copy_out(c, count, cnt, sizeof(int) * nh))) return rc;
   if ((rc = copy_out(c, sumd2, sd, sizeof(double) * nh))) return rc;
   TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
@@ -1011,7 +1030,7 @@ int lsr_stage_refine(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int
   if ((rc = stage_input(c, Q, nQ, Cq.src, &qsrc))) return rc;
   TRY_CUDA(c, cudaMemcpyAsync(Td, T_in, sizeof(double) * 16, cudaMemcpyDefault, s), "copy T");
   TRY_CUDA(c, cudaMemsetAsync(st, 0, sizeof(RansacState), s), "memset");
-  k_pack<<<nblk(nP), 256, 0, s>>>(p, (int)nP, XP);
+  LSR_LAUNCH(k_pack<<<nblk(nP), 256, 0, s>>>(p, (int)nP, XP));
   TRY_CUDA(c, launch_bbox_xyz(p, (int)nP, boxP_part, bbox_blocks((int)nP), boxP, s), "bbox P");
   TRY_CUDA(c, build_cloud(qsrc, Cq, eps, eps, eps, false, true, S, s), "grid Q");
   TRY_CUDA(c, launch_refine_init(st, boxP, Td, s), "init");
@@ -1115,6 +1134,7 @@ static int objective_impl(lsr_ctx *c, int32_t n, const float *const *P, const in
     TRY_CUDA(c, launch_bbox_xyz(Q[i], Cq.n, Cq.box_part, bbox_blocks(Cq.n), Cq.box, s), "bbox");
     TRY_CUDA(c, launch_grid_params(Cq.box, eps, Cq.n, Cq.cap_e, Cq.ge, s), "grid params");
     TRY_CUDA(c, build_grid_xyz(Q[i], Cq.n, Cq.ge, Cq.cap_e, Cq.start_e, Cq.Xe, Cq.inv, S.g, s), "grid");
+    TRY_CUDA(c, build_nbmask(Cq.ge, Cq.start_e, Cq.cap_e, Cq.mask_e, s), "mask");
     if (grad) TRY_CUDA(c, cudaMemsetAsync(dQ[i], 0, sizeof(float) * 3 * nQ[i], s), "memset dQ");
     TRY_CUDA(c,
              launch_objective(P[i], (int)nP[i], Cq.ge, Cq.start_e, Cq.Xe, Rf, tf, vf, eps, mu,

@@ -278,19 +278,19 @@ inline int blocks_for_warps(int n) {
 
 cudaError_t launch_normals(const float4 *X, int n, const GridParams *gn, const int *start_n, const float4 *Xn, float r,
                            float3 vp, float4 *N, int *count, cudaStream_t s) {
-  k_normals<<<blocks_for_warps(n), kThreads, 0, s>>>(X, n, gn, start_n, Xn, r * r, vp, N, count);
+  LSR_LAUNCH(k_normals<<<blocks_for_warps(n), kThreads, 0, s>>>(X, n, gn, start_n, Xn, r * r, vp, N, count));
   return cudaGetLastError();
 }
 
 cudaError_t launch_spfh(const float4 *X, const float4 *N, int n, const GridParams *gf, const int *start_f, float r,
                         float *spfh, int *k, cudaStream_t s) {
-  k_spfh<<<blocks_for_warps(n), kThreads, 0, s>>>(X, N, n, gf, start_f, r * r, spfh, k);
+  LSR_LAUNCH(k_spfh<<<blocks_for_warps(n), kThreads, 0, s>>>(X, N, n, gf, start_f, r * r, spfh, k));
   return cudaGetLastError();
 }
 
 cudaError_t launch_fpfh(const float4 *X, const float4 *N, const float *spfh, int n, const GridParams *gf,
                         const int *start_f, float r, float *fpfh, cudaStream_t s) {
-  k_fpfh<<<blocks_for_warps(n), kThreads, 0, s>>>(X, N, spfh, n, gf, start_f, r * r, fpfh);
+  LSR_LAUNCH(k_fpfh<<<blocks_for_warps(n), kThreads, 0, s>>>(X, N, spfh, n, gf, start_f, r * r, fpfh));
   return cudaGetLastError();
 }
 

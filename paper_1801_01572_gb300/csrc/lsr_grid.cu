@@ -138,7 +138,48 @@ __global__ void k_grid_params(const float *box, float radius, int npts, int cap,
   q.ncells = (int)(wx * wy * wz);
   q.npts = npts;
   q.pad_ = 0;
+  q.nbmask = nullptr;
   *g = q;
+}
+
+// Dilate the occupied storage cells into their 3 x 3 x 3 neighbourhoods
+// (neighbourhoods are symmetric, so a query cell's bit is set iff some point
+// lies in the block around it; wrapped axes dilate modulo the stored extent,
+// which can only add bits).
+__global__ void k_nbmask(const GridParams *gp, const int *start, unsigned *mask) {
+  const GridParams g = *gp;
+  bool wx = g.wx != g.nx, wy = g.wy != g.ny, wz = g.wz != g.nz;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncells; c += gridDim.x * blockDim.x) {
+    if (start[c + 1] == start[c]) continue;
+    int sx = c % g.wx, sy = (c / g.wx) % g.wy, sz = c / (g.wx * g.wy);
+    for (int dz = -1; dz <= 1; ++dz) {
+      int z = sz + dz;
+      if (z < 0 || z >= g.wz) {
+        if (!wz) continue;
+        z = (z + g.wz) % g.wz;
+      }
+      for (int dy = -1; dy <= 1; ++dy) {
+        int y = sy + dy;
+        if (y < 0 || y >= g.wy) {
+          if (!wy) continue;
+          y = (y + g.wy) % g.wy;
+        }
+        for (int dx = -1; dx <= 1; ++dx) {
+          int x = sx + dx;
+          if (x < 0 || x >= g.wx) {
+            if (!wx) continue;
+            x = (x + g.wx) % g.wx;
+          }
+          int s = (z * g.wy + y) * g.wx + x;
+          atomicOr(&mask[s >> 5], 1u << (s & 31));
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_set_mask(GridParams *g, const unsigned *mask) {
+  if (threadIdx.x == 0) g->nbmask = mask;
 }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -300,21 +341,31 @@ int bbox_blocks(int n) { return (int)lsr_div_up(n > 0 ? n : 1, kBoxThreads * kBo
 cudaError_t launch_bbox_xyz(const float *xyz, int n, double *partials, int nblk_cap, float *box, cudaStream_t s) {
   int nb = bbox_blocks(n);
   if (nb > nblk_cap) return cudaErrorInvalidValue;
-  k_bbox_partial<false><<<nb, kBoxThreads, 0, s>>>(xyz, n, partials);
-  k_bbox_final<<<1, 32, 0, s>>>(partials, nb, box);
+  LSR_LAUNCH(k_bbox_partial<false><<<nb, kBoxThreads, 0, s>>>(xyz, n, partials));
+  LSR_LAUNCH(k_bbox_final<<<1, 32, 0, s>>>(partials, nb, box));
   return cudaGetLastError();
 }
 
 cudaError_t launch_bbox_f4(const float4 *x, int n, double *partials, int nblk_cap, float *box, cudaStream_t s) {
   int nb = bbox_blocks(n);
   if (nb > nblk_cap) return cudaErrorInvalidValue;
-  k_bbox_partial<true><<<nb, kBoxThreads, 0, s>>>(x, n, partials);
-  k_bbox_final<<<1, 32, 0, s>>>(partials, nb, box);
+  LSR_LAUNCH(k_bbox_partial<true><<<nb, kBoxThreads, 0, s>>>(x, n, partials));
+  LSR_LAUNCH(k_bbox_final<<<1, 32, 0, s>>>(partials, nb, box));
   return cudaGetLastError();
 }
 
 cudaError_t launch_grid_params(const float *box, float radius, int npts, int cap_cells, GridParams *g, cudaStream_t s) {
-  k_grid_params<<<1, 32, 0, s>>>(box, radius, npts, cap_cells, g);
+  LSR_LAUNCH(k_grid_params<<<1, 32, 0, s>>>(box, radius, npts, cap_cells, g));
+  return cudaGetLastError();
+}
+
+int64_t nbmask_words(int cap_cells) { return cap_cells / 32 + 2; }
+
+cudaError_t build_nbmask(GridParams *g, const int *start, int cap_cells, unsigned *mask, cudaStream_t s) {
+  LSR_CUDA_TRY(cudaMemsetAsync(mask, 0, sizeof(unsigned) * (size_t)nbmask_words(cap_cells), s));
+  int b = (int)lsr_div_up(cap_cells, 256);
+  LSR_LAUNCH(k_nbmask<<<b < 152 * 16 ? b : 152 * 16, 256, 0, s>>>(g, start, mask));
+  LSR_LAUNCH(k_set_mask<<<1, 32, 0, s>>>(g, mask));
   return cudaGetLastError();
 }
 
@@ -322,9 +373,9 @@ int64_t scan_scratch_ints(int64_t n) { return lsr_div_up(n + 1, kScanTile) + 64;
 
 cudaError_t scan_exclusive(const int *in, int *out, const int *n_dev, int cap, int *scratch, cudaStream_t s) {
   int nblocks = (int)lsr_div_up((int64_t)cap + 1, kScanTile);
-  k_scan_local<<<nblocks, kScanThreads, 0, s>>>(in, out, n_dev, scratch);
-  k_scan_blocks<<<1, kScanThreads, 0, s>>>(scratch, nblocks);
-  k_scan_add<<<nblocks, kScanThreads, 0, s>>>(out, n_dev, scratch);
+  LSR_LAUNCH(k_scan_local<<<nblocks, kScanThreads, 0, s>>>(in, out, n_dev, scratch));
+  LSR_LAUNCH(k_scan_blocks<<<1, kScanThreads, 0, s>>>(scratch, nblocks));
+  LSR_LAUNCH(k_scan_add<<<nblocks, kScanThreads, 0, s>>>(out, n_dev, scratch));
   return cudaGetLastError();
 }
 
@@ -332,14 +383,14 @@ template <bool kF4>
 static cudaError_t build_grid_impl(const void *src, int n, const GridParams *g, int cap_cells, int *start, float4 *out,
                                    int *inv_out, GridScratch sc, cudaStream_t s) {
   LSR_CUDA_TRY(cudaMemsetAsync(sc.counts, 0, sizeof(int) * ((size_t)cap_cells + 1), s));
-  k_slots<kF4><<<grid_blocks(n), 256, 0, s>>>(src, n, g, sc.slot, sc.counts);
+  LSR_LAUNCH(k_slots<kF4><<<grid_blocks(n), 256, 0, s>>>(src, n, g, sc.slot, sc.counts));
   // the cell count lives in device memory; keep a copy next to the counts
   int *ncells_dev = sc.counts + cap_cells;  // counts[cap] is never used as a cell
-  k_ncells_ptr<<<1, 32, 0, s>>>(g, ncells_dev);
+  LSR_LAUNCH(k_ncells_ptr<<<1, 32, 0, s>>>(g, ncells_dev));
   LSR_CUDA_TRY(scan_exclusive(sc.counts, start, ncells_dev, cap_cells, sc.scan, s));
   LSR_CUDA_TRY(cudaMemsetAsync(sc.counts, 0, sizeof(int) * (size_t)cap_cells, s));
-  k_scatter<<<grid_blocks(n), 256, 0, s>>>(n, sc.slot, start, sc.counts, sc.tmp);
-  k_cell_order<kF4><<<grid_blocks(cap_cells * 32, 256), 256, 0, s>>>(src, g, start, sc.tmp, out, inv_out);
+  LSR_LAUNCH(k_scatter<<<grid_blocks(n), 256, 0, s>>>(n, sc.slot, start, sc.counts, sc.tmp));
+  LSR_LAUNCH(k_cell_order<kF4><<<grid_blocks(cap_cells * 32, 256), 256, 0, s>>>(src, g, start, sc.tmp, out, inv_out));
   return cudaGetLastError();
 }
 

@@ -21,6 +21,11 @@ constexpr int kWarp = 32;
 // to cover the FP32 rounding of the cell coordinates, so every point within
 // the radius of a query lies in the 3 x 3 x 3 block of cells around it.
 struct GridParams {
+  // Optional bitmap over storage cells: bit set if the 3 x 3 x 3 block around
+  // the cell holds a point. A query whose own cell has a clear bit has no
+  // neighbour within the radius and skips the range lookups (most consensus
+  // queries of wrong hypotheses land in empty space).
+  const unsigned *nbmask;
   float ox, oy, oz;  // origin (bounding-box minimum)
   float cell, inv_cell;
   int nx, ny, nz;    // extent of the bounding box in cells
@@ -52,6 +57,11 @@ struct CloudDev {
 // ----------------------------------------------------------------- helpers
 __host__ __device__ inline int64_t lsr_div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Kernel launches of this library, counted process-wide (lsr_launch_count).
+extern unsigned long long g_launches;
+inline void count_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
+#define LSR_LAUNCH(...) (::lsr::count_launch(), __VA_ARGS__)
+
 #define LSR_CUDA_TRY(call)                         \
   do {                                             \
     cudaError_t e_ = (call);                       \
@@ -75,6 +85,10 @@ __device__ __forceinline__ void grid_ranges(const GridParams &g, const int *__re
   int x0 = cx - 1 < 0 ? 0 : cx - 1, x1 = cx + 1 > g.nx - 1 ? g.nx - 1 : cx + 1;
   if (x0 > x1) return;
   bool wrapped = (g.wx != g.nx) | (g.wy != g.ny) | (g.wz != g.nz);
+  if (g.nbmask && cx >= 0 && cx < g.nx && cy >= 0 && cy < g.ny && cz >= 0 && cz < g.nz) {
+    int slot = wrapped ? ((cz % g.wz) * g.wy + (cy % g.wy)) * g.wx + (cx % g.wx) : (cz * g.wy + cy) * g.wx + cx;
+    if (!((__ldg(g.nbmask + (slot >> 5)) >> (slot & 31)) & 1u)) return;
+  }
   if (!wrapped) {
     for (int dz = -1; dz <= 1; ++dz) {
       int iz = cz + dz;
@@ -126,6 +140,18 @@ __device__ __forceinline__ void group_nn(const GridParams &g, const int *__restr
   int next = sub, base = 0;
   grid_ranges(g, start, x, y, z, [&](int b, int e) {
     int len = e - b;
+    // four independent loads in flight per lane, then the remainder
+    for (; next + 3 * G < base + len; next += 4 * G) {
+      int t = b + next - base;
+      float4 q[4] = {Xe[t], Xe[t + G], Xe[t + 2 * G], Xe[t + 3 * G]};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float dx = q[k].x - x, dy = q[k].y - y, dz = q[k].z - z;
+        float d2 = dx * dx + dy * dy + dz * dz;
+        int qi = __float_as_int(q[k].w);
+        if (d2 < best || (d2 == best && qi < bidx)) best = d2, bt = t + k * G, bidx = qi;
+      }
+    }
     for (; next < base + len; next += G) {
       int t = b + next - base;
       float4 q = Xe[t];
@@ -164,8 +190,12 @@ cudaError_t launch_bbox_xyz(const float *xyz, int n, double *partials, int nblk_
 cudaError_t launch_bbox_f4(const float4 *x, int n, double *partials, int nblk_cap, float *box, cudaStream_t s);
 int bbox_blocks(int n);
 
-// Fill a GridParams from a bounding box on the device.
+// Fill a GridParams from a bounding box on the device (no neighbourhood mask).
 cudaError_t launch_grid_params(const float *box, float radius, int npts, int cap_cells, GridParams *g, cudaStream_t s);
+// Build the neighbourhood bitmap of a built grid (nbmask_words(cap) words)
+// and attach it to g.
+int64_t nbmask_words(int cap_cells);
+cudaError_t build_nbmask(GridParams *g, const int *start, int cap_cells, unsigned *mask, cudaStream_t s);
 
 // Counting sort of points into the grid: out[k] = point sorted k-th by (cell,
 // source index) with w replaced by the carried index (source index if

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kMT) k_match_fp32(const float *__restrict__ FP
 cudaError_t launch_match_fp32(const float *FP, int nP, const float *FQ, int nQ, int *nn, float *d1, cudaStream_t s) {
   int blocks = (int)lsr_div_up(nP, kMT * kQPT);
   if (blocks < 1) blocks = 1;
-  k_match_fp32<<<blocks, kMT, 0, s>>>(FP, nP, FQ, nQ, nn, d1);
+  LSR_LAUNCH(k_match_fp32<<<blocks, kMT, 0, s>>>(FP, nP, FQ, nQ, nn, d1));
   return cudaGetLastError();
 }
 

@@ -299,7 +299,7 @@ __global__ void k_rigid4(const float *ps, const float *qs, int nh, float *pose) 
 // the order of the atomic adds.
 constexpr int kConsThreads = 256;
 constexpr int kConsChunk = 2048;
-constexpr int kConsG = 8;  // lanes per query
+constexpr int kConsG = 1;  // lanes per query (most queries end at the mask test)
 
 // Minimum squared distance below eps2 by a group of G lanes (no index needed).
 template <int G>
@@ -310,6 +310,16 @@ __device__ __forceinline__ float group_min_d2(const GridParams &g, const int *__
   int next = sub, base = 0;
   grid_ranges(g, start, x, y, z, [&](int b, int e) {
     int len = e - b;
+    // four independent loads in flight per lane, then the remainder
+    for (; next + 3 * G < base + len; next += 4 * G) {
+      int t = b + next - base;
+      float4 q0 = Xe[t], q1 = Xe[t + G], q2 = Xe[t + 2 * G], q3 = Xe[t + 3 * G];
+      float d0 = (q0.x - x) * (q0.x - x) + (q0.y - y) * (q0.y - y) + (q0.z - z) * (q0.z - z);
+      float d1 = (q1.x - x) * (q1.x - x) + (q1.y - y) * (q1.y - y) + (q1.z - z) * (q1.z - z);
+      float d2 = (q2.x - x) * (q2.x - x) + (q2.y - y) * (q2.y - y) + (q2.z - z) * (q2.z - z);
+      float d3 = (q3.x - x) * (q3.x - x) + (q3.y - y) * (q3.y - y) + (q3.z - z) * (q3.z - z);
+      best = fminf(best, fminf(fminf(d0, d1), fminf(d2, d3)));
+    }
     for (; next < base + len; next += G) {
       float4 q = Xe[b + next - base];
       float dx = q.x - x, dy = q.y - y, dz = q.z - z;
@@ -443,12 +453,12 @@ cudaError_t launch_hypotheses(const float4 *XP, const int *invP, const float4 *N
                               int *scan_scratch, int *surv, int surv_cap, RansacState *st, cudaStream_t s) {
   HypIn in{XP, invP, NP, nP, XQ, NQ, nQ, nn, seed, pair, tau * tau};
   int nb = hyp_blocks(H);
-  k_hyp_count<<<nb, kHypThreads, 0, s>>>(in, H, block_counts);
+  LSR_LAUNCH(k_hyp_count<<<nb, kHypThreads, 0, s>>>(in, H, block_counts));
   int *nb_dev = block_counts + nb;  // one spare int after the counts holds nb
-  k_set_int<<<1, 32, 0, s>>>(nb_dev, nb);
+  LSR_LAUNCH(k_set_int<<<1, 32, 0, s>>>(nb_dev, nb));
   LSR_CUDA_TRY(scan_exclusive(block_counts, block_offsets, nb_dev, nb, scan_scratch, s));
-  k_hyp_write<<<nb, kHypThreads, 0, s>>>(in, H, block_offsets, surv, surv_cap);
-  k_hyp_finish<<<1, 32, 0, s>>>(block_offsets, nb, surv_cap, st);
+  LSR_LAUNCH(k_hyp_write<<<nb, kHypThreads, 0, s>>>(in, H, block_offsets, surv, surv_cap));
+  LSR_LAUNCH(k_hyp_finish<<<1, 32, 0, s>>>(block_offsets, nb, surv_cap, st));
   return cudaGetLastError();
 }
 
@@ -457,26 +467,26 @@ cudaError_t launch_rigid_survivors(const float4 *XP, const int *invP, const floa
                                    uint64_t seed, uint64_t pair, float cos_normal, float *pose, uint8_t *ok,
                                    int *n_normal_ok, cudaStream_t s) {
   HypIn in{XP, invP, NP, nP, XQ, NQ, 0x7fffffff, nn, seed, pair, 0.f};
-  k_rigid_survivors<<<152 * 4, 256, 0, s>>>(in, surv, st, cos_normal, pose, ok, n_normal_ok);
+  LSR_LAUNCH(k_rigid_survivors<<<152 * 4, 256, 0, s>>>(in, surv, st, cos_normal, pose, ok, n_normal_ok));
   return cudaGetLastError();
 }
 
 cudaError_t launch_rigid4(const float *ps, const float *qs, int nh, float *pose, cudaStream_t s) {
   int b = (int)lsr_div_up(nh > 0 ? nh : 1, 256);
-  k_rigid4<<<b, 256, 0, s>>>(ps, qs, nh, pose);
+  LSR_LAUNCH(k_rigid4<<<b, 256, 0, s>>>(ps, qs, nh, pose));
   return cudaGetLastError();
 }
 
 cudaError_t launch_consensus(const float4 *XP, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
                              const float *pose, const uint8_t *ok, const int *n_dev, int n_host, float eps, int *count,
                              unsigned long long *sum, cudaStream_t s) {
-  k_consensus<<<152 * 8, kConsThreads, 0, s>>>(XP, nP, ge, start_e, Xe, pose, ok, n_dev, n_host, eps * eps, count, sum);
+  LSR_LAUNCH(k_consensus<<<152 * 8, kConsThreads, 0, s>>>(XP, nP, ge, start_e, Xe, pose, ok, n_dev, n_host, eps * eps, count, sum));
   return cudaGetLastError();
 }
 
 cudaError_t launch_select(const int *surv, const int *count, const unsigned long long *sum, const uint8_t *ok,
                           const float *pose, int nP, float min_ratio, RansacState *st, cudaStream_t s) {
-  k_select<<<1, 1024, 0, s>>>(surv, count, sum, ok, pose, nP, min_ratio, st);
+  LSR_LAUNCH(k_select<<<1, 1024, 0, s>>>(surv, count, sum, ok, pose, nP, min_ratio, st));
   return cudaGetLastError();
 }
 

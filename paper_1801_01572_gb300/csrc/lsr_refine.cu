@@ -336,19 +336,19 @@ int gnc_stride(int64_t n, int level, int levels) {
 }
 
 cudaError_t launch_refine_init(RansacState *st, const float *boxP, const double *T_in, cudaStream_t s) {
-  k_refine_init<<<1, 32, 0, s>>>(st, boxP, T_in);
+  LSR_LAUNCH(k_refine_init<<<1, 32, 0, s>>>(st, boxP, T_in));
   return cudaGetLastError();
 }
 
 cudaError_t launch_refine_level_begin(RansacState *st, cudaStream_t s) {
-  k_refine_level_begin<<<1, 32, 0, s>>>(st);
+  LSR_LAUNCH(k_refine_level_begin<<<1, 32, 0, s>>>(st));
   return cudaGetLastError();
 }
 
 cudaError_t launch_subsample(const float *xyz, int n, int stride, float4 *out, cudaStream_t s) {
   int m = (n + stride - 1) / stride;
   int b = (int)lsr_div_up(m > 0 ? m : 1, 256);
-  k_subsample<<<b < 4096 ? b : 4096, 256, 0, s>>>(xyz, n, stride, out);
+  LSR_LAUNCH(k_subsample<<<b < 4096 ? b : 4096, 256, 0, s>>>(xyz, n, stride, out));
   return cudaGetLastError();
 }
 
@@ -356,18 +356,18 @@ cudaError_t launch_refine_step(const float4 *XP, int nP, int strideP, const Grid
                                const float4 *Xe, float eps_r, float mu, int max_iters, RansacState *st,
                                double *partials, cudaStream_t s) {
   int nb = refine_blocks((int)lsr_div_up(nP, strideP));
-  k_refine_step<<<nb, kRefThreads, 0, s>>>(XP, nP, strideP, ge, start_e, Xe, eps_r * eps_r, mu, st, partials,
-                                           max_iters, 1e-6);
+  LSR_LAUNCH(k_refine_step<<<nb, kRefThreads, 0, s>>>(XP, nP, strideP, ge, start_e, Xe, eps_r * eps_r, mu, st, partials,
+                                           max_iters, 1e-6));
   return cudaGetLastError();
 }
 
 cudaError_t launch_final_pose(RansacState *st, float *pose, cudaStream_t s) {
-  k_final_pose<<<1, 32, 0, s>>>(st, pose);
+  LSR_LAUNCH(k_final_pose<<<1, 32, 0, s>>>(st, pose));
   return cudaGetLastError();
 }
 
 cudaError_t launch_final_count(const int *count, const unsigned long long *sum, RansacState *st, cudaStream_t s) {
-  k_final_count<<<1, 32, 0, s>>>(count, sum, st);
+  LSR_LAUNCH(k_final_count<<<1, 32, 0, s>>>(count, sum, st));
   return cudaGetLastError();
 }
 
@@ -387,8 +387,8 @@ cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const
   a.rho_eps = mu * a.eps2 / (mu + a.eps2);
   a.scale = scale;
   int nb = objective_blocks(nP);
-  k_objective<<<nb, kRefThreads, 0, s>>>(P, nP, ge, start_e, Xe, a, want_grad, partials, dP, dQ);
-  k_objective_sum<<<1, 32, 0, s>>>(partials, nb, out7);
+  LSR_LAUNCH(k_objective<<<nb, kRefThreads, 0, s>>>(P, nP, ge, start_e, Xe, a, want_grad, partials, dP, dQ));
+  LSR_LAUNCH(k_objective_sum<<<1, 32, 0, s>>>(partials, nb, out7));
   return cudaGetLastError();
 }
 

@@ -26,7 +26,8 @@ DESC_DIM = 33
 # Names of every entry point declared in include/lsr.h (checked by the tests).
 ABI_FUNCTIONS = (
     "lsr_default_params", "lsr_create", "lsr_destroy", "lsr_set_params", "lsr_get_params", "lsr_set_profiling",
-    "lsr_error_string", "lsr_last_error", "lsr_workspace_bytes", "lsr_register_pair", "lsr_register_batch",
+    "lsr_error_string", "lsr_last_error", "lsr_workspace_bytes", "lsr_launch_count", "lsr_transfer_bytes",
+    "lsr_register_pair", "lsr_register_batch",
     "lsr_stage_normals", "lsr_stage_spfh", "lsr_stage_fpfh", "lsr_stage_match", "lsr_stage_hypotheses",
     "lsr_stage_rigid4", "lsr_stage_consensus", "lsr_stage_refine", "lsr_objective_fwd", "lsr_objective_bwd",
 )
@@ -80,6 +81,8 @@ def lib():
             "lsr_error_string": (C.c_char_p, [C.c_int]),
             "lsr_last_error": (C.c_char_p, [vp]),
             "lsr_workspace_bytes": (i64, [vp]),
+            "lsr_launch_count": (C.c_uint64, []),
+            "lsr_transfer_bytes": (C.c_int, [i64, i64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
             "lsr_register_pair": (C.c_int, [vp, vp, i64, vp, i64, vp, vp, C.POINTER(Result)]),
             "lsr_register_batch": (C.c_int, [vp, i32, pp, vp, pp, vp, vp, C.POINTER(Result)]),
             "lsr_stage_normals": (C.c_int, [vp, vp, i64, vp, f32, vp, vp, vp]),
@@ -131,6 +134,20 @@ def _vec3(v):
         return None, None
     a = np.ascontiguousarray(np.asarray(v, np.float32).reshape(3))
     return C.c_void_p(a.ctypes.data), a
+
+
+def launch_count() -> int:
+    """Kernels launched by the CUDA library in this process so far."""
+    return int(lib().lsr_launch_count())
+
+
+def transfer_bytes(nP: int, nQ: int) -> tuple[int, int]:
+    """(host-to-device, device-to-host) bytes of one registration of host clouds."""
+    a, b = C.c_int64(0), C.c_int64(0)
+    rc = lib().lsr_transfer_bytes(int(nP), int(nQ), C.byref(a), C.byref(b))
+    if rc != LSR_OK:
+        raise LsrError(rc, "transfer_bytes")
+    return int(a.value), int(b.value)
 
 
 def default_params(**overrides) -> Params:
