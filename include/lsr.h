@@ -51,6 +51,7 @@ extern "C" {
 #define LSR_E_OOM (-3)     /* device or host memory allocation failed */
 #define LSR_E_TIMEOUT (-4) /* a bounded device-side wait ran out */
 #define LSR_E_STATE (-5)   /* context not usable (NULL, destroyed, or a previous sticky CUDA error) */
+#define LSR_E_TOO_LARGE (-6) /* input larger than the fixed scratch of lsr_consensus_static allows */
 
 #define LSR_STATUS_ALIGNED 0
 #define LSR_STATUS_NO_ALIGNMENT 1
@@ -204,6 +205,31 @@ LSR_API int lsr_stage_rigid4(lsr_ctx *ctx, const float *ps, const float *qs, int
  * count: nh int32, sumd2: nh double. */
 LSR_API int lsr_stage_consensus(lsr_ctx *ctx, const float *P, int64_t nP, const float *Q, int64_t nQ, const float *Rt,
                         int64_t nh, float eps, int32_t *count, double *sumd2);
+
+/* Pose scoring that allocates nothing. (The paper has no counterpart: this is
+ * a service for callers that must not allocate device memory when they score
+ * poses -- a loop-closure check inside a real-time loop, or a process whose
+ * device memory belongs to another framework's pool.)
+ * Same result as lsr_stage_consensus: for each pose Rt (nh x 12, row-major
+ * [R | t]), count[k] = points of P whose nearest Q point is closer than eps,
+ * sumd2[k] = the sum of their squared distances. P: nP x 3, Q: nQ x 3 float32;
+ * Rt, count (int32, nh), sumd2 (double, nh) may be device or host arrays.
+ * Scratch comes from one fixed 16 MiB array in the library's device image
+ * (held by every GPU that loads the library until the process exits), so:
+ *  - limits: nP <= 65536, nQ <= 65536, nh <= 4096, else LSR_E_TOO_LARGE;
+ *  - no context is needed; work runs on the calling thread's current device,
+ *    on cuda_stream (NULL: the legacy default stream), and the call
+ *    synchronises that stream before returning;
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it: make that first call before any
+ *    stream capture;
+ *  - every call on a device shares the array, which keeps the previous call's
+ *    contents (the call clears what must start at zero): calls that overlap
+ *    on the GPU (other streams, other host threads) race and must not be
+ *    issued.
+ * Returns LSR_OK, LSR_E_ARG, LSR_E_TOO_LARGE or LSR_E_CUDA. */
+LSR_API int lsr_consensus_static(const float *P, int64_t nP, const float *Q, int64_t nQ, const float *Rt, int64_t nh,
+                                 float eps, int32_t *count, double *sumd2, void *cuda_stream);
 
 /* Graduated robust refinement from T_in (host, 4x4 row-major double). Level
  * l = 0..levels-1 iterates Geman-McClure IRLS (at most iters steps) with exact

@@ -529,6 +529,7 @@ const char *lsr_error_string(int code) {
     case LSR_E_OOM: return "out of memory";
     case LSR_E_TIMEOUT: return "device wait timed out";
     case LSR_E_STATE: return "context unusable";
+    case LSR_E_TOO_LARGE: return "input exceeds the fixed scratch of the allocation-free entry point";
     default: return "unknown error";
   }
 }

@@ -18,7 +18,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 _lib = None
 _lock = threading.Lock()
 
-LSR_OK, LSR_E_ARG, LSR_E_CUDA, LSR_E_OOM, LSR_E_TIMEOUT, LSR_E_STATE = 0, -1, -2, -3, -4, -5
+LSR_OK, LSR_E_ARG, LSR_E_CUDA, LSR_E_OOM, LSR_E_TIMEOUT, LSR_E_STATE, LSR_E_TOO_LARGE = 0, -1, -2, -3, -4, -5, -6
 STATUS_ALIGNED, STATUS_NO_ALIGNMENT = 0, 1
 MATCH_FP32, MATCH_BF16 = 0, 1
 DESC_DIM = 33
@@ -30,6 +30,7 @@ ABI_FUNCTIONS = (
     "lsr_register_pair", "lsr_register_batch",
     "lsr_stage_normals", "lsr_stage_spfh", "lsr_stage_fpfh", "lsr_stage_match", "lsr_stage_hypotheses",
     "lsr_stage_rigid4", "lsr_stage_consensus", "lsr_stage_refine", "lsr_objective_fwd", "lsr_objective_bwd",
+    "lsr_consensus_static",
 )
 
 
@@ -95,6 +96,7 @@ def lib():
             "lsr_stage_refine": (C.c_int, [vp, vp, i64, vp, i64, vp, f32, f32, i32, i32, vp, vp]),
             "lsr_objective_fwd": (C.c_int, [vp, i32, pp, vp, pp, vp, vp, vp, f32, f32, vp]),
             "lsr_objective_bwd": (C.c_int, [vp, i32, pp, vp, pp, vp, vp, vp, f32, f32, vp, pp, pp, vp]),
+            "lsr_consensus_static": (C.c_int, [vp, i64, vp, i64, vp, i64, f32, vp, vp, vp]),
         }
         for name in ABI_FUNCTIONS:
             res, args = sig[name]
