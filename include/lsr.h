@@ -57,7 +57,10 @@ extern "C" {
 #define LSR_STATUS_NO_ALIGNMENT 1
 
 #define LSR_MATCH_FP32 0 /* descriptor matching on FP32 SIMT cores */
-#define LSR_MATCH_BF16 1 /* BF16 tensor-core candidates + FP32 re-rank */
+#define LSR_MATCH_BF16 1 /* tensor cores: descriptors as hi + lo BF16 pairs (K = 112),
+                            top-8 candidates, exact FP32 re-rank, certified */
+#define LSR_MATCH_BF16_PLAIN 2 /* tensor cores: descriptors rounded to one BF16 each,
+                                  zero-padded to K = 48; same re-rank and certificate */
 
 #define LSR_DESC_DIM 33 /* FPFH: 3 angular features x 11 bins */
 
@@ -80,7 +83,7 @@ typedef struct {
   int64_t n_hypotheses;   /* sampled hypotheses per pair, default 4,000,000 (at most 2^31 - 1) */
   uint64_t seed;          /* hypothesis RNG key word 0 (Philox-4x64-10 key = (seed, pair_id)) */
   uint64_t pair_id;       /* RNG key word 1 for lsr_register_pair; a batch uses pair_id + i */
-  int32_t match_precision; /* LSR_MATCH_FP32 (default) or LSR_MATCH_BF16 */
+  int32_t match_precision; /* LSR_MATCH_FP32 (default), LSR_MATCH_BF16 or LSR_MATCH_BF16_PLAIN */
   int32_t refine_levels;  /* graduated refinement levels L (1..8), default 3: radius eps * 2^(L-1-l) at level l */
   int32_t reserved_[4];
 } lsr_params;
@@ -179,10 +182,23 @@ LSR_API int lsr_stage_fpfh(lsr_ctx *ctx, const float *P, const float *normals, c
 
 /* Feature pre-matching (Alg. 1): nn[i] = argmin_j |FP_i - FQ_j|^2 (ties to the
  * smallest j), d1[i] its squared distance. FP: nP x 33, FQ: nQ x 33.
- * precision: LSR_MATCH_FP32 or LSR_MATCH_BF16. fallbacks (host, may be NULL):
- * BF16 queries that were re-scanned in FP32. */
+ * precision: LSR_MATCH_FP32, LSR_MATCH_BF16 or LSR_MATCH_BF16_PLAIN; every
+ * precision returns the same nn and d1 (the tensor-core modes re-rank their
+ * top-8 candidates in FP32 and re-scan, in FP32, every query for which a
+ * rounding-error bound cannot prove that the FP32 winner is a candidate).
+ * fallbacks (host, may be NULL): queries re-scanned that way. */
 LSR_API int lsr_stage_match(lsr_ctx *ctx, const float *FP, int64_t nP, const float *FQ, int64_t nQ, int32_t precision,
                     int32_t *nn, float *d1, int64_t *fallbacks);
+
+/* The tensor-core contraction behind the BF16 modes (Alg. 1 feature
+ * pre-matching, |a - b|^2 = |a|^2 + |b|^2 - 2 a.b), for validation. With c a
+ * mean descriptor and a~, b~ the BF16 forms of a - c, b - c (precision as in
+ * lsr_stage_match; LSR_MATCH_FP32 is rejected), d2[i * nQ + j] = |b~_j|^2 -
+ * 2 a~_i . b~_j + |a~_i|^2 as accumulated in FP32 by the tensor cores: an
+ * approximation of |FP_i - FQ_j|^2. FP: nP x 33, FQ: nQ x 33, d2: nP x nQ
+ * (host or device); nP, nQ <= 65536. LSR_E_TIMEOUT if a bounded wait ran out. */
+LSR_API int lsr_match_scores_bf16(lsr_ctx *ctx, const float *FP, int64_t nP, const float *FQ, int64_t nQ,
+                                  int32_t precision, float *d2);
 
 /* Hypothesis sampling + polygon pre-rejection + compaction (Alg. 1). Samples
  * hypotheses h = 0..H-1 with Philox-4x64-10(counter (h,0,0,0), key (seed,

@@ -9,7 +9,7 @@ from __future__ import annotations
 
 from .lsr import (DESC_DIM, LSR_E_ARG, LSR_E_CUDA, LSR_E_OOM, LSR_E_STATE, LSR_E_TIMEOUT, LSR_E_TOO_LARGE,  # noqa: F401
                   LSR_OK,
-                  MATCH_BF16, MATCH_FP32, STATUS_ALIGNED, STATUS_NO_ALIGNMENT, ABI_FUNCTIONS, Context, LsrError,
+                  MATCH_BF16, MATCH_BF16_PLAIN, MATCH_FP32, STATUS_ALIGNED, STATUS_NO_ALIGNMENT, ABI_FUNCTIONS, Context, LsrError,
                   Params, Registration, context, default_params, launch_count, lib, library_path, register_pair,
                   transfer_bytes)
 

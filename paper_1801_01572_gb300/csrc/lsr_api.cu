@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -38,6 +39,9 @@ struct lsr_ctx {
   cudaEvent_t ev[9] = {};
   std::string last_error;
   bool broken = false;
+  // consensus tuning: lanes per nearest-neighbour query (2 measured fastest
+  // on the 150k-point room pair among 1..16; LSR_CONSENSUS_LANES overrides)
+  int cons_lanes = 2;
 };
 
 namespace {
@@ -165,11 +169,13 @@ struct PairLayout {
   int *fcount = nullptr;
   unsigned long long *fsum = nullptr;
   RansacState *st = nullptr;
+  char *tc_ws = nullptr;  // BF16 matcher workspace (BF16 precision only)
 };
 
 int surv_cap_for(int64_t H) { return (int)std::min<int64_t>(H, (int64_t)1 << 22); }
 
-void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int levels, PairLayout &L) {
+void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int levels, int precision,
+               PairLayout &L) {
   plan_cloud(a, nP, stP, true, false, L.P);
   plan_cloud(a, nQ, stQ, true, true, L.Q);
   plan_levels(a, nP, nQ, levels, L.lv);
@@ -191,6 +197,8 @@ void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int leve
   L.fcount = a.take<int>(1);
   L.fsum = a.take<unsigned long long>(1);
   L.st = a.take<RansacState>(1);
+  if (precision != LSR_MATCH_FP32)
+    L.tc_ws = a.take<char>(tc_workspace_bytes(nP, nQ, precision == LSR_MATCH_BF16));
 }
 
 int set_err(lsr_ctx *c, int code, const char *msg) {
@@ -261,12 +269,14 @@ int ensure_host_slots(lsr_ctx *c, int n) {
   return LSR_OK;
 }
 
+bool valid_precision(int p) { return p == LSR_MATCH_FP32 || p == LSR_MATCH_BF16 || p == LSR_MATCH_BF16_PLAIN; }
+
 int check_params(const lsr_params *p) {
   if (!(p->r_normal > 0.f && p->r_feature > 0.f && p->eps_inlier > 0.f && p->tau > 0.f && p->tau <= 1.f &&
         p->cos_normal >= -1.f && p->cos_normal <= 1.f && p->min_inlier_ratio >= 0.f && p->mu_scale > 0.f &&
         p->refine_iters >= 0 && p->refine_iters <= 10000 && p->refine_levels >= 1 &&
         p->refine_levels <= kMaxLevels && p->n_hypotheses >= 1 &&
-        p->n_hypotheses <= 2147483647LL && (p->match_precision == LSR_MATCH_FP32 || p->match_precision == LSR_MATCH_BF16)))
+        p->n_hypotheses <= 2147483647LL && valid_precision(p->match_precision)))
     return LSR_E_ARG;
   if (p->eps_inlier > 10.f) return LSR_E_ARG;  // fixed-point inlier sums assume eps^2 * |P| << 2^23
   return LSR_OK;
@@ -415,7 +425,13 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
   TRY_CUDA(c, launch_fpfh(Pc.X, Pc.N, Pc.S, nP, Pc.gf, Pc.start_f, p.r_feature, Pc.F, s), "fpfh P");
   TRY_CUDA(c, launch_fpfh(Qc.X, Qc.N, Qc.S, nQ, Qc.gf, Qc.start_f, p.r_feature, Qc.F, s), "fpfh Q");
   tm.mark();
-  TRY_CUDA(c, launch_match_fp32(Pc.F, nP, Qc.F, nQ, L.nn, L.d1, s), "match");
+  if (p.match_precision != LSR_MATCH_FP32)
+    TRY_CUDA(c,
+             launch_match_bf16(Pc.F, nP, Qc.F, nQ, p.match_precision == LSR_MATCH_BF16, L.tc_ws, L.nn, L.d1,
+                               &L.st->match_fallbacks, &L.st->match_err, nullptr, s),
+             "match");
+  else
+    TRY_CUDA(c, launch_match_fp32(Pc.F, nP, Qc.F, nQ, L.nn, L.d1, s), "match");
   tm.mark();
   TRY_CUDA(c,
            launch_hypotheses(Pc.X, Pc.inv, Pc.N, nP, Qc.X, Qc.N, nQ, L.nn, nullptr, nullptr, p.n_hypotheses, p.seed,
@@ -430,7 +446,7 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
   TRY_CUDA(c, cudaMemsetAsync(L.sum, 0, sizeof(unsigned long long) * L.surv_cap, s), "memset sum");
   TRY_CUDA(c,
            launch_consensus(Pc.X, nP, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.ok, &L.st->n_surv, 0, p.eps_inlier, L.count,
-                            L.sum, s),
+                            L.sum, s, c->cons_lanes),
            "consensus");
   tm.mark();
   TRY_CUDA(c, launch_select(L.surv, L.count, L.sum, L.ok, L.pose, nP, p.min_inlier_ratio, L.st, s), "select");
@@ -443,7 +459,9 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
   TRY_CUDA(c, launch_final_pose(L.st, L.fpose, s), "final pose");
   TRY_CUDA(c, cudaMemsetAsync(L.fcount, 0, sizeof(int), s), "memset fcount");
   TRY_CUDA(c, cudaMemsetAsync(L.fsum, 0, sizeof(unsigned long long), s), "memset fsum");
-  TRY_CUDA(c, launch_consensus(Pc.X, nP, Qc.ge, Qc.start_e, Qc.Xe, L.fpose, nullptr, nullptr, 1, eps, L.fcount, L.fsum, s),
+  TRY_CUDA(c,
+           launch_consensus(Pc.X, nP, Qc.ge, Qc.start_e, Qc.Xe, L.fpose, nullptr, nullptr, 1, eps, L.fcount, L.fsum, s,
+                            c->cons_lanes),
            "final count");
   TRY_CUDA(c, launch_final_count(L.fcount, L.fsum, L.st, s), "final count");
   tm.mark();
@@ -462,7 +480,7 @@ void fill_result(const RansacState &st, const float *boxP, const float *boxQ, ls
   r->survivors = st.n_surv_total;
   r->n_normal_ok = st.n_normal_ok;
   r->best_h = st.best >= 0 ? st.best_h : -1;
-  r->match_fallbacks = 0;
+  r->match_fallbacks = st.match_fallbacks;
   r->fitness = st.final_count > 0 ? (float)(st.final_sumd2 / st.final_count) : 0.f;
   r->hyp_fitness = st.best_fit;
   r->status = ok ? LSR_STATUS_ALIGNED : LSR_STATUS_NO_ALIGNMENT;
@@ -568,6 +586,10 @@ int lsr_create(lsr_ctx **out, const lsr_params *params, int device, void *cuda_s
     }
     c->own_stream = true;
   }
+  if (const char *e = getenv("LSR_CONSENSUS_LANES")) {
+    int v = atoi(e);
+    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) c->cons_lanes = v;
+  }
   for (auto &e : c->ev)
     if (cudaEventCreate(&e) != cudaSuccess) {
       cudaGetLastError();
@@ -641,14 +663,16 @@ static int register_many(lsr_ctx *c, int32_t n, const float *const *P, const int
   // one workspace sized for the largest pair; pairs run back to back on the stream
   Arena m(nullptr);
   PairLayout Lm;
-  plan_pair(m, (int)maxP, (int)maxQ, true, true, c->prm.n_hypotheses, c->prm.refine_levels, Lm);
+  plan_pair(m, (int)maxP, (int)maxQ, true, true, c->prm.n_hypotheses, c->prm.refine_levels, c->prm.match_precision,
+            Lm);
   if ((rc = ensure_ws(c, m.off))) return rc;
   if ((rc = ensure_host_slots(c, n))) return rc;
   Timer tm{c};
   for (int i = 0; i < n; ++i) {
     Arena a(c->ws);
     PairLayout L;
-    plan_pair(a, (int)nP[i], (int)nQ[i], true, true, c->prm.n_hypotheses, c->prm.refine_levels, L);
+    plan_pair(a, (int)nP[i], (int)nQ[i], true, true, c->prm.n_hypotheses, c->prm.refine_levels,
+              c->prm.match_precision, L);
     const float *dP, *dQ;
     if ((rc = stage_input(c, P[i], nP[i], L.P.src, &dP))) return rc;
     if ((rc = stage_input(c, Q[i], nQ[i], L.Q.src, &dQ))) return rc;
@@ -668,6 +692,7 @@ static int register_many(lsr_ctx *c, int32_t n, const float *const *P, const int
   for (int i = 0; i < n; ++i) {
     if (c->box_host[2 * kBox * i + 6] != 0.f || c->box_host[2 * kBox * i + kBox + 6] != 0.f)
       return set_err(c, LSR_E_ARG, "non-finite input coordinates");
+    if (c->st_host[i].match_err) return set_err(c, LSR_E_TIMEOUT, "BF16 matcher timed out waiting on the tensor cores");
     fill_result(c->st_host[i], &c->box_host[2 * kBox * i], &c->box_host[2 * kBox * i + kBox], &out[i]);
   }
   if (n == 1 && c->profiling && tm.k == 8) {  // 8 marks bound the 7 stages
@@ -807,34 +832,96 @@ int lsr_stage_match(lsr_ctx *c, const float *FP, int64_t nP, const float *FQ, in
   if (rc) return rc;
   if (!FP || !FQ || !nn || nP < 1 || nQ < 1 || nP > kMaxPoints || nQ > kMaxPoints)
     return set_err(c, LSR_E_ARG, "bad argument");
-  if (precision != LSR_MATCH_FP32 && precision != LSR_MATCH_BF16) return set_err(c, LSR_E_ARG, "bad precision");
-  auto plan = [&](Arena &a, float *&fp, float *&fq, float *&FPi, float *&FQi, int *&dn, float *&dd) {
+  if (!valid_precision(precision)) return set_err(c, LSR_E_ARG, "bad precision");
+  const bool tc = precision != LSR_MATCH_FP32, split = precision == LSR_MATCH_BF16;
+  auto plan = [&](Arena &a, float *&fp, float *&fq, float *&FPi, float *&FQi, int *&dn, float *&dd, int *&flags,
+                  char *&tws) {
     fp = a.take<float>(kD * nP);
     fq = a.take<float>(kD * nQ);
     FPi = a.take<float>(kDS * nP);
     FQi = a.take<float>(kDS * nQ);
     dn = a.take<int>(nP);
     dd = a.take<float>(nP);
+    flags = a.take<int>(2);
+    tws = tc ? a.take<char>(tc_workspace_bytes((int)nP, (int)nQ, split)) : nullptr;
   };
   Arena m(nullptr);
   float *x1, *x2, *x3, *x4, *x6;
-  int *x5;
-  plan(m, x1, x2, x3, x4, x5, x6);
+  int *x5, *x7;
+  char *x8;
+  plan(m, x1, x2, x3, x4, x5, x6, x7, x8);
   if ((rc = ensure_ws(c, m.off))) return rc;
   Arena a(c->ws);
   float *fp, *fq, *FPi, *FQi, *dd;
-  int *dn;
-  plan(a, fp, fq, FPi, FQi, dn, dd);
+  int *dn, *flags;
+  char *tws;
+  plan(a, fp, fq, FPi, FQi, dn, dd, flags, tws);
   cudaStream_t s = c->stream;
   TRY_CUDA(c, cudaMemcpyAsync(fp, FP, sizeof(float) * kD * nP, cudaMemcpyDefault, s), "copy FP");
   TRY_CUDA(c, cudaMemcpyAsync(fq, FQ, sizeof(float) * kD * nQ, cudaMemcpyDefault, s), "copy FQ");
   LSR_LAUNCH(k_gather_rows<<<nblk(nP * kDS), 256, 0, s>>>(fp, kD, nullptr, (int)nP, FPi));
   LSR_LAUNCH(k_gather_rows<<<nblk(nQ * kDS), 256, 0, s>>>(fq, kD, nullptr, (int)nQ, FQi));
-  TRY_CUDA(c, launch_match_fp32(FPi, (int)nP, FQi, (int)nQ, dn, dd, s), "match");
+  if (tc)
+    TRY_CUDA(c, launch_match_bf16(FPi, (int)nP, FQi, (int)nQ, split, tws, dn, dd, flags, flags + 1, nullptr, s),
+             "match");
+  else
+    TRY_CUDA(c, launch_match_fp32(FPi, (int)nP, FQi, (int)nQ, dn, dd, s), "match");
+  int hflags[2] = {0, 0};
+  if (tc) TRY_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s), "copy flags");
   if ((rc = copy_out(c, nn, dn, sizeof(int) * nP))) return rc;
   if (d1 && (rc = copy_out(c, d1, dd, sizeof(float) * nP))) return rc;
   TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
-  if (fallbacks) *fallbacks = 0;
+  if (hflags[1]) return set_err(c, LSR_E_TIMEOUT, "BF16 matcher timed out waiting on the tensor cores");
+  if (fallbacks) *fallbacks = hflags[0];
+  return LSR_OK;
+}
+
+int lsr_match_scores_bf16(lsr_ctx *c, const float *FP, int64_t nP, const float *FQ, int64_t nQ, int32_t precision,
+                          float *scores) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!FP || !FQ || !scores || nP < 1 || nQ < 1 || nP > 65536 || nQ > 65536)
+    return set_err(c, LSR_E_ARG, "bad argument");
+  if (precision != LSR_MATCH_BF16 && precision != LSR_MATCH_BF16_PLAIN)
+    return set_err(c, LSR_E_ARG, "bad precision");
+  const bool split = precision == LSR_MATCH_BF16;
+  const int cols = tc_score_cols((int)nQ);
+  auto plan = [&](Arena &a, float *&fp, float *&fq, float *&FPi, float *&FQi, float *&sc, int *&flags,
+                  char *&tws) {
+    fp = a.take<float>(kD * nP);
+    fq = a.take<float>(kD * nQ);
+    FPi = a.take<float>(kDS * nP);
+    FQi = a.take<float>(kDS * nQ);
+    sc = a.take<float>((size_t)nP * cols);
+    flags = a.take<int>(2);
+    tws = a.take<char>(tc_workspace_bytes((int)nP, (int)nQ, split));
+  };
+  Arena m(nullptr);
+  float *x1, *x2, *x3, *x4, *x5;
+  int *x6;
+  char *x7;
+  plan(m, x1, x2, x3, x4, x5, x6, x7);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  float *fp, *fq, *FPi, *FQi, *sc;
+  int *flags;
+  char *tws;
+  plan(a, fp, fq, FPi, FQi, sc, flags, tws);
+  cudaStream_t s = c->stream;
+  TRY_CUDA(c, cudaMemcpyAsync(fp, FP, sizeof(float) * kD * nP, cudaMemcpyDefault, s), "copy FP");
+  TRY_CUDA(c, cudaMemcpyAsync(fq, FQ, sizeof(float) * kD * nQ, cudaMemcpyDefault, s), "copy FQ");
+  LSR_LAUNCH(k_gather_rows<<<nblk(nP * kDS), 256, 0, s>>>(fp, kD, nullptr, (int)nP, FPi));
+  LSR_LAUNCH(k_gather_rows<<<nblk(nQ * kDS), 256, 0, s>>>(fq, kD, nullptr, (int)nQ, FQi));
+  TRY_CUDA(c, launch_match_bf16(FPi, (int)nP, FQi, (int)nQ, split, tws, nullptr, nullptr, flags, flags + 1, sc, s),
+           "scores");
+  int hflags[2] = {0, 0};
+  TRY_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s), "copy flags");
+  TRY_CUDA(c,
+           cudaMemcpy2DAsync(scores, sizeof(float) * nQ, sc, sizeof(float) * cols, sizeof(float) * nQ, nP,
+                             cudaMemcpyDefault, s),
+           "copy scores");
+  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  if (hflags[1]) return set_err(c, LSR_E_TIMEOUT, "BF16 matcher timed out waiting on the tensor cores");
   return LSR_OK;
 }
 
@@ -974,7 +1061,9 @@ int lsr_stage_consensus(lsr_ctx *c, const float *P, int64_t nP, const float *Q, 
   TRY_CUDA(c, build_cloud(qsrc, Cq, eps, eps, eps, false, true, S, s), "grid Q");
   TRY_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int) * nh, s), "memset");
   TRY_CUDA(c, cudaMemsetAsync(sum, 0, sizeof(unsigned long long) * nh, s), "memset");
-  TRY_CUDA(c, launch_consensus(XP, (int)nP, Cq.ge, Cq.start_e, Cq.Xe, pose, nullptr, nullptr, (int)nh, eps, cnt, sum, s),
+  TRY_CUDA(c,
+           launch_consensus(XP, (int)nP, Cq.ge, Cq.start_e, Cq.Xe, pose, nullptr, nullptr, (int)nh, eps, cnt, sum, s,
+                            c->cons_lanes),
            "consensus");
   LSR_LAUNCH(k_sum_to_double<<<nblk(nh), 256, 0, s>>>(sum, (int)nh, sd));
   if ((rc = copy_out(c, count, cnt, sizeof(int) * nh))) return rc;

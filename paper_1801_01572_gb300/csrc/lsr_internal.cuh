@@ -226,6 +226,20 @@ cudaError_t launch_fpfh(const float4 *X, const float4 *N, const float *spfh, int
 
 // ----------------------------------------------------------------- matching (lsr_match.cu)
 cudaError_t launch_match_fp32(const float *FP, int nP, const float *FQ, int nQ, int *nn, float *d1, cudaStream_t s);
+// Exact FP32 scan of the queries rows[0..*nrows) (count read on the device),
+// split over database chunks; packed: scratch of nP 64-bit words.
+cudaError_t launch_match_fp32_rows(const float *FP, int nP, const float *FQ, int nQ, const int *rows,
+                                   const int *nrows, unsigned long long *packed, int *nn, float *d1,
+                                   cudaStream_t s);
+// BF16 tensor-core matcher (split: hi/lo BF16 pairs, K = 112; else K = 48)
+// with exact FP32 re-rank and certified fallback; ws: tc_workspace_bytes.
+// fb_count: queries re-scanned in FP32; err: 1 if a CTA gave up waiting. With
+// d2 != null it writes D~^2 = |b~|^2 - 2 a~.b~ + |a~|^2 for every pair (nP
+// rows of tc_score_cols(nQ)) instead of matching.
+size_t tc_workspace_bytes(int nP, int nQ, bool split);
+int tc_score_cols(int nQ);
+cudaError_t launch_match_bf16(const float *FP, int nP, const float *FQ, int nQ, bool split, char *ws, int *nn,
+                              float *d1, int *fb_count, int *err, float *d2, cudaStream_t s);
 
 // ----------------------------------------------------------------- RANSAC (lsr_ransac.cu)
 // Device-side counters and selection state of one registration.
@@ -243,6 +257,8 @@ struct RansacState {
   int final_count;
   int level_iters;     // refinement steps taken at the current level
   unsigned ticket;     // blocks finished in the current refinement step
+  int match_fallbacks; // BF16 matcher: queries re-scanned exactly in FP32
+  int match_err;       // BF16 matcher: a CTA gave up waiting (result invalid)
   int pad_;
   double final_sumd2;
   double T[16];        // current pose (refinement), row-major
@@ -267,7 +283,7 @@ cudaError_t launch_rigid4(const float *ps, const float *qs, int nh, float *pose,
 // count[k] / sum[k] (fixed point, 2^-40 m^2 units) over all P points.
 cudaError_t launch_consensus(const float4 *XP, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
                              const float *pose, const uint8_t *ok, const int *n_dev, int n_host, float eps,
-                             int *count, unsigned long long *sum, cudaStream_t s);
+                             int *count, unsigned long long *sum, cudaStream_t s, int lanes = 1);
 cudaError_t launch_select(const int *surv, const int *count, const unsigned long long *sum, const uint8_t *ok,
                           const float *pose, int nP, float min_ratio, RansacState *st, cudaStream_t s);
 constexpr double kFixScale = 1099511627776.0;  // 2^40

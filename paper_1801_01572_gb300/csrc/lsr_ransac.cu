@@ -299,7 +299,7 @@ __global__ void k_rigid4(const float *ps, const float *qs, int nh, float *pose) 
 // the order of the atomic adds.
 constexpr int kConsThreads = 256;
 constexpr int kConsChunk = 2048;
-constexpr int kConsG = 1;  // lanes per query (most queries end at the mask test)
+
 
 // Minimum squared distance below eps2 by a group of G lanes (no index needed).
 template <int G>
@@ -332,12 +332,13 @@ __device__ __forceinline__ float group_min_d2(const GridParams &g, const int *__
   return best;
 }
 
+template <int G>
 __global__ void __launch_bounds__(kConsThreads) k_consensus(const float4 *__restrict__ XP, int nP, const GridParams *gep,
                                                             const int *__restrict__ start,
                                                             const float4 *__restrict__ Xe, const float *__restrict__ pose,
                                                             const uint8_t *__restrict__ ok, const int *n_dev, int n_host,
                                                             float eps2, int *count, unsigned long long *sum) {
-  constexpr int G = kConsG, GPB = kConsThreads / G;
+  constexpr int GPB = kConsThreads / G;
   const GridParams g = *gep;
   int nh = n_dev ? *n_dev : n_host;
   int chunks = (nP + kConsChunk - 1) / kConsChunk;
@@ -479,8 +480,19 @@ cudaError_t launch_rigid4(const float *ps, const float *qs, int nh, float *pose,
 
 cudaError_t launch_consensus(const float4 *XP, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
                              const float *pose, const uint8_t *ok, const int *n_dev, int n_host, float eps, int *count,
-                             unsigned long long *sum, cudaStream_t s) {
-  LSR_LAUNCH(k_consensus<<<152 * 8, kConsThreads, 0, s>>>(XP, nP, ge, start_e, Xe, pose, ok, n_dev, n_host, eps * eps, count, sum));
+                             unsigned long long *sum, cudaStream_t s, int lanes) {
+  float e2 = eps * eps;
+#define LSR_CONS(G)                                                                                            \
+  LSR_LAUNCH(k_consensus<G><<<152 * 8, kConsThreads, 0, s>>>(XP, nP, ge, start_e, Xe, pose, ok, n_dev, n_host, e2, \
+                                                             count, sum))
+  switch (lanes) {
+    case 2: LSR_CONS(2); break;
+    case 4: LSR_CONS(4); break;
+    case 8: LSR_CONS(8); break;
+    case 16: LSR_CONS(16); break;
+    default: LSR_CONS(1); break;
+  }
+#undef LSR_CONS
   return cudaGetLastError();
 }
 

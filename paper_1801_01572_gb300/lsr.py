@@ -20,7 +20,7 @@ _lock = threading.Lock()
 
 LSR_OK, LSR_E_ARG, LSR_E_CUDA, LSR_E_OOM, LSR_E_TIMEOUT, LSR_E_STATE, LSR_E_TOO_LARGE = 0, -1, -2, -3, -4, -5, -6
 STATUS_ALIGNED, STATUS_NO_ALIGNMENT = 0, 1
-MATCH_FP32, MATCH_BF16 = 0, 1
+MATCH_FP32, MATCH_BF16, MATCH_BF16_PLAIN = 0, 1, 2
 DESC_DIM = 33
 
 # Names of every entry point declared in include/lsr.h (checked by the tests).
@@ -30,7 +30,7 @@ ABI_FUNCTIONS = (
     "lsr_register_pair", "lsr_register_batch",
     "lsr_stage_normals", "lsr_stage_spfh", "lsr_stage_fpfh", "lsr_stage_match", "lsr_stage_hypotheses",
     "lsr_stage_rigid4", "lsr_stage_consensus", "lsr_stage_refine", "lsr_objective_fwd", "lsr_objective_bwd",
-    "lsr_consensus_static",
+    "lsr_consensus_static", "lsr_match_scores_bf16",
 )
 
 
@@ -90,6 +90,7 @@ def lib():
             "lsr_stage_spfh": (C.c_int, [vp, vp, vp, i64, f32, vp, vp]),
             "lsr_stage_fpfh": (C.c_int, [vp, vp, vp, vp, i64, f32, vp]),
             "lsr_stage_match": (C.c_int, [vp, vp, i64, vp, i64, i32, vp, vp, vp]),
+            "lsr_match_scores_bf16": (C.c_int, [vp, vp, i64, vp, i64, i32, vp]),
             "lsr_stage_hypotheses": (C.c_int, [vp, vp, i64, vp, i64, vp, vp, vp, i64, u64, u64, f32, vp, i64, vp]),
             "lsr_stage_rigid4": (C.c_int, [vp, vp, vp, i64, vp]),
             "lsr_stage_consensus": (C.c_int, [vp, vp, i64, vp, i64, vp, i64, f32, vp, vp]),
@@ -313,6 +314,16 @@ class Context:
         self._check(self._L.lsr_stage_match(self._h, pA, nA, pB, nB, int(precision), C.c_void_p(nn.ctypes.data),
                                             C.c_void_p(d1.ctypes.data), C.byref(fb)))
         return nn, d1, int(fb.value)
+
+    def match_scores_bf16(self, FP, FQ, precision=None):
+        """Tensor-core approximations of |FP_i - FQ_j|^2 (nP x nQ float32)."""
+        precision = MATCH_BF16 if precision is None else precision
+        pA, kA, nA = _prep(FP, np.float32, DESC_DIM)
+        pB, kB, nB = _prep(FQ, np.float32, DESC_DIM)
+        out = np.zeros((nA, nB), np.float32)
+        self._check(self._L.lsr_match_scores_bf16(self._h, pA, nA, pB, nB, int(precision),
+                                                  C.c_void_p(out.ctypes.data)))
+        return out
 
     def stage_hypotheses(self, P, Q, nn, validP, validQ, H, seed, pair_id=0, tau=0.9, cap=None):
         pP, kP, nP = _prep(P, np.float32, 3)
