@@ -8,7 +8,11 @@ workload is the 150,000-point room pair on a 1 cm grid, FP32 end to end.
 Inputs are resident in HBM when the timed region starts and L2 is flushed
 (a 256 MB write) between steps, outside the timed events. Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 0|1] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 0|1] [--match fp32|bf16|bf16_plain]
+                  [--impl ours|reference]
+
+--match selects the descriptor matcher (FP32 SIMT, or the tensor-core matcher
+with hi/lo or plain BF16 operands); every choice gives the same correspondences.
 
 --impl reference times the FP64 CPU oracle (the only reference for this path)
 on a bounded sample of the same workload, scaled to one pair.
@@ -35,6 +39,7 @@ WORKLOADS = {
     0: "objects scene pair, 5,000 points per cloud, 70% overlap, 10% outliers, 4M hypotheses, FP32",
     1: "indoor room pair on a 1 cm voxel grid, 150,000 points per cloud, 50% overlap, 4M hypotheses, FP32",
 }
+MATCH_MODES = {"fp32": 0, "bf16": 1, "bf16_plain": 2}
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
@@ -119,7 +124,7 @@ def run_ours(args, rank, world):
     P = torch.from_numpy(fp.P).cuda()
     Q = torch.from_numpy(fp.Q).cuda()
     stream = torch.cuda.Stream()
-    ctx = lsr.Context(dev, stream=stream.cuda_stream)
+    ctx = lsr.Context(dev, stream=stream.cuda_stream, match_precision=MATCH_MODES[args.match])
     ctx.set_profiling(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
@@ -176,7 +181,7 @@ def run_ours(args, rank, world):
     h2d, d2h = lsr.transfer_bytes(nP, nQ)
     info = dict(fp=fp, nP=nP, nQ=nQ, last=last, stage_ms=stage_ms, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d,
                 d2h=d2h, launches=launches, clocks=clk.summary(pk.get("sm_max_mhz")), peaks=pk,
-                params=ctx.params)
+                params=ctx.params, match=args.match)
     ctx.close()
     return info
 
@@ -190,6 +195,16 @@ def roofline(info):
     k = int(np.argmax(st[:7]))
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # FFMA TFLOP/s
+    if names[k] == "matching" and info["match"] != "fp32":
+        # tensor-core contraction: 2 flop per multiply-add over K = 112 (hi/lo
+        # split) or 48 (plain) operand columns, for every (query, database row)
+        K = 112 if info["match"] == "bf16" else 48
+        flops = 2.0 * float(nP) * float(nQ) * K
+        ach = flops / (st[k] * 1e-3) / 1e12
+        peak = float(pk["bf16_tflops"])
+        return {"kernel": "k_match_tc", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_source": f"{src} bf16 burst (cuBLAS)",
+                "work": f"2*nP*nQ*{K} flop (stage time incl. operand preparation, re-rank and exact fallback)"}
     if names[k] == "matching":
         # brute-force FP32 NN: per (query, candidate) pair 33 subtract + 33 fused multiply-add
         flops = float(nP) * float(nQ) * 33 * 3
@@ -318,6 +333,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--match", default="fp32", choices=sorted(MATCH_MODES))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -347,7 +363,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": info["total_ms"] / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.config], "points": [info["nP"], info["nQ"]],
-                       "hypotheses": int(prm.n_hypotheses), "match": "fp32", "refine_levels": int(prm.refine_levels),
+                       "hypotheses": int(prm.n_hypotheses), "match": args.match, "refine_levels": int(prm.refine_levels),
                        "l2": "flushed between steps by a 256 MB write outside the timed events",
                        "parallelism": "replicas (one pair per GPU)" if world > 1 else "single GPU"},
             "points_per_s": value * (info["nP"] + info["nQ"]),
@@ -355,7 +371,7 @@ def main():
                 ["grids", "normals", "features", "matching", "hypotheses", "consensus", "refinement", "total"],
                 info["stage_ms"])},
             "result": {"inliers": last.inliers, "survivors": last.survivors, "normal_ok": last.n_normal_ok,
-                       "refine_iters": last.refine_iters},
+                       "refine_iters": last.refine_iters, "match_fallbacks": last.match_fallbacks},
             "roofline": roofline(info),
             "e2e": {"value": e2e, "unit": "pairs/s", "h2d_bytes_per_step": info["h2d"] * world,
                     "d2h_bytes_per_step": info["d2h"] * world},

@@ -170,6 +170,14 @@ struct PairLayout {
   unsigned long long *fsum = nullptr;
   RansacState *st = nullptr;
   char *tc_ws = nullptr;  // BF16 matcher workspace (BF16 precision only)
+  ClsParams *cls = nullptr;  // consensus voxel classification of Q
+  unsigned *in_bits = nullptr, *near_bits = nullptr;
+  uint8_t *sel = nullptr;    // the hypotheses with the largest count upper bounds
+  uint8_t *rest = nullptr;   // the others whose upper bound reaches their best count
+  uint8_t *reach = nullptr;  // sel | rest: the hypotheses counted exactly
+  uint8_t *tie = nullptr;    // those tied at the maximum exact count
+  int *amb = nullptr;        // points in undecided voxels per hypothesis
+  int *count2 = nullptr;     // exact counts of the reaching hypotheses
 };
 
 int surv_cap_for(int64_t H) { return (int)std::min<int64_t>(H, (int64_t)1 << 22); }
@@ -197,6 +205,15 @@ void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int leve
   L.fcount = a.take<int>(1);
   L.fsum = a.take<unsigned long long>(1);
   L.st = a.take<RansacState>(1);
+  L.cls = a.take<ClsParams>(1);
+  L.in_bits = a.take<unsigned>(kClsCapWords);
+  L.near_bits = a.take<unsigned>(kClsCapWords);
+  L.sel = a.take<uint8_t>(L.surv_cap);
+  L.rest = a.take<uint8_t>(L.surv_cap);
+  L.reach = a.take<uint8_t>(L.surv_cap);
+  L.tie = a.take<uint8_t>(L.surv_cap);
+  L.amb = a.take<int>(L.surv_cap);
+  L.count2 = a.take<int>(L.surv_cap);
   if (precision != LSR_MATCH_FP32)
     L.tc_ws = a.take<char>(tc_workspace_bytes(nP, nQ, precision == LSR_MATCH_BF16));
 }
@@ -442,14 +459,37 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
            launch_rigid_survivors(Pc.X, Pc.inv, Pc.N, nP, Qc.X, Qc.N, L.nn, L.surv, L.st, p.seed, pair_id,
                                   p.cos_normal, L.pose, L.ok, &L.st->n_normal_ok, s),
            "rigid");
+  // Inlier-count bounds of every survivor from the voxel classification of Q;
+  // exact counts of the 32 largest upper bounds give C; exact counts of the
+  // others whose upper bound reaches C; distance sums of the top ties. No
+  // survivor left out can be selected.
+  TRY_CUDA(c, launch_cls_build(Qc.box, p.eps_inlier, Qc.X, nQ, L.cls, L.in_bits, L.near_bits, s), "classify");
   TRY_CUDA(c, cudaMemsetAsync(L.count, 0, sizeof(int) * L.surv_cap, s), "memset count");
+  TRY_CUDA(c, cudaMemsetAsync(L.amb, 0, sizeof(int) * L.surv_cap, s), "memset count");
+  TRY_CUDA(c, cudaMemsetAsync(L.count2, 0, sizeof(int) * L.surv_cap, s), "memset count");
   TRY_CUDA(c, cudaMemsetAsync(L.sum, 0, sizeof(unsigned long long) * L.surv_cap, s), "memset sum");
   TRY_CUDA(c,
-           launch_consensus(Pc.X, nP, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.ok, &L.st->n_surv, 0, p.eps_inlier, L.count,
-                            L.sum, s, c->cons_lanes),
-           "consensus");
+           launch_consensus_bounds(Pc.X, nP, L.cls, L.in_bits, L.near_bits, L.pose, L.ok, &L.st->n_surv, L.count,
+                                   L.amb, s),
+           "consensus bounds");
+  TRY_CUDA(c, launch_top_upper(L.count, L.amb, L.ok, &L.st->n_surv, 32, L.sel, s), "top");
+  TRY_CUDA(c,
+           launch_consensus_count(Pc.X, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.sel,
+                                  &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
+           "consensus top");
+  TRY_CUDA(c, launch_reach_rest(L.count, L.amb, L.count2, L.sel, L.ok, &L.st->n_surv, L.rest, L.reach, s), "reach");
+  TRY_CUDA(c,
+           launch_consensus_count(Pc.X, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.rest,
+                                  &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
+           "consensus reach");
+  TRY_CUDA(c, launch_reach_mask(L.count2, nullptr, L.reach, &L.st->n_surv, L.tie, s), "ties");
+  // (the exact kernel adds its counts too: into amb, no longer needed)
+  TRY_CUDA(c,
+           launch_consensus(Pc.X, nP, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.tie, &L.st->n_surv, 0, p.eps_inlier,
+                            L.amb, L.sum, s, c->cons_lanes),
+           "consensus sums");
   tm.mark();
-  TRY_CUDA(c, launch_select(L.surv, L.count, L.sum, L.ok, L.pose, nP, p.min_inlier_ratio, L.st, s), "select");
+  TRY_CUDA(c, launch_select(L.surv, L.count2, L.sum, L.reach, L.pose, nP, p.min_inlier_ratio, L.st, s), "select");
   TRY_CUDA(c, launch_refine_init(L.st, Pc.box, nullptr, s), "refine init");
   float eps = p.eps_inlier;
   TRY_CUDA(c,
@@ -1022,49 +1062,65 @@ int lsr_stage_consensus(lsr_ctx *c, const float *P, int64_t nP, const float *Q, 
   if (!P || !Q || !Rt || !count || !sumd2 || nP < 1 || nQ < 1 || nP > kMaxPoints || nQ > kMaxPoints || nh < 1 ||
       nh > ((int64_t)1 << 26) || !(eps > 0.f && eps <= 10.f))
     return set_err(c, LSR_E_ARG, "bad argument");
-  auto plan = [&](Arena &a, float *&p, float4 *&XP, CloudLayout &Cq, ScratchLayout &S, float *&pose, int *&cnt,
-                  unsigned long long *&sum, double *&sd) {
-    p = a.take<float>(3 * nP);
-    XP = a.take<float4>(nP);
-    plan_cloud(a, (int)nQ, true, false, true, Cq);
-    plan_scratch(a, (int)nQ, Cq.cap_f, S);
-    pose = a.take<float>(12 * nh);
-    cnt = a.take<int>(nh);
-    sum = a.take<unsigned long long>(nh);
-    sd = a.take<double>(nh);
+  struct Bufs {
+    float *p, *pose;
+    float4 *XP;
+    CloudLayout Cq;
+    ScratchLayout S;
+    int *cnt, *cnt2;
+    unsigned long long *sum;
+    double *sd;
+    ClsParams *cls;
+    unsigned *in_bits, *near_bits;
+  };
+  auto plan = [&](Arena &a, Bufs &b) {
+    b.p = a.take<float>(3 * nP);
+    b.XP = a.take<float4>(nP);
+    plan_cloud(a, (int)nQ, true, false, true, b.Cq);
+    plan_scratch(a, (int)nQ, b.Cq.cap_f, b.S);
+    b.pose = a.take<float>(12 * nh);
+    b.cnt = a.take<int>(nh);
+    b.cnt2 = a.take<int>(nh);
+    b.sum = a.take<unsigned long long>(nh);
+    b.sd = a.take<double>(nh);
+    b.cls = a.take<ClsParams>(1);
+    b.in_bits = a.take<unsigned>(kClsCapWords);
+    b.near_bits = a.take<unsigned>(kClsCapWords);
   };
   Arena m(nullptr);
-  float *z1, *z5;
-  float4 *z2;
-  CloudLayout z3;
-  ScratchLayout z4;
-  int *z6;
-  unsigned long long *z7;
-  double *z8;
-  plan(m, z1, z2, z3, z4, z5, z6, z7, z8);
+  Bufs bm;
+  plan(m, bm);
   if ((rc = ensure_ws(c, m.off))) return rc;
   Arena a(c->ws);
-  float *p, *pose;
-  float4 *XP;
-  CloudLayout Cq;
-  ScratchLayout S;
-  int *cnt;
-  unsigned long long *sum;
-  double *sd;
-  plan(a, p, XP, Cq, S, pose, cnt, sum, sd);
+  Bufs b;
+  plan(a, b);
+  float *p = b.p, *pose = b.pose;
+  float4 *XP = b.XP;
+  CloudLayout &Cq = b.Cq;
+  int *cnt = b.cnt;
+  unsigned long long *sum = b.sum;
+  double *sd = b.sd;
   cudaStream_t s = c->stream;
   TRY_CUDA(c, cudaMemcpyAsync(p, P, sizeof(float) * 3 * nP, cudaMemcpyDefault, s), "copy P");
   const float *qsrc;
   if ((rc = stage_input(c, Q, nQ, Cq.src, &qsrc))) return rc;
   TRY_CUDA(c, cudaMemcpyAsync(pose, Rt, sizeof(float) * 12 * nh, cudaMemcpyDefault, s), "copy Rt");
   LSR_LAUNCH(k_pack<<<nblk(nP), 256, 0, s>>>(p, (int)nP, XP));
-  TRY_CUDA(c, build_cloud(qsrc, Cq, eps, eps, eps, false, true, S, s), "grid Q");
+  TRY_CUDA(c, build_cloud(qsrc, Cq, eps, eps, eps, false, true, b.S, s), "grid Q");
   TRY_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int) * nh, s), "memset");
+  TRY_CUDA(c, cudaMemsetAsync(b.cnt2, 0, sizeof(int) * nh, s), "memset");
   TRY_CUDA(c, cudaMemsetAsync(sum, 0, sizeof(unsigned long long) * nh, s), "memset");
+  // counts as the registration pipeline takes them (voxel classification),
+  // sums from the exact kernel
+  TRY_CUDA(c, launch_cls_build(Cq.box, eps, Cq.X, (int)nQ, b.cls, b.in_bits, b.near_bits, s), "classify");
   TRY_CUDA(c,
-           launch_consensus(XP, (int)nP, Cq.ge, Cq.start_e, Cq.Xe, pose, nullptr, nullptr, (int)nh, eps, cnt, sum, s,
-                            c->cons_lanes),
+           launch_consensus_count(XP, (int)nP, b.cls, b.in_bits, b.near_bits, Cq.ge, Cq.start_e, Cq.Xe, pose, nullptr,
+                                  nullptr, (int)nh, eps, cnt, s),
            "consensus");
+  TRY_CUDA(c,
+           launch_consensus(XP, (int)nP, Cq.ge, Cq.start_e, Cq.Xe, pose, nullptr, nullptr, (int)nh, eps, b.cnt2, sum, s,
+                            c->cons_lanes),
+           "consensus sums");
   LSR_LAUNCH(k_sum_to_double<<<nblk(nh), 256, 0, s>>>(sum, (int)nh, sd));
   if ((rc = copy_out(c, count, cnt, sizeof(int) * nh))) return rc;
   if ((rc = copy_out(c, sumd2, sd, sizeof(double) * nh))) return rc;

@@ -1,0 +1,359 @@
+// lsr_classify.cu -- hypothesis testing (Alg. 1, "Find all inliers") through a
+// voxel classification of Q.
+//
+// Inlier counting asks, for every (hypothesis, point of P), whether the
+// transformed point x has a Q point closer than eps. Most x are either deep
+// inside the eps-neighbourhood of Q's surface or far from it, so the answer is
+// read from a table: Q's box (grown by eps) is cut into voxels of h = eps / k
+// (k = 8, 6, 4, ... as fits the table), and two bit-sets are splatted from the
+// Q points, with c the voxel centre and rho = sqrt(3) h / 2 its half diagonal:
+//   IN   some q has |c - q| <= eps - rho - m: every x of the voxel is an inlier;
+//   NEAR some q has |c - q| <= eps + rho + m: without it no x of the voxel is.
+// m covers the FP32 rounding of voxel coordinates and of the distance test, so
+// a voxel is IN or not-NEAR only if the exact test (d^2 < eps^2 in FP32 over the
+// eps grid of eq. (1)) gives the same answer for every point it can contain.
+// Points in NEAR-but-not-IN voxels take that exact test, one query at a time
+// across a whole warp, stopping at the first Q point within eps; the counts
+// are then identical to the exact consensus kernel's.
+//
+// Selection (the largest count wins, then the smaller mean squared distance)
+// does not need every count: without the exact tests the table bounds each
+// hypothesis's count between #IN and #IN + #undecided. The registration
+// pipeline counts exactly the K hypotheses with the largest upper bounds, takes
+// the largest of those counts as C, and counts exactly only the hypotheses
+// whose upper bound reaches C: no other can win or tie. The distance sums are
+// then computed for the hypotheses tied at the top.
+#include "lsr_internal.cuh"
+
+namespace lsr {
+
+namespace {
+
+constexpr int kClsThreads = 256;
+constexpr int kClsChunk = 2048;
+
+// Table geometry from Q's box: the finest voxel (eps / k) whose two bit-sets
+// fit kClsCapWords words each; all_amb = 1 if none does (every point then
+// takes the exact test).
+__global__ void k_cls_params(const float *box, float eps, ClsParams *cp) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const float ks[] = {8.f, 6.f, 4.f, 3.f, 2.f, 1.5f, 1.f, 0.5f, 0.25f, 0.125f, 0.0625f};
+  ClsParams c{};
+  c.all_amb = 1;
+  float lo[3] = {box[0], box[1], box[2]}, hi[3] = {box[3], box[4], box[5]};
+  float ext = fmaxf(fmaxf(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
+  float mag = fmaxf(fmaxf(fmaxf(fabsf(lo[0]), fabsf(hi[0])), fmaxf(fabsf(lo[1]), fabsf(hi[1]))),
+                    fmaxf(fabsf(lo[2]), fabsf(hi[2])));
+  if (box[6] == 0.f && ext >= 0.f && isfinite(ext) && isfinite(mag)) {
+    // rounding of coordinates relative to the table and of the FP32 distance test
+    c.m = 1e-6f * (ext + 2.f * eps) + 4e-7f * (mag + eps) + 1e-7f * eps + 1e-9f;
+    for (float k : ks) {
+      float h = eps / k;
+      float pad = eps + 2.f * h + c.m;
+      long long n[3];
+      bool fits = true;
+      for (int d = 0; d < 3; ++d) {
+        float e = (hi[d] - lo[d] + 2.f * pad) / h;
+        if (!(e < 1e9f)) fits = false;
+        n[d] = fits ? (long long)e + 2 : 0;
+      }
+      long long wx = (n[0] + 31) / 32;
+      if (!fits || wx * n[1] * n[2] > kClsCapWords) continue;
+      c.ox = lo[0] - pad, c.oy = lo[1] - pad, c.oz = lo[2] - pad;
+      c.h = h;
+      c.inv_h = 1.f / h;
+      c.nx = (int)n[0], c.ny = (int)n[1], c.nz = (int)n[2], c.wx = (int)wx;
+      float rho = 0.8660254f * h * (1.f + 1e-6f);
+      float r_in = eps - rho - c.m;
+      c.r_in2 = r_in > 0.f ? r_in * r_in * (1.f - 1e-6f) : -1.f;
+      c.r_near = (eps + rho + c.m) * (1.f + 1e-6f);
+      c.R = (int)ceilf(c.r_near / h) + 1;
+      c.all_amb = 0;
+      break;
+    }
+  }
+  *cp = c;
+}
+
+// One thread per (Q point, voxel plane dz around it), looping over the rows
+// dy: the NEAR bits of a row are set over an interval widened beyond the ball
+// (a superset), the IN bits voxel by voxel after an explicit distance check
+// (a subset).
+__global__ void k_cls_splat(const float4 *__restrict__ XQ, int nQ, const ClsParams *__restrict__ cpp,
+                            unsigned *__restrict__ in_bits, unsigned *__restrict__ near_bits) {
+  const ClsParams c = *cpp;
+  if (c.all_amb) return;
+  const int side = 2 * c.R + 1;
+  const long long total = (long long)nQ * side;
+  const float rn2 = c.r_near * c.r_near;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / side);
+    const int dz = (int)(t - (long long)i * side) - c.R;
+    const float4 q = XQ[i];
+    const float fx = (q.x - c.ox) * c.inv_h, fy = (q.y - c.oy) * c.inv_h, fz = (q.z - c.oz) * c.inv_h;
+    const int iz = (int)floorf(fz) + dz;
+    if (iz < 0 || iz >= c.nz) continue;
+    const float ez = fmaf((float)iz + 0.5f, c.h, c.oz) - q.z;
+    if (ez * ez > rn2) continue;
+    const int iy0 = (int)floorf(fy);
+    for (int dy = -c.R; dy <= c.R; ++dy) {
+      const int iy = iy0 + dy;
+      if (iy < 0 || iy >= c.ny) continue;
+      const float ey = fmaf((float)iy + 0.5f, c.h, c.oy) - q.y;
+      const float rem = rn2 - ey * ey - ez * ez;
+      if (rem < 0.f) continue;
+      const float half = sqrtf(rem) * (1.f + 1e-5f) + c.m;
+      int x0 = (int)floorf(fx - half * c.inv_h - 0.5f) - 1, x1 = (int)ceilf(fx + half * c.inv_h - 0.5f) + 1;
+      x0 = x0 < 0 ? 0 : x0;
+      x1 = x1 >= c.nx ? c.nx - 1 : x1;
+      if (x0 > x1) continue;
+      const size_t row = ((size_t)iz * c.ny + iy) * c.wx;
+      const float eyz = fmaf(ey, ey, ez * ez);
+      for (int w = x0 >> 5; w <= (x1 >> 5); ++w) {
+        const int b0 = max(x0, w * 32) - w * 32, b1 = min(x1, w * 32 + 31) - w * 32;
+        const unsigned near = (b1 == 31 ? 0xffffffffu : ((1u << (b1 + 1)) - 1u)) & ~((1u << b0) - 1u);
+        unsigned in = 0u;
+        if (c.r_in2 > 0.f && eyz <= c.r_in2) {
+          for (int b = b0; b <= b1; ++b) {
+            const float ex = fmaf((float)(w * 32 + b) + 0.5f, c.h, c.ox) - q.x;
+            if (fmaf(ex, ex, eyz) <= c.r_in2) in |= 1u << b;
+          }
+        }
+        atomicOr(near_bits + row + w, near);
+        if (in) atomicOr(in_bits + row + w, in);
+      }
+    }
+  }
+}
+
+// Whether a Q point lies closer than eps to (x, y, z): all 32 lanes walk the
+// eps-grid candidates of the same query and stop at the first hit.
+__device__ __forceinline__ bool warp_any_within(const GridParams &g, const int *__restrict__ start,
+                                                const float4 *__restrict__ Xe, float x, float y, float z,
+                                                float eps2) {
+  const int lane = threadIdx.x & 31;
+  bool hit = false;
+  grid_ranges(g, start, x, y, z, [&](int b, int e) {
+    if (hit) return;
+    for (int base = b; base < e; base += 32) {
+      int t = base + lane;
+      bool h = t < e && dist2(Xe[t], x, y, z) < eps2;
+      if (__any_sync(0xffffffffu, h)) {
+        hit = true;
+        return;
+      }
+    }
+  });
+  return hit;
+}
+
+// One thread block per (hypothesis, chunk of P), as the exact kernel; a lane
+// per point. kBounds: count IN points into count and undecided ones into amb.
+// Otherwise the undecided lanes are resolved by the whole warp, one at a time,
+// and count receives the exact inlier count.
+template <bool kBounds>
+__global__ void __launch_bounds__(kClsThreads) k_consensus_count(
+    const float4 *__restrict__ XP, int nP, const ClsParams *__restrict__ cpp, const unsigned *__restrict__ in_bits,
+    const unsigned *__restrict__ near_bits, const GridParams *__restrict__ gep, const int *__restrict__ start,
+    const float4 *__restrict__ Xe, const float *__restrict__ pose, const uint8_t *__restrict__ ok, const int *n_dev,
+    int n_host, float eps2, int *__restrict__ count, int *__restrict__ amb_count) {
+  const ClsParams c = *cpp;
+  const GridParams g = kBounds ? GridParams{} : *gep;
+  const int nh = n_dev ? *n_dev : n_host;
+  const int chunks = (nP + kClsChunk - 1) / kClsChunk;
+  const int64_t items = (int64_t)nh * chunks;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ int s_cnt[kClsThreads / 32], s_amb[kClsThreads / 32];
+  for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+    const int s = (int)(item / chunks), ch = (int)(item - (int64_t)s * chunks);
+    if (ok && !ok[s]) continue;
+    Rigid12 T;
+    T.load(pose + (size_t)s * 12);
+    const int i0 = ch * kClsChunk, i1 = min(nP, (ch + 1) * kClsChunk);
+    int cnt = 0, namb = 0;
+    for (int r = i0; r < i1; r += kClsThreads) {
+      const int i = r + threadIdx.x;
+      bool in = false, amb = false;
+      float x = 0.f, y = 0.f, z = 0.f;
+      if (i < i1) {
+        T.apply(XP[i], x, y, z);
+        if (c.all_amb) {
+          amb = true;
+        } else {
+          float fx = (x - c.ox) * c.inv_h, fy = (y - c.oy) * c.inv_h, fz = (z - c.oz) * c.inv_h;
+          if (fx >= 0.f && fx < (float)c.nx && fy >= 0.f && fy < (float)c.ny && fz >= 0.f && fz < (float)c.nz) {
+            int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+            size_t word = ((size_t)iz * c.ny + iy) * c.wx + (ix >> 5);
+            unsigned bit = 1u << (ix & 31);
+            if (__ldg(in_bits + word) & bit)
+              in = true;
+            else
+              amb = (__ldg(near_bits + word) & bit) != 0u;
+          }
+        }
+      }
+      cnt += in;
+      if (kBounds) {
+        namb += amb;
+        continue;
+      }
+      unsigned pend = __ballot_sync(0xffffffffu, amb);
+      while (pend) {
+        const int src = __ffs(pend) - 1;
+        pend &= pend - 1;
+        float qx = __shfl_sync(0xffffffffu, x, src), qy = __shfl_sync(0xffffffffu, y, src),
+              qz = __shfl_sync(0xffffffffu, z, src);
+        bool hit = warp_any_within(g, start, Xe, qx, qy, qz, eps2);
+        if (lane == src) cnt += hit;
+      }
+    }
+    cnt = warp_sum(cnt);
+    if (kBounds) namb = warp_sum(namb);
+    if (lane == 0) s_cnt[w] = cnt, s_amb[w] = namb;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tc = 0, ta = 0;
+      for (int k = 0; k < kClsThreads / 32; ++k) tc += s_cnt[k], ta += s_amb[k];
+      if (tc) atomicAdd(&count[s], tc);
+      if (kBounds && ta) atomicAdd(&amb_count[s], ta);
+    }
+    __syncthreads();
+  }
+}
+
+// One block: L = the maximum of lo over the ok hypotheses, then
+// mask[k] = ok[k] && lo[k] + extra[k] >= L (extra == null: 0), if L > 0.
+__global__ void __launch_bounds__(1024) k_reach_mask(const int *__restrict__ lo, const int *__restrict__ extra,
+                                                     const uint8_t *__restrict__ ok, const int *n_dev,
+                                                     uint8_t *__restrict__ mask) {
+  __shared__ int s_max[32];
+  const int n = *n_dev;
+  int mx = 0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    if (!ok || ok[k]) mx = max(mx, lo[k]);
+  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (int)(blockDim.x >> 5) ? s_max[threadIdx.x] : 0;
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (threadIdx.x == 0) s_max[0] = mx;
+  }
+  __syncthreads();
+  mx = s_max[0];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int up = lo[k] + (extra ? extra[k] : 0);
+    mask[k] = ((!ok || ok[k]) && (mx == 0 ? extra != nullptr : up >= mx)) ? 1 : 0;
+  }
+}
+
+// One block: the K ok hypotheses with the largest lo + extra (ties to the
+// smaller index), marked in sel (cleared first), by K rounds of block argmax.
+__global__ void __launch_bounds__(1024) k_top_upper(const int *__restrict__ lo, const int *__restrict__ extra,
+                                                    const uint8_t *__restrict__ ok, const int *n_dev, int K,
+                                                    uint8_t *__restrict__ sel) {
+  __shared__ long long s_best[32];
+  const int n = *n_dev;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) sel[k] = 0;
+  __syncthreads();
+  for (int round = 0; round < K; ++round) {
+    // key: upper bound in the high word, complemented index in the low word
+    long long best = -1;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      if ((ok && !ok[k]) || sel[k]) continue;
+      long long key = ((long long)(lo[k] + extra[k]) << 32) | (unsigned)(0x7fffffff - k);
+      best = key > best ? key : best;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      long long o = __shfl_xor_sync(0xffffffffu, best, off);
+      best = o > best ? o : best;
+    }
+    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long b = -1;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = s_best[w] > b ? s_best[w] : b;
+      if (b >= 0) sel[0x7fffffff - (int)(b & 0xffffffff)] = 1;
+    }
+    __syncthreads();
+  }
+}
+
+// One block: C = the maximum exact count among sel; then
+// rest[k] = ok[k] && !sel[k] && lo[k] + extra[k] >= C and all[k] = sel[k] | rest[k].
+__global__ void __launch_bounds__(1024) k_reach_rest(const int *__restrict__ lo, const int *__restrict__ extra,
+                                                     const int *__restrict__ exact, const uint8_t *__restrict__ sel,
+                                                     const uint8_t *__restrict__ ok, const int *n_dev,
+                                                     uint8_t *__restrict__ rest, uint8_t *__restrict__ all) {
+  __shared__ int s_max[32];
+  const int n = *n_dev;
+  int mx = 0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    if (sel[k]) mx = max(mx, exact[k]);
+  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_max[w]);
+    s_max[0] = m;
+  }
+  __syncthreads();
+  mx = s_max[0];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const bool r = (!ok || ok[k]) && !sel[k] && lo[k] + extra[k] >= mx;
+    rest[k] = r ? 1 : 0;
+    all[k] = (r || sel[k]) ? 1 : 0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_cls_build(const float *boxQ, float eps, const float4 *XQ, int nQ, ClsParams *cp, unsigned *in_bits,
+                             unsigned *near_bits, cudaStream_t s) {
+  LSR_CUDA_TRY(cudaMemsetAsync(in_bits, 0, sizeof(unsigned) * (size_t)kClsCapWords, s));
+  LSR_CUDA_TRY(cudaMemsetAsync(near_bits, 0, sizeof(unsigned) * (size_t)kClsCapWords, s));
+  LSR_LAUNCH(k_cls_params<<<1, 32, 0, s>>>(boxQ, eps, cp));
+  LSR_LAUNCH(k_cls_splat<<<152 * 16, 256, 0, s>>>(XQ, nQ, cp, in_bits, near_bits));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_consensus_count(const float4 *XP, int nP, const ClsParams *cp, const unsigned *in_bits,
+                                   const unsigned *near_bits, const GridParams *ge, const int *start_e,
+                                   const float4 *Xe, const float *pose, const uint8_t *ok, const int *n_dev,
+                                   int n_host, float eps, int *count, cudaStream_t s) {
+  LSR_LAUNCH(k_consensus_count<false><<<152 * 8, kClsThreads, 0, s>>>(XP, nP, cp, in_bits, near_bits, ge, start_e, Xe,
+                                                                       pose, ok, n_dev, n_host, eps * eps, count,
+                                                                       nullptr));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_consensus_bounds(const float4 *XP, int nP, const ClsParams *cp, const unsigned *in_bits,
+                                    const unsigned *near_bits, const float *pose, const uint8_t *ok, const int *n_dev,
+                                    int *in_count, int *amb_count, cudaStream_t s) {
+  LSR_LAUNCH(k_consensus_count<true><<<152 * 8, kClsThreads, 0, s>>>(XP, nP, cp, in_bits, near_bits, nullptr, nullptr,
+                                                                      nullptr, pose, ok, n_dev, 0, 0.f, in_count,
+                                                                      amb_count));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_top_upper(const int *lo, const int *extra, const uint8_t *ok, const int *n_dev, int K,
+                             uint8_t *sel, cudaStream_t s) {
+  LSR_LAUNCH(k_top_upper<<<1, 1024, 0, s>>>(lo, extra, ok, n_dev, K, sel));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reach_rest(const int *lo, const int *extra, const int *exact, const uint8_t *sel, const uint8_t *ok,
+                              const int *n_dev, uint8_t *rest, uint8_t *all, cudaStream_t s) {
+  LSR_LAUNCH(k_reach_rest<<<1, 1024, 0, s>>>(lo, extra, exact, sel, ok, n_dev, rest, all));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reach_mask(const int *lo, const int *extra, const uint8_t *ok, const int *n_dev, uint8_t *mask,
+                              cudaStream_t s) {
+  LSR_LAUNCH(k_reach_mask<<<1, 1024, 0, s>>>(lo, extra, ok, n_dev, mask));
+  return cudaGetLastError();
+}
+
+}  // namespace lsr

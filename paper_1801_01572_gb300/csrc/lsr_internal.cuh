@@ -171,6 +171,27 @@ __device__ __forceinline__ void group_nn(const GridParams &g, const int *__restr
   }
 }
 
+// Squared distance with an explicit operation order: every kernel that
+// decides d^2 < eps^2 for the same pair of points decides it the same way.
+__device__ __forceinline__ float dist2(float4 q, float x, float y, float z) {
+  float dx = q.x - x, dy = q.y - y, dz = q.z - z;
+  return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+// x = R p + t for a row-major [R | t] (12 floats), in one fixed order.
+struct Rigid12 {
+  float r0, r1, r2, t0, r3, r4, r5, t1, r6, r7, r8, t2;
+  __device__ __forceinline__ void load(const float *T) {
+    r0 = T[0], r1 = T[1], r2 = T[2], t0 = T[3], r3 = T[4], r4 = T[5], r5 = T[6], t1 = T[7];
+    r6 = T[8], r7 = T[9], r8 = T[10], t2 = T[11];
+  }
+  __device__ __forceinline__ void apply(float4 p, float &x, float &y, float &z) const {
+    x = fmaf(r0, p.x, fmaf(r1, p.y, fmaf(r2, p.z, t0)));
+    y = fmaf(r3, p.x, fmaf(r4, p.y, fmaf(r5, p.z, t1)));
+    z = fmaf(r6, p.x, fmaf(r7, p.y, fmaf(r8, p.z, t2)));
+  }
+};
+
 __device__ __forceinline__ float warp_sum(float v) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
@@ -286,6 +307,40 @@ cudaError_t launch_consensus(const float4 *XP, int nP, const GridParams *ge, con
                              int *count, unsigned long long *sum, cudaStream_t s, int lanes = 1);
 cudaError_t launch_select(const int *surv, const int *count, const unsigned long long *sum, const uint8_t *ok,
                           const float *pose, int nP, float min_ratio, RansacState *st, cudaStream_t s);
+
+// ----------------------------------------------------------------- classified consensus (lsr_classify.cu)
+// A voxel table over Q's box (voxel h = eps / k): bit IN set only if every
+// point of the voxel has a Q point closer than eps, bit NEAR clear only if no
+// point of the voxel has one. Consensus counts then need the exact eps-grid
+// test only for voxels with NEAR set and IN clear.
+struct ClsParams {
+  float ox, oy, oz, h, inv_h, r_in2, r_near, m;
+  int nx, ny, nz, wx, R, all_amb;
+};
+constexpr int kClsCapWords = 1 << 23;  // words per bit-set (32 MB)
+cudaError_t launch_cls_build(const float *boxQ, float eps, const float4 *XQ, int nQ, ClsParams *cp, unsigned *in_bits,
+                             unsigned *near_bits, cudaStream_t s);
+// Inlier counts (as launch_consensus, without the distance sums).
+cudaError_t launch_consensus_count(const float4 *XP, int nP, const ClsParams *cp, const unsigned *in_bits,
+                                   const unsigned *near_bits, const GridParams *ge, const int *start_e,
+                                   const float4 *Xe, const float *pose, const uint8_t *ok, const int *n_dev,
+                                   int n_host, float eps, int *count, cudaStream_t s);
+// Bounds without exact tests: in_count = points in IN voxels (a lower bound
+// of the inlier count), amb_count = points in undecided voxels.
+cudaError_t launch_consensus_bounds(const float4 *XP, int nP, const ClsParams *cp, const unsigned *in_bits,
+                                    const unsigned *near_bits, const float *pose, const uint8_t *ok, const int *n_dev,
+                                    int *in_count, int *amb_count, cudaStream_t s);
+// sel: the K ok hypotheses with the largest lo + extra (ties to the smaller id).
+cudaError_t launch_top_upper(const int *lo, const int *extra, const uint8_t *ok, const int *n_dev, int K,
+                             uint8_t *sel, cudaStream_t s);
+// With C = max over sel of exact: rest = ok && !sel && lo + extra >= C, and
+// all = sel | rest.
+cudaError_t launch_reach_rest(const int *lo, const int *extra, const int *exact, const uint8_t *sel, const uint8_t *ok,
+                              const int *n_dev, uint8_t *rest, uint8_t *all, cudaStream_t s);
+// With L = max over ok of lo: mask[k] = ok[k] && lo[k] + extra[k] >= L. If L is
+// 0: every ok hypothesis when extra is given, none otherwise.
+cudaError_t launch_reach_mask(const int *lo, const int *extra, const uint8_t *ok, const int *n_dev, uint8_t *mask,
+                              cudaStream_t s);
 constexpr double kFixScale = 1099511627776.0;  // 2^40
 
 // ----------------------------------------------------------------- refinement (lsr_refine.cu)

@@ -422,6 +422,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(TcArgs g) {
         if (!ok) break;
         tc_fence_after();
         const uint32_t col = (uint32_t)((j & 1) * kAccCols + qt * kTcN);
+        // two halves of 64 columns through one loop body (the unrolled top-8
+        // insertion stays small enough for the instruction cache); the
+        // accumulator is released as soon as the second half is in registers
 #pragma unroll 1
         for (int h = 0; h < kTcN / 64; ++h) {
           float v[64];
@@ -429,6 +432,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(TcArgs g) {
           tmem_ld32(tbase + lane_base + col + h * 64, v);
           tmem_ld32(tbase + lane_base + col + h * 64 + 32, v + 32);
           tmem_wait_ld();
+          if (h == kTcN / 64 - 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(barEmpty + (j & 1));
+          }
           const int c0 = t * kTcN + h * 64;
           if (g.d2) {
             if (r < g.nP) {
@@ -449,9 +457,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(TcArgs g) {
             for (int k = 0; k < 64; ++k) top8_insert(ts, ti, v[k], c0 + k);
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(barEmpty + (j & 1));
       }
       if (!ok || g.d2 || r >= g.nP) continue;
       // exact FP32 re-rank of the candidates

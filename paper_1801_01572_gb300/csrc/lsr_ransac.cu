@@ -314,17 +314,10 @@ __device__ __forceinline__ float group_min_d2(const GridParams &g, const int *__
     for (; next + 3 * G < base + len; next += 4 * G) {
       int t = b + next - base;
       float4 q0 = Xe[t], q1 = Xe[t + G], q2 = Xe[t + 2 * G], q3 = Xe[t + 3 * G];
-      float d0 = (q0.x - x) * (q0.x - x) + (q0.y - y) * (q0.y - y) + (q0.z - z) * (q0.z - z);
-      float d1 = (q1.x - x) * (q1.x - x) + (q1.y - y) * (q1.y - y) + (q1.z - z) * (q1.z - z);
-      float d2 = (q2.x - x) * (q2.x - x) + (q2.y - y) * (q2.y - y) + (q2.z - z) * (q2.z - z);
-      float d3 = (q3.x - x) * (q3.x - x) + (q3.y - y) * (q3.y - y) + (q3.z - z) * (q3.z - z);
+      float d0 = dist2(q0, x, y, z), d1 = dist2(q1, x, y, z), d2 = dist2(q2, x, y, z), d3 = dist2(q3, x, y, z);
       best = fminf(best, fminf(fminf(d0, d1), fminf(d2, d3)));
     }
-    for (; next < base + len; next += G) {
-      float4 q = Xe[b + next - base];
-      float dx = q.x - x, dy = q.y - y, dz = q.z - z;
-      best = fminf(best, dx * dx + dy * dy + dz * dz);
-    }
+    for (; next < base + len; next += G) best = fminf(best, dist2(Xe[b + next - base], x, y, z));
     base += len;
   });
 #pragma unroll
@@ -349,9 +342,8 @@ __global__ void __launch_bounds__(kConsThreads) k_consensus(const float4 *__rest
   for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
     int s = (int)(item / chunks), c = (int)(item - (int64_t)s * chunks);
     if (ok && !ok[s]) continue;
-    const float *T = pose + (size_t)s * 12;
-    float r0 = T[0], r1 = T[1], r2 = T[2], t0 = T[3], r3 = T[4], r4 = T[5], r5 = T[6], t1 = T[7], r6 = T[8],
-          r7 = T[9], r8 = T[10], t2 = T[11];
+    Rigid12 T;
+    T.load(pose + (size_t)s * 12);
     int cnt = 0;
     unsigned long long acc = 0ull;
     int i0 = c * kConsChunk, i1 = (c + 1) * kConsChunk < nP ? (c + 1) * kConsChunk : nP;
@@ -360,9 +352,8 @@ __global__ void __launch_bounds__(kConsThreads) k_consensus(const float4 *__rest
       int i = r + grp;
       bool valid = i < i1;
       float4 p = valid ? XP[i] : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
-      float x = fmaf(r0, p.x, fmaf(r1, p.y, fmaf(r2, p.z, t0)));
-      float y = fmaf(r3, p.x, fmaf(r4, p.y, fmaf(r5, p.z, t1)));
-      float z = fmaf(r6, p.x, fmaf(r7, p.y, fmaf(r8, p.z, t2)));
+      float x, y, z;
+      T.apply(p, x, y, z);
       float best = group_min_d2<G>(g, start, Xe, x, y, z, eps2);
       if (valid && sub == 0 && best < eps2) {
         ++cnt;

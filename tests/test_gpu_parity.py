@@ -184,6 +184,48 @@ def test_consensus_parity(ctx, pair0):
     assert cnt_ref.max() > 0.5 * len(P)
 
 
+@gpu
+@pytest.mark.parametrize("config,n", [(0, None), (1, 60000)])
+def test_consensus_classified_counts_equal_exact(ctx, config, n):
+    """Inlier counts through the voxel classification (lsr_stage_consensus)
+    equal, bit for bit, those of the exact eps-grid kernel (the allocation-free
+    entry point) for poses near the truth, perturbed, and random."""
+    import ctypes as C
+    import torch
+    import paper_1801_01572_gb300 as lsr
+    from synth import random_pose
+    fp = make_pair(config, 3, n_p=n, n_q=n)
+    rng = np.random.default_rng(17 + config)
+    Rt = []
+    from scipy.spatial.transform import Rotation
+    for k in range(400):
+        if k % 4 < 2:  # near the truth (within ~0.3 deg / 2 mm), or perturbed (~3 deg / 2 cm)
+            s_r, s_t = (0.005, 0.002) if k % 4 == 0 else (0.05, 0.02)
+            dT = np.eye(4)
+            dT[:3, :3] = Rotation.from_rotvec(rng.normal(0, s_r, 3)).as_matrix()
+            dT[:3, 3] = rng.normal(0, s_t, 3)
+            T = dT @ fp.T
+        else:
+            T = random_pose(rng)
+            T[:3, 3] = fp.T[:3, 3] + rng.normal(0, 0.3, 3)
+        Rt.append(np.concatenate([T[:3, :3], T[:3, 3:]], axis=1).reshape(12))
+    Rt = np.asarray(Rt, np.float32)
+    cnt, sd = ctx.stage_consensus(fp.P, fp.Q, Rt, 0.0375)
+    nh = len(Rt)
+    P, Q, R = (torch.from_numpy(a).cuda() for a in (fp.P, fp.Q, Rt))
+    ref = torch.zeros(nh, dtype=torch.int32, device="cuda")
+    rsd = torch.zeros(nh, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    rc = lsr.lib().lsr_consensus_static(C.c_void_p(P.data_ptr()), len(fp.P), C.c_void_p(Q.data_ptr()), len(fp.Q),
+                                        C.c_void_p(R.data_ptr()), nh, C.c_float(0.0375), C.c_void_p(ref.data_ptr()),
+                                        C.c_void_p(rsd.data_ptr()), None)
+    assert rc == lsr.LSR_OK
+    ref = ref.cpu().numpy()
+    assert np.array_equal(cnt, ref)
+    assert np.allclose(sd, rsd.cpu().numpy(), rtol=1e-9, atol=1e-12)
+    assert ref.max() > len(fp.P) // 3 and (ref < len(fp.P) // 10).sum() > 100
+
+
 # ------------------------------------------------------------------ refinement
 @gpu
 def test_refine_parity(ctx, pair0):
