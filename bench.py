@@ -183,6 +183,33 @@ def run_ours(args, rank, world):
                 d2h=d2h, launches=launches, clocks=clk.summary(pk.get("sm_max_mhz")), peaks=pk,
                 params=ctx.params, match=args.match)
     ctx.close()
+
+    # the other descriptor matchers on the same resident inputs (same result required)
+    info["variants"] = {}
+    if world == 1 and args.variants:
+        for name in sorted(MATCH_MODES):
+            if name == args.match:
+                continue
+            vctx = lsr.Context(dev, stream=stream.cuda_stream, match_precision=MATCH_MODES[name])
+            vctx.set_profiling(True)
+            for _ in range(args.warmup):
+                vctx.register_pair(P, Q, fp.vpP, fp.vpQ)
+            vt, vst, vl = [], np.zeros(8), None
+            for _ in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                vl = vctx.register_pair(P, Q, fp.vpP, fp.vpQ)
+                e1.record(stream)
+                e1.synchronize()
+                vt.append(e0.elapsed_time(e1))
+                vst += np.array(vl.stage_ms)
+            vctx.close()
+            info["variants"][name] = {
+                "value": args.steps / (sum(vt) * 1e-3), "unit": "pairs/s", "ms_per_step": sum(vt) / args.steps,
+                "match_ms": float(vst[3] / args.steps), "match_fallbacks": vl.match_fallbacks,
+                "identical_pose": bool(np.array_equal(vl.T, last.T)) and vl.inliers == last.inliers}
     return info
 
 
@@ -336,6 +363,8 @@ def main():
     ap.add_argument("--match", default="fp32", choices=sorted(MATCH_MODES))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="do not also time the other descriptor matchers")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -376,6 +405,7 @@ def main():
             "e2e": {"value": e2e, "unit": "pairs/s", "h2d_bytes_per_step": info["h2d"] * world,
                     "d2h_bytes_per_step": info["d2h"] * world},
             "gpu_launches": int(info["launches"]),
+            "variants": info["variants"],
             "clocks": info["clocks"],
         }
         if world == 1 and not args.no_cpu_baseline:

@@ -1,0 +1,92 @@
+"""The differentiable robust alignment objective at the config-4 size: 32
+pairs of 50,000-point room clouds in one batched forward and one backward
+through RobustAlignBatch (a torch.autograd.Function over lsr_objective_fwd /
+lsr_objective_bwd), the nearest neighbours recomputed in the backward.
+
+Gradients with respect to the se(3) 6-vector are checked against FP64 central
+finite differences (h = 1e-6) and against the oracle's analytic gradient, at
+relative tolerance 1e-4. The objective is piecewise smooth: with 50,000 points
+some nearest neighbours switch within +-h of any pose, so the finite
+differences are taken of the objective with the correspondences of the base
+pose held (the function the analytic gradient differentiates), evaluated in
+FP64 from the oracle's neighbours and pose update. Point gradients are checked
+against the oracle's, except for the few points whose nearest neighbour is a
+near-tie or lies at the eps boundary, where FP32 and FP64 may legitimately
+pick differently.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_pair
+
+gpu = pytest.mark.gpu
+EPS = 0.0375
+MU = EPS * EPS
+
+
+@pytest.fixture(scope="module")
+def run4():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1801_01572_gb300 as lsr
+    pairs = [make_pair(4, i) for i in range(32)]
+    rng = np.random.default_rng(44)
+    xis = np.concatenate([rng.normal(0, 2e-3, (32, 3)), rng.normal(0, 3e-3, (32, 3))], axis=1)
+    T0s = np.stack([p.T for p in pairs])
+    clouds = []
+    for p in pairs:
+        clouds.append(torch.tensor(p.P, device="cuda", requires_grad=True))
+        clouds.append(torch.tensor(p.Q, device="cuda", requires_grad=True))
+    xt = torch.tensor(xis, dtype=torch.float64, requires_grad=True)
+    with lsr.Context(0) as ctx:
+        E = lsr.RobustAlignBatch.apply(xt, torch.tensor(T0s), EPS, MU, ctx, *clouds)
+        E.sum().backward()
+        torch.cuda.synchronize()
+    return dict(pairs=pairs, xis=xis, T0s=T0s, E=E.detach().cpu().numpy(), dxi=xt.grad.numpy(),
+                dP=[c.grad.cpu().numpy() for c in clouds[0::2]], dQ=[c.grad.cpu().numpy() for c in clouds[1::2]])
+
+
+def held_objective(P, Q, nn, xi, T0):
+    """E with the correspondences nn held: sum rho~(|T(xi) p_i - q_nn(i)|^2)."""
+    T = oracle.apply_xi(xi, T0)
+    m = nn >= 0
+    r = P[m] @ T[:3, :3].T + T[:3, 3] - Q[nn[m]]
+    s = (r * r).sum(1)
+    return float((MU * s / (MU + s) - MU * EPS ** 2 / (MU + EPS ** 2)).sum())
+
+
+@gpu
+@pytest.mark.parametrize("i", [0, 11, 31])
+def test_config4_objective_and_pose_gradient(run4, i):
+    p, xi, T0 = run4["pairs"][i], run4["xis"][i], run4["T0s"][i]
+    P, Q = p.P.astype(np.float64), p.Q.astype(np.float64)
+    E_ref, dP_ref, dQ_ref, dxi_ref, nn = oracle.objective(P, Q, xi, T0, EPS, MU)
+    assert (nn >= 0).sum() > 0.3 * len(P)
+    assert abs(run4["E"][i] - E_ref) <= 1e-5 * abs(E_ref)
+    g = run4["dxi"][i]
+    scale = np.abs(dxi_ref).max()
+    assert np.abs(g - dxi_ref).max() <= 1e-4 * scale, (g, dxi_ref)
+    h = 1e-6
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h
+        fd = (held_objective(P, Q, nn, xi + e, T0) - held_objective(P, Q, nn, xi - e, T0)) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-4 * scale, (k, g[k], fd)
+    assert abs(held_objective(P, Q, nn, xi, T0) - E_ref) <= 1e-9 * abs(E_ref)
+
+
+@gpu
+@pytest.mark.parametrize("i", [0, 11, 31])
+def test_config4_point_gradients(run4, i):
+    p, xi, T0 = run4["pairs"][i], run4["xis"][i], run4["T0s"][i]
+    P, Q = p.P.astype(np.float64), p.Q.astype(np.float64)
+    _, dP_ref, dQ_ref, _, nn = oracle.objective(P, Q, xi, T0, EPS, MU)
+    for got, ref in ((run4["dP"][i], dP_ref), (run4["dQ"][i], dQ_ref)):
+        tol = 1e-4 * np.abs(ref).max()
+        bad = np.abs(got - ref).max(1) > tol
+        assert bad.mean() < 2e-3, bad.sum()
+    # points with no neighbour within eps have no gradient on either side
+    far = nn < 0
+    assert np.all(run4["dP"][i][far] == 0)
