@@ -17,7 +17,9 @@
 // database tile) and streams the database in tiles of 128 rows: one thread
 // issues tcgen05.mma from shared memory into TMEM (two accumulator buffers, so
 // the tensor pipe runs while the epilogue drains the other), and eight
-// epilogue warps, one query per thread, keep the 8 smallest scores.
+// epilogue warps, one query per thread, read a whole accumulator row with one
+// wait and keep the 8 smallest scores: a min-prefilter per 32 columns, then
+// bit-mask insertion of the few values that beat a lane's current 8th.
 //
 // The 8 candidates are re-ranked with the exact FP32 distance of the original
 // descriptors in the FP32 matcher's operation order. A certificate proves, per
@@ -59,6 +61,8 @@ constexpr int kStages = 4;                      // database tiles in flight
 constexpr int kTopK = 8;
 constexpr int kEpiWarps = 4 * kQT;              // warps 0..7: epilogue; warp 8: copies + MMA
 constexpr int kTcThreads = (kEpiWarps + 1) * 32;
+constexpr int kUnitQ = kQT * kTcM;              // queries of one work unit
+constexpr int kChunks = kTcN / 32;              // 32-column TMEM loads per accumulator row
 constexpr uint32_t kAccCols = kQT * kTcN;       // one accumulator buffer
 constexpr uint32_t kTmemCols = 2 * kAccCols;    // double-buffered (512 columns, all of TMEM)
 constexpr unsigned long long kWaitNs = 2000000000ull;  // give up after 2 s
@@ -298,6 +302,20 @@ __device__ __forceinline__ float exact_d2(const float *__restrict__ a, const flo
   return s;
 }
 
+// w[k] for a runtime k < 32, by a tree of selects (w stays in registers).
+__device__ __forceinline__ float pick32(const float (&w)[32], int k) {
+  float a[16], b[8], c[4], d[2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = (k & 1) ? w[2 * i + 1] : w[2 * i];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) b[i] = (k & 2) ? a[2 * i + 1] : a[2 * i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) c[i] = (k & 4) ? b[2 * i + 1] : b[2 * i];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) d[i] = (k & 8) ? c[2 * i + 1] : c[2 * i];
+  return (k & 16) ? d[1] : d[0];
+}
+
 __device__ __forceinline__ void top8_insert(float (&ts)[kTopK], int (&ti)[kTopK], float v, int id) {
   if (!(v < ts[kTopK - 1])) return;
   ts[kTopK - 1] = v;
@@ -411,52 +429,75 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(TcArgs g) {
     bool ok = true;
     for (int m = 0; m < nuloc && ok; ++m) {
       const int u = blockIdx.x + m * gridDim.x;
-      const int r = u * (kQT * kTcM) + row_in_unit;
+      const int r = u * kUnitQ + row_in_unit;
       float ts[kTopK];
       int ti[kTopK];
 #pragma unroll
       for (int q = 0; q < kTopK; ++q) ts[q] = FLT_MAX, ti[q] = -1;
       for (int t = 0; t < g.nNT; ++t, ++j) {
-        ok = mbar_wait(barDone + (j & 1), (j >> 1) & 1, fail);
+        const int buf = j & 1;
+        ok = mbar_wait(barDone + buf, (j >> 1) & 1, fail);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t col = (uint32_t)((j & 1) * kAccCols + qt * kTcN);
-        // two halves of 64 columns through one loop body (the unrolled top-8
-        // insertion stays small enough for the instruction cache); the
-        // accumulator is released as soon as the second half is in registers
-#pragma unroll 1
-        for (int h = 0; h < kTcN / 64; ++h) {
-          float v[64];
-          __syncwarp();  // the loads below are warp-collective
-          tmem_ld32(tbase + lane_base + col + h * 64, v);
-          tmem_ld32(tbase + lane_base + col + h * 64 + 32, v + 32);
-          tmem_wait_ld();
-          if (h == kTcN / 64 - 1) {
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(barEmpty + (j & 1));
-          }
-          const int c0 = t * kTcN + h * 64;
-          if (g.d2) {
-            if (r < g.nP) {
-              const float aa = g.aa[r];
-              for (int k = 0; k < 64; ++k) g.d2[(size_t)r * ncols + c0 + k] = v[k] + aa;
-            }
-            continue;
-          }
-          float mn[8];
+        // the whole row of the accumulator with one wait
+        const uint32_t row = tbase + lane_base + (uint32_t)(buf * kAccCols + qt * kTcN);
+        float v[kTcN];
+        __syncwarp();  // the loads below are warp-collective
 #pragma unroll
-          for (int k = 0; k < 8; ++k) mn[k] = v[k];
-#pragma unroll
-          for (int k = 8; k < 64; ++k) mn[k & 7] = fminf(mn[k & 7], v[k]);
-          const float m0 = fminf(fminf(fminf(mn[0], mn[1]), fminf(mn[2], mn[3])),
-                                 fminf(fminf(mn[4], mn[5]), fminf(mn[6], mn[7])));
-          if (m0 < ts[kTopK - 1]) {
-#pragma unroll
-            for (int k = 0; k < 64; ++k) top8_insert(ts, ti, v[k], c0 + k);
+        for (int q = 0; q < kChunks; ++q) tmem_ld32(row + q * 32, v + q * 32);
+        tmem_wait_ld();
+        const int c0 = t * kTcN;
+        if (g.d2) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(barEmpty + buf);
+          if (r < g.nP) {
+            const float aa = g.aa[r];
+            for (int k = 0; k < kTcN; ++k) g.d2[(size_t)r * ncols + c0 + k] = v[k] + aa;
           }
+          continue;
         }
+        // minimum of each 32-column chunk
+        float mh[kChunks];
+#pragma unroll
+        for (int q = 0; q < kChunks; ++q) {
+          float a0 = v[q * 32], a1 = v[q * 32 + 1], a2 = v[q * 32 + 2], a3 = v[q * 32 + 3];
+#pragma unroll
+          for (int k = 4; k < 32; k += 4) {
+            a0 = fminf(a0, v[q * 32 + k]), a1 = fminf(a1, v[q * 32 + k + 1]);
+            a2 = fminf(a2, v[q * 32 + k + 2]), a3 = fminf(a3, v[q * 32 + k + 3]);
+          }
+          mh[q] = fminf(fminf(a0, a1), fminf(a2, a3));
+        }
+        // A chunk whose minimum beats a lane's 8th score is read again from
+        // TMEM (the buffer is released only afterwards) and only its values
+        // below that score are inserted, one by one, picked by selects so that
+        // everything stays in registers. After the first tiles that is one or
+        // two values per tile and warp; most tiles release the buffer at once.
+#pragma unroll 1
+        for (int q = 0; q < kChunks; ++q) {
+          float mq = mh[0];
+#pragma unroll
+          for (int qq = 1; qq < kChunks; ++qq) mq = q == qq ? mh[qq] : mq;
+          if (!__any_sync(0xffffffffu, mq < ts[kTopK - 1])) continue;
+          float w[32];
+          tmem_ld32(row + q * 32, w);
+          tmem_wait_ld();
+          const float thr = ts[kTopK - 1];
+          unsigned below = 0u;
+#pragma unroll
+          for (int k = 0; k < 32; ++k) below |= (w[k] < thr ? 1u : 0u) << k;
+          while (below) {
+            const int k = __ffs(below) - 1;
+            below &= below - 1u;
+            top8_insert(ts, ti, pick32(w, k), c0 + q * 32 + k);
+          }
+          __syncwarp();
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(barEmpty + buf);
       }
       if (!ok || g.d2 || r >= g.nP) continue;
       // exact FP32 re-rank of the candidates
