@@ -85,7 +85,14 @@ typedef struct {
   uint64_t pair_id;       /* RNG key word 1 for lsr_register_pair; a batch uses pair_id + i */
   int32_t match_precision; /* LSR_MATCH_FP32 (default), LSR_MATCH_BF16 or LSR_MATCH_BF16_PLAIN */
   int32_t refine_levels;  /* graduated refinement levels L (1..8), default 3: radius eps * 2^(L-1-l) at level l */
-  int32_t reserved_[4];
+  int32_t batch_streams;  /* lsr_register_batch: pairs run concurrently on this many streams (1..16), each with
+                             its own workspace; 0 (default) = chosen by the autotuner on the first batch */
+  int32_t batch_graph;    /* lsr_register_batch with device-resident clouds: 1 = capture the whole batch as one
+                             CUDA graph and replay it when the same batch (same pointers, sizes, viewpoints and
+                             parameters) is registered again; 0 (default) = launch directly */
+  int32_t match_tile;     /* tensor-core matcher work unit: 1 or 2 query tiles of 128 per CTA; 0 (default) =
+                             chosen per cloud size by the autotuner */
+  int32_t reserved_;
 } lsr_params;
 
 /* Result of one registration. */

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -42,6 +43,20 @@ struct lsr_ctx {
   // consensus tuning: lanes per nearest-neighbour query (2 measured fastest
   // on the 150k-point room pair among 1..16; LSR_CONSENSUS_LANES overrides)
   int cons_lanes = 2;
+  // concurrent batches: worker streams, each with its own workspace
+  std::vector<cudaStream_t> lanes;
+  std::vector<char *> lane_ws;
+  std::vector<size_t> lane_cap;
+  std::vector<cudaEvent_t> lane_done;
+  cudaEvent_t fork = nullptr;
+  // the last captured batch graph, its signature and its kernel count
+  cudaGraphExec_t gexec = nullptr;
+  std::string gkey;
+  unsigned long long glaunches = 0;
+  // autotuner choices: matcher tile shape per size bucket (ceil log2 of the
+  // query count; 0 = not tuned yet) and the number of batch streams
+  int tile_choice[32] = {};
+  int streams_choice = 0;
 };
 
 namespace {
@@ -272,6 +287,7 @@ int ensure_ws(lsr_ctx *c, size_t bytes) {
 
 int ensure_host_slots(lsr_ctx *c, int n) {
   if (n <= c->st_host_cap) return LSR_OK;
+  c->gkey.clear();  // a captured batch copies its results into the old slots
   if (c->st_host) cudaFreeHost(c->st_host);
   if (c->box_host) cudaFreeHost(c->box_host);
   c->st_host = nullptr;
@@ -296,6 +312,9 @@ int check_params(const lsr_params *p) {
         p->n_hypotheses <= 2147483647LL && valid_precision(p->match_precision)))
     return LSR_E_ARG;
   if (p->eps_inlier > 10.f) return LSR_E_ARG;  // fixed-point inlier sums assume eps^2 * |P| << 2^23
+  if (p->batch_streams < 0 || p->batch_streams > 16 || (p->batch_graph != 0 && p->batch_graph != 1) ||
+      p->match_tile < 0 || p->match_tile > 2)
+    return LSR_E_ARG;
   return LSR_OK;
 }
 
@@ -420,10 +439,23 @@ struct Timer {
   }
 };
 
-// The registration of one pair, enqueued on the stream. Results stay in L.st.
+int size_bucket(int n) {
+  int b = 0;
+  while (b < 31 && (1 << b) < n) ++b;
+  return b;
+}
+
+// Tensor-core matcher tile shape for nP queries: the parameter, else the
+// autotuner's choice for the size bucket, else the static default.
+int match_tile_for(const lsr_ctx *c, int nP) {
+  if (c->prm.match_tile) return c->prm.match_tile;
+  int t = c->tile_choice[size_bucket(nP)];
+  return t ? t : tc_default_tile(nP);
+}
+
+// The registration of one pair, enqueued on stream s. Results stay in L.st.
 int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q, const float *vpP, const float *vpQ,
-                 uint64_t pair_id, Timer &tm) {
-  cudaStream_t s = c->stream;
+                 uint64_t pair_id, Timer &tm, cudaStream_t s) {
   const lsr_params &p = c->prm;
   int nP = L.P.n, nQ = L.Q.n;
   tm.mark();
@@ -444,7 +476,8 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
   tm.mark();
   if (p.match_precision != LSR_MATCH_FP32)
     TRY_CUDA(c,
-             launch_match_bf16(Pc.F, nP, Qc.F, nQ, p.match_precision == LSR_MATCH_BF16, L.tc_ws, L.nn, L.d1,
+             launch_match_bf16(Pc.F, nP, Qc.F, nQ, p.match_precision == LSR_MATCH_BF16, match_tile_for(c, nP), L.tc_ws,
+                               L.nn, L.d1,
                                &L.st->match_fallbacks, &L.st->match_err, nullptr, s),
              "match");
   else
@@ -530,12 +563,12 @@ void fill_result(const RansacState &st, const float *boxP, const float *boxQ, ls
 }
 
 // Stage a cloud to the device if it lives in host memory.
-int stage_input(lsr_ctx *c, const float *src, int64_t n, float *dst, const float **out) {
+int stage_input(lsr_ctx *c, const float *src, int64_t n, float *dst, const float **out, cudaStream_t s = nullptr) {
   if (is_device_ptr(src)) {
     *out = src;
     return LSR_OK;
   }
-  TRY_CUDA(c, cudaMemcpyAsync(dst, src, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream), "H2D");
+  TRY_CUDA(c, cudaMemcpyAsync(dst, src, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s ? s : c->stream), "H2D");
   *out = dst;
   return LSR_OK;
 }
@@ -553,6 +586,248 @@ int guard(lsr_ctx *c) {
 // Generic copy of a result array to a caller pointer (device or host).
 int copy_out(lsr_ctx *c, void *dst, const void *src, size_t bytes) {
   TRY_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream), "copy out");
+  return LSR_OK;
+}
+
+// ---------------------------------------------------------------- batches
+// A batch of pairs (lsr_register_batch). Pairs run on S worker streams, each
+// with its own workspace, assigned longest-first to the least loaded stream;
+// the context stream forks to the workers and joins them. The same enqueue
+// can be captured into one CUDA graph and replayed.
+struct BatchIn {
+  int n;
+  const float *const *P;
+  const int64_t *nP;
+  const float *const *Q;
+  const int64_t *nQ;
+  const float *vp;
+  uint64_t pair0;
+};
+
+size_t pair_bytes(const lsr_ctx *c, int64_t nP, int64_t nQ) {
+  Arena m(nullptr);
+  PairLayout L;
+  plan_pair(m, (int)nP, (int)nQ, true, true, c->prm.n_hypotheses, c->prm.refine_levels, c->prm.match_precision, L);
+  return m.off;
+}
+
+int ensure_lanes(lsr_ctx *c, int S, size_t bytes) {
+  while ((int)c->lanes.size() < S) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(c, LSR_E_CUDA, "stream creation failed");
+    }
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamDestroy(st);
+      return set_err(c, LSR_E_CUDA, "event creation failed");
+    }
+    c->lanes.push_back(st);
+    c->lane_done.push_back(ev);
+    c->lane_ws.push_back(nullptr);
+    c->lane_cap.push_back(0);
+  }
+  if (!c->fork && cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    c->fork = nullptr;
+    return set_err(c, LSR_E_CUDA, "event creation failed");
+  }
+  for (int l = 0; l < S; ++l) {
+    if (c->lane_cap[l] >= bytes) continue;
+    TRY_CUDA(c, cudaStreamSynchronize(c->lanes[l]), "workspace sync");
+    if (c->lane_ws[l]) cudaFree(c->lane_ws[l]);
+    c->lane_ws[l] = nullptr;
+    c->lane_cap[l] = 0;
+    c->gkey.clear();  // a captured batch points into the old workspace
+    size_t want = bytes + bytes / 8;
+    if (cudaMalloc(&c->lane_ws[l], want) != cudaSuccess) {
+      cudaGetLastError();
+      c->lane_ws[l] = nullptr;
+      return set_err(c, LSR_E_OOM, "batch workspace allocation failed");
+    }
+    c->lane_cap[l] = want;
+  }
+  return LSR_OK;
+}
+
+// Longest processing time first: descending nP * nQ + nP (ties by index),
+// each pair to the stream with the least work so far.
+std::vector<std::vector<int>> assign_pairs(const BatchIn &b, int m, int S) {
+  std::vector<int> order(m);
+  for (int i = 0; i < m; ++i) order[i] = i;
+  auto cost = [&](int i) { return (double)b.nP[i] * (double)b.nQ[i] + 1e4 * (double)b.nP[i]; };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+  std::vector<std::vector<int>> lanes(S);
+  std::vector<double> load(S, 0.0);
+  for (int i : order) {
+    int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    lanes[l].push_back(i);
+    load[l] += cost(i);
+  }
+  return lanes;
+}
+
+int enqueue_batch(lsr_ctx *c, const BatchIn &b, const std::vector<std::vector<int>> &lanes) {
+  const int S = (int)lanes.size();
+  TRY_CUDA(c, cudaEventRecord(c->fork, c->stream), "fork");
+  for (int l = 0; l < S; ++l) {
+    cudaStream_t s = c->lanes[l];
+    TRY_CUDA(c, cudaStreamWaitEvent(s, c->fork, 0), "fork");
+    for (int i : lanes[l]) {
+      Arena a(c->lane_ws[l]);
+      PairLayout L;
+      plan_pair(a, (int)b.nP[i], (int)b.nQ[i], true, true, c->prm.n_hypotheses, c->prm.refine_levels,
+                c->prm.match_precision, L);
+      const float *dP, *dQ;
+      int rc;
+      if ((rc = stage_input(c, b.P[i], b.nP[i], L.P.src, &dP, s))) return rc;
+      if ((rc = stage_input(c, b.Q[i], b.nQ[i], L.Q.src, &dQ, s))) return rc;
+      Timer t{c};
+      t.k = 9;  // no per-stage timing inside batches
+      if ((rc = enqueue_pair(c, L, dP, dQ, b.vp ? b.vp + 6 * i : nullptr, b.vp ? b.vp + 6 * i + 3 : nullptr,
+                             b.pair0 + i, t, s)))
+        return rc;
+      TRY_CUDA(c, cudaMemcpyAsync(&c->st_host[i], L.st, sizeof(RansacState), cudaMemcpyDeviceToHost, s), "D2H");
+      TRY_CUDA(c,
+               cudaMemcpyAsync(&c->box_host[2 * kBox * i], L.P.box, sizeof(float) * kBox, cudaMemcpyDeviceToHost, s),
+               "D2H");
+      TRY_CUDA(c,
+               cudaMemcpyAsync(&c->box_host[2 * kBox * i + kBox], L.Q.box, sizeof(float) * kBox,
+                               cudaMemcpyDeviceToHost, s),
+               "D2H");
+    }
+    TRY_CUDA(c, cudaEventRecord(c->lane_done[l], s), "join");
+    TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->lane_done[l], 0), "join");
+  }
+  return LSR_OK;
+}
+
+// Signature of everything a captured batch graph bakes in.
+std::string batch_key(const lsr_ctx *c, const BatchIn &b, const std::vector<std::vector<int>> &lanes) {
+  std::string k;
+  auto put = [&](const void *p, size_t n) { k.append(reinterpret_cast<const char *>(p), n); };
+  put(&c->prm, sizeof(c->prm));
+  put(&b.n, sizeof(b.n));
+  put(&b.pair0, sizeof(b.pair0));
+  for (int i = 0; i < b.n; ++i) {
+    put(&b.P[i], sizeof(void *));
+    put(&b.Q[i], sizeof(void *));
+    put(&b.nP[i], sizeof(int64_t));
+    put(&b.nQ[i], sizeof(int64_t));
+    if (b.vp) put(b.vp + 6 * i, 6 * sizeof(float));
+    int t = match_tile_for(c, (int)b.nP[i]);
+    put(&t, sizeof(t));
+  }
+  for (size_t l = 0; l < lanes.size(); ++l) {
+    put(&c->lane_ws[l], sizeof(void *));
+    int m = (int)lanes[l].size();
+    put(&m, sizeof(m));
+    for (int i : lanes[l]) put(&i, sizeof(i));
+  }
+  put(&c->st_host, sizeof(void *));
+  put(&c->box_host, sizeof(void *));
+  put(&c->cons_lanes, sizeof(int));
+  return k;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Synthetic FPFH-like rows for tuning: three 11-bin sub-histograms, each the
+// cube of counter-based uniform numbers normalised to sum 1 (peaked, as
+// FPFH of planar-dominated scenes).
+__global__ void k_fake_desc(uint64_t seed, int n, float *F) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * 3; t += gridDim.x * blockDim.x) {
+    const int row = t / 3, sub = t - 3 * row;
+    float v[kNB], sum = 0.f;
+    for (int b = 0; b < kNB; ++b) {
+      uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(row * kD + sub * kNB + b + 1);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      float u = (float)(z >> 40) * 5.9604645e-8f;
+      v[b] = u * u * u;
+      sum += v[b];
+    }
+    for (int b = 0; b < kNB; ++b) F[(size_t)row * kDS + sub * kNB + b] = v[b] / fmaxf(sum, 1e-30f);
+    if (sub == 2)
+      for (int b = kD; b < kDS; ++b) F[(size_t)row * kDS + b] = 0.f;
+  }
+}
+
+// Tensor-core tile shape per size bucket: both shapes timed (CUDA events) on
+// synthetic descriptors of the largest query count of that bucket in the batch.
+int tune_tiles(lsr_ctx *c, const BatchIn &b) {
+  if (c->prm.match_precision == LSR_MATCH_FP32 || c->prm.match_tile) return LSR_OK;
+  const bool split = c->prm.match_precision == LSR_MATCH_BF16;
+  int want[32] = {};
+  for (int i = 0; i < b.n; ++i) {
+    int k = size_bucket((int)b.nP[i]);
+    if (!c->tile_choice[k]) want[k] = std::max(want[k], (int)std::max(b.nP[i], b.nQ[i]));
+  }
+  cudaStream_t s = c->stream;
+  for (int k = 0; k < 32; ++k) {
+    const int n = want[k];
+    if (!n) continue;
+    auto plan = [&](Arena &a, float *&FP, float *&FQ, int *&nn, float *&d1, int *&flags, char *&tws) {
+      FP = a.take<float>((size_t)kDS * n);
+      FQ = a.take<float>((size_t)kDS * n);
+      nn = a.take<int>(n);
+      d1 = a.take<float>(n);
+      flags = a.take<int>(2);
+      tws = a.take<char>(tc_workspace_bytes(n, n, split));
+    };
+    Arena m(nullptr);
+    float *x1, *x2, *x4;
+    int *x3, *x5;
+    char *x6;
+    plan(m, x1, x2, x3, x4, x5, x6);
+    int rc;
+    if ((rc = ensure_ws(c, m.off))) return rc;
+    Arena a(c->ws);
+    float *FP, *FQ, *d1;
+    int *nn, *flags;
+    char *tws;
+    plan(a, FP, FQ, nn, d1, flags, tws);
+    LSR_LAUNCH(k_fake_desc<<<nblk(3 * n), 256, 0, s>>>(0x243F6A8885A308D3ull, n, FP));
+    LSR_LAUNCH(k_fake_desc<<<nblk(3 * n), 256, 0, s>>>(0x13198A2E03707344ull, n, FQ));
+    float best_ms = 0.f;
+    int best = 0;
+    for (int qt = 1; qt <= 2; ++qt) {
+      TRY_CUDA(c, launch_match_bf16(FP, n, FQ, n, split, qt, tws, nn, d1, flags, flags + 1, nullptr, s), "tune");
+      TRY_CUDA(c, cudaEventRecord(c->ev[0], s), "tune");
+      for (int r = 0; r < 2; ++r)
+        TRY_CUDA(c, launch_match_bf16(FP, n, FQ, n, split, qt, tws, nn, d1, flags, flags + 1, nullptr, s), "tune");
+      TRY_CUDA(c, cudaEventRecord(c->ev[1], s), "tune");
+      TRY_CUDA(c, cudaEventSynchronize(c->ev[1]), "tune");
+      float ms = 0.f;
+      TRY_CUDA(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]), "tune");
+      if (!best || ms < best_ms) best = qt, best_ms = ms;
+    }
+    c->tile_choice[k] = best;
+  }
+  return LSR_OK;
+}
+
+// Number of batch streams: 1, 2, 4 and 8 timed on the first pairs of the
+// batch (their results are discarded; the real run follows).
+int tune_streams(lsr_ctx *c, const BatchIn &b, size_t bytes) {
+  const int m = std::min(b.n, 16);
+  float best_ms = 0.f;
+  int best = 0;
+  for (int S = 1; S <= 8 && S <= m; S *= 2) {
+    int rc;
+    if ((rc = ensure_lanes(c, S, bytes))) return rc;
+    auto lanes = assign_pairs(b, m, S);
+    TRY_CUDA(c, cudaEventRecord(c->ev[0], c->stream), "tune");
+    if ((rc = enqueue_batch(c, b, lanes))) return rc;
+    TRY_CUDA(c, cudaEventRecord(c->ev[1], c->stream), "tune");
+    TRY_CUDA(c, cudaEventSynchronize(c->ev[1]), "tune");
+    float ms = 0.f;
+    TRY_CUDA(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]), "tune");
+    if (!best || ms < best_ms) best = S, best_ms = ms;
+  }
+  c->streams_choice = best;
   return LSR_OK;
 }
 
@@ -644,6 +919,14 @@ int lsr_destroy(lsr_ctx *c) {
   if (!c) return LSR_OK;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  for (size_t l = 0; l < c->lanes.size(); ++l) {
+    cudaStreamSynchronize(c->lanes[l]);
+    if (c->lane_ws[l]) cudaFree(c->lane_ws[l]);
+    cudaStreamDestroy(c->lanes[l]);
+    cudaEventDestroy(c->lane_done[l]);
+  }
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->ws) cudaFree(c->ws);
   if (c->st_host) cudaFreeHost(c->st_host);
   if (c->box_host) cudaFreeHost(c->box_host);
@@ -675,7 +958,12 @@ int lsr_set_profiling(lsr_ctx *c, int enable) {
   return LSR_OK;
 }
 
-int64_t lsr_workspace_bytes(const lsr_ctx *c) { return c ? (int64_t)c->ws_cap : 0; }
+int64_t lsr_workspace_bytes(const lsr_ctx *c) {
+  if (!c) return 0;
+  size_t b = c->ws_cap;
+  for (size_t x : c->lane_cap) b += x;
+  return (int64_t)b;
+}
 
 uint64_t lsr_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
@@ -700,32 +988,84 @@ static int register_many(lsr_ctx *c, int32_t n, const float *const *P, const int
     maxP = std::max(maxP, nP[i]);
     maxQ = std::max(maxQ, nQ[i]);
   }
-  // one workspace sized for the largest pair; pairs run back to back on the stream
-  Arena m(nullptr);
-  PairLayout Lm;
-  plan_pair(m, (int)maxP, (int)maxQ, true, true, c->prm.n_hypotheses, c->prm.refine_levels, c->prm.match_precision,
-            Lm);
-  if ((rc = ensure_ws(c, m.off))) return rc;
   if ((rc = ensure_host_slots(c, n))) return rc;
+  const BatchIn b{n, P, nP, Q, nQ, vp, pair0};
+  if ((rc = tune_tiles(c, b))) return rc;
+  const size_t bytes = pair_bytes(c, maxP, maxQ);
+  int S = c->prm.batch_streams;
+  if (!S && n >= 8) {
+    if (!c->streams_choice && (rc = tune_streams(c, b, bytes))) return rc;
+    S = c->streams_choice;
+  }
+  S = std::max(1, std::min(S, (int)n));
+  const bool graph = c->prm.batch_graph == 1 && n > 1;
   Timer tm{c};
-  for (int i = 0; i < n; ++i) {
-    Arena a(c->ws);
-    PairLayout L;
-    plan_pair(a, (int)nP[i], (int)nQ[i], true, true, c->prm.n_hypotheses, c->prm.refine_levels,
-              c->prm.match_precision, L);
-    const float *dP, *dQ;
-    if ((rc = stage_input(c, P[i], nP[i], L.P.src, &dP))) return rc;
-    if ((rc = stage_input(c, Q[i], nQ[i], L.Q.src, &dQ))) return rc;
-    Timer t1{c};
-    Timer &t = (n == 1) ? tm : t1;
-    if (n != 1) t.k = 9;  // per-stage timing only for single pairs
-    if ((rc = enqueue_pair(c, L, dP, dQ, vp ? vp + 6 * i : nullptr, vp ? vp + 6 * i + 3 : nullptr, pair0 + i, t)))
-      return rc;
-    TRY_CUDA(c, cudaMemcpyAsync(&c->st_host[i], L.st, sizeof(RansacState), cudaMemcpyDeviceToHost, c->stream), "D2H");
-    TRY_CUDA(c, cudaMemcpyAsync(&c->box_host[2 * kBox * i], L.P.box, sizeof(float) * kBox, cudaMemcpyDeviceToHost, c->stream),
-             "D2H");
-    TRY_CUDA(c, cudaMemcpyAsync(&c->box_host[2 * kBox * i + kBox], L.Q.box, sizeof(float) * kBox, cudaMemcpyDeviceToHost, c->stream),
-             "D2H");
+  if (S == 1 && !graph) {
+    // pairs back to back on the context stream, one workspace
+    if ((rc = ensure_ws(c, bytes))) return rc;
+    for (int i = 0; i < n; ++i) {
+      Arena a(c->ws);
+      PairLayout L;
+      plan_pair(a, (int)nP[i], (int)nQ[i], true, true, c->prm.n_hypotheses, c->prm.refine_levels,
+                c->prm.match_precision, L);
+      const float *dP, *dQ;
+      if ((rc = stage_input(c, P[i], nP[i], L.P.src, &dP))) return rc;
+      if ((rc = stage_input(c, Q[i], nQ[i], L.Q.src, &dQ))) return rc;
+      Timer t1{c};
+      Timer &t = (n == 1) ? tm : t1;
+      if (n != 1) t.k = 9;  // per-stage timing only for single pairs
+      if ((rc = enqueue_pair(c, L, dP, dQ, vp ? vp + 6 * i : nullptr, vp ? vp + 6 * i + 3 : nullptr, pair0 + i, t,
+                             c->stream)))
+        return rc;
+      TRY_CUDA(c, cudaMemcpyAsync(&c->st_host[i], L.st, sizeof(RansacState), cudaMemcpyDeviceToHost, c->stream),
+               "D2H");
+      TRY_CUDA(c,
+               cudaMemcpyAsync(&c->box_host[2 * kBox * i], L.P.box, sizeof(float) * kBox, cudaMemcpyDeviceToHost,
+                               c->stream),
+               "D2H");
+      TRY_CUDA(c,
+               cudaMemcpyAsync(&c->box_host[2 * kBox * i + kBox], L.Q.box, sizeof(float) * kBox,
+                               cudaMemcpyDeviceToHost, c->stream),
+               "D2H");
+    }
+  } else {
+    if ((rc = ensure_lanes(c, S, bytes))) return rc;
+    auto lanes = assign_pairs(b, n, S);
+    bool device_inputs = true;
+    for (int i = 0; i < n && device_inputs; ++i) device_inputs = is_device_ptr(P[i]) && is_device_ptr(Q[i]);
+    if (graph && device_inputs) {
+      std::string key = batch_key(c, b, lanes);
+      if (!c->gexec || key != c->gkey) {
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+        c->gkey.clear();
+        // the launches of a capture are counted when the graph runs
+        const unsigned long long g0 = lsr_launch_count();
+        TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed), "capture");
+        rc = enqueue_batch(c, b, lanes);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        const unsigned long long captured = lsr_launch_count() - g0;
+        __atomic_fetch_sub(&g_launches, captured, __ATOMIC_RELAXED);
+        if (rc || e != cudaSuccess) {
+          if (g) cudaGraphDestroy(g);
+          cudaGetLastError();
+          return rc ? rc : cuda_err(c, e, "capture");
+        }
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          c->gexec = nullptr;
+          return cuda_err(c, e, "graph instantiate");
+        }
+        c->gkey = key;
+        c->glaunches = captured;
+      }
+      TRY_CUDA(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+      __atomic_fetch_add(&g_launches, c->glaunches, __ATOMIC_RELAXED);
+    } else {
+      if ((rc = enqueue_batch(c, b, lanes))) return rc;
+    }
   }
   TRY_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
   TRY_CUDA(c, cudaGetLastError(), "kernel");
@@ -902,7 +1242,8 @@ int lsr_stage_match(lsr_ctx *c, const float *FP, int64_t nP, const float *FQ, in
   LSR_LAUNCH(k_gather_rows<<<nblk(nP * kDS), 256, 0, s>>>(fp, kD, nullptr, (int)nP, FPi));
   LSR_LAUNCH(k_gather_rows<<<nblk(nQ * kDS), 256, 0, s>>>(fq, kD, nullptr, (int)nQ, FQi));
   if (tc)
-    TRY_CUDA(c, launch_match_bf16(FPi, (int)nP, FQi, (int)nQ, split, tws, dn, dd, flags, flags + 1, nullptr, s),
+    TRY_CUDA(c, launch_match_bf16(FPi, (int)nP, FQi, (int)nQ, split, match_tile_for(c, (int)nP), tws, dn, dd, flags, flags + 1,
+                                  nullptr, s),
              "match");
   else
     TRY_CUDA(c, launch_match_fp32(FPi, (int)nP, FQi, (int)nQ, dn, dd, s), "match");
@@ -952,7 +1293,8 @@ int lsr_match_scores_bf16(lsr_ctx *c, const float *FP, int64_t nP, const float *
   TRY_CUDA(c, cudaMemcpyAsync(fq, FQ, sizeof(float) * kD * nQ, cudaMemcpyDefault, s), "copy FQ");
   LSR_LAUNCH(k_gather_rows<<<nblk(nP * kDS), 256, 0, s>>>(fp, kD, nullptr, (int)nP, FPi));
   LSR_LAUNCH(k_gather_rows<<<nblk(nQ * kDS), 256, 0, s>>>(fq, kD, nullptr, (int)nQ, FQi));
-  TRY_CUDA(c, launch_match_bf16(FPi, (int)nP, FQi, (int)nQ, split, tws, nullptr, nullptr, flags, flags + 1, sc, s),
+  TRY_CUDA(c, launch_match_bf16(FPi, (int)nP, FQi, (int)nQ, split, match_tile_for(c, (int)nP), tws, nullptr, nullptr,
+                                flags, flags + 1, sc, s),
            "scores");
   int hflags[2] = {0, 0};
   TRY_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s), "copy flags");

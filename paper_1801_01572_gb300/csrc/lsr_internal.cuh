@@ -257,9 +257,11 @@ cudaError_t launch_match_fp32_rows(const float *FP, int nP, const float *FQ, int
 // fb_count: queries re-scanned in FP32; err: 1 if a CTA gave up waiting. With
 // d2 != null it writes D~^2 = |b~|^2 - 2 a~.b~ + |a~|^2 for every pair (nP
 // rows of tc_score_cols(nQ)) instead of matching.
+// qt: query tiles of 128 per CTA work unit (1 or 2; 0 = tc_default_tile(nP)).
 size_t tc_workspace_bytes(int nP, int nQ, bool split);
 int tc_score_cols(int nQ);
-cudaError_t launch_match_bf16(const float *FP, int nP, const float *FQ, int nQ, bool split, char *ws, int *nn,
+int tc_default_tile(int nP);
+cudaError_t launch_match_bf16(const float *FP, int nP, const float *FQ, int nQ, bool split, int qt, char *ws, int *nn,
                               float *d1, int *fb_count, int *err, float *d2, cudaStream_t s);
 
 // ----------------------------------------------------------------- RANSAC (lsr_ransac.cu)

@@ -54,17 +54,10 @@ namespace lsr {
 namespace {
 
 constexpr int kTcM = 128;                       // queries per MMA tile (TMEM lanes)
-constexpr int kQT = 2;                          // query tiles per CTA work unit
 constexpr int kTcN = 128;                       // database rows per tile
 constexpr int kLBO = 128;                       // bytes between K-adjacent core matrices
-constexpr int kStages = 4;                      // database tiles in flight
 constexpr int kTopK = 8;
-constexpr int kEpiWarps = 4 * kQT;              // warps 0..7: epilogue; warp 8: copies + MMA
-constexpr int kTcThreads = (kEpiWarps + 1) * 32;
-constexpr int kUnitQ = kQT * kTcM;              // queries of one work unit
 constexpr int kChunks = kTcN / 32;              // 32-column TMEM loads per accumulator row
-constexpr uint32_t kAccCols = kQT * kTcN;       // one accumulator buffer
-constexpr uint32_t kTmemCols = 2 * kAccCols;    // double-buffered (512 columns, all of TMEM)
 constexpr unsigned long long kWaitNs = 2000000000ull;  // give up after 2 s
 constexpr float kPadScore = 1.2676506e30f;      // 2^100: |b~|^2 of padding rows
 constexpr float kAccErr = 1.5e-5f;              // accumulation error per unit of sum |products|
@@ -77,13 +70,31 @@ struct Shape {
   static constexpr int K = 16 * KS;
   static constexpr int SBO = (K / 8) * 128;      // bytes between 8-row groups
   static constexpr int TileBytes = kTcM * K * 2;
-  static constexpr int UnitBytes = kQT * TileBytes;
   static constexpr int SqCol = kSplit ? 3 * kD : kD;  // first |b~|^2 column
-  static constexpr int SmemUsed = UnitBytes + kStages * TileBytes + 128;
-  // more than half an SM, so that one CTA per SM owns all of TMEM
-  static constexpr int SmemBytes = SmemUsed > 120 * 1024 ? SmemUsed : 120 * 1024;
   static_assert(SqCol + 3 <= K, "operand layout");
-  static_assert(SmemUsed <= 227 * 1024, "shared memory plan");
+};
+
+// Tile shape of the persistent CTA: QT query tiles of 128 per work unit.
+//   QT = 2: 256 queries share every database tile; 4 copy stages; 512 TMEM
+//           columns (two buffers of 2 x 128): one CTA per SM.
+//   QT = 1: 128 queries; 3 stages; 256 TMEM columns: two CTAs per SM, so
+//           small clouds still spread over every SM.
+template <int KS, int QT>
+struct Cfg {
+  static constexpr int Stages = QT == 2 ? 4 : 3;
+  static constexpr int EpiWarps = 4 * QT;        // warps 0..EpiWarps-1: epilogue; the next: copies + MMA
+  static constexpr int Threads = (EpiWarps + 1) * 32;
+  static constexpr int UnitQ = QT * kTcM;
+  static constexpr uint32_t AccCols = QT * kTcN; // one accumulator buffer
+  static constexpr uint32_t TmemCols = 2 * AccCols;
+  static constexpr int CtasPerSm = QT == 2 ? 1 : 2;
+  static constexpr int UnitBytes = QT * Shape<KS>::TileBytes;
+  static constexpr int SmemUsed = UnitBytes + Stages * Shape<KS>::TileBytes + 128;
+  // enough shared memory that no more CTAs than TMEM holds share an SM
+  static constexpr int SmemFloor = CtasPerSm == 1 ? 120 * 1024 : 80 * 1024;
+  static constexpr int SmemBytes = SmemUsed > SmemFloor ? SmemUsed : SmemFloor;
+  static_assert(CtasPerSm * (SmemBytes + 1024) <= 228 * 1024, "shared memory plan");
+  static_assert(CtasPerSm * TmemCols <= 512, "tensor memory plan");
 };
 
 template <int KS>
@@ -332,12 +343,15 @@ __device__ __forceinline__ void top8_insert(float (&ts)[kTopK], int (&ti)[kTopK]
     }
 }
 
-template <int KS>
-__global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(TcArgs g) {
+template <int KS, int QT>
+__global__ void __launch_bounds__(Cfg<KS, QT>::Threads, Cfg<KS, QT>::CtasPerSm) k_match_tc(TcArgs g) {
   using S = Shape<KS>;
+  using C = Cfg<KS, QT>;
+  constexpr int kStages = C::Stages, kEpiWarps = C::EpiWarps, kUnitQ = C::UnitQ;
+  constexpr uint32_t kAccCols = C::AccCols, kTmemCols = C::TmemCols;
   extern __shared__ __align__(128) unsigned char smem[];
   char *sA = reinterpret_cast<char *>(smem);
-  char *sB = sA + S::UnitBytes;
+  char *sB = sA + C::UnitBytes;
   uint64_t *bars = reinterpret_cast<uint64_t *>(sB + kStages * S::TileBytes);
   uint64_t *barA = bars;                 // 1
   uint64_t *barB = bars + 1;             // kStages
@@ -391,8 +405,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(TcArgs g) {
           // the previous unit's MMAs must be done reading the query tiles
           if (j > 0 && !mbar_wait(barDone + ((j - 1) & 1), ((j - 1) >> 1) & 1, fail)) break;
           int u = blockIdx.x + (j / g.nNT) * gridDim.x;
-          mbar_expect_tx(barA, S::UnitBytes);
-          bulk_g2s(sA, g.A + (size_t)u * S::UnitBytes, S::UnitBytes, barA);
+          mbar_expect_tx(barA, C::UnitBytes);
+          bulk_g2s(sA, g.A + (size_t)u * C::UnitBytes, C::UnitBytes, barA);
           a_pending = units & 1;
           if (!mbar_wait(barA, units & 1, fail)) break;
           a_pending = -1;
@@ -405,7 +419,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_match_tc(TcArgs g) {
         tc_fence_after();
         const uint32_t d = tbase + (uint32_t)((j & 1) * kAccCols);
 #pragma unroll
-        for (int qt = 0; qt < kQT; ++qt)
+        for (int qt = 0; qt < QT; ++qt)
 #pragma unroll
           for (int k = 0; k < KS; ++k)
             mma_bf16(d + qt * kTcN, smem_desc<KS>(sA + qt * S::TileBytes + k * 2 * kLBO),
@@ -556,12 +570,14 @@ struct TcLayout {
   size_t bytes = 0;
 };
 
+// Query rows are padded to a multiple of 256 (a whole number of units for
+// either tile shape); unit u of shape QT is tiles QT u .. QT u + QT - 1.
 template <int KS>
 TcLayout tc_layout(char *base, int nP, int nQ) {
   using S = Shape<KS>;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-  size_t nU = (size_t)lsr_div_up(nP, kQT * kTcM), nNT = (size_t)lsr_div_up(nQ, kTcN);
-  size_t rowsA = nU * kQT * kTcM;
+  size_t tilesA = 2 * (size_t)lsr_div_up(nP, 2 * kTcM), nNT = (size_t)lsr_div_up(nQ, kTcN);
+  size_t rowsA = tilesA * kTcM;
   size_t off = 0;
   TcLayout L;
   auto take = [&](size_t bytes) {
@@ -569,7 +585,7 @@ TcLayout tc_layout(char *base, int nP, int nQ) {
     off += al(bytes);
     return p;
   };
-  L.A = take(nU * S::UnitBytes);
+  L.A = take(tilesA * S::TileBytes);
   L.B = take(nNT * S::TileBytes);
   L.aa = reinterpret_cast<float *>(take(rowsA * 4));
   L.eta = reinterpret_cast<float *>(take(rowsA * 4));
@@ -591,28 +607,38 @@ int sm_count() {
   return n > 0 ? n : 148;
 }
 
+template <int KS, int QT>
+cudaError_t launch_tc(const TcLayout &L, const float *FP, int nP, const float *FQ, int nQ, int *nn, float *d1,
+                      int *fb_count, int *err, float *d2, cudaStream_t s) {
+  using C = Cfg<KS, QT>;
+  const int nU = (int)lsr_div_up(nP, C::UnitQ), nNT = (int)lsr_div_up(nQ, kTcN);
+  LSR_CUDA_TRY(cudaFuncSetAttribute(k_match_tc<KS, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SmemBytes));
+  TcArgs g{L.A, L.B, L.aa, L.eta, L.maxes, L.maxes + 1, FP, FQ, nP, nQ, nU, nNT,
+           nn, d1, L.fb_rows, fb_count, err, d2};
+  const int slots = sm_count() * C::CtasPerSm;
+  const int grid = nU < slots ? nU : slots;
+  LSR_LAUNCH(k_match_tc<KS, QT><<<grid, C::Threads, C::SmemBytes, s>>>(g));
+  return cudaGetLastError();
+}
+
 template <int KS>
-cudaError_t run_tc(const float *FP, int nP, const float *FQ, int nQ, char *ws, int *nn, float *d1, int *fb_count,
-                   int *err, float *d2, cudaStream_t s) {
-  using S = Shape<KS>;
+cudaError_t run_tc(const float *FP, int nP, const float *FQ, int nQ, int qt, char *ws, int *nn, float *d1,
+                   int *fb_count, int *err, float *d2, cudaStream_t s) {
   TcLayout L = tc_layout<KS>(ws, nP, nQ);
-  const int nU = (int)lsr_div_up(nP, kQT * kTcM), nNT = (int)lsr_div_up(nQ, kTcN);
+  const int nNT = (int)lsr_div_up(nQ, kTcN);
   LSR_CUDA_TRY(cudaMemsetAsync(L.maxes, 0, 2 * sizeof(unsigned), s));
   LSR_CUDA_TRY(cudaMemsetAsync(fb_count, 0, sizeof(int), s));
   LSR_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   LSR_LAUNCH(k_center<<<1, kCenterGroups * kD, 0, s>>>(FQ, nQ, L.center));
-  const int rowsA = nU * kQT * kTcM, rowsB = nNT * kTcN;
+  const int rowsA = 2 * (int)lsr_div_up(nP, 2 * kTcM) * kTcM, rowsB = nNT * kTcN;
   PrepOut pa{L.A, L.aa, L.eta, nullptr, nullptr};
   PrepOut pb{L.B, nullptr, nullptr, L.maxes, L.maxes + 1};
   LSR_LAUNCH(k_prep_tiles<KS><<<(int)lsr_div_up(rowsA, 256), 256, 0, s>>>(FP, nP, rowsA, true, L.center, pa));
   LSR_LAUNCH(k_prep_tiles<KS><<<(int)lsr_div_up(rowsB, 256), 256, 0, s>>>(FQ, nQ, rowsB, false, L.center, pb));
-  LSR_CUDA_TRY(cudaFuncSetAttribute(k_match_tc<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SmemBytes));
-  TcArgs g{L.A, L.B, L.aa, L.eta, L.maxes, L.maxes + 1, FP, FQ, nP, nQ, nU, nNT,
-           nn, d1, L.fb_rows, fb_count, err, d2};
-  const int sms = sm_count();
-  const int grid = nU < sms ? nU : sms;
-  LSR_LAUNCH(k_match_tc<KS><<<grid, kTcThreads, S::SmemBytes, s>>>(g));
-  LSR_CUDA_TRY(cudaGetLastError());
+  if (qt == 1)
+    LSR_CUDA_TRY((launch_tc<KS, 1>(L, FP, nP, FQ, nQ, nn, d1, fb_count, err, d2, s)));
+  else
+    LSR_CUDA_TRY((launch_tc<KS, 2>(L, FP, nP, FQ, nQ, nn, d1, fb_count, err, d2, s)));
   if (!d2) LSR_CUDA_TRY(launch_match_fp32_rows(FP, nP, FQ, nQ, L.fb_rows, fb_count, L.packed, nn, d1, s));
   return cudaGetLastError();
 }
@@ -627,11 +653,14 @@ size_t tc_workspace_bytes(int nP, int nQ, bool split) {
 
 int tc_score_cols(int nQ) { return (int)lsr_div_up(nQ, kTcN) * kTcN; }
 
-cudaError_t launch_match_bf16(const float *FP, int nP, const float *FQ, int nQ, bool split, char *ws, int *nn,
+int tc_default_tile(int nP) { return lsr_div_up(nP, 2 * kTcM) >= 152 ? 2 : 1; }
+
+cudaError_t launch_match_bf16(const float *FP, int nP, const float *FQ, int nQ, bool split, int qt, char *ws, int *nn,
                               float *d1, int *fb_count, int *err, float *d2, cudaStream_t s) {
-  if (nP < 1 || nQ < 1) return cudaErrorInvalidValue;
-  return split ? run_tc<kKsSplit>(FP, nP, FQ, nQ, ws, nn, d1, fb_count, err, d2, s)
-               : run_tc<kKsPlain>(FP, nP, FQ, nQ, ws, nn, d1, fb_count, err, d2, s);
+  if (nP < 1 || nQ < 1 || (qt != 0 && qt != 1 && qt != 2)) return cudaErrorInvalidValue;
+  if (qt == 0) qt = tc_default_tile(nP);
+  return split ? run_tc<kKsSplit>(FP, nP, FQ, nQ, qt, ws, nn, d1, fb_count, err, d2, s)
+               : run_tc<kKsPlain>(FP, nP, FQ, nQ, qt, ws, nn, d1, fb_count, err, d2, s);
 }
 
 }  // namespace lsr

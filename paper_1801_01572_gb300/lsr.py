@@ -45,7 +45,8 @@ class Params(C.Structure):
                 ("cos_normal", C.c_float), ("min_inlier_ratio", C.c_float), ("mu_scale", C.c_float),
                 ("refine_iters", C.c_int32), ("n_hypotheses", C.c_int64), ("seed", C.c_uint64),
                 ("pair_id", C.c_uint64), ("match_precision", C.c_int32), ("refine_levels", C.c_int32),
-                ("reserved_", C.c_int32 * 4)]
+                ("batch_streams", C.c_int32), ("batch_graph", C.c_int32), ("match_tile", C.c_int32),
+                ("reserved_", C.c_int32)]
 
 
 class Result(C.Structure):
