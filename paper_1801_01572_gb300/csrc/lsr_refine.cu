@@ -17,7 +17,7 @@ namespace lsr {
 namespace {
 
 constexpr int kRefThreads = 256;
-constexpr int kRefG = 16;  // lanes per nearest-neighbour query in refinement
+constexpr int kRefG = 4;   // lanes per nearest-neighbour query in refinement (4 measured fastest of 4/8/16)
 constexpr int kObjG = 8;   // lanes per query in the objective
 // 21 (upper triangle of A) + 6 (b) + count + sum w + sum w x (3)
 constexpr int kNAcc = kRefAcc;
@@ -128,7 +128,7 @@ __device__ void refine_solve(const double *acc, RansacState *st, int max_iters, 
 
 // One IRLS step. Every block accumulates its points; the last block to
 // finish (atomic ticket, no waiting) sums all block partials and solves.
-__global__ void __launch_bounds__(kRefThreads) k_refine_step(const float4 *__restrict__ XP, int nP, int strideP,
+__global__ void __launch_bounds__(kRefThreads, 3) k_refine_step(const float4 *__restrict__ XP, int nP, int strideP,
                                                              const GridParams *gep, const int *__restrict__ start,
                                                              const float4 *__restrict__ Xe, float eps2, float mu,
                                                              RansacState *st, double *partials, int max_iters,
@@ -144,11 +144,23 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_step(const float4 *__res
     c[r] = (float)st->center[r];
     tc[r] = (float)(T[4 * r + 3] - st->center[r]);
   }
-  float acc[kNAcc];
-#pragma unroll
-  for (int k = 0; k < kNAcc; ++k) acc[k] = 0.f;
-  constexpr int G = kRefG, GPB = kRefThreads / G;
+  // every lane of a point group holds the same correspondence after the
+  // group search: lane sub accumulates the sums U sub .. U sub + U - 1 of the
+  // 32 (the 21 entries of J^T W J, the 6 of J^T W r, count, sum w, sum w x)
+  constexpr int G = kRefG, GPB = kRefThreads / G, U = kNAcc / G;
+  static_assert(U * G == kNAcc && G <= 32, "sums per lane of a point group");
   int grp = threadIdx.x / G, sub = threadIdx.x & (G - 1);
+  int qa[U], qb[U];  // the (a, b) column pair of a J^T W J entry, or -1
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    int k = U * sub + u, a = 0;
+    while (a < 6 && k >= 6 - a) k -= 6 - a, ++a;  // k-th entry of the row-major upper triangle
+    qa[u] = a < 6 ? a : -1;
+    qb[u] = a < 6 ? a + k : -1;
+  }
+  float acc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) acc[u] = 0.f;
   // block-uniform trip count: every lane reaches the group shuffles
   for (int r0 = blockIdx.x * GPB; r0 < nP; r0 += gridDim.x * GPB) {
     int i = r0 + grp;
@@ -163,38 +175,73 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_step(const float4 *__res
     float best;
     int bt, bidx;
     group_nn<G>(g, start, Xe, x, y, z, eps2, best, bt, bidx);
-    if (!valid || sub != 0 || bt < 0) continue;
+    if (!valid || bt < 0) continue;
     float4 q = Xe[bt];
     float r[3] = {x - q.x, y - q.y, z - q.z};
     float s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
     float l = mu / (mu + s);
     float w = l * l;
     // J = [-[xc]_x | I] (rows: x, y, z; columns: alpha, beta, gamma, tx, ty, tz)
-    float J[3][6] = {{0.f, xc2, -xc1, 1.f, 0.f, 0.f}, {-xc2, 0.f, xc0, 0.f, 1.f, 0.f}, {xc1, -xc0, 0.f, 0.f, 0.f, 1.f}};
-    int k = 0;
+    auto col = [&](int a, float (&v)[3]) {
+      v[0] = a == 1 ? xc2 : (a == 2 ? -xc1 : (a == 3 ? 1.f : 0.f));
+      v[1] = a == 0 ? -xc2 : (a == 2 ? xc0 : (a == 4 ? 1.f : 0.f));
+      v[2] = a == 0 ? xc1 : (a == 1 ? -xc0 : (a == 5 ? 1.f : 0.f));
+    };
 #pragma unroll
-    for (int a = 0; a < 6; ++a)
-#pragma unroll
-      for (int b = a; b < 6; ++b) {
-        acc[k++] += w * (J[0][a] * J[0][b] + J[1][a] * J[1][b] + J[2][a] * J[2][b]);
+    for (int u = 0; u < U; ++u) {
+      const int k = U * sub + u;
+      float va[3], vb[3];
+      if (qa[u] >= 0) {
+        col(qa[u], va);
+        col(qb[u], vb);
+        acc[u] += w * (va[0] * vb[0] + va[1] * vb[1] + va[2] * vb[2]);
+      } else if (k < 27) {
+        col(k - 21, va);
+        acc[u] += w * (va[0] * r[0] + va[1] * r[1] + va[2] * r[2]);
+      } else {
+        acc[u] += k == 27 ? 1.f : (k == 28 ? w : w * (k == 29 ? x : (k == 30 ? y : z)));
       }
-#pragma unroll
-    for (int a = 0; a < 6; ++a) acc[21 + a] += w * (J[0][a] * r[0] + J[1][a] * r[1] + J[2][a] * r[2]);
-    acc[27] += 1.f;
-    acc[28] += w;
-    acc[29] += w * x, acc[30] += w * y, acc[31] += w * z;
+    }
   }
-  block_reduce_to<kNAcc>(acc, partials + (size_t)blockIdx.x * kNAcc);
+  {
+    // the lanes sub, sub + G, ... of a warp hold the same sums
+    __shared__ float sm[kRefThreads / 32][kNAcc];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off >= G; off >>= 1)
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u] += __shfl_down_sync(0xffffffffu, acc[u], off);
+    if (lane < G)
+#pragma unroll
+      for (int u = 0; u < U; ++u) sm[wp][U * lane + u] = acc[u];
+    __syncthreads();
+    if (threadIdx.x < kNAcc) {
+      double t = 0.0;
+      for (int k = 0; k < kRefThreads / 32; ++k) t += (double)sm[k][threadIdx.x];
+      partials[(size_t)blockIdx.x * kNAcc + threadIdx.x] = t;
+    }
+  }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (threadIdx.x < kNAcc) {
+  {
+    // all threads: quantity k = t % 32 over the blocks t / 32, t / 32 + 8, ...,
+    // then the 8 segments in order (a fixed order: the sums are deterministic)
+    constexpr int kSeg = kRefThreads / kNAcc;
+    __shared__ double seg[kSeg][kNAcc];
+    const int k = threadIdx.x % kNAcc, sg = threadIdx.x / kNAcc;
     double sum = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) sum += __ldcg(partials + (size_t)b * kNAcc + threadIdx.x);
-    tot[threadIdx.x] = sum;
+    for (unsigned b = sg; b < gridDim.x; b += kSeg) sum += __ldcg(partials + (size_t)b * kNAcc + k);
+    seg[sg][k] = sum;
+    __syncthreads();
+    if (threadIdx.x < kNAcc) {
+      double t = 0.0;
+      for (int q = 0; q < kSeg; ++q) t += seg[q][threadIdx.x];
+      tot[threadIdx.x] = t;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -324,7 +371,7 @@ __global__ void k_objective_sum(const double *partials, int nblocks, double *out
 // that the launch-closing block sums few partials.
 int refine_blocks(int nP) {
   int64_t b = lsr_div_up((int64_t)(nP > 0 ? nP : 1) * kRefG, kRefThreads);
-  return (int)(b < 1 ? 1 : (b > 152 * 2 ? 152 * 2 : b));
+  return (int)(b < 1 ? 1 : (b > 152 * 3 ? 152 * 3 : b));  // three resident blocks per SM
 }
 
 int gnc_stride(int64_t n, int level, int levels) {
@@ -373,7 +420,7 @@ cudaError_t launch_final_count(const int *count, const unsigned long long *sum, 
 
 int objective_blocks(int nP) {
   int64_t b = lsr_div_up((int64_t)(nP > 0 ? nP : 1) * kObjG, kRefThreads);
-  return (int)(b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b));
+  return (int)(b < 1 ? 1 : (b > 152 * 2 ? 152 * 2 : b));
 }
 
 cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
