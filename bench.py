@@ -127,7 +127,7 @@ def run_ours(args, rank, world):
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    fp = make_pair(args.config, pair=rank)
+    fp = make_pair(args.config, pair=rank, n_p=args.points, n_q=args.points)
     nP, nQ = len(fp.P), len(fp.Q)
     P = torch.from_numpy(fp.P).cuda()
     Q = torch.from_numpy(fp.Q).cuda()
@@ -347,8 +347,11 @@ def roofline(info):
         # brute-force FP32 NN: per (query, candidate) pair 33 subtract + 33 fused multiply-add
         flops = float(nP) * float(nQ) * 33 * 3
         ach = flops / (st[k] * 1e-3) / 1e12
+        # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
+        # (profiles/k_match_fp32_room150k_dram.md); the two descriptor tables, read once
+        traffic = 43748864 + 21760 if (nP, nQ) == (150000, 150000) else None
         return {"kernel": "k_match_fp32", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None,
+                "frac": ach / fp32_peak, "traffic": traffic,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (FFMA issue peak)",
                 "work": "nP*nQ*33*3 flop"}
     if names[k] == "consensus":
@@ -472,6 +475,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--match", default="fp32", choices=sorted(MATCH_MODES))
+    ap.add_argument("--points", type=int, default=None,
+                    help="points per cloud instead of the configuration's (a smaller case of the same scene, "
+                         "for profiler captures)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
@@ -534,7 +540,9 @@ def main():
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": info["total_ms"] / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.config], "points": [info["nP"], info["nQ"]],
+            "config": {"workload": WORKLOADS[args.config] if args.points is None else
+                       f"{WORKLOADS[args.config]}, resized to {args.points} points per cloud",
+                       "points": [info["nP"], info["nQ"]],
                        "hypotheses": int(prm.n_hypotheses), "match": args.match, "refine_levels": int(prm.refine_levels),
                        "l2": "flushed between steps by a 256 MB write outside the timed events",
                        "parallelism": "replicas (one pair per GPU)" if world > 1 else "single GPU"},
