@@ -2,9 +2,13 @@
 // "Parallel FPFH feature pre-matching": nn[i] = NN of F(p_i) in F(Q)).
 //
 // Exact brute force: nn[i] = argmin_j sum_k (a_k - b_k)^2 with ties to the
-// smallest j. Each thread keeps two query descriptors in registers; tiles of
-// database descriptors are staged in shared memory and read as broadcasts,
-// so one shared load feeds two distance accumulations.
+// smallest j, accumulated as s = fma(t, t, s) over k = 0..32. Each thread keeps
+// two query descriptors in registers; tiles of database descriptors are
+// staged in shared memory and read as broadcasts, so one shared load feeds two
+// distance accumulations. The partial sums only grow (t^2 >= 0 and rounding is
+// monotone), so a row whose partial sum already exceeds every query's current
+// best in the warp can neither win nor tie: after 8, 16 and 24 components the
+// warp tests that and skips the rest of the row (same result).
 #include <float.h>
 
 #include "lsr_internal.cuh"
@@ -49,6 +53,12 @@ __global__ void __launch_bounds__(kMT) k_match_fp32(const float *__restrict__ FP
       for (int u = 0; u < kQPT; ++u) s[u] = 0.f;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
+        if (c % 2 == 0 && c > 0) {
+          bool past = true;
+#pragma unroll
+          for (int u = 0; u < kQPT; ++u) past &= s[u] > best[u];
+          if (__all_sync(0xffffffffu, past)) break;
+        }
         float4 b = tile[j][c];
 #pragma unroll
         for (int u = 0; u < kQPT; ++u) {
@@ -59,13 +69,15 @@ __global__ void __launch_bounds__(kMT) k_match_fp32(const float *__restrict__ FP
           s[u] = fmaf(t2, t2, s[u]);
           s[u] = fmaf(t3, t3, s[u]);
         }
-      }
-      float b32 = tile[j][8].x;
+        if (c == 7) {
+          float b32 = tile[j][8].x;
 #pragma unroll
-      for (int u = 0; u < kQPT; ++u) {
-        float t = a[u][32] - b32;
-        s[u] = fmaf(t, t, s[u]);
-        if (s[u] < best[u]) best[u] = s[u], bj[u] = base + j;
+          for (int u = 0; u < kQPT; ++u) {
+            float t = a[u][32] - b32;
+            s[u] = fmaf(t, t, s[u]);
+            if (s[u] < best[u]) best[u] = s[u], bj[u] = base + j;
+          }
+        }
       }
     }
   }
@@ -123,6 +135,12 @@ __global__ void __launch_bounds__(kMT) k_match_rows_chunked(const float *__restr
         for (int u = 0; u < kQPT; ++u) s[u] = 0.f;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
+          if (c % 2 == 0 && c > 0) {
+            bool past = true;
+#pragma unroll
+            for (int u = 0; u < kQPT; ++u) past &= s[u] > best[u];
+            if (__all_sync(0xffffffffu, past)) break;
+          }
           float4 b = tile[j][c];
 #pragma unroll
           for (int u = 0; u < kQPT; ++u) {
@@ -133,13 +151,15 @@ __global__ void __launch_bounds__(kMT) k_match_rows_chunked(const float *__restr
             s[u] = fmaf(t2, t2, s[u]);
             s[u] = fmaf(t3, t3, s[u]);
           }
-        }
-        float b32 = tile[j][8].x;
+          if (c == 7) {
+            float b32 = tile[j][8].x;
 #pragma unroll
-        for (int u = 0; u < kQPT; ++u) {
-          float t = a[u][32] - b32;
-          s[u] = fmaf(t, t, s[u]);
-          if (s[u] < best[u]) best[u] = s[u], bj[u] = base + j;
+            for (int u = 0; u < kQPT; ++u) {
+              float t = a[u][32] - b32;
+              s[u] = fmaf(t, t, s[u]);
+              if (s[u] < best[u]) best[u] = s[u], bj[u] = base + j;
+            }
+          }
         }
       }
     }
