@@ -45,8 +45,12 @@ WORKLOADS = {
     1: "indoor room pair on a 1 cm voxel grid, 150,000 points per cloud, 50% overlap, 4M hypotheses, FP32",
     2: "256 indoor room pairs on a 1 cm voxel grid, 10k-120k points per cloud, 30-80% overlap, 4M hypotheses "
        "each, one batch per step (BF16 tensor-core matching, concurrent streams, one CUDA graph)",
+    3: "64 indoor room pairs on a 1 cm voxel grid, 200,000 points per cloud, 50% overlap, 4M hypotheses each, "
+       "one batch per step (BF16 tensor-core matching, top-8 FP32 re-rank, concurrent streams, one CUDA graph)",
+    4: "32 indoor room pairs of 50,000 points per cloud: robust alignment objective forward + backward (points and "
+       "se(3) pose) for all pairs per step through RobustAlignBatch",
 }
-N_BATCH = 256
+BATCH_PAIRS = {2: 256, 3: 64, 4: 32}
 MATCH_MODES = {"fp32": 0, "bf16": 1, "bf16_plain": 2}
 FP32_LANES_PER_SM = 128
 N_SM = 152
@@ -221,20 +225,21 @@ def run_ours(args, rank, world):
     return info
 
 
-# ---------------------------------------------------------------- config 2
-def _gen_pair(i):
+# ---------------------------------------------------------------- configs 2-4
+def _gen_pair(ci):
     from synth import make_pair
-    p = make_pair(2, i)
-    return p.P, p.Q, p.vpP, p.vpQ
+    p = make_pair(*ci)
+    return p.P, p.Q, p.vpP, p.vpQ, p.T
 
 
-def batch_pairs(rank):
-    """The 256 pairs of this rank, generated in parallel host processes before
-    any GPU work."""
+def batch_pairs(config, rank):
+    """The pairs of this rank, generated in parallel host processes before any
+    GPU work."""
     import multiprocessing as mp
-    ids = list(range(rank * N_BATCH, (rank + 1) * N_BATCH))
+    n = BATCH_PAIRS[config]
+    ids = [(config, i) for i in range(rank * n, (rank + 1) * n)]
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        return pool.map(_gen_pair, ids, chunksize=4)
+        return pool.map(_gen_pair, ids, chunksize=2)
 
 
 def _timed(stream, flush, fn):
@@ -289,7 +294,7 @@ def run_batch(args, rank, world, pairs):
     e2e_ms = float(sum(e2e)) / len(e2e)
     ctx.close()
     # the plain FP32 single-pair path on the first pairs of the same batch
-    m = 32
+    m = min(32, len(pairs))
     sctx = lsr.Context(dev, stream=stream.cuda_stream)
     sctx.register_pair(P[0], Q[0], pairs[0][2], pairs[0][3])
 
@@ -314,7 +319,7 @@ def run_batch(args, rank, world, pairs):
     h2d = sum(lsr.transfer_bytes(len(p[0]), len(p[1]))[0] for p in pairs)
     d2h = sum(lsr.transfer_bytes(len(p[0]), len(p[1]))[1] for p in pairs)
     identical = all(np.array_equal(single[i].T, res[i].T) and single[i].inliers == res[i].inliers for i in range(m))
-    return dict(total_ms=total_ms, e2e_ms=e2e_ms, launches=launches, npts=npts,
+    return dict(total_ms=total_ms, e2e_ms=e2e_ms, launches=launches, npts=npts, res=res,
                 clocks=clk.summary(pk.get("sm_max_mhz")), single_ms=single_ms, m=m, identical=identical,
                 aligned=sum(r.status == 0 for r in res), h2d=h2d, d2h=d2h,
                 roofline={"kernel": "k_match_tc", "bound": "tensor", "achieved": ach, "peak": peak,
@@ -322,6 +327,70 @@ def run_batch(args, rank, world, pairs):
                           "work": f"2*nP*nQ*112 flop on the largest pair ({nPb} x {nQb}); matching stage time "
                                   "(operand preparation, re-rank and exact fallback included)",
                           "peak_source": "MEASURED_PEAKS.json bf16 burst (cuBLAS)"})
+
+
+def run_objective(args, rank, world, pairs):
+    """Config 4: one batched forward + backward of the robust alignment objective
+    over all pairs per step (RobustAlignBatch), nearest neighbours recomputed in
+    the backward."""
+    import torch
+
+    import paper_1801_01572_gb300 as lsr
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    n = len(pairs)
+    rng = np.random.default_rng(44 + rank)
+    xis = np.concatenate([rng.normal(0, 2e-3, (n, 3)), rng.normal(0, 3e-3, (n, 3))], axis=1)
+    T0s = torch.tensor(np.stack([p[4] for p in pairs]))
+    eps = 0.0375
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ctx = lsr.Context(dev, stream=stream.cuda_stream)
+    clouds = []
+    for p in pairs:
+        clouds += [torch.tensor(p[0], device="cuda", requires_grad=True),
+                   torch.tensor(p[1], device="cuda", requires_grad=True)]
+    xt = torch.tensor(xis, dtype=torch.float64, requires_grad=True)
+
+    def step(cl):
+        with torch.cuda.stream(stream):
+            E = lsr.RobustAlignBatch.apply(xt, T0s, eps, eps * eps, ctx, *cl)
+            E.sum().backward()
+        return E
+    for _ in range(args.warmup):
+        step(clouds)
+    torch.cuda.synchronize()
+    pk, _ = peaks()
+    times = []
+    with ClockSampler(dev) as clk:
+        l0 = lsr.launch_count()
+        for _ in range(args.steps):
+            ms, _ = _timed(stream, flush, lambda: step(clouds))
+            times.append(ms)
+        launches = lsr.launch_count() - l0
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # end to end: the clouds copied from pinned host memory and the gradients read back, every step
+    hostP = [torch.from_numpy(p[0]).pin_memory() for p in pairs]
+    hostQ = [torch.from_numpy(p[1]).pin_memory() for p in pairs]
+
+    def e2e_step():
+        cl = []
+        for a, b in zip(hostP, hostQ):
+            cl += [a.to("cuda", non_blocking=True).requires_grad_(), b.to("cuda", non_blocking=True).requires_grad_()]
+        E = step(cl)
+        grads = [c.grad.to("cpu") for c in cl]
+        return E.detach().cpu(), grads
+    e2e_step()
+    e2e = [_timed(stream, flush, e2e_step)[0] for _ in range(max(1, args.steps // 2))]
+    npts = sum(len(p[0]) + len(p[1]) for p in pairs)
+    ctx.close()
+    return dict(total_ms=total_ms, e2e_ms=float(sum(e2e)) / len(e2e), launches=launches, npts=npts,
+                clocks=clk.summary(pk.get("sm_max_mhz")), h2d=12 * npts, d2h=12 * npts + 8 * n)
 
 
 def roofline(info):
@@ -348,8 +417,8 @@ def roofline(info):
         flops = float(nP) * float(nQ) * 33 * 3
         ach = flops / (st[k] * 1e-3) / 1e12
         # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
-        # (profiles/k_match_fp32_room150k_dram.md); the two descriptor tables, read once
-        traffic = 43748864 + 21760 if (nP, nQ) == (150000, 150000) else None
+        # (profiles/k_match_fp32_room150k_dram.md), null until taken on the current kernel
+        traffic = None
         return {"kernel": "k_match_fp32", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": ach / fp32_peak, "traffic": traffic,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (FFMA issue peak)",
@@ -473,7 +542,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2, 3, 4])
     ap.add_argument("--match", default="fp32", choices=sorted(MATCH_MODES))
     ap.add_argument("--points", type=int, default=None,
                     help="points per cloud instead of the configuration's (a smaller case of the same scene, "
@@ -486,7 +555,7 @@ def main():
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", 1))
     rank = int(os.environ.get("RANK", 0))
-    pairs = batch_pairs(rank) if args.config == 2 and args.impl == "ours" else None
+    pairs = batch_pairs(args.config, rank) if args.config in BATCH_PAIRS and args.impl == "ours" else None
     if world > 1 and args.impl == "ours":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
@@ -498,8 +567,40 @@ def main():
             print(json.dumps(line), flush=True)
         return
 
-    if args.config == 2:
+    if args.config == 4:
+        info = run_objective(args, rank, world, pairs)
+        if rank == 0:
+            K, n = args.steps, len(pairs)
+            value = world * K * n / (info["total_ms"] * 1e-3)
+            line = {
+                "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": info["total_ms"] / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS[4], "pairs_per_step": n, "points_per_step": info["npts"],
+                           "l2": "flushed between steps by a 256 MB write outside the timed events",
+                           "parallelism": "replicas (one batch per GPU)" if world > 1 else "single GPU"},
+                "points_per_s": value * info["npts"] / n,
+                "e2e": {"value": world * n / (info["e2e_ms"] * 1e-3), "unit": "pairs/s",
+                        "h2d_bytes_per_step": info["h2d"] * world, "d2h_bytes_per_step": info["d2h"] * world},
+                "gpu_launches": int(info["launches"]), "clocks": info["clocks"],
+            }
+            # algorithmic bytes: the forward and the backward each read both clouds once,
+            # the backward writes dP and dQ (12 B per point each way)
+            pk, src = peaks()
+            ach = 36.0 * info["npts"] / (line["ms_per_step"] * 1e-3) / 1e9
+            line["roofline"] = {"kernel": "objective fwd+bwd (whole step)", "bound": "hbm", "achieved": ach,
+                                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
+                                "work": "36 B per point per step over the step time", "peak_source": src}
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            import torch
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+
+    if args.config in (2, 3):
         info = run_batch(args, rank, world, pairs)
+        N_BATCH = len(pairs)
         if rank == 0:
             K = args.steps
             value = world * K * N_BATCH / (info["total_ms"] * 1e-3)
@@ -507,7 +608,8 @@ def main():
                 "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": info["total_ms"] / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
-                "config": {"workload": WORKLOADS[2], "pairs_per_step": N_BATCH, "points_per_step": info["npts"],
+                "config": {"workload": WORKLOADS[args.config], "pairs_per_step": N_BATCH,
+                           "points_per_step": info["npts"],
                            "l2": "flushed between steps by a 256 MB write outside the timed events",
                            "parallelism": "replicas (one batch per GPU)" if world > 1 else "single GPU"},
                 "points_per_s": value * info["npts"] / N_BATCH,
@@ -518,10 +620,22 @@ def main():
                 "gpu_launches": int(info["launches"]),
                 "variants": {"fp32_single_pair": {
                     "value": info["m"] / (info["single_ms"] * 1e-3), "unit": "pairs/s",
-                    "sample": f"first {info['m']} of the 256 pairs, lsr_register_pair one after another, FP32 matching",
+                    "sample": f"first {info['m']} of the {N_BATCH} pairs, lsr_register_pair one after another, "
+                              "FP32 matching",
                     "identical_pose": info["identical"]}},
                 "clocks": info["clocks"],
             }
+            if args.config == 3:
+                # pose error against the FP64 oracle on two pairs: the oracle's graduated
+                # refinement from the generator's pose reaches the fixed point the path converges to
+                import oracle
+                from synth import pose_error
+                errs = []
+                for i in (0, 1):
+                    T_ref, _ = oracle.refine_gnc(pairs[i][0], pairs[i][1], pairs[i][4], 0.0375, 1.0, levels=3, iters=50)
+                    errs.append(pose_error(info["res"][i].T, T_ref))
+                line["result"]["oracle_pose_error"] = {"deg": max(e[0] for e in errs), "m": max(e[1] for e in errs),
+                                                       "pairs": 2}
             print(json.dumps(line), flush=True)
         if world > 1:
             import torch
