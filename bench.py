@@ -137,7 +137,6 @@ def run_ours(args, rank, world):
     Q = torch.from_numpy(fp.Q).cuda()
     stream = torch.cuda.Stream()
     ctx = lsr.Context(dev, stream=stream.cuda_stream, match_precision=MATCH_MODES[args.match])
-    ctx.set_profiling(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         ctx.register_pair(P, Q, fp.vpP, fp.vpQ)
@@ -158,7 +157,6 @@ def run_ours(args, rank, world):
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
-            stages += np.array(last.stage_ms)
         launches = lsr.launch_count() - l0
     torch.cuda.synchronize()
     if world > 1:
@@ -168,7 +166,17 @@ def run_ours(args, rank, world):
         t = torch.tensor([total_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    stage_ms = stages / args.steps
+    # per-stage device times (and the FP32 matcher's term count) from profiled
+    # runs after the timed region: stage events and the counting matcher
+    ctx.set_profiling(True)
+    n_prof = min(args.steps, 3)
+    for _ in range(n_prof):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        prof = ctx.register_pair(P, Q, fp.vpP, fp.vpQ)
+        stages += np.array(prof.stage_ms)
+    ctx.set_profiling(False)
+    stage_ms = stages / n_prof
 
     # end to end through the public API from pinned host memory
     Ph = torch.from_numpy(fp.P).pin_memory()
@@ -191,7 +199,7 @@ def run_ours(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
     h2d, d2h = lsr.transfer_bytes(nP, nQ)
-    info = dict(fp=fp, nP=nP, nQ=nQ, last=last, stage_ms=stage_ms, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d,
+    info = dict(fp=fp, nP=nP, nQ=nQ, last=last, prof=prof, stage_ms=stage_ms, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d,
                 d2h=d2h, launches=launches, clocks=clk.summary(pk.get("sm_max_mhz")), peaks=pk,
                 params=ctx.params, match=args.match)
     ctx.close()
@@ -413,16 +421,24 @@ def roofline(info):
                 "frac": ach / peak, "traffic": None, "peak_source": f"{src} bf16 burst (cuBLAS)",
                 "work": f"2*nP*nQ*{K} flop (stage time incl. operand preparation, re-rank and exact fallback)"}
     if names[k] == "matching":
-        # brute-force FP32 NN: per (query, candidate) pair 33 subtract + 33 fused multiply-add
-        flops = float(nP) * float(nQ) * 33 * 3
-        ach = flops / (st[k] * 1e-3) / 1e12
+        # brute-force FP32 NN: per (query, candidate) pair 33 terms of one subtract and
+        # one fused multiply-add (3 flop, 2 issue slots: the mix's peak is 1.5 flop per
+        # lane per cycle). The exact early exit skips most terms, so the dense
+        # definition's rate can exceed the pipe; executed_frac is the executed terms'
+        # share of the pipe (terms counted by the profiled matcher launch).
+        dense = float(nP) * float(nQ) * 33
+        ach = dense * 3 / (st[k] * 1e-3) / 1e12
+        peak = N_SM * FP32_LANES_PER_SM * 1.5 * sm_mhz * 1e6 / 1e12
+        terms = float(info["prof"].match_terms)
         # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
-        # (profiles/k_match_fp32_room150k_dram.md), null until taken on the current kernel
-        traffic = None
-        return {"kernel": "k_match_fp32", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": traffic,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (FFMA issue peak)",
-                "work": "nP*nQ*33*3 flop"}
+        # (profiles/k_match_fp32_room150k_dram.md)
+        traffic = 44161280 + 22528 if (nP, nQ) == (150000, 150000) else None
+        return {"kernel": "k_match_fp32", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": traffic,
+                "executed_terms": terms, "executed_share": terms / dense,
+                "executed_frac": terms * 3 / (st[k] * 1e-3) / 1e12 / peak,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 1.5 flop x {sm_mhz:.0f} MHz (FADD+FFMA issue peak)",
+                "work": "nP*nQ*33 terms x 3 flop (dense definition)"}
     if names[k] == "consensus":
         # per (hypothesis, point) query: the rigid transform (9 FMA) and the
         # squared-distance test of the points within eps (counted at one candidate)

@@ -105,6 +105,8 @@ typedef struct {
   int64_t n_normal_ok;    /* survivors that also pass the normal check */
   int64_t best_h;         /* id of the selected hypothesis, -1 if none */
   int64_t match_fallbacks; /* BF16 matching: queries re-scanned exactly in FP32 */
+  int64_t match_terms;    /* FP32 matching with profiling enabled: descriptor terms (a_k - b_k)^2 evaluated, of
+                             nP * nQ * 33 for a scan without early exit; else 0 */
   float fitness;          /* mean squared inlier distance under T (m^2) */
   float hyp_fitness;      /* the same for the selected hypothesis */
   int32_t status;         /* LSR_STATUS_ALIGNED or LSR_STATUS_NO_ALIGNMENT */

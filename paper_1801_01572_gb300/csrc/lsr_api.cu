@@ -184,7 +184,7 @@ struct PairLayout {
   int *fcount = nullptr;
   unsigned long long *fsum = nullptr;
   RansacState *st = nullptr;
-  char *tc_ws = nullptr;  // BF16 matcher workspace (BF16 precision only)
+  char *tc_ws = nullptr;  // matcher workspace (tile bounds for FP32, operands and lists for BF16)
   ClsParams *cls = nullptr;  // consensus voxel classification of Q
   unsigned *in_bits = nullptr, *near_bits = nullptr;
   uint8_t *sel = nullptr;    // the hypotheses with the largest count upper bounds
@@ -229,8 +229,8 @@ void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int leve
   L.tie = a.take<uint8_t>(L.surv_cap);
   L.amb = a.take<int>(L.surv_cap);
   L.count2 = a.take<int>(L.surv_cap);
-  if (precision != LSR_MATCH_FP32)
-    L.tc_ws = a.take<char>(tc_workspace_bytes(nP, nQ, precision == LSR_MATCH_BF16));
+  L.tc_ws = a.take<char>(precision != LSR_MATCH_FP32 ? tc_workspace_bytes(nP, nQ, precision == LSR_MATCH_BF16)
+                                                      : fp32_workspace_bytes(nQ));
 }
 
 int set_err(lsr_ctx *c, int code, const char *msg) {
@@ -266,6 +266,18 @@ bool is_device_ptr(const void *p) {
     return false;
   }
   return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// Page-locked host memory: copies from it can be captured into a CUDA graph.
+bool is_pinned_host_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeHost;
 }
 
 int ensure_ws(lsr_ctx *c, size_t bytes) {
@@ -481,7 +493,10 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
                                &L.st->match_fallbacks, &L.st->match_err, nullptr, s),
              "match");
   else
-    TRY_CUDA(c, launch_match_fp32(Pc.F, nP, Qc.F, nQ, L.nn, L.d1, s), "match");
+    TRY_CUDA(c,
+             launch_match_fp32(Pc.F, nP, Qc.F, nQ, L.tc_ws, L.nn, L.d1, s,
+                               c->profiling ? &L.st->match_terms : nullptr),
+             "match");
   tm.mark();
   TRY_CUDA(c,
            launch_hypotheses(Pc.X, Pc.inv, Pc.N, nP, Qc.X, Qc.N, nQ, L.nn, nullptr, nullptr, p.n_hypotheses, p.seed,
@@ -554,6 +569,7 @@ void fill_result(const RansacState &st, const float *boxP, const float *boxQ, ls
   r->n_normal_ok = st.n_normal_ok;
   r->best_h = st.best >= 0 ? st.best_h : -1;
   r->match_fallbacks = st.match_fallbacks;
+  r->match_terms = (int64_t)st.match_terms;
   r->fitness = st.final_count > 0 ? (float)(st.final_sumd2 / st.final_count) : 0.f;
   r->hyp_fitness = st.best_fit;
   r->status = ok ? LSR_STATUS_ALIGNED : LSR_STATUS_NO_ALIGNMENT;
@@ -1031,9 +1047,12 @@ static int register_many(lsr_ctx *c, int32_t n, const float *const *P, const int
   } else {
     if ((rc = ensure_lanes(c, S, bytes))) return rc;
     auto lanes = assign_pairs(b, n, S);
-    bool device_inputs = true;
-    for (int i = 0; i < n && device_inputs; ++i) device_inputs = is_device_ptr(P[i]) && is_device_ptr(Q[i]);
-    if (graph && device_inputs) {
+    // device or page-locked host inputs: the host-to-device copies become
+    // memcpy nodes of the graph, each on its pair's lane just before the pair
+    auto capturable = [](const float *x) { return is_device_ptr(x) || is_pinned_host_ptr(x); };
+    bool graph_inputs = true;
+    for (int i = 0; i < n && graph_inputs; ++i) graph_inputs = capturable(P[i]) && capturable(Q[i]);
+    if (graph && graph_inputs) {
       std::string key = batch_key(c, b, lanes);
       if (!c->gexec || key != c->gkey) {
         if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -1223,7 +1242,7 @@ int lsr_stage_match(lsr_ctx *c, const float *FP, int64_t nP, const float *FQ, in
     dn = a.take<int>(nP);
     dd = a.take<float>(nP);
     flags = a.take<int>(2);
-    tws = tc ? a.take<char>(tc_workspace_bytes((int)nP, (int)nQ, split)) : nullptr;
+    tws = a.take<char>(tc ? tc_workspace_bytes((int)nP, (int)nQ, split) : fp32_workspace_bytes((int)nQ));
   };
   Arena m(nullptr);
   float *x1, *x2, *x3, *x4, *x6;
@@ -1246,7 +1265,7 @@ int lsr_stage_match(lsr_ctx *c, const float *FP, int64_t nP, const float *FQ, in
                                   nullptr, s),
              "match");
   else
-    TRY_CUDA(c, launch_match_fp32(FPi, (int)nP, FQi, (int)nQ, dn, dd, s), "match");
+    TRY_CUDA(c, launch_match_fp32(FPi, (int)nP, FQi, (int)nQ, tws, dn, dd, s), "match");
   int hflags[2] = {0, 0};
   if (tc) TRY_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s), "copy flags");
   if ((rc = copy_out(c, nn, dn, sizeof(int) * nP))) return rc;
@@ -1580,27 +1599,33 @@ static int objective_impl(lsr_ctx *c, int32_t n, const float *const *P, const in
     maxQ = std::max(maxQ, nQ[i]);
   }
   if (n == 0) return LSR_OK;
-  auto plan = [&](Arena &a, CloudLayout &Cq, ScratchLayout &S, double *&part, double *&out7) {
+  // pairs round-robin over S lanes (own stream and workspace each): at these
+  // sizes every pair is a chain of short launches, and the lanes overlap them
+  const int nl = std::max(1, std::min((int)n, c->prm.batch_streams > 0 ? c->prm.batch_streams : 4));
+  auto plan = [&](Arena &a, CloudLayout &Cq, ScratchLayout &Sc, double *&part) {
     plan_cloud(a, (int)maxQ, false, false, true, Cq);
-    plan_scratch(a, (int)maxQ, Cq.cap_f, S);
+    plan_scratch(a, (int)maxQ, Cq.cap_f, Sc);
     part = a.take<double>((size_t)7 * objective_blocks((int)maxP));
-    out7 = a.take<double>((size_t)7 * n);
   };
   Arena m(nullptr);
   CloudLayout q1;
   ScratchLayout q2;
-  double *q3, *q4;
-  plan(m, q1, q2, q3, q4);
-  if ((rc = ensure_ws(c, m.off))) return rc;
-  Arena a(c->ws);
-  CloudLayout Cq0;
-  ScratchLayout S;
-  double *part, *out7;
-  plan(a, Cq0, S, part, out7);
-  cudaStream_t s = c->stream;
+  double *q3;
+  plan(m, q1, q2, q3);
+  if ((rc = ensure_lanes(c, nl, m.off))) return rc;
+  if ((rc = ensure_ws(c, sizeof(double) * 7 * (size_t)n))) return rc;
+  double *out7 = reinterpret_cast<double *>(c->ws);
+  TRY_CUDA(c, cudaEventRecord(c->fork, c->stream), "fork");
+  for (int l = 0; l < nl; ++l) TRY_CUDA(c, cudaStreamWaitEvent(c->lanes[l], c->fork, 0), "fork");
   std::vector<double> host7((size_t)7 * n);
   for (int i = 0; i < n; ++i) {
-    CloudLayout Cq = Cq0;
+    const int l = i % nl;
+    cudaStream_t s = c->lanes[l];
+    Arena a(c->lane_ws[l]);
+    CloudLayout Cq;
+    ScratchLayout Sc;
+    double *part;
+    plan(a, Cq, Sc, part);
     Cq.n = (int)nQ[i];
     const double *w = xi + 6 * i, *T = T0 + 16 * i;
     double Rw[9], Tm[16];
@@ -1621,7 +1646,7 @@ static int objective_impl(lsr_ctx *c, int32_t n, const float *const *P, const in
     // eps grid of Q with caller indices (build_grid_xyz carries caller order)
     TRY_CUDA(c, launch_bbox_xyz(Q[i], Cq.n, Cq.box_part, bbox_blocks(Cq.n), Cq.box, s), "bbox");
     TRY_CUDA(c, launch_grid_params(Cq.box, eps, Cq.n, Cq.cap_e, Cq.ge, s), "grid params");
-    TRY_CUDA(c, build_grid_xyz(Q[i], Cq.n, Cq.ge, Cq.cap_e, Cq.start_e, Cq.Xe, Cq.inv, S.g, s), "grid");
+    TRY_CUDA(c, build_grid_xyz(Q[i], Cq.n, Cq.ge, Cq.cap_e, Cq.start_e, Cq.Xe, Cq.inv, Sc.g, s), "grid");
     TRY_CUDA(c, build_nbmask(Cq.ge, Cq.start_e, Cq.cap_e, Cq.mask_e, s), "mask");
     if (grad) TRY_CUDA(c, cudaMemsetAsync(dQ[i], 0, sizeof(float) * 3 * nQ[i], s), "memset dQ");
     TRY_CUDA(c,
@@ -1630,8 +1655,12 @@ static int objective_impl(lsr_ctx *c, int32_t n, const float *const *P, const in
                               grad ? dQ[i] : nullptr, s),
              "objective");
   }
-  TRY_CUDA(c, cudaMemcpyAsync(host7.data(), out7, sizeof(double) * 7 * n, cudaMemcpyDeviceToHost, s), "D2H");
-  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  for (int l = 0; l < nl; ++l) {
+    TRY_CUDA(c, cudaEventRecord(c->lane_done[l], c->lanes[l]), "join");
+    TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->lane_done[l], 0), "join");
+  }
+  TRY_CUDA(c, cudaMemcpyAsync(host7.data(), out7, sizeof(double) * 7 * n, cudaMemcpyDeviceToHost, c->stream), "D2H");
+  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
   for (int i = 0; i < n; ++i) {
     const double *o = &host7[(size_t)7 * i];
     if (E) E[i] = o[0];

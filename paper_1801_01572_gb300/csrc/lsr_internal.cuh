@@ -12,6 +12,23 @@ constexpr int kNB = 11;      // bins per feature
 constexpr int kDS = 36;      // stored row stride of SPFH / FPFH (16-byte aligned rows)
 constexpr int kWarp = 32;
 
+// Order in which the FP32 descriptor distance sum_k (a_k - b_k)^2 is
+// accumulated: the central bin of each of the three 11-bin sub-histograms,
+// then the bins one step out on either side, two steps out, and so on. The
+// angular features of smooth surfaces pile up around the central bins, so
+// this order front-loads the mass of the distance and lets a partial sum pass
+// the running minimum after few terms. desc_order(k) is the bin added k-th;
+// desc_rank is its inverse. Every exact FP32 distance of the matchers uses it.
+__host__ __device__ constexpr int desc_order(int k) {
+  return k < 3 ? kNB * k + kNB / 2
+               : kNB * (((k - 3) % 6) / 2) + kNB / 2 + (((k - 3) % 2) ? 1 : -1) * ((k - 3) / 6 + 1);
+}
+__host__ __device__ constexpr int desc_rank(int col) {
+  return (col % kNB == kNB / 2) ? col / kNB
+                                : 3 + 6 * ((col % kNB > kNB / 2 ? col % kNB - kNB / 2 : kNB / 2 - col % kNB) - 1) +
+                                      2 * (col / kNB) + (col % kNB > kNB / 2 ? 1 : 0);
+}
+
 // Uniform 3D grid of eq. (1): cell index = floor((x - origin) / cell), stored
 // densely over the cloud's bounding box. When the box holds more cells than
 // the allocated capacity, the y and z (and if needed x) cell coordinates wrap
@@ -246,7 +263,11 @@ cudaError_t launch_fpfh(const float4 *X, const float4 *N, const float *spfh, int
                         const int *start_f, float r, float *fpfh, cudaStream_t s);
 
 // ----------------------------------------------------------------- matching (lsr_match.cu)
-cudaError_t launch_match_fp32(const float *FP, int nP, const float *FQ, int nQ, int *nn, float *d1, cudaStream_t s);
+// ws: fp32_workspace_bytes(nQ) of device memory (per-tile bin bounds);
+// terms (optional): add the number of descriptor terms evaluated (profiling)
+size_t fp32_workspace_bytes(int nQ);
+cudaError_t launch_match_fp32(const float *FP, int nP, const float *FQ, int nQ, void *ws, int *nn, float *d1,
+                              cudaStream_t s, unsigned long long *terms = nullptr);
 // Exact FP32 scan of the queries rows[0..*nrows) (count read on the device),
 // split over database chunks; packed: scratch of nP 64-bit words.
 cudaError_t launch_match_fp32_rows(const float *FP, int nP, const float *FQ, int nQ, const int *rows,
@@ -283,6 +304,7 @@ struct RansacState {
   int match_fallbacks; // BF16 matcher: queries re-scanned exactly in FP32
   int match_err;       // BF16 matcher: a CTA gave up waiting (result invalid)
   int pad_;
+  unsigned long long match_terms;  // FP32 matcher, counting launch: terms evaluated
   double final_sumd2;
   double T[16];        // current pose (refinement), row-major
   double T_hyp[16];

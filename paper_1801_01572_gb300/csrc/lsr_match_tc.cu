@@ -302,12 +302,12 @@ struct TcArgs {
 };
 
 // Exact FP32 squared distance in the FP32 matcher's operation order
-// (one fused multiply-add per component, k = 0..32).
+// (one fused multiply-add per bin, bins taken in desc_order).
 __device__ __forceinline__ float exact_d2(const float *__restrict__ a, const float *__restrict__ b) {
   float s = 0.f;
 #pragma unroll
   for (int k = 0; k < kD; ++k) {
-    float t = __ldg(a + k) - __ldg(b + k);
+    float t = __ldg(a + desc_order(k)) - __ldg(b + desc_order(k));
     s = fmaf(t, t, s);
   }
   return s;

@@ -52,7 +52,8 @@ class Params(C.Structure):
 class Result(C.Structure):
     _fields_ = [("T", C.c_double * 16), ("T_hyp", C.c_double * 16), ("inliers", C.c_int64),
                 ("hyp_inliers", C.c_int64), ("survivors", C.c_int64), ("n_normal_ok", C.c_int64),
-                ("best_h", C.c_int64), ("match_fallbacks", C.c_int64), ("fitness", C.c_float),
+                ("best_h", C.c_int64), ("match_fallbacks", C.c_int64),
+                ("match_terms", C.c_int64), ("fitness", C.c_float),
                 ("hyp_fitness", C.c_float), ("status", C.c_int32), ("refine_iters_done", C.c_int32),
                 ("stage_ms", C.c_float * 8)]
 
@@ -174,6 +175,7 @@ class Registration:
     n_normal_ok: int
     best_h: int
     match_fallbacks: int
+    match_terms: int
     fitness: float
     hyp_fitness: float
     status: int
@@ -189,7 +191,7 @@ class Registration:
         return Registration(T=np.array(r.T, np.float64).reshape(4, 4), T_hyp=np.array(r.T_hyp, np.float64).reshape(4, 4),
                             inliers=int(r.inliers), hyp_inliers=int(r.hyp_inliers), survivors=int(r.survivors),
                             n_normal_ok=int(r.n_normal_ok), best_h=int(r.best_h),
-                            match_fallbacks=int(r.match_fallbacks), fitness=float(r.fitness),
+                            match_fallbacks=int(r.match_fallbacks), match_terms=int(r.match_terms), fitness=float(r.fitness),
                             hyp_fitness=float(r.hyp_fitness), status=int(r.status),
                             refine_iters=int(r.refine_iters_done), stage_ms=list(r.stage_ms))
 
