@@ -432,7 +432,7 @@ def roofline(info):
         terms = float(info["prof"].match_terms)
         # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
         # (profiles/k_match_fp32_room150k_dram.md)
-        traffic = 44161280 + 22528 if (nP, nQ) == (150000, 150000) else None
+        traffic = 43850752 + 2816 if (nP, nQ) == (150000, 150000) else None
         return {"kernel": "k_match_fp32", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": traffic,
                 "executed_terms": terms, "executed_share": terms / dense,

@@ -3,16 +3,17 @@
 //
 // Exact brute force: nn[i] = argmin_j sum_k (a_k - b_k)^2 with ties to the
 // smallest j, accumulated as s = fma(t, t, s) over the 33 bins taken in
-// desc_order (central bins first). Each thread keeps two query descriptors in
+// desc_order (central bins first). Each thread keeps one query descriptor in
 // registers; tiles of database descriptors are staged in shared memory in
-// that order and read as broadcasts, so one shared load feeds two distance
-// accumulations. The partial sums only grow (t^2 >= 0 and rounding is
-// monotone), so a row whose partial sum already exceeds every query's current
-// best in the warp can neither win nor tie: after 4, 8, 12, 16 and 24 terms
-// the warp tests that and skips the rest of the row (same result). Queries
-// arrive in grid order (points sorted by feature-radius cell), so the 64
-// queries of a warp lie close together and have similar descriptors, and the
-// test succeeds for most rows after the first four terms.
+// that order and read as broadcasts. The partial sums only grow (t^2 >= 0 and
+// rounding is monotone), so a row whose partial sum already exceeds every
+// query's current best in the warp can neither win nor tie: after 4, 8, 12, 16
+// and 24 terms the warp tests that and skips the rest of the row (same
+// result). Queries arrive in grid order (points sorted by feature-radius
+// cell), so the 32 queries of a warp lie close together and have similar
+// descriptors, and the test succeeds for most rows after the first four terms.
+// (One query per thread prunes better and keeps more warps resident than two
+// or four, which share every test.)
 //
 // Whole tiles are skipped as well. The database is in grid order too, so the
 // 64 rows of a tile have similar descriptors; k_tile_bounds stores per tile
@@ -33,10 +34,12 @@ namespace lsr {
 namespace {
 
 constexpr int kMT = 128;   // threads per block
-constexpr int kQPT = 2;    // queries per thread
+constexpr int kQF = 1;     // queries per thread, full scan (k_match_fp32)
+constexpr int kQR = 2;     // queries per thread, listed rows (k_match_rows_chunked)
 constexpr int kTile = 64;  // database rows per shared-memory tile
 constexpr int kStageThreads = 9 * (kMT / 9);  // staging threads: one float4 column each
 constexpr int kTB = 72;    // floats per tile bound: lo[36], hi[36], bins in desc_order
+constexpr int kLB = 33;    // leading bins (desc_order) summed in the tile bound
 static_assert(kTile * 9 > kStageThreads, "staging covers the tile in several passes");
 
 // Database rows [base, base + kTile) (zero past lim) into the tile, bin
@@ -67,28 +70,28 @@ __device__ __forceinline__ void stage_ranks(int (&rk)[4]) {
   for (int i = 0; i < 4; ++i) rk[i] = 4 * c + i < kD ? desc_rank(4 * c + i) : -1;
 }
 
-// Scan the m staged rows for the kQPT queries of this thread (a in
+// Scan the m staged rows for the Q queries of this thread (a in
 // desc_order), updating best / bj; row j of the tile is database row base + j.
 // kCount: add the terms evaluated per query to terms.
-template <bool kCount = false>
-__device__ __forceinline__ void scan_tile(const float4 (*tile)[9], int m, int base, const float (&a)[kQPT][kD],
-                                          float (&best)[kQPT], int (&bj)[kQPT], unsigned *terms = nullptr) {
+template <int Q, bool kCount = false>
+__device__ __forceinline__ void scan_tile(const float4 (*tile)[9], int m, int base, const float (&a)[Q][kD],
+                                          float (&best)[Q], int (&bj)[Q], unsigned *terms = nullptr) {
   for (int j = 0; j < m; ++j) {
-    float s[kQPT];
+    float s[Q];
 #pragma unroll
-    for (int u = 0; u < kQPT; ++u) s[u] = 0.f;
+    for (int u = 0; u < Q; ++u) s[u] = 0.f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       if (c >= 1 && (c <= 4 || c == 6)) {
         bool past = true;
 #pragma unroll
-        for (int u = 0; u < kQPT; ++u) past &= s[u] > best[u];
+        for (int u = 0; u < Q; ++u) past &= s[u] > best[u];
         if (__all_sync(0xffffffffu, past)) break;
       }
       float4 b = tile[j][c];
       if (kCount) *terms += c == 7 ? 5 : 4;
 #pragma unroll
-      for (int u = 0; u < kQPT; ++u) {
+      for (int u = 0; u < Q; ++u) {
         float t0 = a[u][4 * c] - b.x, t1 = a[u][4 * c + 1] - b.y, t2 = a[u][4 * c + 2] - b.z,
               t3 = a[u][4 * c + 3] - b.w;
         s[u] = fmaf(t0, t0, s[u]);
@@ -99,7 +102,7 @@ __device__ __forceinline__ void scan_tile(const float4 (*tile)[9], int m, int ba
       if (c == 7) {
         float b32 = tile[j][8].x;
 #pragma unroll
-        for (int u = 0; u < kQPT; ++u) {
+        for (int u = 0; u < Q; ++u) {
           float t = a[u][32] - b32;
           s[u] = fmaf(t, t, s[u]);
           if (s[u] < best[u]) best[u] = s[u], bj[u] = base + j;
@@ -124,26 +127,35 @@ __global__ void k_tile_bounds(const float *__restrict__ FQ, int nQ, float *__res
   tb[(size_t)t * kTB + 36 + k] = hi;
 }
 
-// True if some query of this thread may find a row of tile t at or below its
-// current best (the exact bound of the tile's rows does not exceed best).
-__device__ __forceinline__ bool tile_needed(const float *__restrict__ tb, int t, const float (&a)[kQPT][kD],
-                                            const float (&best)[kQPT]) {
+// The bound of tile t for each query of this thread: no row of the tile has
+// a computed distance below L[u].
+template <int Q>
+__device__ __forceinline__ void tile_bound(const float *__restrict__ tb, int t, const float (&a)[Q][kD],
+                                           float (&L)[Q]) {
   const float *lo = tb + (size_t)t * kTB, *hi = lo + 36;
-  float L[kQPT];
 #pragma unroll
-  for (int u = 0; u < kQPT; ++u) L[u] = 0.f;
+  for (int u = 0; u < Q; ++u) L[u] = 0.f;
 #pragma unroll
-  for (int k = 0; k < kD; ++k) {
+  for (int k = 0; k < kLB; ++k) {
     const float l = __ldg(lo + k), h = __ldg(hi + k);
 #pragma unroll
-    for (int u = 0; u < kQPT; ++u) {
+    for (int u = 0; u < Q; ++u) {
       const float g = fmaxf(fmaxf(l - a[u][k], a[u][k] - h), 0.f);
       L[u] = fmaf(g, g, L[u]);
     }
   }
+}
+
+// True if some query of this thread may find a row of tile t at or below its
+// current best (the exact bound of the tile's rows does not exceed best).
+template <int Q>
+__device__ __forceinline__ bool tile_needed(const float *__restrict__ tb, int t, const float (&a)[Q][kD],
+                                            const float (&best)[Q]) {
+  float L[Q];
+  tile_bound<Q>(tb, t, a, L);
   bool need = false;
 #pragma unroll
-  for (int u = 0; u < kQPT; ++u) need |= !(L[u] > best[u]);
+  for (int u = 0; u < Q; ++u) need |= !(L[u] > best[u]);
   return need;
 }
 
@@ -154,31 +166,31 @@ __global__ void __launch_bounds__(kMT) k_match_fp32(const float *__restrict__ FP
                                                     int nQ, const float *__restrict__ tb, int *__restrict__ nn,
                                                     float *__restrict__ d1, unsigned long long *__restrict__ terms) {
   __shared__ float4 tile[kTile][9];
-  float a[kQPT][kD];
-  int qi[kQPT], rk[4];
+  float a[kQF][kD];
+  int qi[kQF], rk[4];
   stage_ranks(rk);
 #pragma unroll
-  for (int u = 0; u < kQPT; ++u) {
-    qi[u] = blockIdx.x * (kMT * kQPT) + u * kMT + threadIdx.x;
+  for (int u = 0; u < kQF; ++u) {
+    qi[u] = blockIdx.x * (kMT * kQF) + u * kMT + threadIdx.x;
     const float *row = FP + (size_t)(qi[u] < nP ? qi[u] : 0) * kDS;
 #pragma unroll
     for (int k = 0; k < kD; ++k) a[u][k] = row[desc_order(k)];
   }
-  float best[kQPT];
-  int bj[kQPT];
+  float best[kQF];
+  int bj[kQF];
 #pragma unroll
-  for (int u = 0; u < kQPT; ++u) best[u] = FLT_MAX, bj[u] = -1;
+  for (int u = 0; u < kQF; ++u) best[u] = FLT_MAX, bj[u] = -1;
   unsigned nterm = 0;
   for (int base = 0, t = 0; base < nQ; base += kTile, ++t) {
-    const bool need = __any_sync(0xffffffffu, tile_needed(tb, t, a, best));
+    const bool need = __any_sync(0xffffffffu, tile_needed<kQF>(tb, t, a, best));
     // (also the barrier after the previous tile's scan)
     if (!__syncthreads_or(need)) continue;
     stage_tile(tile, FQ, base, nQ, rk);
     __syncthreads();
-    if (need) scan_tile<kCount>(tile, nQ - base < kTile ? nQ - base : kTile, base, a, best, bj, &nterm);
+    if (need) scan_tile<kQF, kCount>(tile, nQ - base < kTile ? nQ - base : kTile, base, a, best, bj, &nterm);
   }
 #pragma unroll
-  for (int u = 0; u < kQPT; ++u)
+  for (int u = 0; u < kQF; ++u)
     if (qi[u] < nP) {
       nn[qi[u]] = bj[u];
       if (d1) d1[qi[u]] = best[u];
@@ -186,7 +198,7 @@ __global__ void __launch_bounds__(kMT) k_match_fp32(const float *__restrict__ FP
   if (kCount) {
     int valid = 0;
 #pragma unroll
-    for (int u = 0; u < kQPT; ++u) valid += qi[u] < nP;
+    for (int u = 0; u < kQF; ++u) valid += qi[u] < nP;
     // nterm <= nQ * 33 < 2^32 (at most 2^26 points per cloud)
     unsigned long long mine = (unsigned long long)nterm * (unsigned)valid;
 #pragma unroll
@@ -211,30 +223,30 @@ __global__ void __launch_bounds__(kMT) k_match_rows_chunked(const float *__restr
   if (j0 >= j1) return;
   int rk[4];
   stage_ranks(rk);
-  for (int t0 = blockIdx.x; t0 * (kMT * kQPT) < nq; t0 += gridDim.x) {
-    float a[kQPT][kD];
-    int slot[kQPT];
+  for (int t0 = blockIdx.x; t0 * (kMT * kQR) < nq; t0 += gridDim.x) {
+    float a[kQR][kD];
+    int slot[kQR];
 #pragma unroll
-    for (int u = 0; u < kQPT; ++u) {
-      int q = t0 * (kMT * kQPT) + u * kMT + threadIdx.x;
+    for (int u = 0; u < kQR; ++u) {
+      int q = t0 * (kMT * kQR) + u * kMT + threadIdx.x;
       slot[u] = q < nq ? q : -1;
       int qi = q < nq ? rows[q] : 0;
       const float *row = FP + (size_t)(qi < nP ? qi : 0) * kDS;
 #pragma unroll
       for (int k = 0; k < kD; ++k) a[u][k] = row[desc_order(k)];
     }
-    float best[kQPT];
-    int bj[kQPT];
+    float best[kQR];
+    int bj[kQR];
 #pragma unroll
-    for (int u = 0; u < kQPT; ++u) best[u] = FLT_MAX, bj[u] = -1;
+    for (int u = 0; u < kQR; ++u) best[u] = FLT_MAX, bj[u] = -1;
     for (int base = j0; base < j1; base += kTile) {
       __syncthreads();
       stage_tile(tile, FQ, base, j1, rk);
       __syncthreads();
-      scan_tile(tile, j1 - base < kTile ? j1 - base : kTile, base, a, best, bj);
+      scan_tile<kQR>(tile, j1 - base < kTile ? j1 - base : kTile, base, a, best, bj);
     }
 #pragma unroll
-    for (int u = 0; u < kQPT; ++u)
+    for (int u = 0; u < kQR; ++u)
       if (slot[u] >= 0 && bj[u] >= 0)
         atomicMin(packed + slot[u], ((unsigned long long)__float_as_uint(best[u]) << 32) | (unsigned)bj[u]);
     __syncthreads();
@@ -264,7 +276,7 @@ size_t fp32_workspace_bytes(int nQ) { return sizeof(float) * kTB * (size_t)lsr_d
 
 cudaError_t launch_match_fp32(const float *FP, int nP, const float *FQ, int nQ, void *ws, int *nn, float *d1,
                               cudaStream_t s, unsigned long long *terms) {
-  int blocks = (int)lsr_div_up(nP, kMT * kQPT);
+  int blocks = (int)lsr_div_up(nP, kMT * kQF);
   if (blocks < 1) blocks = 1;
   float *tb = static_cast<float *>(ws);
   LSR_LAUNCH(k_tile_bounds<<<(int)lsr_div_up(nQ, kTile), 64, 0, s>>>(FQ, nQ, tb));
@@ -281,7 +293,7 @@ cudaError_t launch_match_fp32_rows(const float *FP, int nP, const float *FQ, int
   constexpr int kChunks = 64;
   int chunk = (int)lsr_div_up(lsr_div_up(nQ, kChunks), kTile) * kTile;
   int ny = (int)lsr_div_up(nQ, chunk);
-  int nx = (int)lsr_div_up(nP, kMT * kQPT);
+  int nx = (int)lsr_div_up(nP, kMT * kQR);
   nx = nx < 1 ? 1 : (nx > 10 ? 10 : nx);
   int fin = (int)lsr_div_up(nP, 256);
   fin = fin < 1 ? 1 : (fin > 1216 ? 1216 : fin);
