@@ -510,30 +510,32 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
   // Inlier-count bounds of every survivor from the voxel classification of Q;
   // exact counts of the 32 largest upper bounds give C; exact counts of the
   // others whose upper bound reaches C; distance sums of the top ties. No
-  // survivor left out can be selected.
+  // survivor left out can be selected. P is read in normal-grid order (5 cm
+  // cells): the counts and fixed-point sums do not depend on the order, and
+  // a warp's points then land on fewer table words.
   TRY_CUDA(c, launch_cls_build(Qc.box, p.eps_inlier, Qc.X, nQ, L.cls, L.in_bits, L.near_bits, s), "classify");
   TRY_CUDA(c, cudaMemsetAsync(L.count, 0, sizeof(int) * L.surv_cap, s), "memset count");
   TRY_CUDA(c, cudaMemsetAsync(L.amb, 0, sizeof(int) * L.surv_cap, s), "memset count");
   TRY_CUDA(c, cudaMemsetAsync(L.count2, 0, sizeof(int) * L.surv_cap, s), "memset count");
   TRY_CUDA(c, cudaMemsetAsync(L.sum, 0, sizeof(unsigned long long) * L.surv_cap, s), "memset sum");
   TRY_CUDA(c,
-           launch_consensus_bounds(Pc.X, nP, L.cls, L.in_bits, L.near_bits, L.pose, L.ok, &L.st->n_surv, L.count,
+           launch_consensus_bounds(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, L.pose, L.ok, &L.st->n_surv, L.count,
                                    L.amb, s),
            "consensus bounds");
   TRY_CUDA(c, launch_top_upper(L.count, L.amb, L.ok, &L.st->n_surv, 32, L.sel, s), "top");
   TRY_CUDA(c,
-           launch_consensus_count(Pc.X, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.sel,
+           launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.sel,
                                   &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
            "consensus top");
   TRY_CUDA(c, launch_reach_rest(L.count, L.amb, L.count2, L.sel, L.ok, &L.st->n_surv, L.rest, L.reach, s), "reach");
   TRY_CUDA(c,
-           launch_consensus_count(Pc.X, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.rest,
+           launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.rest,
                                   &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
            "consensus reach");
   TRY_CUDA(c, launch_reach_mask(L.count2, nullptr, L.reach, &L.st->n_surv, L.tie, s), "ties");
   // (the exact kernel adds its counts too: into amb, no longer needed)
   TRY_CUDA(c,
-           launch_consensus(Pc.X, nP, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.tie, &L.st->n_surv, 0, p.eps_inlier,
+           launch_consensus(Pc.Xn, nP, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.tie, &L.st->n_surv, 0, p.eps_inlier,
                             L.amb, L.sum, s, c->cons_lanes),
            "consensus sums");
   tm.mark();

@@ -146,6 +146,13 @@ __device__ __forceinline__ void grid_ranges(const GridParams &g, const int *__re
 // index) minima with shuffles. Ties go to the smaller carried index (w of the
 // grid's sorted points). Every lane returns the group's result; bt = -1 if no
 // point is within the radius.
+//
+// The query's own row of cells is searched first; each of the other eight
+// rows, and the x-neighbour cells of every row, is visited only if its
+// distance from the query (less a margin of 2e-4 cells, above the FP32
+// rounding of cell coordinates) can still reach the group's best so far. A
+// skipped cell holds no point at or below that best, so the result is the
+// one of the full walk. (Grids with wrapped storage walk all cells.)
 template <int G>
 __device__ __forceinline__ void group_nn(const GridParams &g, const int *__restrict__ start,
                                          const float4 *__restrict__ Xe, float x, float y, float z, float eps2,
@@ -155,7 +162,7 @@ __device__ __forceinline__ void group_nn(const GridParams &g, const int *__restr
   bt = -1;
   bidx = 0x7fffffff;
   int next = sub, base = 0;
-  grid_ranges(g, start, x, y, z, [&](int b, int e) {
+  auto scan = [&](int b, int e) {
     int len = e - b;
     // four independent loads in flight per lane, then the remainder
     for (; next + 3 * G < base + len; next += 4 * G) {
@@ -178,7 +185,56 @@ __device__ __forceinline__ void group_nn(const GridParams &g, const int *__restr
       if (d2 < best || (d2 == best && qi < bidx)) best = d2, bt = t, bidx = qi;
     }
     base += len;
-  });
+  };
+  const bool wrapped = (g.wx != g.nx) | (g.wy != g.ny) | (g.wz != g.nz);
+  if (wrapped) {
+    grid_ranges(g, start, x, y, z, scan);
+  } else {
+    const float fx = (x - g.ox) * g.inv_cell, fy = (y - g.oy) * g.inv_cell, fz = (z - g.oz) * g.inv_cell;
+    bool go = fx >= -1.f && fx < (float)g.nx + 1.f && fy >= -1.f && fy < (float)g.ny + 1.f && fz >= -1.f &&
+              fz < (float)g.nz + 1.f;
+    const int cx = go ? __float2int_rd(fx) : 0, cy = go ? __float2int_rd(fy) : 0, cz = go ? __float2int_rd(fz) : 0;
+    const int x0 = cx - 1 < 0 ? 0 : cx - 1, x1 = cx + 1 > g.nx - 1 ? g.nx - 1 : cx + 1;
+    go = go && x0 <= x1;
+    if (go && g.nbmask && cx >= 0 && cx < g.nx && cy >= 0 && cy < g.ny && cz >= 0 && cz < g.nz) {
+      const int slot = (cz * g.wy + cy) * g.wx + cx;
+      go = (__ldg(g.nbmask + (slot >> 5)) >> (slot & 31)) & 1u;
+    }
+    if (go) {
+      const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+      const float mg = 2e-4f * g.cell;
+      auto gsq = [&](float d) {
+        const float t = fmaxf(d - mg, 0.f);
+        return t * t;
+      };
+      // squared distances to the lower / upper faces of the query's cell
+      const float gxl = gsq((fx - (float)cx) * g.cell), gxh = gsq(((float)cx + 1.f - fx) * g.cell);
+      const float gyl = gsq((fy - (float)cy) * g.cell), gyh = gsq(((float)cy + 1.f - fy) * g.cell);
+      const float gzl = gsq((fz - (float)cz) * g.cell), gzh = gsq(((float)cz + 1.f - fz) * g.cell);
+      constexpr float kShrink = 1.f - 1e-6f;  // the FP32 rounding of d^2 itself
+      float gb = eps2;
+#pragma unroll 1
+      for (int k = 0; k < 9; ++k) {
+        // rows: own, then the four edge neighbours, then the four corners
+        const int dy = k == 1 ? -1 : k == 2 ? 1 : (k >= 5 ? ((k & 1) ? -1 : 1) : 0);
+        const int dz = k == 3 ? -1 : k == 4 ? 1 : (k >= 5 ? (k < 7 ? -1 : 1) : 0);
+        const int iy = cy + dy, iz = cz + dz;
+        if (iy < 0 || iy >= g.ny || iz < 0 || iz >= g.nz) continue;
+        const float r2 = (dy < 0 ? gyl : dy > 0 ? gyh : 0.f) + (dz < 0 ? gzl : dz > 0 ? gzh : 0.f);
+        if (r2 * kShrink > gb) continue;
+        int a = x0, e = x1;
+        if (a < cx && (r2 + gxl) * kShrink > gb) a = cx;
+        if (e > cx && (r2 + gxh) * kShrink > gb) e = cx;
+        if (a > e) continue;
+        const int row = (iz * g.wy + iy) * g.wx;
+        scan(start[row + a], start[row + e + 1]);
+        float m = best;
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) m = fminf(m, __shfl_xor_sync(gmask, m, off));
+        gb = m;
+      }
+    }
+  }
 #pragma unroll
   for (int off = G / 2; off > 0; off >>= 1) {
     float ob = __shfl_xor_sync(0xffffffffu, best, off);
