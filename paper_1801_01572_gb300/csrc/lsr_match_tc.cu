@@ -18,18 +18,19 @@
 // issues tcgen05.mma from shared memory into TMEM (two accumulator buffers, so
 // the tensor pipe runs while the epilogue drains the other), and eight
 // epilogue warps, one query per thread, read a whole accumulator row with one
-// wait and keep the 8 smallest scores: a min-prefilter per 32 columns, then
-// bit-mask insertion of the few values that beat a lane's current 8th.
+// wait, release the buffer at once, and keep the 8 smallest minima of 16-row
+// chunks (a chunk enters when its minimum beats the lane's current 8th).
 //
-// The 8 candidates are re-ranked with the exact FP32 distance of the original
-// descriptors in the FP32 matcher's operation order. A certificate proves, per
-// query, that the FP32 winner is among them:
+// The 128 rows of those 8 chunks are re-ranked with the exact FP32 distance of
+// the original descriptors in the FP32 matcher's operation order. A
+// certificate proves, per query, that the FP32 winner is among them:
 //   D~^2 = s + |a~|^2 is within efp of |a~ - b~|^2 (accumulation, the left-out
 //   term, the BF16 split of |b~|^2), and | |a - b| - |a~ - b~| | <= eta =
 //   |a - c - a~| + max_b |b - c - b~| (+ the rounding of the centring);
-//   every row outside the candidates has s >= s_(8), so its distance is at
-//   least lo8 = sqrt(s_(8) + |a~|^2 - efp) - eta, while the best candidate's is
-//   at most hi1 = sqrt(s_(1) + |a~|^2 + efp) + eta; if lo8 > hi1 beyond the FP32
+//   every row outside the candidate chunks has s >= s_(8), the 8th smallest
+//   chunk minimum, so its distance is at least lo8 = sqrt(s_(8) + |a~|^2 -
+//   efp) - eta, while the row of the smallest score has one of at most hi1 =
+//   sqrt(s_(1) + |a~|^2 + efp) + eta; if lo8 > hi1 beyond the FP32
 //   evaluation error (35 roundings of 2^-24 on D^2), no outside row can win.
 // The accumulation error is bounded with the truncating-adder model of tensor
 // core FP32 accumulation: each MMA of 16 products adds at most 17 errors of
@@ -56,8 +57,10 @@ namespace {
 constexpr int kTcM = 128;                       // queries per MMA tile (TMEM lanes)
 constexpr int kTcN = 128;                       // database rows per tile
 constexpr int kLBO = 128;                       // bytes between K-adjacent core matrices
-constexpr int kTopK = 8;
-constexpr int kChunks = kTcN / 32;              // 32-column TMEM loads per accumulator row
+constexpr int kTopK = 8;                        // candidate chunks per query
+constexpr int kChunkW = 16;                     // database rows per chunk
+constexpr int kChunks = kTcN / kChunkW;         // chunks per tile
+constexpr int kLoads = kTcN / 32;               // 32-column TMEM loads per accumulator row
 constexpr unsigned long long kWaitNs = 2000000000ull;  // give up after 2 s
 constexpr float kPadScore = 1.2676506e30f;      // 2^100: |b~|^2 of padding rows
 constexpr float kAccErr = 1.5e-5f;              // accumulation error per unit of sum |products|
@@ -301,30 +304,23 @@ struct TcArgs {
   float *d2;                    // optional: all D~^2 = s + |a~|^2 (nP x nNT * kTcN) instead of the top-8
 };
 
-// Exact FP32 squared distance in the FP32 matcher's operation order
-// (one fused multiply-add per bin, bins taken in desc_order).
-__device__ __forceinline__ float exact_d2(const float *__restrict__ a, const float *__restrict__ b) {
+// Exact FP32 squared distance in the FP32 matcher's operation order (one
+// fused multiply-add per bin, bins taken in desc_order; a already in it). The
+// row is read as nine 16-byte loads, the order applied in registers.
+__device__ __forceinline__ float exact_d2(const float (&a)[kD], const float *__restrict__ b) {
+  float r[36];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const float4 x = __ldg(reinterpret_cast<const float4 *>(b) + q);
+    r[4 * q] = x.x, r[4 * q + 1] = x.y, r[4 * q + 2] = x.z, r[4 * q + 3] = x.w;
+  }
   float s = 0.f;
 #pragma unroll
   for (int k = 0; k < kD; ++k) {
-    float t = __ldg(a + desc_order(k)) - __ldg(b + desc_order(k));
+    float t = a[k] - r[desc_order(k)];
     s = fmaf(t, t, s);
   }
   return s;
-}
-
-// w[k] for a runtime k < 32, by a tree of selects (w stays in registers).
-__device__ __forceinline__ float pick32(const float (&w)[32], int k) {
-  float a[16], b[8], c[4], d[2];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) a[i] = (k & 1) ? w[2 * i + 1] : w[2 * i];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) b[i] = (k & 2) ? a[2 * i + 1] : a[2 * i];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) c[i] = (k & 4) ? b[2 * i + 1] : b[2 * i];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) d[i] = (k & 8) ? c[2 * i + 1] : c[2 * i];
-  return (k & 16) ? d[1] : d[0];
 }
 
 __device__ __forceinline__ void top8_insert(float (&ts)[kTopK], int (&ti)[kTopK], float v, int id) {
@@ -459,7 +455,7 @@ __global__ void __launch_bounds__(Cfg<KS, QT>::Threads, Cfg<KS, QT>::CtasPerSm) 
         float v[kTcN];
         __syncwarp();  // the loads below are warp-collective
 #pragma unroll
-        for (int q = 0; q < kChunks; ++q) tmem_ld32(row + q * 32, v + q * 32);
+        for (int q = 0; q < kLoads; ++q) tmem_ld32(row + q * 32, v + q * 32);
         tmem_wait_ld();
         const int c0 = t * kTcN;
         if (g.d2) {
@@ -472,60 +468,41 @@ __global__ void __launch_bounds__(Cfg<KS, QT>::Threads, Cfg<KS, QT>::CtasPerSm) 
           }
           continue;
         }
-        // minimum of each 32-column chunk
-        float mh[kChunks];
-#pragma unroll
-        for (int q = 0; q < kChunks; ++q) {
-          float a0 = v[q * 32], a1 = v[q * 32 + 1], a2 = v[q * 32 + 2], a3 = v[q * 32 + 3];
-#pragma unroll
-          for (int k = 4; k < 32; k += 4) {
-            a0 = fminf(a0, v[q * 32 + k]), a1 = fminf(a1, v[q * 32 + k + 1]);
-            a2 = fminf(a2, v[q * 32 + k + 2]), a3 = fminf(a3, v[q * 32 + k + 3]);
-          }
-          mh[q] = fminf(fminf(a0, a1), fminf(a2, a3));
-        }
-        // A chunk whose minimum beats a lane's 8th score is read again from
-        // TMEM (the buffer is released only afterwards) and only its values
-        // below that score are inserted, one by one, picked by selects so that
-        // everything stays in registers. After the first tiles that is one or
-        // two values per tile and warp; most tiles release the buffer at once.
-#pragma unroll 1
-        for (int q = 0; q < kChunks; ++q) {
-          float mq = mh[0];
-#pragma unroll
-          for (int qq = 1; qq < kChunks; ++qq) mq = q == qq ? mh[qq] : mq;
-          if (!__any_sync(0xffffffffu, mq < ts[kTopK - 1])) continue;
-          float w[32];
-          tmem_ld32(row + q * 32, w);
-          tmem_wait_ld();
-          const float thr = ts[kTopK - 1];
-          unsigned below = 0u;
-#pragma unroll
-          for (int k = 0; k < 32; ++k) below |= (w[k] < thr ? 1u : 0u) << k;
-          while (below) {
-            const int k = __ffs(below) - 1;
-            below &= below - 1u;
-            top8_insert(ts, ti, pick32(w, k), c0 + q * 32 + k);
-          }
-          __syncwarp();
-        }
+        // the scores are in registers: the buffer goes back to the MMA at once
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(barEmpty + buf);
+        // minimum of each chunk; the 8 smallest chunk minima are kept
+#pragma unroll
+        for (int q = 0; q < kChunks; ++q) {
+          const float *w = v + q * kChunkW;
+          float a0 = w[0], a1 = w[1], a2 = w[2], a3 = w[3];
+#pragma unroll
+          for (int k = 4; k < kChunkW; k += 4) {
+            a0 = fminf(a0, w[k]), a1 = fminf(a1, w[k + 1]);
+            a2 = fminf(a2, w[k + 2]), a3 = fminf(a3, w[k + 3]);
+          }
+          top8_insert(ts, ti, fminf(fminf(a0, a1), fminf(a2, a3)), t * kChunks + q);
+        }
       }
       if (!ok || g.d2 || r >= g.nP) continue;
-      // exact FP32 re-rank of the candidates
-      const float *a = g.FP + (size_t)r * kDS;
+      // exact FP32 re-rank of the rows of the candidate chunks
+      float a[kD];
+#pragma unroll
+      for (int k = 0; k < kD; ++k) a[k] = __ldg(g.FP + (size_t)r * kDS + desc_order(k));
       float best = FLT_MAX;
       int bi = -1;
 #pragma unroll 1
       for (int q = 0; q < kTopK; ++q) {
-        const int c = ti[q];
-        if (c < 0 || c >= g.nQ) continue;
-        const float d = exact_d2(a, g.FQ + (size_t)c * kDS);
-        if (d < best || (d == best && c < bi)) best = d, bi = c;
+        if (ti[q] < 0) continue;
+        const int c0 = ti[q] * kChunkW, c1 = min(g.nQ, c0 + kChunkW);
+#pragma unroll 1
+        for (int c = c0; c < c1; ++c) {
+          const float d = exact_d2(a, g.FQ + (size_t)c * kDS);
+          if (d < best || (d == best && c < bi)) best = d, bi = c;
+        }
       }
-      bool cert = g.nQ <= kTopK;
+      bool cert = g.nQ <= kTopK * kChunkW;
       if (!cert && ti[kTopK - 1] >= 0) {
         const float aa = g.aa[r], bbm = __uint_as_float(*g.bb);
         const float na = sqrtf(aa), nb = sqrtf(bbm);

@@ -145,15 +145,16 @@ def test_tc_match_equals_fp32_random(ctx, nP, nQ, precision):
 @pytest.mark.parametrize("precision", [1, 2])
 def test_tc_match_ties_and_near_duplicates(ctx, precision):
     """Exact duplicate rows (ties go to the smaller index), a pair of rows 1e-6
-    apart (both among the top 8: the exact re-rank decides), and clusters of 12
-    rows within 1e-6 of each other (more near-ties than candidates: no BF16
+    apart (both in the candidate chunks: the exact re-rank decides), and
+    clusters of 12 rows within 1e-6 of each other, each row in a different
+    32-row chunk (more near-tied chunks than the 8 candidate chunks: no BF16
     certificate is possible and the exact fallback must decide)."""
     rng = np.random.default_rng(5)
-    B = fpfh_like(2000, rng)
+    B = fpfh_like(2400, rng)
     B[1500:1600] = B[100:200]                       # exact duplicates
     B[1600:1700] = B[200:300] + 1e-6                # near-duplicate pairs
-    for c in range(20):                             # 20 clusters of 12
-        B[1700 + 12 * c:1712 + 12 * c] = B[300 + c] + 1e-7 * rng.random((12, D), dtype=np.float32)
+    for c in range(20):                             # 20 clusters of 12, rows 32 apart
+        B[1700 + c:1700 + c + 32 * 12:32] = B[300 + c] + 1e-7 * rng.random((12, D), dtype=np.float32)
     A = np.concatenate([B[100:200], B[200:300] + 3e-7, B[300:320] + 2e-7, fpfh_like(500, rng)])
     nn, d, fb = _check_same(ctx, A, B, precision)
     assert np.array_equal(nn[:100], np.arange(100, 200))
