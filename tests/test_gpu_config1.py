@@ -83,3 +83,22 @@ def test_config1_register_matches_oracle_fixed_point(ctx, pair1):
     assert ang < 0.05 and tr < 5e-4, (ang, tr)
     cnt, sd, amb = oracle.consensus(pair1.P, pair1.Q, T_ref[None, :3, :3], T_ref[None, :3, 3], 0.0375, band=1e-4)
     assert abs(r.inliers - cnt[0]) <= amb[0] + 0.001 * cnt[0]
+
+
+@gpu
+def test_config1_profiled_run_counts_terms_and_changes_nothing(ctx, pair1):
+    """With profiling on, the FP32 matcher runs its counting instantiation:
+    the pose must be the unprofiled run's bit for bit, and the count of
+    evaluated terms lies between one term per (query, row) tile visit and
+    the 33 terms per (query, row) of the definition."""
+    plain = ctx.register_pair(pair1.P, pair1.Q, pair1.vpP, pair1.vpQ)
+    ctx.set_profiling(True)
+    try:
+        prof = ctx.register_pair(pair1.P, pair1.Q, pair1.vpP, pair1.vpQ)
+    finally:
+        ctx.set_profiling(False)
+    assert np.array_equal(prof.T, plain.T) and prof.inliers == plain.inliers
+    dense = len(pair1.P) * len(pair1.Q) * 33
+    assert 0 < prof.match_terms <= dense
+    assert plain.match_terms == 0
+    assert all(t >= 0 for t in prof.stage_ms) and prof.stage_ms[7] > 0
