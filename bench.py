@@ -437,6 +437,8 @@ def roofline(info):
                 "frac": ach / peak, "traffic": traffic,
                 "executed_terms": terms, "executed_share": terms / dense,
                 "executed_frac": terms * 3 / (st[k] * 1e-3) / 1e12 / peak,
+                "note": "frac counts the dense definition's work; the exact early exits skip most terms, so it "
+                        "exceeds 1 by design; executed_frac is the pipe share of the terms actually evaluated",
                 "peak_source": f"152 SMs x 128 FP32 lanes x 1.5 flop x {sm_mhz:.0f} MHz (FADD+FFMA issue peak)",
                 "work": "nP*nQ*33 terms x 3 flop (dense definition)"}
     if names[k] == "consensus":

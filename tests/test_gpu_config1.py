@@ -89,8 +89,8 @@ def test_config1_register_matches_oracle_fixed_point(ctx, pair1):
 def test_config1_profiled_run_counts_terms_and_changes_nothing(ctx, pair1):
     """With profiling on, the FP32 matcher runs its counting instantiation:
     the pose must be the unprofiled run's bit for bit, and the count of
-    evaluated terms lies between one term per (query, row) tile visit and
-    the 33 terms per (query, row) of the definition."""
+    evaluated terms is positive and at most the 33 terms per (query, row) of
+    the definition (unprofiled runs report none)."""
     plain = ctx.register_pair(pair1.P, pair1.Q, pair1.vpP, pair1.vpQ)
     ctx.set_profiling(True)
     try:
