@@ -31,6 +31,7 @@ namespace {
 
 constexpr int kClsThreads = 256;
 constexpr int kClsChunk = 2048;
+constexpr int kClsMinBlocks = 8;  // resident blocks per SM
 
 // Table geometry from Q's box: the finest voxel (eps / k) whose two bit-sets
 // fit kClsCapWords words each; all_amb = 1 if none does (every point then
@@ -153,7 +154,7 @@ __device__ __forceinline__ bool warp_any_within(const GridParams &g, const int *
 // Otherwise the undecided lanes are resolved by the whole warp, one at a time,
 // and count receives the exact inlier count.
 template <bool kBounds>
-__global__ void __launch_bounds__(kClsThreads) k_consensus_count(
+__global__ void __launch_bounds__(kClsThreads, kClsMinBlocks) k_consensus_count(
     const float4 *__restrict__ XP, int nP, const ClsParams *__restrict__ cpp, const unsigned *__restrict__ in_bits,
     const unsigned *__restrict__ near_bits, const GridParams *__restrict__ gep, const int *__restrict__ start,
     const float4 *__restrict__ Xe, const float *__restrict__ pose, const uint8_t *__restrict__ ok, const int *n_dev,
