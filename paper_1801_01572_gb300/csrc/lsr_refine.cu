@@ -18,6 +18,7 @@ namespace {
 
 constexpr int kRefThreads = 256;
 constexpr int kRefG = 4;   // lanes per nearest-neighbour query in refinement (4 measured fastest of 4/8/16)
+constexpr int kRefBlocksPerSm = 4;  // resident refinement blocks per SM (64 registers a thread; 3 measured slower)
 constexpr int kObjG = 8;   // lanes per query in the objective
 // 21 (upper triangle of A) + 6 (b) + count + sum w + sum w x (3)
 constexpr int kNAcc = kRefAcc;
@@ -128,7 +129,7 @@ __device__ void refine_solve(const double *acc, RansacState *st, int max_iters, 
 
 // One IRLS step. Every block accumulates its points; the last block to
 // finish (atomic ticket, no waiting) sums all block partials and solves.
-__global__ void __launch_bounds__(kRefThreads, 3) k_refine_step(const float4 *__restrict__ XP, int nP, int strideP,
+__global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(const float4 *__restrict__ XP, int nP, int strideP,
                                                              const GridParams *gep, const int *__restrict__ start,
                                                              const float4 *__restrict__ Xe, float eps2, float mu,
                                                              RansacState *st, double *partials, int max_iters,
@@ -371,7 +372,7 @@ __global__ void k_objective_sum(const double *partials, int nblocks, double *out
 // that the launch-closing block sums few partials.
 int refine_blocks(int nP) {
   int64_t b = lsr_div_up((int64_t)(nP > 0 ? nP : 1) * kRefG, kRefThreads);
-  return (int)(b < 1 ? 1 : (b > 152 * 3 ? 152 * 3 : b));  // three resident blocks per SM
+  return (int)(b < 1 ? 1 : (b > 152 * kRefBlocksPerSm ? 152 * kRefBlocksPerSm : b));  // all blocks resident
 }
 
 int gnc_stride(int64_t n, int level, int levels) {
