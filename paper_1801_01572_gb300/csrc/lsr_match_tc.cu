@@ -13,10 +13,11 @@
 // the query side is pre-scaled by -2 (exact), so the FP32 accumulator holds the
 // score s = |b~|^2 - 2 a~.b~ and the epilogue only compares.
 //
-// Each persistent CTA takes 256 queries (two M = 128 tiles sharing every
-// database tile) and streams the database in tiles of 128 rows: one thread
-// issues tcgen05.mma from shared memory into TMEM (two accumulator buffers, so
-// the tensor pipe runs while the epilogue drains the other), and eight
+// Each persistent CTA takes units of 128 or 256 queries (one or two M = 128
+// tiles sharing every database tile; the shape is chosen per size by the
+// autotuner) and streams the database in tiles of 128 rows: one thread issues
+// tcgen05.mma from shared memory into TMEM (two accumulator buffers, so the
+// tensor pipe runs while the epilogue drains the other), and four or eight
 // epilogue warps, one query per thread, read a whole accumulator row with one
 // wait, release the buffer at once, and keep the 8 smallest minima of 16-row
 // chunks (a chunk enters when its minimum beats the lane's current 8th).
