@@ -39,7 +39,7 @@ constexpr int kQR = 2;     // queries per thread, listed rows (k_match_rows_chun
 constexpr int kTile = 64;  // database rows per shared-memory tile
 constexpr int kStageThreads = 9 * (kMT / 9);  // staging threads: one float4 column each
 constexpr int kTB = 72;    // floats per tile bound: lo[36], hi[36], bins in desc_order
-constexpr int kLB = 33;    // leading bins (desc_order) summed in the tile bound
+constexpr int kLB = 33;    // bins (desc_order) summed in the tile bound: all (fewer loosen it more than they save)
 static_assert(kTile * 9 > kStageThreads, "staging covers the tile in several passes");
 
 // Database rows [base, base + kTile) (zero past lim) into the tile, bin
