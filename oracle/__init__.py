@@ -95,6 +95,7 @@ def lib():
                 "orc_refine_gnc": (C.c_int, [dp, i64, dp, i64, dp, dbl, dbl, C.c_int, C.c_int, dbl, dp]),
                 "orc_gnc_stride": (i64, [i64, C.c_int, C.c_int]),
                 "orc_objective": (C.c_double, [dp, i64, dp, i64, dp, dp, dbl, dbl, dp, dp, dp, ip]),
+                "orc_information": (None, [dp, i64, dp, i64, dp, dbl, dbl, dp, ip, ip, dp]),
                 "orc_register": (C.c_int, [dp, i64, dp, i64, dp, dp, C.POINTER(Params), C.POINTER(Result), dp, dp, ip]),
             }
             for name, (res, args) in sig.items():
@@ -302,6 +303,20 @@ def refine_gnc(P, Q, T, eps, mu_scale=1.0, levels=3, iters=50, tol=1e-10):
 
 def gnc_stride(n, level, levels):
     return int(lib().orc_gnc_stride(int(n), int(level), int(levels)))
+
+
+def information(P, Q, T, eps=0.05, band=0.0):
+    """Information matrix of eq. (5)-(6): sum of G_p^T G_p, G_p = [-[p]_x | I],
+    over the points p of T P whose NN in Q lies closer than eps. Returns
+    (info 6x6, n, namb, amb_max): namb points have their NN distance within
+    band of eps, the largest |T p|^2 among them is amb_max."""
+    P, Q = _f64(P, 3), _f64(Q, 3)
+    T = _f64(T).reshape(16)
+    info = np.zeros(36)
+    n, namb, amb_max = C.c_int64(0), C.c_int64(0), C.c_double(0.0)
+    lib().orc_information(_P(P, C.c_double), len(P), _P(Q, C.c_double), len(Q), _P(T, C.c_double), eps, band,
+                          _P(info, C.c_double), C.byref(n), C.byref(namb), C.byref(amb_max))
+    return info.reshape(6, 6), n.value, namb.value, amb_max.value
 
 
 def objective(P, Q, xi, T0, eps, mu, grad=True):

@@ -1252,6 +1252,46 @@ int orc_refine_gnc(const double *P, int64_t nP, const double *Q, int64_t nQ, con
 }
 
 /* ------------------------------------------------------------------------ */
+/* Information matrix of a verified pair (loop verification, eq. (5)-(6)):  */
+/* the quadratic form that approximates the alignment error of the pair is  */
+/* xi^T (sum over (p, q) in K of G_p^T G_p) xi with G_p = [-[p]_x | I] and K */
+/* the nearest-neighbour pairs between the moved cloud T P and Q closer     */
+/* than eps (the paper uses eps = 0.05 m). Reading: both clouds are in Q's  */
+/* frame, so p in G_p is the moved point T p. info is row-major 6 x 6, n the */
+/* size of K. namb counts the points of P whose NN distance lies within     */
+/* band of eps (FP32 may decide those either way) and amb_max is the largest */
+/* |T p|^2 among them.                                                      */
+/* ------------------------------------------------------------------------ */
+void orc_information(const double *P, int64_t nP, const double *Q, int64_t nQ, const double T[16], double eps,
+                     double band, double info[36], int64_t *n, int64_t *namb, double *amb_max) {
+  const double R[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]}, t[3] = {T[3], T[7], T[11]};
+  orc_grid g;
+  grid_build(&g, Q, nQ, eps + band);
+  for (int k = 0; k < 36; ++k) info[k] = 0.0;
+  *n = 0;
+  *namb = 0;
+  *amb_max = 0.0;
+  for (int64_t i = 0; i < nP; ++i) {
+    double x[3], d2;
+    xform(R, t, P + 3 * i, x);
+    if (nn_within(&g, Q, x, eps + band, &d2) < 0) continue;
+    if (fabs(sqrt(d2) - eps) <= band) {
+      ++*namb;
+      if (dot3(x, x) > *amb_max) *amb_max = dot3(x, x);
+    }
+    if (!(d2 < eps * eps)) continue;
+    /* G = [-[x]_x | I], three rows of six */
+    const double G[3][6] = {{0.0, x[2], -x[1], 1.0, 0.0, 0.0},
+                            {-x[2], 0.0, x[0], 0.0, 1.0, 0.0},
+                            {x[1], -x[0], 0.0, 0.0, 0.0, 1.0}};
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b < 6; ++b) info[6 * a + b] += G[0][a] * G[0][b] + G[1][a] * G[1][b] + G[2][a] * G[2][b];
+    ++*n;
+  }
+  grid_free(&g);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Robust alignment objective and its analytic gradient (the objective of   */
 /* the refinement above, with NN correspondences recomputed at the given   */
 /* pose): E = sum_i rho~(s_i), s_i = |T(xi) p_i - q_n(i)|^2 over the points */
