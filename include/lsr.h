@@ -285,6 +285,20 @@ LSR_API int lsr_objective_bwd(lsr_ctx *ctx, int32_t n, const float *const *P, co
                       const int64_t *nQ, const double *xi, const double *T0, float eps, float mu, const double *dE,
                       float *const *dP, float *const *dQ, double *dxi);
 
+/* Information matrix of a verified pair (loop verification, eq. (5)-(6)):
+ * info = sum over the correspondences K of G_p^T G_p, G_p = [-[p]_x | I],
+ * where K holds the points p = T p' (p' in P, moved into Q's frame by the
+ * row-major 4x4 pose T) whose nearest Q point is closer than eps (the paper
+ * takes eps = 0.05 m). xi^T info xi is then the first-order alignment error of
+ * the pair under a small motion xi = (alpha, beta, gamma, x, y, z).
+ * P: nP x 3, Q: nQ x 3 float32, device or host. T: 16 double, host.
+ * info: 36 double, host, row-major (symmetric); n_corr (host, may be NULL):
+ * |K|. Sums in FP32 per thread about the centre of Q's box, FP64 across
+ * blocks in a fixed order (deterministic). Errors: LSR_E_ARG for null
+ * pointers, sizes outside [1, 2^26], eps outside (0, 10] or a non-finite T. */
+LSR_API int lsr_information_matrix(lsr_ctx *ctx, const float *P, int64_t nP, const float *Q, int64_t nQ,
+                                   const double *T, float eps, double *info, int64_t *n_corr);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1556,6 +1556,54 @@ int lsr_stage_refine(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int
 }
 
 // ------------------------------------------------------------------ objective
+int lsr_information_matrix(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int64_t nQ, const double *T,
+                           float eps, double *info, int64_t *n_corr) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!P || !Q || !T || !info || nP < 1 || nQ < 1 || nP > kMaxPoints || nQ > kMaxPoints || !(eps > 0.f && eps <= 10.f))
+    return set_err(c, LSR_E_ARG, "bad argument");
+  for (int k = 0; k < 16; ++k)
+    if (!std::isfinite(T[k])) return set_err(c, LSR_E_ARG, "non-finite pose");
+  struct Bufs {
+    float *p;
+    CloudLayout Cq;
+    ScratchLayout S;
+    double *part, *out;
+  };
+  auto plan = [&](Arena &a, Bufs &b) {
+    b.p = a.take<float>(3 * nP);
+    plan_cloud(a, (int)nQ, true, false, true, b.Cq);
+    plan_scratch(a, (int)nQ, b.Cq.cap_f, b.S);
+    b.part = a.take<double>((size_t)10 * information_blocks((int)nP));
+    b.out = a.take<double>(37);
+  };
+  Arena m(nullptr);
+  Bufs bm;
+  plan(m, bm);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  Bufs b;
+  plan(a, b);
+  cudaStream_t s = c->stream;
+  const float *psrc, *qsrc;
+  if ((rc = stage_input(c, P, nP, b.p, &psrc))) return rc;
+  if ((rc = stage_input(c, Q, nQ, b.Cq.src, &qsrc))) return rc;
+  TRY_CUDA(c, build_cloud(qsrc, b.Cq, eps, eps, eps, false, true, b.S, s), "grid Q");
+  float R[9], t[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 3; ++q) R[3 * r + q] = (float)T[4 * r + q];
+    t[r] = (float)T[4 * r + 3];
+  }
+  TRY_CUDA(c, launch_information(psrc, (int)nP, b.Cq.ge, b.Cq.start_e, b.Cq.Xe, b.Cq.box, R, t, eps, b.part, b.out, s),
+           "information");
+  double host[37];
+  TRY_CUDA(c, cudaMemcpyAsync(host, b.out, sizeof(host), cudaMemcpyDeviceToHost, s), "D2H");
+  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  for (int k = 0; k < 36; ++k) info[k] = host[k];
+  if (n_corr) *n_corr = (int64_t)host[36];
+  return LSR_OK;
+}
+
 static void host_exp_so3(const double w[3], double R[9]) {
   double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2], th = sqrt(th2);
   double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};

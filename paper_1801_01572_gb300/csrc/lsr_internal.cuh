@@ -448,6 +448,13 @@ cudaError_t launch_final_count(const int *count, const unsigned long long *sum, 
 // E, g_v[3], g_w[3]. dP / dQ (device, caller order) are written when want_grad
 // (dQ must be zeroed by the caller), scaled by `scale`.
 int objective_blocks(int nP);
+// Information matrix of eq. (5)-(6) for the pose [R | t]: out[0..35] row-major
+// Lambda, out[36] = |K|. boxQ: Q's box (lo, hi); partials: 10 x
+// information_blocks(nP) doubles.
+int information_blocks(int nP);
+cudaError_t launch_information(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
+                               const float *boxQ, const float R[9], const float t[3], float eps, double *partials,
+                               double *out, cudaStream_t s);
 cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
                              const float R[9], const float t[3], const float v[3], float eps, float mu, float scale,
                              int want_grad, double *partials, double *out7, float *dP, float *dQ, cudaStream_t s);

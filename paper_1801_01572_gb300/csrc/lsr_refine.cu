@@ -297,6 +297,82 @@ __global__ void k_final_count(const int *count, const unsigned long long *sum, R
   }
 }
 
+// ---------------------------------------------------------------- information matrix
+// Loop verification (eq. (5)-(6)): Lambda = sum over K of G_p^T G_p with
+// G_p = [-[p]_x | I], K the moved points p = R p' + t whose nearest Q point
+// lies within eps. Written out, G_p^T G_p = [[|p|^2 I - p p^T, [p]_x],
+// [-[p]_x, I]], so Lambda needs only |K|, sum p and sum p p^T. Each group of
+// kRefG lanes searches one point; its first lane adds 1, d and d d^T with
+// d = p - c (c: the centre of Q's box, which keeps the FP32 sums small) to ten
+// per-thread sums; blocks reduce them to FP64 partials, and one thread adds
+// the partials in block order and expands them about c.
+struct InfoArgs {
+  float R[9], t[3];
+  float eps2;
+};
+
+__global__ void __launch_bounds__(kRefThreads) k_info_sums(const float *__restrict__ P, int nP, const GridParams *gep,
+                                                           const int *__restrict__ start, const float4 *__restrict__ Xe,
+                                                           const float *__restrict__ boxQ, InfoArgs a,
+                                                           double *__restrict__ partials) {
+  constexpr int G = kRefG, GPB = kRefThreads / G;
+  const GridParams g = *gep;
+  const float c0 = 0.5f * (boxQ[0] + boxQ[3]), c1 = 0.5f * (boxQ[1] + boxQ[4]), c2 = 0.5f * (boxQ[2] + boxQ[5]);
+  const int grp = threadIdx.x / G, sub = threadIdx.x & (G - 1);
+  float acc[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) acc[k] = 0.f;
+  // block-uniform trip count: every lane reaches the group shuffles
+  for (int r0 = blockIdx.x * GPB; r0 < nP; r0 += gridDim.x * GPB) {
+    const int i = r0 + grp;
+    const bool valid = i < nP;
+    float px = valid ? P[3 * i] : __int_as_float(0x7fc00000), py = valid ? P[3 * i + 1] : 0.f,
+          pz = valid ? P[3 * i + 2] : 0.f;  // NaN: the query visits no cell
+    const float x = fmaf(a.R[0], px, fmaf(a.R[1], py, fmaf(a.R[2], pz, a.t[0])));
+    const float y = fmaf(a.R[3], px, fmaf(a.R[4], py, fmaf(a.R[5], pz, a.t[1])));
+    const float z = fmaf(a.R[6], px, fmaf(a.R[7], py, fmaf(a.R[8], pz, a.t[2])));
+    float best;
+    int bt, bidx;
+    group_nn<G>(g, start, Xe, x, y, z, a.eps2, best, bt, bidx);
+    if (!valid || bt < 0 || sub != 0) continue;
+    const float dx = x - c0, dy = y - c1, dz = z - c2;
+    acc[0] += 1.f;
+    acc[1] += dx, acc[2] += dy, acc[3] += dz;
+    acc[4] += dx * dx, acc[5] += dx * dy, acc[6] += dx * dz;
+    acc[7] += dy * dy, acc[8] += dy * dz, acc[9] += dz * dz;
+  }
+  block_reduce_to<10>(acc, partials + (size_t)blockIdx.x * 10);
+}
+
+__global__ void k_info_final(const double *__restrict__ partials, int nb, const float *__restrict__ boxQ,
+                             double *__restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double S[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < nb; ++b)
+    for (int k = 0; k < 10; ++k) S[k] += partials[(size_t)b * 10 + k];
+  const double c[3] = {0.5 * ((double)boxQ[0] + (double)boxQ[3]), 0.5 * ((double)boxQ[1] + (double)boxQ[4]),
+                       0.5 * ((double)boxQ[2] + (double)boxQ[5])};
+  const double n = S[0];
+  // sum p = sum d + n c; sum p p^T = sum d d^T + c (sum d)^T + (sum d) c^T + n c c^T
+  double sp[3], spp[3][3];
+  const double sdd[3][3] = {{S[4], S[5], S[6]}, {S[5], S[7], S[8]}, {S[6], S[8], S[9]}};
+  for (int r = 0; r < 3; ++r) sp[r] = S[1 + r] + n * c[r];
+  for (int r = 0; r < 3; ++r)
+    for (int q = r; q < 3; ++q)  // upper triangle, mirrored: Lambda is exactly symmetric
+      spp[r][q] = spp[q][r] = sdd[r][q] + c[r] * S[1 + q] + S[1 + r] * c[q] + n * c[r] * c[q];
+  const double tr = spp[0][0] + spp[1][1] + spp[2][2];
+  // [sp]_x
+  const double K[3][3] = {{0.0, -sp[2], sp[1]}, {sp[2], 0.0, -sp[0]}, {-sp[1], sp[0], 0.0}};
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) {
+      out[6 * r + q] = (r == q ? tr : 0.0) - spp[r][q];
+      out[6 * r + 3 + q] = K[r][q];
+      out[6 * (3 + r) + q] = -K[r][q];
+      out[6 * (3 + r) + 3 + q] = r == q ? n : 0.0;
+    }
+  out[36] = n;
+}
+
 // ---------------------------------------------------------------- objective
 // E = sum_i rho(s_i) - rho(eps^2) over points with an NN closer than eps.
 // Forward and backward share this kernel; the backward also writes
@@ -416,6 +492,24 @@ cudaError_t launch_final_pose(RansacState *st, float *pose, cudaStream_t s) {
 
 cudaError_t launch_final_count(const int *count, const unsigned long long *sum, RansacState *st, cudaStream_t s) {
   LSR_LAUNCH(k_final_count<<<1, 32, 0, s>>>(count, sum, st));
+  return cudaGetLastError();
+}
+
+int information_blocks(int nP) {
+  int64_t b = lsr_div_up((int64_t)(nP > 0 ? nP : 1) * kRefG, kRefThreads);
+  return (int)(b < 1 ? 1 : (b > 152 * 4 ? 152 * 4 : b));
+}
+
+cudaError_t launch_information(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
+                               const float *boxQ, const float R[9], const float t[3], float eps, double *partials,
+                               double *out, cudaStream_t s) {
+  InfoArgs a;
+  for (int k = 0; k < 9; ++k) a.R[k] = R[k];
+  for (int k = 0; k < 3; ++k) a.t[k] = t[k];
+  a.eps2 = eps * eps;
+  const int nb = information_blocks(nP);
+  LSR_LAUNCH(k_info_sums<<<nb, kRefThreads, 0, s>>>(P, nP, ge, start_e, Xe, boxQ, a, partials));
+  LSR_LAUNCH(k_info_final<<<1, 32, 0, s>>>(partials, nb, boxQ, out));
   return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ ABI_FUNCTIONS = (
     "lsr_register_pair", "lsr_register_batch",
     "lsr_stage_normals", "lsr_stage_spfh", "lsr_stage_fpfh", "lsr_stage_match", "lsr_stage_hypotheses",
     "lsr_stage_rigid4", "lsr_stage_consensus", "lsr_stage_refine", "lsr_objective_fwd", "lsr_objective_bwd",
-    "lsr_consensus_static", "lsr_match_scores_bf16",
+    "lsr_consensus_static", "lsr_match_scores_bf16", "lsr_information_matrix",
 )
 
 
@@ -100,6 +100,7 @@ def lib():
             "lsr_objective_fwd": (C.c_int, [vp, i32, pp, vp, pp, vp, vp, vp, f32, f32, vp]),
             "lsr_objective_bwd": (C.c_int, [vp, i32, pp, vp, pp, vp, vp, vp, f32, f32, vp, pp, pp, vp]),
             "lsr_consensus_static": (C.c_int, [vp, i64, vp, i64, vp, i64, f32, vp, vp, vp]),
+            "lsr_information_matrix": (C.c_int, [vp, vp, i64, vp, i64, vp, f32, vp, vp]),
         }
         for name in ABI_FUNCTIONS:
             res, args = sig[name]
@@ -369,6 +370,18 @@ class Context:
                                              C.c_float(mu_scale), int(levels), int(iters),
                                              C.c_void_p(Tout.ctypes.data), C.byref(it)))
         return Tout.reshape(4, 4), int(it.value)
+
+    def information_matrix(self, P, Q, T, eps=0.05):
+        """Information matrix of eq. (5)-(6) for the pose T (P into Q's frame):
+        returns (6x6 float64 array, number of correspondences)."""
+        pP, kP, nP = _prep(P, np.float32, 3)
+        pQ, kQ, nQ = _prep(Q, np.float32, 3)
+        Tin = np.ascontiguousarray(np.asarray(T, np.float64).reshape(16))
+        info = np.zeros(36, np.float64)
+        n = C.c_int64(0)
+        self._check(self._L.lsr_information_matrix(self._h, pP, nP, pQ, nQ, C.c_void_p(Tin.ctypes.data),
+                                                   C.c_float(eps), C.c_void_p(info.ctypes.data), C.byref(n)))
+        return info.reshape(6, 6), int(n.value)
 
     # -- objective (device tensors)
     def _obj_args(self, Ps, Qs, xi, T0):
