@@ -319,6 +319,47 @@ def information(P, Q, T, eps=0.05, band=0.0):
     return info.reshape(6, 6), n.value, namb.value, amb_max.value
 
 
+def surfel_correct(pos, nrm, t0, tu, T_old, T_new, t_kf, cam):
+    """Dense model correction of eq. (7), in FP64 with numpy.
+
+    For each surfel (position p, normal n, time stamps t0 < tu), F is the set
+    of keyframes f with t0 < t_f < tu that observe the surfel before the
+    correction: the point T_f_old^-1 p lies in front of the camera, no farther
+    than the maximum depth, and projects inside the image (reading: pinhole
+    camera cam = (fx, fy, cx, cy, width, height, max depth), u = fx x / z + cx,
+    0 <= u < width, likewise v). With k = |F|,
+        p' = (1/k) sum_f T_f_new T_f_old^-1 p,
+        n' = normalize((1/k) sum_f R_f_new R_f_old^-1 n),
+    and a surfel with k = 0 is removed (keep = False; p, n returned unchanged).
+    T_old, T_new: m x 4 x 4 camera-to-world poses; t_kf: m time stamps.
+    Returns (p', n', keep)."""
+    pos, nrm = np.asarray(pos, np.float64), np.asarray(nrm, np.float64)
+    t0, tu = np.asarray(t0, np.float64), np.asarray(tu, np.float64)
+    T_old, T_new = np.asarray(T_old, np.float64), np.asarray(T_new, np.float64)
+    fx, fy, cx, cy, W, H, dmax = (float(v) for v in cam)
+    sp = np.zeros_like(pos)
+    sn = np.zeros_like(nrm)
+    k = np.zeros(len(pos), np.int64)
+    for f in range(len(T_old)):
+        inv = np.linalg.inv(T_old[f])
+        M = T_new[f] @ inv
+        xc = pos @ inv[:3, :3].T + inv[:3, 3]
+        z = xc[:, 2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = fx * xc[:, 0] / z + cx
+            v = fy * xc[:, 1] / z + cy
+        seen = (t0 < t_kf[f]) & (t_kf[f] < tu) & (z > 0) & (z <= dmax) & (u >= 0) & (u < W) & (v >= 0) & (v < H)
+        k += seen
+        sp[seen] += pos[seen] @ M[:3, :3].T + M[:3, 3]
+        sn[seen] += nrm[seen] @ M[:3, :3].T
+    keep = k > 0
+    p_out, n_out = pos.copy(), nrm.copy()
+    p_out[keep] = sp[keep] / k[keep, None]
+    m = sn[keep] / k[keep, None]
+    n_out[keep] = m / np.linalg.norm(m, axis=1, keepdims=True)
+    return p_out, n_out, keep
+
+
 def objective(P, Q, xi, T0, eps, mu, grad=True):
     """E and (if grad) dE/dP, dE/dQ, dE/dxi, plus the NN index of each point."""
     P, Q = _f64(P, 3), _f64(Q, 3)
