@@ -208,10 +208,28 @@ def run_ours(args, rank, world):
         e1.record(stream)
         e1.synchronize()
         info_ms.append(e0.elapsed_time(e1))
+    # dense model correction of eq. (7) on a 2M-surfel room map and a 300-keyframe loop, resident
+    # inputs; algorithmic bytes 32 in + 25 out per surfel
+    from synth.surfels import make_surfels
+    smap = make_surfels(2_000_000, 300, seed=3)
+    sd = [torch.from_numpy(x).cuda() for x in (smap.pos, smap.nrm, smap.t0, smap.tu)]
+    ctx.surfel_correct(*sd, smap.T_old, smap.T_new, smap.t_kf, smap.cam)
+    surf_ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, _, n_kept = ctx.surfel_correct(*sd, smap.T_old, smap.T_new, smap.t_kf, smap.cam)
+        e1.record(stream)
+        e1.synchronize()
+        surf_ms.append(e0.elapsed_time(e1))
     h2d, d2h = lsr.transfer_bytes(nP, nQ)
     info = dict(fp=fp, nP=nP, nQ=nQ, last=last, prof=prof, stage_ms=stage_ms, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d,
                 d2h=d2h, launches=launches, clocks=clk.summary(pk.get("sm_max_mhz")), peaks=pk,
                 information={"ms": float(np.median(info_ms)), "correspondences": int(n_corr), "eps": 0.05},
+                surfels={"ms": float(np.median(surf_ms)), "surfels": len(smap.pos), "keyframes": len(smap.t_kf),
+                         "kept": int(n_kept),
+                         "GB/s": 57.0 * len(smap.pos) / (float(np.median(surf_ms)) * 1e-3) / 1e9,
+                         "note": "call time incl. the keyframe transforms' upload; 57 B per surfel"},
                 params=ctx.params, match=args.match)
     ctx.close()
 
@@ -697,6 +715,7 @@ def main():
                        "refine_iters": last.refine_iters, "match_fallbacks": last.match_fallbacks},
             "roofline": roofline(info),
             "information_matrix": info["information"],
+            "surfel_correction": info["surfels"],
             "e2e": {"value": e2e, "unit": "pairs/s", "h2d_bytes_per_step": info["h2d"] * world,
                     "d2h_bytes_per_step": info["d2h"] * world},
             "gpu_launches": int(info["launches"]),

@@ -299,6 +299,28 @@ LSR_API int lsr_objective_bwd(lsr_ctx *ctx, int32_t n, const float *const *P, co
 LSR_API int lsr_information_matrix(lsr_ctx *ctx, const float *P, int64_t nP, const float *Q, int64_t nQ,
                                    const double *T, float eps, double *info, int64_t *n_corr);
 
+/* Dense model correction after a loop closure (eq. (7)): every surfel moves
+ * with the keyframes that observe it,
+ *   p' = (1/k) sum_{f in F} T_f_new T_f_old^-1 p,
+ *   n' = normalize(sum_{f in F} R_f_new R_f_old^-1 n),
+ * F = the keyframes with t0 < t_f < tu (the surfel's initialisation and
+ * last-update stamps) whose camera before the correction sees the surfel:
+ * z > 0 and z <= max depth in the camera frame, and the pinhole projection
+ * u = fx x / z + cx, v = fy y / z + cy inside [0, width) x [0, height).
+ * A surfel with k = |F| = 0 is removed: keep = 0, p and n copied unchanged.
+ * pos, nrm: n x 3 float32; t0, tu: n float32 (device or host). T_old, T_new:
+ * m x 16 double row-major rigid camera-to-world poses; t_kf: m float32 in
+ * ascending order; cam: 7 float32 (fx, fy, cx, cy, width, height, max depth)
+ * (all host). pos_out, nrm_out (n x 3 float32) and keep (n bytes): all device
+ * or all host; n_keep (host, may be NULL): surfels kept. FP32 on the device,
+ * the keyframe transforms composed in FP64 on the host. Errors: LSR_E_ARG for
+ * null pointers, n outside [1, 2^31], m outside [1, 2^20], non-ascending
+ * stamps, a non-finite pose or a non-positive camera parameter. */
+LSR_API int lsr_surfel_correct(lsr_ctx *ctx, int64_t n, const float *pos, const float *nrm, const float *t0,
+                               const float *tu, int32_t m, const double *T_old, const double *T_new,
+                               const float *t_kf, const float *cam, float *pos_out, float *nrm_out, uint8_t *keep,
+                               int64_t *n_keep);
+
 #ifdef __cplusplus
 }
 #endif

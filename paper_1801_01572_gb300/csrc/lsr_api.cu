@@ -1604,6 +1604,92 @@ int lsr_information_matrix(lsr_ctx *c, const float *P, int64_t nP, const float *
   return LSR_OK;
 }
 
+int lsr_surfel_correct(lsr_ctx *c, int64_t n, const float *pos, const float *nrm, const float *t0, const float *tu,
+                       int32_t m, const double *T_old, const double *T_new, const float *t_kf, const float *cam,
+                       float *pos_out, float *nrm_out, uint8_t *keep, int64_t *n_keep) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!pos || !nrm || !t0 || !tu || !T_old || !T_new || !t_kf || !cam || !pos_out || !nrm_out || !keep || n < 1 ||
+      n > ((int64_t)1 << 31) || m < 1 || m > (1 << 20))
+    return set_err(c, LSR_E_ARG, "bad argument");
+  for (int k = 0; k < 7; ++k)
+    if (!(std::isfinite(cam[k]) && cam[k] > 0.f) && !(k >= 2 && k <= 3 && std::isfinite(cam[k])))
+      return set_err(c, LSR_E_ARG, "bad camera");
+  std::vector<KfPose> kf((size_t)m);
+  for (int f = 0; f < m; ++f) {
+    if (f > 0 && !(t_kf[f] >= t_kf[f - 1])) return set_err(c, LSR_E_ARG, "keyframe stamps must ascend");
+    const double *To = T_old + 16 * (size_t)f, *Tn = T_new + 16 * (size_t)f;
+    for (int k = 0; k < 16; ++k)
+      if (!std::isfinite(To[k]) || !std::isfinite(Tn[k])) return set_err(c, LSR_E_ARG, "non-finite pose");
+    // rigid inverse of the camera-to-world pose: [R^T | -R^T t]
+    double A[12], M[12];
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) A[4 * r + q] = To[4 * q + r];
+      A[4 * r + 3] = -(To[r] * To[3] + To[4 + r] * To[7] + To[8 + r] * To[11]);
+    }
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 4; ++q)
+        M[4 * r + q] = Tn[4 * r] * A[q] + Tn[4 * r + 1] * A[4 + q] + Tn[4 * r + 2] * A[8 + q] + (q == 3 ? Tn[4 * r + 3] : 0.0);
+    for (int k = 0; k < 12; ++k) kf[f].A[k] = (float)A[k], kf[f].M[k] = (float)M[k];
+  }
+  const SurfelCam sc{cam[0], cam[1], cam[2], cam[3], cam[4], cam[5], cam[6]};
+  struct Bufs {
+    float *pos, *nrm, *t0, *tu, *tk, *po, *no;
+    KfPose *kf;
+    uint8_t *keep;
+    unsigned long long *cnt;
+  };
+  auto plan = [&](Arena &a, Bufs &b) {
+    b.pos = a.take<float>(3 * (size_t)n);
+    b.nrm = a.take<float>(3 * (size_t)n);
+    b.t0 = a.take<float>((size_t)n);
+    b.tu = a.take<float>((size_t)n);
+    b.po = a.take<float>(3 * (size_t)n);
+    b.no = a.take<float>(3 * (size_t)n);
+    b.keep = a.take<uint8_t>((size_t)n);
+    b.kf = a.take<KfPose>((size_t)m);
+    b.tk = a.take<float>((size_t)m);
+    b.cnt = a.take<unsigned long long>(1);
+  };
+  Arena mm(nullptr);
+  Bufs bm;
+  plan(mm, bm);
+  if ((rc = ensure_ws(c, mm.off))) return rc;
+  Arena a(c->ws);
+  Bufs b;
+  plan(a, b);
+  cudaStream_t s = c->stream;
+  auto in = [&](const float *src, size_t cnt, float *dst, const float **out) -> int {
+    if (is_device_ptr(src)) {
+      *out = src;
+      return LSR_OK;
+    }
+    TRY_CUDA(c, cudaMemcpyAsync(dst, src, sizeof(float) * cnt, cudaMemcpyHostToDevice, s), "H2D");
+    *out = dst;
+    return LSR_OK;
+  };
+  const float *dpos, *dnrm, *dt0, *dtu;
+  if ((rc = in(pos, 3 * (size_t)n, b.pos, &dpos)) || (rc = in(nrm, 3 * (size_t)n, b.nrm, &dnrm)) ||
+      (rc = in(t0, (size_t)n, b.t0, &dt0)) || (rc = in(tu, (size_t)n, b.tu, &dtu)))
+    return rc;
+  TRY_CUDA(c, cudaMemcpyAsync(b.kf, kf.data(), sizeof(KfPose) * (size_t)m, cudaMemcpyHostToDevice, s), "H2D");
+  TRY_CUDA(c, cudaMemcpyAsync(b.tk, t_kf, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice, s), "H2D");
+  const bool dev_out = is_device_ptr(pos_out) && is_device_ptr(nrm_out) && is_device_ptr(keep);
+  float *po = dev_out ? pos_out : b.po, *no = dev_out ? nrm_out : b.no;
+  uint8_t *ko = dev_out ? keep : b.keep;
+  TRY_CUDA(c, launch_surfel_correct(n, dpos, dnrm, dt0, dtu, m, b.kf, b.tk, sc, po, no, ko, b.cnt, s), "surfels");
+  if (!dev_out) {
+    if ((rc = copy_out(c, pos_out, po, sizeof(float) * 3 * (size_t)n))) return rc;
+    if ((rc = copy_out(c, nrm_out, no, sizeof(float) * 3 * (size_t)n))) return rc;
+    if ((rc = copy_out(c, keep, ko, (size_t)n))) return rc;
+  }
+  unsigned long long cnt = 0;
+  TRY_CUDA(c, cudaMemcpyAsync(&cnt, b.cnt, sizeof(cnt), cudaMemcpyDeviceToHost, s), "D2H");
+  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  if (n_keep) *n_keep = (int64_t)cnt;
+  return LSR_OK;
+}
+
 static void host_exp_so3(const double w[3], double R[9]) {
   double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2], th = sqrt(th2);
   double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};

@@ -448,6 +448,18 @@ cudaError_t launch_final_count(const int *count, const unsigned long long *sum, 
 // E, g_v[3], g_w[3]. dP / dQ (device, caller order) are written when want_grad
 // (dQ must be zeroed by the caller), scaled by `scale`.
 int objective_blocks(int nP);
+// Dense model correction (eq. (7), lsr_surfel.cu). Per keyframe: A = T_old^-1
+// and M = T_new T_old^-1 as row-major 3 x 4 (camera-to-world poses).
+struct KfPose {
+  float A[12], M[12];
+};
+struct SurfelCam {
+  float fx, fy, cx, cy, w, h, dmax;
+};
+cudaError_t launch_surfel_correct(int64_t n, const float *pos, const float *nrm, const float *t0, const float *tu,
+                                  int m, const KfPose *kf, const float *t_kf, const SurfelCam &cam, float *pos_out,
+                                  float *nrm_out, uint8_t *keep, unsigned long long *n_keep, cudaStream_t s);
+
 // Information matrix of eq. (5)-(6) for the pose [R | t]: out[0..35] row-major
 // Lambda, out[36] = |K|. boxQ: Q's box (lo, hi); partials: 10 x
 // information_blocks(nP) doubles.

@@ -30,7 +30,7 @@ ABI_FUNCTIONS = (
     "lsr_register_pair", "lsr_register_batch",
     "lsr_stage_normals", "lsr_stage_spfh", "lsr_stage_fpfh", "lsr_stage_match", "lsr_stage_hypotheses",
     "lsr_stage_rigid4", "lsr_stage_consensus", "lsr_stage_refine", "lsr_objective_fwd", "lsr_objective_bwd",
-    "lsr_consensus_static", "lsr_match_scores_bf16", "lsr_information_matrix",
+    "lsr_consensus_static", "lsr_match_scores_bf16", "lsr_information_matrix", "lsr_surfel_correct",
 )
 
 
@@ -101,6 +101,7 @@ def lib():
             "lsr_objective_bwd": (C.c_int, [vp, i32, pp, vp, pp, vp, vp, vp, f32, f32, vp, pp, pp, vp]),
             "lsr_consensus_static": (C.c_int, [vp, i64, vp, i64, vp, i64, f32, vp, vp, vp]),
             "lsr_information_matrix": (C.c_int, [vp, vp, i64, vp, i64, vp, f32, vp, vp]),
+            "lsr_surfel_correct": (C.c_int, [vp, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
         }
         for name in ABI_FUNCTIONS:
             res, args = sig[name]
@@ -382,6 +383,34 @@ class Context:
         self._check(self._L.lsr_information_matrix(self._h, pP, nP, pQ, nQ, C.c_void_p(Tin.ctypes.data),
                                                    C.c_float(eps), C.c_void_p(info.ctypes.data), C.byref(n)))
         return info.reshape(6, 6), int(n.value)
+
+    def surfel_correct(self, pos, nrm, t0, tu, T_old, T_new, t_kf, cam):
+        """Dense model correction of eq. (7). pos, nrm: n x 3, t0, tu: n (numpy
+        or CUDA tensors); T_old, T_new: m x 4 x 4, t_kf: m ascending, cam: 7.
+        Returns (pos', nrm', keep, kept) as numpy arrays (or CUDA tensors when
+        pos is one)."""
+        pp, kp, n = _prep(pos, np.float32, 3)
+        pn, kn, _ = _prep(nrm, np.float32, 3)
+        p0, k0, _ = _prep(t0, np.float32, 1)
+        pu, ku, _ = _prep(tu, np.float32, 1)
+        To = np.ascontiguousarray(np.asarray(T_old, np.float64).reshape(-1, 16))
+        Tn = np.ascontiguousarray(np.asarray(T_new, np.float64).reshape(-1, 16))
+        tk = np.ascontiguousarray(np.asarray(t_kf, np.float32).reshape(-1))
+        cm = np.ascontiguousarray(np.asarray(cam, np.float32).reshape(7))
+        if _is_torch(pos):
+            import torch
+            po = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+            no = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+            ko = torch.empty(n, dtype=torch.uint8, device=pos.device)
+            ptrs = (C.c_void_p(po.data_ptr()), C.c_void_p(no.data_ptr()), C.c_void_p(ko.data_ptr()))
+        else:
+            po, no, ko = np.zeros((n, 3), np.float32), np.zeros((n, 3), np.float32), np.zeros(n, np.uint8)
+            ptrs = (C.c_void_p(po.ctypes.data), C.c_void_p(no.ctypes.data), C.c_void_p(ko.ctypes.data))
+        kept = C.c_int64(0)
+        self._check(self._L.lsr_surfel_correct(self._h, n, pp, pn, p0, pu, len(To), C.c_void_p(To.ctypes.data),
+                                               C.c_void_p(Tn.ctypes.data), C.c_void_p(tk.ctypes.data),
+                                               C.c_void_p(cm.ctypes.data), *ptrs, C.byref(kept)))
+        return po, no, ko, int(kept.value)
 
     # -- objective (device tensors)
     def _obj_args(self, Ps, Qs, xi, T0):
