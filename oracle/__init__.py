@@ -319,6 +319,26 @@ def information(P, Q, T, eps=0.05, band=0.0):
     return info.reshape(6, 6), n.value, namb.value, amb_max.value
 
 
+def voxel_downsample(P, leaf):
+    """Downsampling of Algorithm 1 (first line): one point per occupied voxel of
+    edge leaf, the mean of the points in it. Reading: voxels are aligned to the
+    coordinate origin, key = floor(p / leaf) per axis in FP64, and the output
+    is ordered by (k_z, k_y, k_x) ascending. Returns (points m x 3 float64,
+    counts m)."""
+    P = np.asarray(P, np.float64)
+    keys = np.floor(P / float(leaf)).astype(np.int64)
+    order = np.lexsort((keys[:, 0], keys[:, 1], keys[:, 2]))
+    ks = keys[order]
+    new = np.ones(len(ks), bool)
+    new[1:] = np.any(ks[1:] != ks[:-1], axis=1)
+    group = np.cumsum(new) - 1
+    m = int(group[-1]) + 1 if len(group) else 0
+    sums = np.zeros((m, 3))
+    np.add.at(sums, group, P[order])
+    counts = np.bincount(group, minlength=m)
+    return sums / counts[:, None], counts
+
+
 def surfel_correct(pos, nrm, t0, tu, T_old, T_new, t_kf, cam):
     """Dense model correction of eq. (7), in FP64 with numpy.
 
