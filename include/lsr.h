@@ -299,6 +299,20 @@ LSR_API int lsr_objective_bwd(lsr_ctx *ctx, int32_t n, const float *const *P, co
 LSR_API int lsr_information_matrix(lsr_ctx *ctx, const float *P, int64_t nP, const float *Q, int64_t nQ,
                                    const double *T, float eps, double *info, int64_t *n_corr);
 
+/* Voxel downsampling (Algorithm 1, first line): one point per occupied voxel
+ * of edge leaf, the mean of the points in it. Voxels are aligned to the
+ * coordinate origin (key = floor(x / leaf) per axis, evaluated in FP64) and
+ * the output is ordered by voxel, z slowest, then y, then x. The means come
+ * from 64-bit integer sums of the offsets from the voxel corner (units of
+ * leaf / 2^36), so they do not depend on the order of the points.
+ * P: n x 3 float32 (device or host). out: cap x 3 float32 (device or host);
+ * at most cap points are written and *n_out (host) receives the number of
+ * occupied voxels (cap = n always suffices). Errors: LSR_E_ARG for null
+ * pointers, n outside [1, 2^26], leaf outside (0, 100]; LSR_E_TOO_LARGE when
+ * the keys' bounding box holds more than 2^26 voxels. */
+LSR_API int lsr_voxel_downsample(lsr_ctx *ctx, const float *P, int64_t n, float leaf, float *out, int64_t cap,
+                                 int64_t *n_out);
+
 /* Dense model correction after a loop closure (eq. (7)): every surfel moves
  * with the keyframes that observe it,
  *   p' = (1/k) sum_{f in F} T_f_new T_f_old^-1 p,

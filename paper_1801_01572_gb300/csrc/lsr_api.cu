@@ -1604,6 +1604,71 @@ int lsr_information_matrix(lsr_ctx *c, const float *P, int64_t nP, const float *
   return LSR_OK;
 }
 
+int lsr_voxel_downsample(lsr_ctx *c, const float *P, int64_t n, float leaf, float *out, int64_t cap,
+                         int64_t *n_out) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!P || !out || !n_out || n < 1 || n > kMaxPoints || cap < 0 || !(leaf > 0.f && leaf <= 100.f))
+    return set_err(c, LSR_E_ARG, "bad argument");
+  constexpr int64_t kMaxCells = (int64_t)1 << 26;
+  int64_t ncells = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    struct Bufs {
+      float *p, *o;
+      int *kb, *ncd, *cnt, *flag, *pos, *scan;
+      unsigned long long *sums;
+      int64_t *nout;
+    };
+    auto plan = [&](Arena &a, Bufs &b) {
+      b.p = a.take<float>(3 * (size_t)n);
+      b.o = a.take<float>(3 * (size_t)(cap > 0 ? cap : 1));
+      b.kb = a.take<int>(6);
+      b.ncd = a.take<int>(1);
+      b.nout = a.take<int64_t>(1);
+      b.cnt = a.take<int>((size_t)ncells);
+      b.flag = a.take<int>((size_t)ncells);
+      b.pos = a.take<int>((size_t)ncells + 1);
+      b.scan = a.take<int>((size_t)scan_scratch_ints(ncells));
+      b.sums = a.take<unsigned long long>(3 * (size_t)ncells);
+    };
+    Arena m(nullptr);
+    Bufs bm;
+    plan(m, bm);
+    if ((rc = ensure_ws(c, m.off))) return rc;
+    Arena a(c->ws);
+    Bufs b;
+    plan(a, b);
+    cudaStream_t s = c->stream;
+    const float *src;
+    if ((rc = stage_input(c, P, n, b.p, &src))) return rc;
+    TRY_CUDA(c, launch_vox_bounds(src, n, leaf, b.kb, s), "voxel bounds");
+    int kb[6];
+    TRY_CUDA(c, cudaMemcpyAsync(kb, b.kb, sizeof(kb), cudaMemcpyDeviceToHost, s), "D2H");
+    TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+    const int64_t need = ((int64_t)kb[3] - kb[0] + 1) * ((int64_t)kb[4] - kb[1] + 1) * ((int64_t)kb[5] - kb[2] + 1);
+    if (kb[0] > kb[3] || need > kMaxCells) return set_err(c, LSR_E_TOO_LARGE, "voxel grid of the cloud too large");
+    if (pass == 0) {
+      ncells = need;  // plan again with the cells (the workspace may move)
+      continue;
+    }
+    const int ncells_i = (int)ncells;
+    TRY_CUDA(c, cudaMemcpyAsync(b.ncd, &ncells_i, sizeof(int), cudaMemcpyHostToDevice, s), "H2D");
+    const bool dev_out = is_device_ptr(out);
+    TRY_CUDA(c,
+             launch_vox_cells(src, n, leaf, b.kb, ncells, b.ncd, b.cnt, b.sums, b.flag, b.pos, b.scan,
+                              dev_out ? out : b.o, cap, b.nout, s),
+             "voxel cells");
+    int64_t m_out = 0;
+    TRY_CUDA(c, cudaMemcpyAsync(&m_out, b.nout, sizeof(m_out), cudaMemcpyDeviceToHost, s), "D2H");
+    TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+    if (!dev_out && cap > 0 && (rc = copy_out(c, out, b.o, sizeof(float) * 3 * (size_t)std::min(m_out, cap))))
+      return rc;
+    TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+    *n_out = m_out;
+  }
+  return LSR_OK;
+}
+
 int lsr_surfel_correct(lsr_ctx *c, int64_t n, const float *pos, const float *nrm, const float *t0, const float *tu,
                        int32_t m, const double *T_old, const double *T_new, const float *t_kf, const float *cam,
                        float *pos_out, float *nrm_out, uint8_t *keep, int64_t *n_keep) {

@@ -448,6 +448,16 @@ cudaError_t launch_final_count(const int *count, const unsigned long long *sum, 
 // E, g_v[3], g_w[3]. dP / dQ (device, caller order) are written when want_grad
 // (dQ must be zeroed by the caller), scaled by `scale`.
 int objective_blocks(int nP);
+// Voxel downsampling (Algorithm 1, first line; lsr_voxel.cu). kb: 6 ints (key
+// minima, maxima). launch_vox_cells needs kb's box on the host (ncells) and on
+// the device (ncells_dev); cnt, flag: ncells ints, pos: ncells + 1 ints, sums:
+// 3 ncells 64-bit words, scan: scan_scratch_ints(ncells) ints; writes at most
+// cap points to out and the number of voxels to *n_out.
+cudaError_t launch_vox_bounds(const float *P, int64_t n, float leaf, int *kb, cudaStream_t s);
+cudaError_t launch_vox_cells(const float *P, int64_t n, float leaf, const int *kb, int64_t ncells,
+                             const int *ncells_dev, int *cnt, unsigned long long *sums, int *flag, int *pos,
+                             int *scan, float *out, int64_t cap, int64_t *n_out, cudaStream_t s);
+
 // Dense model correction (eq. (7), lsr_surfel.cu). Per keyframe: A = T_old^-1
 // and M = T_new T_old^-1 as row-major 3 x 4 (camera-to-world poses).
 struct KfPose {

@@ -31,6 +31,7 @@ ABI_FUNCTIONS = (
     "lsr_stage_normals", "lsr_stage_spfh", "lsr_stage_fpfh", "lsr_stage_match", "lsr_stage_hypotheses",
     "lsr_stage_rigid4", "lsr_stage_consensus", "lsr_stage_refine", "lsr_objective_fwd", "lsr_objective_bwd",
     "lsr_consensus_static", "lsr_match_scores_bf16", "lsr_information_matrix", "lsr_surfel_correct",
+    "lsr_voxel_downsample",
 )
 
 
@@ -102,6 +103,7 @@ def lib():
             "lsr_consensus_static": (C.c_int, [vp, i64, vp, i64, vp, i64, f32, vp, vp, vp]),
             "lsr_information_matrix": (C.c_int, [vp, vp, i64, vp, i64, vp, f32, vp, vp]),
             "lsr_surfel_correct": (C.c_int, [vp, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "lsr_voxel_downsample": (C.c_int, [vp, vp, i64, f32, vp, i64, vp]),
         }
         for name in ABI_FUNCTIONS:
             res, args = sig[name]
@@ -383,6 +385,16 @@ class Context:
         self._check(self._L.lsr_information_matrix(self._h, pP, nP, pQ, nQ, C.c_void_p(Tin.ctypes.data),
                                                    C.c_float(eps), C.c_void_p(info.ctypes.data), C.byref(n)))
         return info.reshape(6, 6), int(n.value)
+
+    def voxel_downsample(self, P, leaf=0.05):
+        """Voxel downsampling of Algorithm 1: (m x 3 float32 numpy array of
+        voxel means in voxel order)."""
+        pP, kP, n = _prep(P, np.float32, 3)
+        out = np.zeros((n, 3), np.float32)
+        m = C.c_int64(0)
+        self._check(self._L.lsr_voxel_downsample(self._h, pP, n, C.c_float(leaf), C.c_void_p(out.ctypes.data), n,
+                                                 C.byref(m)))
+        return out[:m.value].copy()
 
     def surfel_correct(self, pos, nrm, t0, tu, T_old, T_new, t_kf, cam):
         """Dense model correction of eq. (7). pos, nrm: n x 3, t0, tu: n (numpy
