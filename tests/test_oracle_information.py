@@ -65,6 +65,9 @@ def test_information_invariants(pair0):
     # the consensus routine counts the same correspondences
     cnt, _, _ = oracle.consensus(pair0.P, pair0.Q, pair0.T[None, :3, :3], pair0.T[None, :3, 3], EPS)
     assert cnt[0] == n
+    # a search band past eps changes what is reported as ambiguous, not K
+    info_b, n_b, namb, _ = oracle.information(pair0.P, pair0.Q, pair0.T, EPS, band=2e-3)
+    assert n_b == n and namb > 0 and np.array_equal(info_b, info)
 
 
 def test_information_symmetric_set_has_no_coupling():
