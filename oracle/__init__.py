@@ -339,6 +339,31 @@ def voxel_downsample(P, leaf):
     return sums / counts[:, None], counts
 
 
+def nn_single_cell(Q, X, cell):
+    """The O(1) grid lookup of eq. (1) (a speed mode, not exact): each query
+    looks only in its own cell, index = floor((x - c) / cell) per axis with c
+    the centroid of Q (reading: floor, and "centre" as the centroid), and takes
+    the nearest Q point there. Returns (nn index or -1, squared distance or
+    inf), ties to the smaller index."""
+    Q, X = np.asarray(Q, np.float64), np.asarray(X, np.float64)
+    c = Q.mean(axis=0)
+    kq = np.floor((Q - c) / cell).astype(np.int64)
+    kx = np.floor((X - c) / cell).astype(np.int64)
+    table = {}
+    for j, k in enumerate(map(tuple, kq)):
+        table.setdefault(k, []).append(j)
+    nn = np.full(len(X), -1, np.int64)
+    d2 = np.full(len(X), np.inf)
+    for i, k in enumerate(map(tuple, kx)):
+        js = table.get(k)
+        if not js:
+            continue
+        dd = ((Q[js] - X[i]) ** 2).sum(1)
+        a = int(np.argmin(dd))
+        nn[i], d2[i] = js[a], dd[a]
+    return nn, d2
+
+
 def surfel_correct(pos, nrm, t0, tu, T_old, T_new, t_kf, cam):
     """Dense model correction of eq. (7), in FP64 with numpy.
 
