@@ -387,7 +387,7 @@ __global__ void k_scatter_int(const int *src, const float4 *X, int n, int32_t *d
 __global__ void k_sum_to_double(const unsigned long long *s, int n, double *d) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) d[k] = (double)s[k] / kFixScale;
 }
-int nblk(int64_t n, int t = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 152 * 32)); }
+int nblk(int64_t n, int t = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, kSms * 32)); }
 
 // Build the feature-radius grid (internal order) and, optionally, the
 // normal-radius and eps grids of one cloud.

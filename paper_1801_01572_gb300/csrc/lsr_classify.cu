@@ -316,7 +316,7 @@ cudaError_t launch_cls_build(const float *boxQ, float eps, const float4 *XQ, int
   LSR_CUDA_TRY(cudaMemsetAsync(in_bits, 0, sizeof(unsigned) * (size_t)kClsCapWords, s));
   LSR_CUDA_TRY(cudaMemsetAsync(near_bits, 0, sizeof(unsigned) * (size_t)kClsCapWords, s));
   LSR_LAUNCH(k_cls_params<<<1, 32, 0, s>>>(boxQ, eps, cp));
-  LSR_LAUNCH(k_cls_splat<<<152 * 16, 256, 0, s>>>(XQ, nQ, cp, in_bits, near_bits));
+  LSR_LAUNCH(k_cls_splat<<<kSms * 16, 256, 0, s>>>(XQ, nQ, cp, in_bits, near_bits));
   return cudaGetLastError();
 }
 
@@ -324,7 +324,7 @@ cudaError_t launch_consensus_count(const float4 *XP, int nP, const ClsParams *cp
                                    const unsigned *near_bits, const GridParams *ge, const int *start_e,
                                    const float4 *Xe, const float *pose, const uint8_t *ok, const int *n_dev,
                                    int n_host, float eps, int *count, cudaStream_t s) {
-  LSR_LAUNCH(k_consensus_count<false><<<152 * 8, kClsThreads, 0, s>>>(XP, nP, cp, in_bits, near_bits, ge, start_e, Xe,
+  LSR_LAUNCH(k_consensus_count<false><<<kSms * 8, kClsThreads, 0, s>>>(XP, nP, cp, in_bits, near_bits, ge, start_e, Xe,
                                                                        pose, ok, n_dev, n_host, eps * eps, count,
                                                                        nullptr));
   return cudaGetLastError();
@@ -333,7 +333,7 @@ cudaError_t launch_consensus_count(const float4 *XP, int nP, const ClsParams *cp
 cudaError_t launch_consensus_bounds(const float4 *XP, int nP, const ClsParams *cp, const unsigned *in_bits,
                                     const unsigned *near_bits, const float *pose, const uint8_t *ok, const int *n_dev,
                                     int *in_count, int *amb_count, cudaStream_t s) {
-  LSR_LAUNCH(k_consensus_count<true><<<152 * 8, kClsThreads, 0, s>>>(XP, nP, cp, in_bits, near_bits, nullptr, nullptr,
+  LSR_LAUNCH(k_consensus_count<true><<<kSms * 8, kClsThreads, 0, s>>>(XP, nP, cp, in_bits, near_bits, nullptr, nullptr,
                                                                       nullptr, pose, ok, n_dev, 0, 0.f, in_count,
                                                                       amb_count));
   return cudaGetLastError();

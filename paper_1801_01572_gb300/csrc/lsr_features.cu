@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) k_fpfh(const float4 *__restrict__ X,
 
 inline int blocks_for_warps(int n) {
   int b = (int)lsr_div_up(n, kWarps);
-  return b < 1 ? 1 : (b > 152 * 64 ? 152 * 64 : b);
+  return b < 1 ? 1 : (b > kSms * 64 ? kSms * 64 : b);
 }
 
 }  // namespace

@@ -364,7 +364,7 @@ int64_t nbmask_words(int cap_cells) { return cap_cells / 32 + 2; }
 cudaError_t build_nbmask(GridParams *g, const int *start, int cap_cells, unsigned *mask, cudaStream_t s) {
   LSR_CUDA_TRY(cudaMemsetAsync(mask, 0, sizeof(unsigned) * (size_t)nbmask_words(cap_cells), s));
   int b = (int)lsr_div_up(cap_cells, 256);
-  LSR_LAUNCH(k_nbmask<<<b < 152 * 16 ? b : 152 * 16, 256, 0, s>>>(g, start, mask));
+  LSR_LAUNCH(k_nbmask<<<b < kSms * 16 ? b : kSms * 16, 256, 0, s>>>(g, start, mask));
   LSR_LAUNCH(k_set_mask<<<1, 32, 0, s>>>(g, mask));
   return cudaGetLastError();
 }

@@ -11,6 +11,7 @@ constexpr int kD = 33;       // FPFH length: 3 features x 11 bins
 constexpr int kNB = 11;      // bins per feature
 constexpr int kDS = 36;      // stored row stride of SPFH / FPFH (16-byte aligned rows)
 constexpr int kWarp = 32;
+constexpr int kSms = 152;    // GB300 streaming multiprocessors (2 dies x 76): grid caps are multiples of it
 
 // Order in which the FP32 descriptor distance sum_k (a_k - b_k)^2 is
 // accumulated: the central bin of each of the three 11-bin sub-histograms,

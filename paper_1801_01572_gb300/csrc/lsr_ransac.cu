@@ -459,7 +459,7 @@ cudaError_t launch_rigid_survivors(const float4 *XP, const int *invP, const floa
                                    uint64_t seed, uint64_t pair, float cos_normal, float *pose, uint8_t *ok,
                                    int *n_normal_ok, cudaStream_t s) {
   HypIn in{XP, invP, NP, nP, XQ, NQ, 0x7fffffff, nn, seed, pair, 0.f};
-  LSR_LAUNCH(k_rigid_survivors<<<152 * 4, 256, 0, s>>>(in, surv, st, cos_normal, pose, ok, n_normal_ok));
+  LSR_LAUNCH(k_rigid_survivors<<<kSms * 4, 256, 0, s>>>(in, surv, st, cos_normal, pose, ok, n_normal_ok));
   return cudaGetLastError();
 }
 
@@ -474,7 +474,7 @@ cudaError_t launch_consensus(const float4 *XP, int nP, const GridParams *ge, con
                              unsigned long long *sum, cudaStream_t s, int lanes) {
   float e2 = eps * eps;
 #define LSR_CONS(G)                                                                                            \
-  LSR_LAUNCH(k_consensus<G><<<152 * 8, kConsThreads, 0, s>>>(XP, nP, ge, start_e, Xe, pose, ok, n_dev, n_host, e2, \
+  LSR_LAUNCH(k_consensus<G><<<kSms * 8, kConsThreads, 0, s>>>(XP, nP, ge, start_e, Xe, pose, ok, n_dev, n_host, e2, \
                                                              count, sum))
   switch (lanes) {
     case 2: LSR_CONS(2); break;

@@ -448,7 +448,7 @@ __global__ void k_objective_sum(const double *partials, int nblocks, double *out
 // that the launch-closing block sums few partials.
 int refine_blocks(int nP) {
   int64_t b = lsr_div_up((int64_t)(nP > 0 ? nP : 1) * kRefG, kRefThreads);
-  return (int)(b < 1 ? 1 : (b > 152 * kRefBlocksPerSm ? 152 * kRefBlocksPerSm : b));  // all blocks resident
+  return (int)(b < 1 ? 1 : (b > kSms * kRefBlocksPerSm ? kSms * kRefBlocksPerSm : b));  // all blocks resident
 }
 
 int gnc_stride(int64_t n, int level, int levels) {
@@ -497,7 +497,7 @@ cudaError_t launch_final_count(const int *count, const unsigned long long *sum, 
 
 int information_blocks(int nP) {
   int64_t b = lsr_div_up((int64_t)(nP > 0 ? nP : 1) * kRefG, kRefThreads);
-  return (int)(b < 1 ? 1 : (b > 152 * 4 ? 152 * 4 : b));
+  return (int)(b < 1 ? 1 : (b > kSms * 4 ? kSms * 4 : b));
 }
 
 cudaError_t launch_information(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
@@ -515,7 +515,7 @@ cudaError_t launch_information(const float *P, int nP, const GridParams *ge, con
 
 int objective_blocks(int nP) {
   int64_t b = lsr_div_up((int64_t)(nP > 0 ? nP : 1) * kObjG, kRefThreads);
-  return (int)(b < 1 ? 1 : (b > 152 * 2 ? 152 * 2 : b));
+  return (int)(b < 1 ? 1 : (b > kSms * 2 ? kSms * 2 : b));
 }
 
 cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,

@@ -84,7 +84,7 @@ cudaError_t launch_surfel_correct(int64_t n, const float *pos, const float *nrm,
                                   float *nrm_out, uint8_t *keep, unsigned long long *n_keep, cudaStream_t s) {
   LSR_CUDA_TRY(cudaMemsetAsync(n_keep, 0, sizeof(unsigned long long), s));
   const int64_t nb = lsr_div_up(n, kSurfThreads);
-  const int blocks = (int)(nb < 1 ? 1 : (nb > 152 * 16 ? 152 * 16 : nb));
+  const int blocks = (int)(nb < 1 ? 1 : (nb > kSms * 16 ? kSms * 16 : nb));
   LSR_LAUNCH(k_surfel_correct<<<blocks, kSurfThreads, 0, s>>>(n, pos, nrm, t0, tu, m, kf, t_kf, cam, pos_out, nrm_out,
                                                                keep, n_keep));
   return cudaGetLastError();
