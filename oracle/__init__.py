@@ -364,6 +364,91 @@ def nn_single_cell(Q, X, cell):
     return nn, d2
 
 
+def _gm(s, mu):
+    """Geman-McClure rho(s) = mu s / (mu + s) of eq. (4) and its first two
+    derivatives in s."""
+    d = mu + s
+    return mu * s / d, mu * mu / (d * d), -2.0 * mu * mu / (d * d * d)
+
+
+def _skew(a):
+    return np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+
+
+def pose_grad_hess(X, Y, T, mu):
+    """E(xi) = sum_i rho(|T(xi) x_i - y_i|^2) with the pairs (x_i, y_i) held and
+    T(xi) = [Exp(w) | v] T (the left perturbation of the refinement): E, its
+    gradient g and its exact Hessian H in xi = (w, v) at xi = 0.
+
+    With z = R x + t, r = z - y, s = |r|^2 and J = [-[z]_x | I]:
+      g = sum 2 rho'(s) J^T r,
+      H = sum 4 rho''(s) (J^T r)(J^T r)^T + 2 rho'(s) (J^T J + S),
+    S the second derivative of r . Exp(w) z at w = 0, nonzero in the rotation
+    block only: S_ab = (r_a z_b + r_b z_a) / 2 - (r . z) delta_ab."""
+    X, Y = _f64(X, 3), _f64(Y, 3)
+    T = np.asarray(T, np.float64)
+    Z = X @ T[:3, :3].T + T[:3, 3]
+    Rr = Z - Y
+    s = (Rr * Rr).sum(1)
+    rho, d1, d2 = _gm(s, mu)
+    g, H = np.zeros(6), np.zeros((6, 6))
+    for z, r, a1, a2 in zip(Z, Rr, d1, d2):
+        J = np.hstack([-_skew(z), np.eye(3)])
+        Jr = J.T @ r
+        g += 2.0 * a1 * Jr
+        Sm = np.zeros((6, 6))
+        Sm[:3, :3] = 0.5 * (np.outer(r, z) + np.outer(z, r)) - (r @ z) * np.eye(3)
+        H += 4.0 * a2 * np.outer(Jr, Jr) + 2.0 * a1 * (J.T @ J + Sm)
+    return float(rho.sum()), g, H
+
+
+def pose_optimum(X, Y, T0, mu, iters=60, tol=1e-15):
+    """The pose minimising E over the held pairs, by Newton steps with the exact
+    Hessian of pose_grad_hess (each step solves H d = -g and moves T to
+    [Exp(d_w) | d_v] T), halving a step that does not lower E. Stops when
+    |d| < tol. Returns (T, |g| at the end)."""
+    T = np.asarray(T0, np.float64).copy()
+    E, g, H = pose_grad_hess(X, Y, T, mu)
+    for _ in range(iters):
+        d = np.linalg.solve(H, -g)
+        step = 1.0
+        while True:
+            Tn = apply_xi(step * d, T)
+            En, gn, Hn = pose_grad_hess(X, Y, Tn, mu)
+            if En <= E or step < 1e-6:
+                break
+            step *= 0.5
+        T, E, g, H = Tn, En, gn, Hn
+        if np.linalg.norm(step * d) < tol:
+            break
+    return T, float(np.linalg.norm(g))
+
+
+def pose_implicit_grad(X, Y, T, mu, dL_dxi):
+    """Gradient of a loss L of the optimal pose with respect to the held pairs
+    (implicit function theorem at the optimum T, where g = 0): with dL_dxi the
+    gradient of L in the left perturbation xi of T, lambda = H^-1 dL_dxi and
+    phi_i = lambda . g_i = 2 rho'(s_i) a_i . r_i, a_i = w_l x z_i + v_l,
+      dL/dx_i = -R^T dphi_i/dz_i,  dL/dy_i = -dphi_i/dy_i,
+      dphi/dz = 4 rho''(s) (a . r) r + 2 rho'(s) (a + r x w_l),
+      dphi/dy = -4 rho''(s) (a . r) r - 2 rho'(s) a.
+    Returns (dL/dX, dL/dY)."""
+    X, Y = _f64(X, 3), _f64(Y, 3)
+    T = np.asarray(T, np.float64)
+    _, _, H = pose_grad_hess(X, Y, T, mu)
+    lam = np.linalg.solve(H, np.asarray(dL_dxi, np.float64).reshape(6))
+    wl, vl = lam[:3], lam[3:]
+    Z = X @ T[:3, :3].T + T[:3, 3]
+    Rr = Z - Y
+    s = (Rr * Rr).sum(1)
+    _, d1, d2 = _gm(s, mu)
+    A = np.cross(wl, Z) + vl
+    ar = (A * Rr).sum(1)
+    dz = 4.0 * d2[:, None] * ar[:, None] * Rr + 2.0 * d1[:, None] * (A + np.cross(Rr, wl))
+    dy = -4.0 * d2[:, None] * ar[:, None] * Rr - 2.0 * d1[:, None] * A
+    return -(dz @ T[:3, :3]), -dy
+
+
 def surfel_correct(pos, nrm, t0, tu, T_old, T_new, t_kf, cam):
     """Dense model correction of eq. (7), in FP64 with numpy.
 
