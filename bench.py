@@ -8,13 +8,18 @@ workload is the 150,000-point room pair on a 1 cm grid, FP32 end to end.
 Inputs are resident in HBM when the timed region starts and L2 is flushed
 (a 256 MB write) between steps, outside the timed events. Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 0|1|2] [--match fp32|bf16|bf16_plain]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 0|1|2|3|4] [--match fp32|bf16|bf16_plain]
                   [--impl ours|reference]
 
 --config 2 times the batched workload instead: 256 room pairs of 10k-120k
 points per cloud registered by one lsr_register_batch call per step (BF16
 tensor-core matching, concurrent streams, one CUDA graph), beside the plain
-FP32 single-pair path on the same pairs.
+FP32 single-pair path on the same pairs. --config 3 does the same for 64
+pairs of 200k points; --config 4 times the batched robust objective forward
+and backward of 32 pairs of 50k points.
+
+Under torchrun every rank runs its own pairs; the only collective is the
+max over ranks of the timed region.
 
 --match selects the descriptor matcher (FP32 SIMT, or the tensor-core matcher
 with hi/lo or plain BF16 operands); every choice gives the same correspondences.
@@ -46,7 +51,8 @@ WORKLOADS = {
     2: "256 indoor room pairs on a 1 cm voxel grid, 10k-120k points per cloud, 30-80% overlap, 4M hypotheses "
        "each, one batch per step (BF16 tensor-core matching, concurrent streams, one CUDA graph)",
     3: "64 indoor room pairs on a 1 cm voxel grid, 200,000 points per cloud, 50% overlap, 4M hypotheses each, "
-       "one batch per step (BF16 tensor-core matching, top-8 FP32 re-rank, concurrent streams, one CUDA graph)",
+       "one batch per step (BF16 tensor-core matching, FP32 re-rank of the 8 best 16-row candidate chunks, a superset "
+       "of the top 8; concurrent streams, one CUDA graph)",
     4: "32 indoor room pairs of 50,000 points per cloud: robust alignment objective forward + backward (points and "
        "se(3) pose) for all pairs per step through RobustAlignBatch",
 }
@@ -54,6 +60,30 @@ BATCH_PAIRS = {2: 256, 3: 64, 4: 32}
 MATCH_MODES = {"fp32": 0, "bf16": 1, "bf16_plain": 2}
 FP32_LANES_PER_SM = 128
 N_SM = 152
+
+
+# ---------------------------------------------------------------- ranks
+def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time: the job ends when its last rank does."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, total_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (every rank does the same amount of work: weak scaling)."""
+    return world * units_per_rank / (total_ms * 1e-3)
+
+
+def rank_pair_ids(config: int, rank: int) -> list:
+    """The generator pair ids a rank registers in the batched configurations:
+    disjoint blocks, so N ranks run N different batches."""
+    n = BATCH_PAIRS[config]
+    return list(range(rank * n, (rank + 1) * n))
 
 
 def peaks():
@@ -162,10 +192,7 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     # per-stage device times (and the FP32 matcher's term count) from profiled
     # runs after the timed region: stage events and the counting matcher
     ctx.set_profiling(True)
@@ -194,10 +221,7 @@ def run_ours(args, rank, world):
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
     e2e_ms = float(sum(e2e_times))
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world)
     # the information matrix of eq. (5)-(6) of the registered pair (loop
     # verification; eps = 0.05 m as the paper), clouds resident, Q's grid built per call
     info_ms = []
@@ -281,8 +305,7 @@ def batch_pairs(config, rank):
     """The pairs of this rank, generated in parallel host processes before any
     GPU work."""
     import multiprocessing as mp
-    n = BATCH_PAIRS[config]
-    ids = [(config, i) for i in range(rank * n, (rank + 1) * n)]
+    ids = [(config, i) for i in rank_pair_ids(config, rank)]
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         return pool.map(_gen_pair, ids, chunksize=2)
 
@@ -327,10 +350,7 @@ def run_batch(args, rank, world, pairs):
             times.append(ms)
         launches = lsr.launch_count() - l0
     total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     # end to end from pinned host memory (host-to-device copies inside the call)
     Ph = [torch.from_numpy(p[0]).pin_memory() for p in pairs]
     Qh = [torch.from_numpy(p[1]).pin_memory() for p in pairs]
@@ -415,10 +435,7 @@ def run_objective(args, rank, world, pairs):
             times.append(ms)
         launches = lsr.launch_count() - l0
     total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     # end to end: the clouds copied from pinned host memory and the gradients read back, every step
     hostP = [torch.from_numpy(p[0]).pin_memory() for p in pairs]
     hostQ = [torch.from_numpy(p[1]).pin_memory() for p in pairs]
@@ -626,7 +643,7 @@ def main():
         info = run_objective(args, rank, world, pairs)
         if rank == 0:
             K, n = args.steps, len(pairs)
-            value = world * K * n / (info["total_ms"] * 1e-3)
+            value = job_rate(K * n, world, info["total_ms"])
             line = {
                 "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": info["total_ms"] / K, "higher_is_better": True,
@@ -658,7 +675,7 @@ def main():
         N_BATCH = len(pairs)
         if rank == 0:
             K = args.steps
-            value = world * K * N_BATCH / (info["total_ms"] * 1e-3)
+            value = job_rate(K * N_BATCH, world, info["total_ms"])
             line = {
                 "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": info["total_ms"] / K, "higher_is_better": True,
@@ -701,8 +718,8 @@ def main():
     info = run_ours(args, rank, world)
     if rank == 0:
         K = args.steps
-        value = world * K / (info["total_ms"] * 1e-3)
-        e2e = world * K / (info["e2e_ms"] * 1e-3)
+        value = job_rate(K, world, info["total_ms"])
+        e2e = job_rate(K, world, info["e2e_ms"])
         last = info["last"]
         prm = info["params"]
         line = {
