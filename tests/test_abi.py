@@ -74,3 +74,23 @@ def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(m, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         m.lib()
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/lsr.h compiles as C99 and as C++ on its own: plain pointers and
+    sizes, no C++ or framework types in the boundary."""
+    src = tmp_path / "use.c"
+    src.write_text('#include "lsr.h"\nint main(void) {\n  lsr_params p;\n  lsr_default_params(&p);\n'
+                   '  return p.n_hypotheses > 0 ? 0 : 1;\n}\n')
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)], check=True)
+    subprocess.run(["g++", "-x", "c++", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)], check=True)
+
+
+def test_next_row_entry_points_reject_a_null_context(libpath):
+    import paper_1801_01572_gb300 as pkg
+    L = pkg.lib()
+    assert L.lsr_information_matrix(None, None, 0, None, 0, None, C.c_float(0.05), None, None) == pkg.LSR_E_STATE
+    assert L.lsr_voxel_downsample(None, None, 0, C.c_float(0.05), None, 0, None) == pkg.LSR_E_STATE
+    assert L.lsr_surfel_correct(None, 0, None, None, None, None, 0, None, None, None, None, None, None, None,
+                                None) == pkg.LSR_E_STATE
