@@ -62,3 +62,13 @@ def test_information_matrix_host_and_device_inputs_agree(ctx):
     a, na = ctx.information_matrix(p.P, p.Q, p.T, EPS)
     b, nb = ctx.information_matrix(torch.from_numpy(p.P).cuda(), torch.from_numpy(p.Q).cuda(), p.T, EPS)
     assert na == nb and np.array_equal(a, b)
+
+
+@gpu
+def test_information_matrix_without_correspondences(ctx):
+    """A pose that moves P far from Q: no correspondence, a zero matrix."""
+    p = make_pair(0, 0)
+    T = p.T.copy()
+    T[0, 3] += 100.0
+    info, n = ctx.information_matrix(p.P, p.Q, T, EPS)
+    assert n == 0 and np.array_equal(info, np.zeros((6, 6)))

@@ -60,3 +60,14 @@ def test_surfel_correction_device_inputs_equal_host(ctx, smap):
     assert a[3] == b[3]
     for x, y in zip(a[:3], b[:3]):
         assert np.array_equal(x, y.cpu().numpy())
+
+
+@gpu
+def test_surfels_outside_every_window_are_removed_unchanged(ctx, smap):
+    S = smap
+    n = 1000
+    t0 = np.full(n, -10.0, np.float32)
+    tu = np.full(n, -5.0, np.float32)  # before the first keyframe
+    p, nr, keep, kept = ctx.surfel_correct(S.pos[:n], S.nrm[:n], t0, tu, S.T_old, S.T_new, S.t_kf, S.cam)
+    assert kept == 0 and not keep.any()
+    assert np.array_equal(p, S.pos[:n]) and np.array_equal(nr, S.nrm[:n])

@@ -40,3 +40,17 @@ def test_voxel_downsample_order_independent(ctx):
     a = ctx.voxel_downsample(P, 0.05)
     b = ctx.voxel_downsample(P[perm], 0.05)
     assert np.array_equal(a, b)
+
+
+@gpu
+def test_voxel_downsample_degenerate_inputs(ctx):
+    # one point: itself; all points in one voxel: their mean; a lattice of voxel centres: unchanged, sorted
+    one = np.array([[0.1234, -0.5, 2.0]], np.float32)
+    assert np.allclose(ctx.voxel_downsample(one, 0.05), one, rtol=0, atol=1e-7)
+    same = np.random.default_rng(3).uniform(0.0, 0.049, (1000, 3)).astype(np.float32)
+    out = ctx.voxel_downsample(same, 0.05)
+    assert out.shape == (1, 3) and np.allclose(out[0], same.astype(np.float64).mean(0), rtol=0, atol=1e-7)
+    g = np.stack(np.meshgrid(np.arange(3), np.arange(2), np.arange(2), indexing="ij"), -1).reshape(-1, 3)
+    P = ((g + 0.5) * 0.25).astype(np.float32)
+    ref, _ = oracle.voxel_downsample(P[::-1], 0.25)
+    assert np.allclose(ctx.voxel_downsample(P[::-1], 0.25), ref, rtol=0, atol=1e-7)
