@@ -55,6 +55,12 @@ class Result(C.Structure):
                 ("status", C.c_int32), ("refine_iters_done", C.c_int32)]
 
 
+class Diag(C.Structure):
+    _fields_ = [("nn_amb", C.c_int64), ("hyp_amb", C.c_int64), ("surv_touch", C.c_int64), ("n_top", C.c_int64),
+                ("top_h", C.c_int64 * 16), ("top_count", C.c_int64 * 16), ("top_amb", C.c_int64 * 16), ("top_touch", C.c_int64 * 16),
+                ("top_fitness", C.c_double * 16), ("final_amb", C.c_int64)]
+
+
 DEFAULTS = dict(r_normal=0.05, r_feature=0.125, eps_inlier=0.0375, tau=0.9,
                 cos_normal=float(np.cos(np.deg2rad(30.0))), min_inlier_ratio=0.05, mu_scale=1.0,
                 n_hypotheses=4_000_000, refine_iters=50, refine_levels=3, seed=0, pair_id=0)
@@ -96,7 +102,8 @@ def lib():
                 "orc_gnc_stride": (i64, [i64, C.c_int, C.c_int]),
                 "orc_objective": (C.c_double, [dp, i64, dp, i64, dp, dp, dbl, dbl, dp, dp, dp, ip]),
                 "orc_information": (None, [dp, i64, dp, i64, dp, dbl, dbl, dp, ip, ip, dp]),
-                "orc_register": (C.c_int, [dp, i64, dp, i64, dp, dp, C.POINTER(Params), C.POINTER(Result), dp, dp, ip]),
+                "orc_register": (C.c_int, [dp, i64, dp, i64, dp, dp, C.POINTER(Params), C.POINTER(Result), dp, dp, ip,
+                                          C.POINTER(Diag)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -515,23 +522,39 @@ def make_params(**kw) -> Params:
     return p
 
 
-def register(P, Q, vpP=(0, 0, 0), vpQ=(0, 0, 0), debug=False, **kw):
-    """Algorithm 1 end to end, then the robust refinement. Returns a dict."""
+def register(P, Q, vpP=(0, 0, 0), vpQ=(0, 0, 0), debug=False, diag=False, **kw):
+    """Algorithm 1 end to end, then the robust refinement. Returns a dict.
+
+    diag=True adds what an FP32 implementation may decide the other way
+    (reporting only, the result is unchanged): ``nn_amb`` points of P whose
+    descriptor NN gap is at most 1e-5, ``hyp_amb`` hypotheses whose
+    pre-rejection lies in its band, ``surv_touch`` survivors with a sampled
+    point in ``nn_amb``, the 16 best normal-checked hypotheses in selection
+    order (``top``: id, count, points within 1e-5 m of eps, whether a sampled
+    point is in ``nn_amb``, fitness) and
+    ``final_amb`` at the refined pose."""
     P, Q = _f64(P, 3), _f64(Q, 3)
     vpP = _f64(vpP).reshape(3)
     vpQ = _f64(vpQ).reshape(3)
     prm = make_params(**kw)
     res = Result()
+    dg = Diag() if diag else None
     fP = np.zeros((len(P), D)) if debug else None
     fQ = np.zeros((len(Q), D)) if debug else None
     nn = np.zeros(len(P), np.int64) if debug else None
     rc = lib().orc_register(_P(P, C.c_double), len(P), _P(Q, C.c_double), len(Q), _P(vpP, C.c_double),
                             _P(vpQ, C.c_double), C.byref(prm), C.byref(res), _P(fP, C.c_double),
-                            _P(fQ, C.c_double), _P(nn, C.c_int64))
+                            _P(fQ, C.c_double), _P(nn, C.c_int64), C.byref(dg) if dg is not None else None)
     out = dict(rc=rc, T=np.array(res.T).reshape(4, 4), T_hyp=np.array(res.T_hyp).reshape(4, 4),
                inliers=res.inliers, fitness=res.fitness, status=res.status, survivors=res.survivors,
                best_h=res.best_h, hyp_inliers=res.hyp_inliers, hyp_fitness=res.hyp_fitness,
                n_normal_ok=res.n_normal_ok, refine_iters=res.refine_iters_done)
     if debug:
         out.update(FP=fP, FQ=fQ, nn=nn)
+    if diag:
+        k = int(dg.n_top)
+        out.update(nn_amb=int(dg.nn_amb), hyp_amb=int(dg.hyp_amb), surv_touch=int(dg.surv_touch),
+                   final_amb=int(dg.final_amb),
+                   top=[dict(h=int(dg.top_h[i]), count=int(dg.top_count[i]), amb=int(dg.top_amb[i]),
+                             touch=int(dg.top_touch[i]), fitness=float(dg.top_fitness[i])) for i in range(k)])
     return out

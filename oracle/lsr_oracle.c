@@ -1374,6 +1374,25 @@ typedef struct {
   int32_t refine_iters_done;
 } orc_result;
 
+/* What an FP32 implementation of the same steps may legitimately decide the */
+/* other way, reported beside a registration (reporting only: nothing here  */
+/* changes the result). Bands: 1e-5 on the descriptor NN gap (d2 - d1),    */
+/* the relative band of the pre-rejection comparisons, and 1e-5 m about eps */
+/* for the inlier test.                                                    */
+#define ORC_DIAG_TOP 16
+typedef struct {
+  int64_t nn_amb;     /* points of P whose second-nearest descriptor is within 1e-5 of the nearest */
+  int64_t hyp_amb;    /* hypotheses whose pre-rejection is decided within its band */
+  int64_t surv_touch; /* survivors with at least one sampled point counted in nn_amb */
+  int64_t n_top;      /* entries of top[] filled */
+  int64_t top_h[ORC_DIAG_TOP];     /* the best normal-checked hypotheses, in selection order */
+  int64_t top_count[ORC_DIAG_TOP]; /* their inlier counts */
+  int64_t top_amb[ORC_DIAG_TOP];   /* their points whose NN distance lies within 1e-5 of eps */
+  int64_t top_touch[ORC_DIAG_TOP]; /* 1 if one of their sampled points is counted in nn_amb */
+  double top_fitness[ORC_DIAG_TOP];
+  int64_t final_amb;  /* the same band count at the refined pose */
+} orc_diag;
+
 /* Selection (Alg. 1, "Find the hypothesis that has max inlier ratio and     */
 /* fitness score passing minimum threshold"): reading: the largest inlier   */
 /* count wins, then the smaller fitness, then the smaller hypothesis id; it */
@@ -1385,8 +1404,10 @@ static int better(int64_t c, double f, int64_t h, int64_t bc, double bf, int64_t
 }
 
 int orc_register(const double *P, int64_t nP, const double *Q, int64_t nQ, const double vpP[3], const double vpQ[3],
-                 const orc_params *prm, orc_result *res, double *dbg_fP, double *dbg_fQ, int64_t *dbg_nn) {
+                 const orc_params *prm, orc_result *res, double *dbg_fP, double *dbg_fQ, int64_t *dbg_nn,
+                 orc_diag *diag) {
   memset(res, 0, sizeof(*res));
+  if (diag) memset(diag, 0, sizeof(*diag));
   for (int i = 0; i < 16; ++i) res->T[i] = res->T_hyp[i] = (i % 5 == 0) ? 1.0 : 0.0;
   res->status = 1;
   res->best_h = -1;
@@ -1419,6 +1440,10 @@ int orc_register(const double *P, int64_t nP, const double *Q, int64_t nQ, const
   orc_hypotheses(P, nP, Q, nQ, nn, vP, vQ, H, prm->seed, prm->pair_id, prm->tau, flag);
   int64_t S = 0;
   for (int64_t h = 0; h < H; ++h) S += flag[h] != 0;
+  if (diag) {
+    for (int64_t i = 0; i < nP; ++i) diag->nn_amb += (d2[i] - d1[i]) <= 1e-5;
+    for (int64_t h = 0; h < H; ++h) diag->hyp_amb += flag[h] == 2;
+  }
   int64_t *surv = malloc(sizeof(int64_t) * (S > 0 ? S : 1));
   S = 0;
   for (int64_t h = 0; h < H; ++h)
@@ -1438,6 +1463,11 @@ int orc_register(const double *P, int64_t nP, const double *Q, int64_t nQ, const
         qs[3 * a + d] = Q[3 * nn[idx[a]] + d];
       }
     orc_kabsch(ps, qs, 4, Rs + 9 * s, ts + 3 * s);
+    if (diag) {
+      int touch = 0;
+      for (int a = 0; a < 4; ++a) touch |= (d2[idx[a]] - d1[idx[a]]) <= 1e-5;
+      diag->surv_touch += touch;
+    }
     /* Reading: the normal check compares R n_p with n_q for the 4 samples */
     uint8_t ok = 1;
     for (int a = 0; a < 4; ++a) {
@@ -1464,7 +1494,33 @@ int orc_register(const double *P, int64_t nP, const double *Q, int64_t nQ, const
   int64_t *cnt = malloc(sizeof(int64_t) * (m > 0 ? m : 1)), *amb = malloc(sizeof(int64_t) * (m > 0 ? m : 1));
   double *sd = malloc(sizeof(double) * (m > 0 ? m : 1));
   double eps = prm->eps_inlier;
-  orc_consensus(P, nP, Q, nQ, Rv, tv, m, eps, 0.0, cnt, sd, amb);
+  /* the band only widens the search to see points just past eps: the counts are exact either way */
+  const double band = diag ? 1e-5 : 0.0;
+  orc_consensus(P, nP, Q, nQ, Rv, tv, m, eps, band, cnt, sd, amb);
+  if (diag) {
+    /* the ORC_DIAG_TOP best hypotheses in selection order (repeated selection of the best not yet taken) */
+    uint8_t *taken = calloc((size_t)(m > 0 ? m : 1), 1);
+    for (int k = 0; k < ORC_DIAG_TOP; ++k) {
+      int64_t b = -1;
+      for (int64_t s = 0; s < m; ++s) {
+        if (taken[s]) continue;
+        double f = cnt[s] > 0 ? sd[s] / (double)cnt[s] : INFINITY;
+        double fb = b >= 0 && cnt[b] > 0 ? sd[b] / (double)cnt[b] : INFINITY;
+        if (b < 0 || better(cnt[s], f, hv[s], cnt[b], fb, hv[b])) b = s;
+      }
+      if (b < 0) break;
+      taken[b] = 1;
+      diag->top_h[k] = hv[b];
+      diag->top_count[k] = cnt[b];
+      diag->top_amb[k] = amb[b];
+      diag->top_fitness[k] = cnt[b] > 0 ? sd[b] / (double)cnt[b] : 0.0;
+      int64_t idx[4];
+      sample4(prm->seed, prm->pair_id, hv[b], nP, idx);
+      for (int a = 0; a < 4; ++a) diag->top_touch[k] |= (d2[idx[a]] - d1[idx[a]]) <= 1e-5;
+      diag->n_top = k + 1;
+    }
+    free(taken);
+  }
   int64_t best = -1, bc = -1;
   double bf = INFINITY;
   int64_t bh = INT64_MAX;
@@ -1494,7 +1550,8 @@ int orc_register(const double *P, int64_t nP, const double *Q, int64_t nQ, const
     }
     int64_t c1, a1;
     double s1;
-    orc_consensus(P, nP, Q, nQ, R, t, 1, eps, 0.0, &c1, &s1, &a1);
+    orc_consensus(P, nP, Q, nQ, R, t, 1, eps, band, &c1, &s1, &a1);
+    if (diag) diag->final_amb = a1;
     res->inliers = c1;
     res->fitness = c1 > 0 ? s1 / (double)c1 : 0.0;
     res->status = 0;
