@@ -52,6 +52,7 @@ extern "C" {
 #define LSR_E_TIMEOUT (-4) /* a bounded device-side wait ran out */
 #define LSR_E_STATE (-5)   /* context not usable (NULL, destroyed, or a previous sticky CUDA error) */
 #define LSR_E_TOO_LARGE (-6) /* input larger than the fixed scratch of lsr_consensus_static allows */
+#define LSR_E_CHECK (-7)   /* checked build only: a device bounds check failed (the access was skipped) */
 
 #define LSR_STATUS_ALIGNED 0
 #define LSR_STATUS_NO_ALIGNMENT 1
@@ -130,6 +131,52 @@ LSR_API int lsr_destroy(lsr_ctx *ctx);
 /* Replace the context's parameters (validated; LSR_E_ARG if out of range). */
 LSR_API int lsr_set_params(lsr_ctx *ctx, const lsr_params *params);
 LSR_API int lsr_get_params(const lsr_ctx *ctx, lsr_params *params);
+
+/* Test hooks: make failures happen without faulting or hanging a GPU, so
+ * that the error paths can be exercised. (The paper has no counterpart.)
+ *  LSR_INJECT_ALLOC: the next `count` device workspace allocations of this
+ *    context fail as if the device were out of memory (no cudaMalloc is made);
+ *    the call returns LSR_E_OOM and the context stays usable.
+ *  LSR_INJECT_MATCH_STALL: the next `count` tensor-core matcher launches of
+ *    this context issue no copy and no MMA, so the first bounded wait of their
+ *    epilogue runs out (after 20 ms instead of the normal 2 s); the kernel
+ *    releases its tensor memory and returns, and the call returns
+ *    LSR_E_TIMEOUT. A batch graph captured while a stall is pending keeps it.
+ *  LSR_INJECT_CHECK (checked build only, else LSR_E_ARG): with count > 0, the
+ *    next hypothesis-count kernel on the context's stream asks the bounds
+ *    checks about one out-of-range index (no memory access follows), so that
+ *    call returns LSR_E_CHECK through the same path a real violation takes.
+ *  LSR_INJECT_NONE: clear the first two.
+ * Returns LSR_OK, LSR_E_ARG (unknown kind, count outside [0, 10^6]) or
+ * LSR_E_STATE (NULL context). */
+#define LSR_INJECT_NONE 0
+#define LSR_INJECT_ALLOC 1
+#define LSR_INJECT_MATCH_STALL 2
+#define LSR_INJECT_CHECK 3
+LSR_API int lsr_debug_inject(lsr_ctx *ctx, int32_t kind, int32_t count);
+
+/* 1 if this library is the checked build (compiled with LSR_CHECKED: device
+ * bounds checks on the grid walks, the hypothesis samples and the matchers'
+ * rows record the first violation and skip the access; every synchronising
+ * call then returns LSR_E_CHECK with the site, index and bound in
+ * lsr_last_error), else 0. Results of the two builds are identical. */
+LSR_API int lsr_checked_build(void);
+
+/* Per-kernel timing (a profiling aid; the paper has no counterpart). With a
+ * non-NULL filter, every kernel launch of a later lsr_register_pair (and of a
+ * lsr_register_batch that runs on one stream without a graph) whose kernel
+ * name starts with `filter` ("" = every kernel) is bracketed by two CUDA
+ * events on the context's stream; after the call has synchronised, the
+ * elapsed times are added to a per-kernel table. NULL turns timing off. Each
+ * call clears the table. The events add a few microseconds per timed launch.
+ * lsr_kernel_timing_count returns the table's entries; lsr_kernel_timing_entry
+ * gives entry i: the kernel name (valid until the table is cleared), its timed
+ * launches and their total milliseconds. Returns LSR_OK, LSR_E_ARG (filter
+ * over 200 characters, i out of range, timing off) or LSR_E_STATE. */
+LSR_API int lsr_set_kernel_timing(lsr_ctx *ctx, const char *filter);
+LSR_API int32_t lsr_kernel_timing_count(const lsr_ctx *ctx);
+LSR_API int lsr_kernel_timing_entry(const lsr_ctx *ctx, int32_t i, const char **name, int64_t *launches,
+                                    double *total_ms);
 
 /* Enable (1) or disable (0) per-stage CUDA-event timing in lsr_result.stage_ms. */
 LSR_API int lsr_set_profiling(lsr_ctx *ctx, int enable);
@@ -247,7 +294,8 @@ LSR_API int lsr_stage_consensus(lsr_ctx *ctx, const float *P, int64_t nP, const 
  *    synchronises that stream before returning;
  *  - the first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) and caches it: make that first call before any
- *    stream capture;
+ *    stream capture; the cached address does not survive a reset of the
+ *    device (cudaDeviceReset), after which the call must not be used;
  *  - every call on a device shares the array, which keeps the previous call's
  *    contents (the call clears what must start at zero): calls that overlap
  *    on the GPU (other streams, other host threads) race and must not be

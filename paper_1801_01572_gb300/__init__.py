@@ -11,7 +11,7 @@ from .lsr import (DESC_DIM, LSR_E_ARG, LSR_E_CUDA, LSR_E_OOM, LSR_E_STATE, LSR_E
                   LSR_OK,
                   MATCH_BF16, MATCH_BF16_PLAIN, MATCH_FP32, STATUS_ALIGNED, STATUS_NO_ALIGNMENT, ABI_FUNCTIONS, Context, LsrError,
                   Params, Registration, context, default_params, launch_count, lib, library_path, register_pair,
-                  transfer_bytes)
+                  transfer_bytes, INJECT_ALLOC, INJECT_CHECK, INJECT_MATCH_STALL, INJECT_NONE, LSR_E_CHECK)
 
 
 def _torch():

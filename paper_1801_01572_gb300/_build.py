@@ -18,6 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "liblsr.so")
+CHECKED_LIB = os.path.join(OUT, "liblsr_checked.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 FLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-extended-lambda", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden", f"-I{os.path.join(ROOT, 'include')}"]
@@ -39,19 +40,24 @@ def _digest(paths, extra) -> str:
     return h.hexdigest()[:16]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile csrc/*.cu for sm_103a and link _lib/liblsr.so; returns its path."""
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile csrc/*.cu for sm_103a and link _lib/liblsr.so; returns its path.
+    checked=True builds _lib/liblsr_checked.so instead: the same sources with
+    LSR_CHECKED defined (device bounds checks that report instead of trapping)."""
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
+    flags = FLAGS + (["-DLSR_CHECKED"] if checked else [])
+    lib = CHECKED_LIB if checked else LIB
+    suffix = ".chk" if checked else ""
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     objs, jobs = [], []
     for src in sources:
-        tag = _digest([src] + headers, FLAGS)
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + f".{tag}.o")
+        tag = _digest([src] + headers, flags)
+        obj = os.path.join(OUT, os.path.basename(src)[:-3] + f"{suffix}.{tag}.o")
         objs.append(obj)
         if force or not os.path.exists(obj):
-            jobs.append([nvcc, *FLAGS, "-c", src, "-o", obj])
+            jobs.append([nvcc, *flags, "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -63,20 +69,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    link_tag = _digest(objs, FLAGS)
-    stamp = LIB + ".stamp"
-    if force or not os.path.exists(LIB) or not os.path.exists(stamp) or open(stamp).read() != link_tag:
-        tmp = LIB + f".tmp{os.getpid()}"
+    link_tag = _digest(objs, flags)
+    stamp = lib + ".stamp"
+    if force or not os.path.exists(lib) or not os.path.exists(stamp) or open(stamp).read() != link_tag:
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc, ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
         with open(stamp, "w") as f:
             f.write(link_tag)
-    # drop objects of older source versions
+    # drop objects of older source versions of this build
     keep = set(objs)
     for o in glob.glob(os.path.join(OUT, "*.o")):
-        if o not in keep:
+        if o not in keep and (o.split(".")[-3] == "chk") == checked:
             os.remove(o)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -24,7 +24,109 @@ using namespace lsr;
 
 namespace lsr {
 unsigned long long g_launches = 0;
+
+// Per-kernel timing: events from a reusable pool bracket the matching
+// launches; after the call has synchronised, their elapsed times are added to
+// a table keyed by kernel name (the launch expression up to its <<<).
+struct KernelTimer {
+  cudaStream_t stream = nullptr;
+  std::string filter;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Open {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Open> open;
+  cudaEvent_t pending_start = nullptr;
+  bool failed = false;
+  struct Entry {
+    std::string name;
+    int64_t launches = 0;
+    double ms = 0.0;
+  };
+  std::vector<Entry> table;
+
+  cudaEvent_t take() {
+    if (used == pool.size()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        failed = true;
+        return nullptr;
+      }
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  // After the stream has synchronised: fold the bracketed launches into the table.
+  void collect() {
+    for (const Open &o : open) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, o.a, o.b) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      Entry *e = nullptr;
+      for (Entry &x : table)
+        if (x.name == o.name) e = &x;
+      if (!e) {
+        table.push_back(Entry{o.name});
+        e = &table.back();
+      }
+      e->launches += 1;
+      e->ms += ms;
+    }
+    open.clear();
+    used = 0;
+  }
+  ~KernelTimer() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+thread_local KernelTimer *g_ktimer = nullptr;
+
+static std::string kernel_name_of(const char *expr) {
+  const char *p = expr;
+  while (*p == ' ' || *p == '(' || *p == '\n') ++p;
+  const char *q = strstr(p, "<<<");
+  std::string n = q ? std::string(p, q) : std::string(p);
+  std::string out;
+  for (char ch : n)
+    if (ch != ' ' && ch != '\n') out.push_back(ch);
+  return out;
 }
+
+void ktimer_mark(const char *launch_expr, bool after) {
+  KernelTimer *t = g_ktimer;
+  if (!t || t->failed) return;
+  if (!after) {
+    t->pending_start = nullptr;
+    std::string name = kernel_name_of(launch_expr);
+    if (name.compare(0, t->filter.size(), t->filter) != 0) return;
+    cudaEvent_t a = t->take();
+    if (!a || cudaEventRecord(a, t->stream) != cudaSuccess) {
+      cudaGetLastError();
+      t->failed = true;
+      return;
+    }
+    t->pending_start = a;
+    t->open.push_back(KernelTimer::Open{name, a, nullptr});
+  } else {
+    if (!t->pending_start) return;
+    cudaEvent_t b = t->take();
+    if (!b || cudaEventRecord(b, t->stream) != cudaSuccess) {
+      cudaGetLastError();
+      t->failed = true;
+      t->open.pop_back();
+      return;
+    }
+    t->open.back().b = b;
+    t->pending_start = nullptr;
+  }
+}
+}  // namespace lsr
 
 struct lsr_ctx {
   int device = 0;
@@ -57,6 +159,12 @@ struct lsr_ctx {
   // query count; 0 = not tuned yet) and the number of batch streams
   int tile_choice[32] = {};
   int streams_choice = 0;
+  // test-only fault injection (lsr_debug_inject): device workspace
+  // allocations to fail, tensor-core matcher launches to stall
+  int inject_alloc = 0;
+  int inject_stall = 0;
+  // per-kernel event timing (lsr_set_kernel_timing); null when off
+  KernelTimer *ktimer = nullptr;
 };
 
 namespace {
@@ -257,6 +365,37 @@ int cuda_err(lsr_ctx *c, cudaError_t e, const char *where) {
     if (e__ != cudaSuccess) return cuda_err(ctx, e__, where); \
   } while (0)
 
+// Checked build: the first bounds-check violation recorded by any unit since
+// the last report becomes LSR_E_CHECK; the normal build's readers report none.
+int check_report(lsr_ctx *c) {
+  static cudaError_t (*const readers[])(CheckReport *) = {check_read_features, check_read_match,
+                                                          check_read_match_tc, check_read_ransac,
+                                                          check_read_classify, check_read_refine};
+  static const char *const units[] = {"features", "match", "match_tc", "ransac", "classify", "refine"};
+  static const char *const sites[] = {"?", "grid row", "grid cell", "grid point", "hypothesis sample",
+                                      "hypothesis match", "matcher row", "matcher query", "probe"};
+  int rc = LSR_OK;
+  for (int u = 0; u < 6; ++u) {
+    CheckReport r{0, 0, 0};
+    cudaError_t e = readers[u](&r);
+    if (e != cudaSuccess) return cuda_err(c, e, "check words");
+    if (r.site && rc == LSR_OK) {
+      char buf[200];
+      snprintf(buf, sizeof(buf), "bounds check failed in %s at the %s index: %lld outside [0, %lld)", units[u],
+               r.site < 9 ? sites[r.site] : "?", r.index, r.bound);
+      rc = set_err(c, LSR_E_CHECK, buf);
+    }
+  }
+  return rc;
+}
+
+#define SYNC_CHECKED(ctx, stream)                                     \
+  do {                                                                \
+    TRY_CUDA(ctx, cudaStreamSynchronize(stream), "sync");             \
+    int rc_chk__ = check_report(ctx);                                 \
+    if (rc_chk__) return rc_chk__;                                    \
+  } while (0)
+
 bool is_device_ptr(const void *p) {
   if (!p) return false;
   cudaPointerAttributes attr;
@@ -280,8 +419,28 @@ bool is_pinned_host_ptr(const void *p) {
   return attr.type == cudaMemoryTypeHost;
 }
 
+// Injected allocation failure (test hook): consumes one pending failure.
+bool injected_alloc_failure(lsr_ctx *c) {
+  if (c->inject_alloc <= 0) return false;
+  --c->inject_alloc;
+  return true;
+}
+
+// The matcher's fault settings: a pending injected stall (20 ms wait limit,
+// the producer issues nothing), else the defaults.
+TcFault take_tc_fault(lsr_ctx *c) {
+  TcFault f;
+  if (c->inject_stall > 0) {
+    --c->inject_stall;
+    f.wait_ns = 20000000ull;
+    f.stall = 1;
+  }
+  return f;
+}
+
 int ensure_ws(lsr_ctx *c, size_t bytes) {
   if (bytes <= c->ws_cap) return LSR_OK;
+  if (injected_alloc_failure(c)) return set_err(c, LSR_E_OOM, "device workspace allocation failed (injected)");
   TRY_CUDA(c, cudaStreamSynchronize(c->stream), "workspace sync");
   if (c->ws) cudaFree(c->ws);
   c->ws = nullptr;
@@ -490,7 +649,7 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
     TRY_CUDA(c,
              launch_match_bf16(Pc.F, nP, Qc.F, nQ, p.match_precision == LSR_MATCH_BF16, match_tile_for(c, nP), L.tc_ws,
                                L.nn, L.d1,
-                               &L.st->match_fallbacks, &L.st->match_err, nullptr, s),
+                               &L.st->match_fallbacks, &L.st->match_err, nullptr, s, take_tc_fault(c)),
              "match");
   else
     TRY_CUDA(c,
@@ -660,6 +819,7 @@ int ensure_lanes(lsr_ctx *c, int S, size_t bytes) {
     c->lane_cap[l] = 0;
     c->gkey.clear();  // a captured batch points into the old workspace
     size_t want = bytes + bytes / 8;
+    if (injected_alloc_failure(c)) return set_err(c, LSR_E_OOM, "batch workspace allocation failed (injected)");
     if (cudaMalloc(&c->lane_ws[l], want) != cudaSuccess) {
       cudaGetLastError();
       c->lane_ws[l] = nullptr;
@@ -881,6 +1041,7 @@ const char *lsr_error_string(int code) {
     case LSR_E_TIMEOUT: return "device wait timed out";
     case LSR_E_STATE: return "context unusable";
     case LSR_E_TOO_LARGE: return "input exceeds the fixed scratch of the allocation-free entry point";
+    case LSR_E_CHECK: return "a device bounds check failed (checked build)";
     default: return "unknown error";
   }
 }
@@ -951,8 +1112,39 @@ int lsr_destroy(lsr_ctx *c) {
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c->ktimer;
   cudaGetLastError();
   delete c;
+  return LSR_OK;
+}
+
+int lsr_set_kernel_timing(lsr_ctx *c, const char *filter) {
+  if (!c) return LSR_E_STATE;
+  if (cudaSetDevice(c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(c, LSR_E_CUDA, "cudaSetDevice failed");
+  }
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  delete c->ktimer;
+  c->ktimer = nullptr;
+  if (!filter) return LSR_OK;
+  if (strlen(filter) > 200) return set_err(c, LSR_E_ARG, "kernel filter too long");
+  c->ktimer = new KernelTimer();
+  c->ktimer->filter = filter;
+  return LSR_OK;
+}
+
+int32_t lsr_kernel_timing_count(const lsr_ctx *c) {
+  return c && c->ktimer ? (int32_t)c->ktimer->table.size() : 0;
+}
+
+int lsr_kernel_timing_entry(const lsr_ctx *c, int32_t i, const char **name, int64_t *launches, double *total_ms) {
+  if (!c) return LSR_E_STATE;
+  if (!c->ktimer || i < 0 || i >= (int32_t)c->ktimer->table.size()) return LSR_E_ARG;
+  const KernelTimer::Entry &e = c->ktimer->table[(size_t)i];
+  if (name) *name = e.name.c_str();
+  if (launches) *launches = e.launches;
+  if (total_ms) *total_ms = e.ms;
   return LSR_OK;
 }
 
@@ -968,6 +1160,35 @@ int lsr_get_params(const lsr_ctx *c, lsr_params *p) {
   if (!p) return LSR_E_ARG;
   *p = c->prm;
   return LSR_OK;
+}
+
+int lsr_checked_build(void) {
+#ifdef LSR_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int lsr_debug_inject(lsr_ctx *c, int32_t kind, int32_t count) {
+  if (!c) return LSR_E_STATE;
+  if (count < 0 || count > 1000000) return set_err(c, LSR_E_ARG, "bad injection count");
+  switch (kind) {
+    case LSR_INJECT_NONE: c->inject_alloc = c->inject_stall = 0; return LSR_OK;
+    case LSR_INJECT_ALLOC: c->inject_alloc = count; return LSR_OK;
+    case LSR_INJECT_MATCH_STALL: c->inject_stall = count; return LSR_OK;
+    case LSR_INJECT_CHECK: {
+      if (!lsr_checked_build()) return set_err(c, LSR_E_ARG, "LSR_INJECT_CHECK needs the checked build");
+      if (count == 0) return LSR_OK;
+      if (cudaSetDevice(c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, LSR_E_CUDA, "cudaSetDevice failed");
+      }
+      TRY_CUDA(c, check_probe_arm(c->stream), "arm probe");
+      return LSR_OK;
+    }
+    default: return set_err(c, LSR_E_ARG, "bad injection kind");
+  }
 }
 
 int lsr_set_profiling(lsr_ctx *c, int enable) {
@@ -991,6 +1212,34 @@ int lsr_transfer_bytes(int64_t nP, int64_t nQ, int64_t *h2d, int64_t *d2h) {
   if (d2h) *d2h = (int64_t)(sizeof(RansacState) + 2 * sizeof(float) * kBox);
   return LSR_OK;
 }
+
+// Installs the context's kernel timer for the calling thread while a call
+// enqueues on the context stream; launches bracketed by a call that fails
+// before its synchronisation are dropped.
+struct KernelTimerScope {
+  KernelTimer *t = nullptr;
+  bool done = false;
+  KernelTimerScope(lsr_ctx *c, bool on) {
+    if (on && c->ktimer) {
+      t = c->ktimer;
+      t->stream = c->stream;
+      t->failed = false;
+      g_ktimer = t;
+    }
+  }
+  void collect() {
+    if (t) t->collect();
+    done = true;
+  }
+  ~KernelTimerScope() {
+    if (!t) return;
+    g_ktimer = nullptr;
+    if (!done) {
+      t->open.clear();
+      t->used = 0;
+    }
+  }
+};
 
 static int register_many(lsr_ctx *c, int32_t n, const float *const *P, const int64_t *nP, const float *const *Q,
                          const int64_t *nQ, const float *vp, uint64_t pair0, lsr_result *out) {
@@ -1018,6 +1267,7 @@ static int register_many(lsr_ctx *c, int32_t n, const float *const *P, const int
   S = std::max(1, std::min(S, (int)n));
   const bool graph = c->prm.batch_graph == 1 && n > 1;
   Timer tm{c};
+  KernelTimerScope kts(c, S == 1 && !graph);
   if (S == 1 && !graph) {
     // pairs back to back on the context stream, one workspace
     if ((rc = ensure_ws(c, bytes))) return rc;
@@ -1088,8 +1338,9 @@ static int register_many(lsr_ctx *c, int32_t n, const float *const *P, const int
       if ((rc = enqueue_batch(c, b, lanes))) return rc;
     }
   }
-  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+  SYNC_CHECKED(c, c->stream);
   TRY_CUDA(c, cudaGetLastError(), "kernel");
+  kts.collect();
   for (int i = 0; i < n; ++i) {
     if (c->box_host[2 * kBox * i + 6] != 0.f || c->box_host[2 * kBox * i + kBox + 6] != 0.f)
       return set_err(c, LSR_E_ARG, "non-finite input coordinates");
@@ -1161,7 +1412,7 @@ int lsr_stage_normals(lsr_ctx *c, const float *P, int64_t n, const float *vp, fl
   if (normals && (rc = copy_out(c, normals, dn, sizeof(float) * 3 * n))) return rc;
   if (count && (rc = copy_out(c, count, dc, sizeof(int) * n))) return rc;
   if (curvature && (rc = copy_out(c, curvature, dv, sizeof(float) * n))) return rc;
-  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  SYNC_CHECKED(c, s);
   return LSR_OK;
 }
 
@@ -1212,7 +1463,7 @@ static int stage_desc_common(lsr_ctx *c, const float *P, const float *normals, c
   TRY_CUDA(c, cudaGetLastError(), "stage kernels");
   if ((rc = copy_out(c, out, o, sizeof(float) * kD * n))) return rc;
   if (k_out && !spfh_in && (rc = copy_out(c, k_out, ko, sizeof(int) * n))) return rc;
-  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  SYNC_CHECKED(c, s);
   return LSR_OK;
 }
 
@@ -1264,7 +1515,7 @@ int lsr_stage_match(lsr_ctx *c, const float *FP, int64_t nP, const float *FQ, in
   LSR_LAUNCH(k_gather_rows<<<nblk(nQ * kDS), 256, 0, s>>>(fq, kD, nullptr, (int)nQ, FQi));
   if (tc)
     TRY_CUDA(c, launch_match_bf16(FPi, (int)nP, FQi, (int)nQ, split, match_tile_for(c, (int)nP), tws, dn, dd, flags, flags + 1,
-                                  nullptr, s),
+                                  nullptr, s, take_tc_fault(c)),
              "match");
   else
     TRY_CUDA(c, launch_match_fp32(FPi, (int)nP, FQi, (int)nQ, tws, dn, dd, s), "match");
@@ -1272,7 +1523,7 @@ int lsr_stage_match(lsr_ctx *c, const float *FP, int64_t nP, const float *FQ, in
   if (tc) TRY_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s), "copy flags");
   if ((rc = copy_out(c, nn, dn, sizeof(int) * nP))) return rc;
   if (d1 && (rc = copy_out(c, d1, dd, sizeof(float) * nP))) return rc;
-  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  SYNC_CHECKED(c, s);
   if (hflags[1]) return set_err(c, LSR_E_TIMEOUT, "BF16 matcher timed out waiting on the tensor cores");
   if (fallbacks) *fallbacks = hflags[0];
   return LSR_OK;
@@ -1315,7 +1566,7 @@ int lsr_match_scores_bf16(lsr_ctx *c, const float *FP, int64_t nP, const float *
   LSR_LAUNCH(k_gather_rows<<<nblk(nP * kDS), 256, 0, s>>>(fp, kD, nullptr, (int)nP, FPi));
   LSR_LAUNCH(k_gather_rows<<<nblk(nQ * kDS), 256, 0, s>>>(fq, kD, nullptr, (int)nQ, FQi));
   TRY_CUDA(c, launch_match_bf16(FPi, (int)nP, FQi, (int)nQ, split, match_tile_for(c, (int)nP), tws, nullptr, nullptr,
-                                flags, flags + 1, sc, s),
+                                flags, flags + 1, sc, s, take_tc_fault(c)),
            "scores");
   int hflags[2] = {0, 0};
   TRY_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s), "copy flags");
@@ -1323,7 +1574,7 @@ int lsr_match_scores_bf16(lsr_ctx *c, const float *FP, int64_t nP, const float *
            cudaMemcpy2DAsync(scores, sizeof(float) * nQ, sc, sizeof(float) * cols, sizeof(float) * nQ, nP,
                              cudaMemcpyDefault, s),
            "copy scores");
-  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  SYNC_CHECKED(c, s);
   if (hflags[1]) return set_err(c, LSR_E_TIMEOUT, "BF16 matcher timed out waiting on the tensor cores");
   return LSR_OK;
 }
@@ -1389,7 +1640,7 @@ int lsr_stage_hypotheses(lsr_ctx *c, const float *P, int64_t nP, const float *Q,
            "hypotheses");
   RansacState st;
   TRY_CUDA(c, cudaMemcpyAsync(&st, L.st, sizeof(st), cudaMemcpyDeviceToHost, s), "D2H");
-  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  SYNC_CHECKED(c, s);
   *nsurv = st.n_surv_total;
   int64_t ncopy = std::min<int64_t>(std::min<int64_t>(st.n_surv, cap), st.n_surv_total);
   if (ncopy > 0) {
@@ -1414,7 +1665,7 @@ int lsr_stage_rigid4(lsr_ctx *c, const float *ps, const float *qs, int64_t nh, f
   TRY_CUDA(c, cudaMemcpyAsync(dq, qs, sizeof(float) * 12 * nh, cudaMemcpyDefault, s), "copy");
   TRY_CUDA(c, launch_rigid4(dp, dq, (int)nh, dr, s), "rigid4");
   if ((rc = copy_out(c, Rt, dr, sizeof(float) * 12 * nh))) return rc;
-  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  SYNC_CHECKED(c, s);
   return LSR_OK;
 }
 
@@ -1487,7 +1738,7 @@ int lsr_stage_consensus(lsr_ctx *c, const float *P, int64_t nP, const float *Q, 
   LSR_LAUNCH(k_sum_to_double<<<nblk(nh), 256, 0, s>>>(sum, (int)nh, sd));
   if ((rc = copy_out(c, count, cnt, sizeof(int) * nh))) return rc;
   if ((rc = copy_out(c, sumd2, sd, sizeof(double) * nh))) return rc;
-  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  SYNC_CHECKED(c, s);
   return LSR_OK;
 }
 
@@ -1549,7 +1800,7 @@ int lsr_stage_refine(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int
            "refine");
   RansacState h;
   TRY_CUDA(c, cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H");
-  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  SYNC_CHECKED(c, s);
   memcpy(T_out, h.T, sizeof(double) * 16);
   if (iters_done) *iters_done = h.iters_done;
   return LSR_OK;
@@ -1598,7 +1849,7 @@ int lsr_information_matrix(lsr_ctx *c, const float *P, int64_t nP, const float *
            "information");
   double host[37];
   TRY_CUDA(c, cudaMemcpyAsync(host, b.out, sizeof(host), cudaMemcpyDeviceToHost, s), "D2H");
-  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  SYNC_CHECKED(c, s);
   for (int k = 0; k < 36; ++k) info[k] = host[k];
   if (n_corr) *n_corr = (int64_t)host[36];
   return LSR_OK;
@@ -1644,7 +1895,7 @@ int lsr_voxel_downsample(lsr_ctx *c, const float *P, int64_t n, float leaf, floa
     TRY_CUDA(c, launch_vox_bounds(src, n, leaf, b.kb, s), "voxel bounds");
     int kb[6];
     TRY_CUDA(c, cudaMemcpyAsync(kb, b.kb, sizeof(kb), cudaMemcpyDeviceToHost, s), "D2H");
-    TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+    SYNC_CHECKED(c, s);
     const int64_t need = ((int64_t)kb[3] - kb[0] + 1) * ((int64_t)kb[4] - kb[1] + 1) * ((int64_t)kb[5] - kb[2] + 1);
     if (kb[0] > kb[3] || need > kMaxCells) return set_err(c, LSR_E_TOO_LARGE, "voxel grid of the cloud too large");
     if (pass == 0) {
@@ -1660,10 +1911,10 @@ int lsr_voxel_downsample(lsr_ctx *c, const float *P, int64_t n, float leaf, floa
              "voxel cells");
     int64_t m_out = 0;
     TRY_CUDA(c, cudaMemcpyAsync(&m_out, b.nout, sizeof(m_out), cudaMemcpyDeviceToHost, s), "D2H");
-    TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+    SYNC_CHECKED(c, s);
     if (!dev_out && cap > 0 && (rc = copy_out(c, out, b.o, sizeof(float) * 3 * (size_t)std::min(m_out, cap))))
       return rc;
-    TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+    SYNC_CHECKED(c, s);
     *n_out = m_out;
   }
   return LSR_OK;
@@ -1750,7 +2001,7 @@ int lsr_surfel_correct(lsr_ctx *c, int64_t n, const float *pos, const float *nrm
   }
   unsigned long long cnt = 0;
   TRY_CUDA(c, cudaMemcpyAsync(&cnt, b.cnt, sizeof(cnt), cudaMemcpyDeviceToHost, s), "D2H");
-  TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+  SYNC_CHECKED(c, s);
   if (n_keep) *n_keep = (int64_t)cnt;
   return LSR_OK;
 }
@@ -1861,7 +2112,7 @@ static int objective_impl(lsr_ctx *c, int32_t n, const float *const *P, const in
     TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->lane_done[l], 0), "join");
   }
   TRY_CUDA(c, cudaMemcpyAsync(host7.data(), out7, sizeof(double) * 7 * n, cudaMemcpyDeviceToHost, c->stream), "D2H");
-  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+  SYNC_CHECKED(c, c->stream);
   for (int i = 0; i < n; ++i) {
     const double *o = &host7[(size_t)7 * i];
     if (E) E[i] = o[0];

@@ -357,4 +357,6 @@ cudaError_t launch_reach_mask(const int *lo, const int *extra, const uint8_t *ok
   return cudaGetLastError();
 }
 
+LSR_CHECK_READER(classify)
+
 }  // namespace lsr

@@ -294,4 +294,6 @@ cudaError_t launch_fpfh(const float4 *X, const float4 *N, const float *spfh, int
   return cudaGetLastError();
 }
 
+LSR_CHECK_READER(features)
+
 }  // namespace lsr

@@ -75,10 +75,79 @@ struct CloudDev {
 // ----------------------------------------------------------------- helpers
 __host__ __device__ inline int64_t lsr_div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Checked build (-DLSR_CHECKED): the index checks below record the first
+// violation of a translation unit (site, index, bound) in that unit's device
+// words instead of trapping, and the guarded access is skipped; the host reads
+// the words after each synchronising call (check_report) and returns
+// LSR_E_CHECK. In the normal build every check is the constant true.
+enum CheckSite : int {
+  kSiteGridRow = 1,   // grid walk: cell-start index of a row of cells
+  kSiteGridSlot,      // grid walk (wrapped storage): cell-start index of a cell
+  kSiteGridPoint,     // grid walk: sorted point index
+  kSiteHypSample,     // hypotheses: sampled point index
+  kSiteHypMatch,      // hypotheses: descriptor NN of a sampled point
+  kSiteMatchRow,      // matchers: database row of a candidate
+  kSiteMatchQuery,    // matchers: query row written
+  kSiteProbe,         // test probe (lsr_debug_inject LSR_INJECT_CHECK): never an access
+};
+struct CheckReport {
+  unsigned long long site;
+  long long index, bound;
+};
+#ifdef LSR_CHECKED
+static __device__ unsigned long long g_check_site;
+static __device__ long long g_check_index, g_check_bound;
+__device__ __forceinline__ bool check_in_bounds(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  if (atomicCAS(&g_check_site, 0ull, (unsigned long long)site) == 0ull) {
+    g_check_index = i;
+    g_check_bound = n;
+  }
+  return false;
+}
+#define LSR_IN_BOUNDS(i, n, site) ::lsr::check_in_bounds((long long)(i), (long long)(n), (site))
+// Host reader of this translation unit's words (clears them).
+#define LSR_CHECK_READER(unit)                                                                \
+  cudaError_t check_read_##unit(CheckReport *r) {                                             \
+    CheckReport z{0, 0, 0};                                                                   \
+    cudaError_t e = cudaMemcpyFromSymbol(&r->site, g_check_site, sizeof(r->site));            \
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&r->index, g_check_index, sizeof(r->index)); \
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&r->bound, g_check_bound, sizeof(r->bound)); \
+    if (e == cudaSuccess && r->site) e = cudaMemcpyToSymbol(g_check_site, &z.site, sizeof(z.site)); \
+    return e;                                                                                 \
+  }
+#else
+#define LSR_IN_BOUNDS(i, n, site) true
+#define LSR_CHECK_READER(unit)                     \
+  cudaError_t check_read_##unit(CheckReport *r) { \
+    r->site = 0;                                   \
+    r->index = r->bound = 0;                       \
+    return cudaSuccess;                            \
+  }
+#endif
+// Readers of the units that hold checks.
+cudaError_t check_read_features(CheckReport *r);
+cudaError_t check_read_match(CheckReport *r);
+cudaError_t check_read_match_tc(CheckReport *r);
+cudaError_t check_read_ransac(CheckReport *r);
+cudaError_t check_read_classify(CheckReport *r);
+cudaError_t check_read_refine(CheckReport *r);
+cudaError_t check_probe_arm(cudaStream_t s);
+
 // Kernel launches of this library, counted process-wide (lsr_launch_count).
 extern unsigned long long g_launches;
 inline void count_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
-#define LSR_LAUNCH(...) (::lsr::count_launch(), __VA_ARGS__)
+
+// Per-kernel CUDA-event timing (lsr_set_kernel_timing): while a timer is
+// installed for the calling thread, every launch whose kernel name starts with
+// the timer's filter is bracketed by two events recorded on the timer's stream
+// (the stream every launch of that call is ordered on).
+struct KernelTimer;
+extern thread_local KernelTimer *g_ktimer;
+void ktimer_mark(const char *launch_expr, bool after);
+#define LSR_LAUNCH(...)                                                                  \
+  (::lsr::count_launch(), ::lsr::g_ktimer ? ::lsr::ktimer_mark(#__VA_ARGS__, false) : void(), \
+   __VA_ARGS__, ::lsr::g_ktimer ? ::lsr::ktimer_mark(#__VA_ARGS__, true) : void())
 
 #define LSR_CUDA_TRY(call)                         \
   do {                                             \
@@ -115,6 +184,15 @@ __device__ __forceinline__ void grid_ranges(const GridParams &g, const int *__re
         int iy = cy + dy;
         if (iy < 0 || iy >= g.ny) continue;
         int row = (iz * g.wy + iy) * g.wx;
+        if (!LSR_IN_BOUNDS(row + x1 + 1, g.ncells + 1, kSiteGridRow) || !LSR_IN_BOUNDS(row + x0, g.ncells + 1, kSiteGridRow))
+          continue;
+#ifdef LSR_CHECKED
+        {
+          const int b = start[row + x0], e = start[row + x1 + 1];
+          if (e > b && (!LSR_IN_BOUNDS(e - 1, g.npts, kSiteGridPoint) || !LSR_IN_BOUNDS(b, g.npts, kSiteGridPoint)))
+            continue;
+        }
+#endif
         f(start[row + x0], start[row + x1 + 1]);
       }
     }
@@ -134,6 +212,15 @@ __device__ __forceinline__ void grid_ranges(const GridParams &g, const int *__re
         for (int k = 0; k < ns; ++k) dup |= (seen[k] == slot);
         if (dup) continue;
         seen[ns++] = slot;
+        if (!LSR_IN_BOUNDS(slot + 1, g.ncells + 1, kSiteGridSlot) || !LSR_IN_BOUNDS(slot, g.ncells + 1, kSiteGridSlot))
+          continue;
+#ifdef LSR_CHECKED
+        {
+          const int b = start[slot], e = start[slot + 1];
+          if (e > b && (!LSR_IN_BOUNDS(e - 1, g.npts, kSiteGridPoint) || !LSR_IN_BOUNDS(b, g.npts, kSiteGridPoint)))
+            continue;
+        }
+#endif
         f(start[slot], start[slot + 1]);
       }
     }
@@ -166,6 +253,14 @@ __device__ __forceinline__ void group_nn(const GridParams &g, const int *__restr
   auto scan = [&](int b, int e) {
     int len = e - b;
     // four independent loads in flight per lane, then the remainder
+#ifdef LSR_CHECKED
+    if (len > 0 && (!LSR_IN_BOUNDS(e - 1, g.npts, kSiteGridPoint) || !LSR_IN_BOUNDS(b, g.npts, kSiteGridPoint))) {
+      for (; next < base + len; next += G) {
+      }
+      base += len;
+      return;
+    }
+#endif
     for (; next + 3 * G < base + len; next += 4 * G) {
       int t = b + next - base;
       float4 q[4] = {Xe[t], Xe[t + G], Xe[t + 2 * G], Xe[t + 3 * G]};
@@ -228,6 +323,8 @@ __device__ __forceinline__ void group_nn(const GridParams &g, const int *__restr
         if (e > cx && (r2 + gxh) * kShrink > gb) e = cx;
         if (a > e) continue;
         const int row = (iz * g.wy + iy) * g.wx;
+        if (!LSR_IN_BOUNDS(row + e + 1, g.ncells + 1, kSiteGridRow) || !LSR_IN_BOUNDS(row + a, g.ncells + 1, kSiteGridRow))
+          continue;
         scan(start[row + a], start[row + e + 1]);
         float m = best;
 #pragma unroll
@@ -336,11 +433,18 @@ cudaError_t launch_match_fp32_rows(const float *FP, int nP, const float *FQ, int
 // d2 != null it writes D~^2 = |b~|^2 - 2 a~.b~ + |a~|^2 for every pair (nP
 // rows of tc_score_cols(nQ)) instead of matching.
 // qt: query tiles of 128 per CTA work unit (1 or 2; 0 = tc_default_tile(nP)).
+// f: the limit of the pipeline's waits (0 = 2 s) and the test-only stall
+// (the producer issues no copy or MMA, so the epilogue's first wait runs out
+// and err is set; see lsr_debug_inject).
+struct TcFault {
+  unsigned long long wait_ns = 0;
+  int stall = 0;
+};
 size_t tc_workspace_bytes(int nP, int nQ, bool split);
 int tc_score_cols(int nQ);
 int tc_default_tile(int nP);
 cudaError_t launch_match_bf16(const float *FP, int nP, const float *FQ, int nQ, bool split, int qt, char *ws, int *nn,
-                              float *d1, int *fb_count, int *err, float *d2, cudaStream_t s);
+                              float *d1, int *fb_count, int *err, float *d2, cudaStream_t s, TcFault f = TcFault());
 
 // ----------------------------------------------------------------- RANSAC (lsr_ransac.cu)
 // Device-side counters and selection state of one registration.

@@ -247,21 +247,23 @@ __global__ void __launch_bounds__(kMT) k_match_rows_chunked(const float *__restr
     }
 #pragma unroll
     for (int u = 0; u < kQR; ++u)
-      if (slot[u] >= 0 && bj[u] >= 0)
+      if (slot[u] >= 0 && bj[u] >= 0 && LSR_IN_BOUNDS(slot[u], nP, kSiteMatchQuery))
         atomicMin(packed + slot[u], ((unsigned long long)__float_as_uint(best[u]) << 32) | (unsigned)bj[u]);
     __syncthreads();
   }
 }
 
-__global__ void k_rows_init(const int *nrows, unsigned long long *packed) {
+__global__ void k_rows_init(const int *nrows, int nP, unsigned long long *packed) {
   const int nq = *nrows;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) packed[q] = ~0ull;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x)
+    if (LSR_IN_BOUNDS(q, nP, kSiteMatchQuery)) packed[q] = ~0ull;
 }
 
-__global__ void k_rows_finish(const int *rows, const int *nrows, const unsigned long long *packed, int *nn,
+__global__ void k_rows_finish(const int *rows, const int *nrows, int nP, const unsigned long long *packed, int *nn,
                               float *d1) {
   const int nq = *nrows;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    if (!LSR_IN_BOUNDS(q, nP, kSiteMatchQuery) || !LSR_IN_BOUNDS(rows[q], nP, kSiteMatchQuery)) continue;
     unsigned long long v = packed[q];
     int r = rows[q];
     bool none = v == ~0ull;
@@ -271,6 +273,8 @@ __global__ void k_rows_finish(const int *rows, const int *nrows, const unsigned 
 }
 
 }  // namespace
+
+LSR_CHECK_READER(match)
 
 size_t fp32_workspace_bytes(int nQ) { return sizeof(float) * kTB * (size_t)lsr_div_up(nQ, kTile) + 256; }
 
@@ -297,9 +301,9 @@ cudaError_t launch_match_fp32_rows(const float *FP, int nP, const float *FQ, int
   nx = nx < 1 ? 1 : (nx > 10 ? 10 : nx);
   int fin = (int)lsr_div_up(nP, 256);
   fin = fin < 1 ? 1 : (fin > 1216 ? 1216 : fin);
-  LSR_LAUNCH(k_rows_init<<<fin, 256, 0, s>>>(nrows, packed));
+  LSR_LAUNCH(k_rows_init<<<fin, 256, 0, s>>>(nrows, nP, packed));
   LSR_LAUNCH(k_match_rows_chunked<<<dim3(nx, ny), kMT, 0, s>>>(FP, nP, FQ, nQ, chunk, rows, nrows, packed));
-  LSR_LAUNCH(k_rows_finish<<<fin, 256, 0, s>>>(rows, nrows, packed, nn, d1));
+  LSR_LAUNCH(k_rows_finish<<<fin, 256, 0, s>>>(rows, nrows, nP, packed, nn, d1));
   return cudaGetLastError();
 }
 

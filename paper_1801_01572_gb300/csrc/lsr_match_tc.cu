@@ -62,7 +62,7 @@ constexpr int kTopK = 8;                        // candidate chunks per query
 constexpr int kChunkW = 16;                     // database rows per chunk
 constexpr int kChunks = kTcN / kChunkW;         // chunks per tile
 constexpr int kLoads = kTcN / 32;               // 32-column TMEM loads per accumulator row
-constexpr unsigned long long kWaitNs = 2000000000ull;  // give up after 2 s
+constexpr unsigned long long kWaitNs = 2000000000ull;  // give up after 2 s (the default limit; drains always)
 constexpr float kPadScore = 1.2676506e30f;      // 2^100: |b~|^2 of padding rows
 constexpr float kAccErr = 1.5e-5f;              // accumulation error per unit of sum |products|
 constexpr int kCenterGroups = 8;                // row groups of the centring kernel
@@ -125,15 +125,16 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase of the given parity; gives up after kWaitNs (flagging
+// Waits for the phase of the given parity; gives up after limit_ns (flagging
 // the CTA) or as soon as another thread of the CTA has given up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *fail) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *fail,
+                                          unsigned long long limit_ns) {
   if (mbar_try(b, parity)) return true;
   unsigned long long t0 = gtime();
   for (;;) {
     if (mbar_try(b, parity)) return true;
     if (*fail) return false;
-    if (gtime() - t0 > kWaitNs) {
+    if (gtime() - t0 > limit_ns) {
       *fail = 1;
       return false;
     }
@@ -303,6 +304,8 @@ struct TcArgs {
   int *fb_rows, *fb_count;      // queries left to the exact FP32 scan
   int *err;                     // set to 1 by a CTA that gave up
   float *d2;                    // optional: all D~^2 = s + |a~|^2 (nP x nNT * kTcN) instead of the top-8
+  unsigned long long wait_ns;   // limit of every wait of the pipeline (the drain after a failure keeps kWaitNs)
+  int stall;                    // fault injection: the producer issues nothing, so the first wait runs out
 };
 
 // Exact FP32 squared distance in the FP32 matcher's operation order (one
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(Cfg<KS, QT>::Threads, Cfg<KS, QT>::CtasPerSm) 
 
   if (warp == kEpiWarps) {
     // ------------------------------------------------ copies + MMA (one thread)
-    if (lane == 0 && total > 0) {
+    if (lane == 0 && total > 0 && !g.stall) {
       auto load_b = [&](int jj) {
         int st = jj % kStages, t = jj % g.nNT;
         mbar_expect_tx(barB + st, S::TileBytes);
@@ -400,19 +403,19 @@ __global__ void __launch_bounds__(Cfg<KS, QT>::Threads, Cfg<KS, QT>::CtasPerSm) 
         const int t = j % g.nNT;
         if (t == 0) {
           // the previous unit's MMAs must be done reading the query tiles
-          if (j > 0 && !mbar_wait(barDone + ((j - 1) & 1), ((j - 1) >> 1) & 1, fail)) break;
+          if (j > 0 && !mbar_wait(barDone + ((j - 1) & 1), ((j - 1) >> 1) & 1, fail, g.wait_ns)) break;
           int u = blockIdx.x + (j / g.nNT) * gridDim.x;
           mbar_expect_tx(barA, C::UnitBytes);
           bulk_g2s(sA, g.A + (size_t)u * C::UnitBytes, C::UnitBytes, barA);
           a_pending = units & 1;
-          if (!mbar_wait(barA, units & 1, fail)) break;
+          if (!mbar_wait(barA, units & 1, fail, g.wait_ns)) break;
           a_pending = -1;
           ++units;
         }
         const int st = j % kStages;
-        if (!mbar_wait(barB + st, (j / kStages) & 1, fail)) break;
+        if (!mbar_wait(barB + st, (j / kStages) & 1, fail, g.wait_ns)) break;
         loaded[st] = -1;
-        if (j >= 2 && !mbar_wait(barEmpty + (j & 1), ((j - 2) >> 1) & 1, fail)) break;
+        if (j >= 2 && !mbar_wait(barEmpty + (j & 1), ((j - 2) >> 1) & 1, fail, g.wait_ns)) break;
         tc_fence_after();
         const uint32_t d = tbase + (uint32_t)((j & 1) * kAccCols);
 #pragma unroll
@@ -425,7 +428,7 @@ __global__ void __launch_bounds__(Cfg<KS, QT>::Threads, Cfg<KS, QT>::CtasPerSm) 
         last_commit = j;
         // refill the stage of tile j-1 with tile j+3 once its MMAs are done
         if (j >= 1 && j + kStages - 1 < total) {
-          if (!mbar_wait(barDone + ((j - 1) & 1), ((j - 1) >> 1) & 1, fail)) break;
+          if (!mbar_wait(barDone + ((j - 1) & 1), ((j - 1) >> 1) & 1, fail, g.wait_ns)) break;
           load_b(j + kStages - 1);
         }
       }
@@ -447,7 +450,7 @@ __global__ void __launch_bounds__(Cfg<KS, QT>::Threads, Cfg<KS, QT>::CtasPerSm) 
       for (int q = 0; q < kTopK; ++q) ts[q] = FLT_MAX, ti[q] = -1;
       for (int t = 0; t < g.nNT; ++t, ++j) {
         const int buf = j & 1;
-        ok = mbar_wait(barDone + buf, (j >> 1) & 1, fail);
+        ok = mbar_wait(barDone + buf, (j >> 1) & 1, fail, g.wait_ns);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         tc_fence_after();
@@ -499,6 +502,7 @@ __global__ void __launch_bounds__(Cfg<KS, QT>::Threads, Cfg<KS, QT>::CtasPerSm) 
         const int c0 = ti[q] * kChunkW, c1 = min(g.nQ, c0 + kChunkW);
 #pragma unroll 1
         for (int c = c0; c < c1; ++c) {
+          if (!LSR_IN_BOUNDS(c, g.nQ, kSiteMatchRow)) break;
           const float d = exact_d2(a, g.FQ + (size_t)c * kDS);
           if (d < best || (d == best && c < bi)) best = d, bi = c;
         }
@@ -517,7 +521,10 @@ __global__ void __launch_bounds__(Cfg<KS, QT>::Threads, Cfg<KS, QT>::CtasPerSm) 
       }
       g.nn[r] = bi;
       if (g.d1) g.d1[r] = best;
-      if (!cert) g.fb_rows[atomicAdd(g.fb_count, 1)] = r;
+      if (!cert) {
+        const int slot = atomicAdd(g.fb_count, 1);
+        if (LSR_IN_BOUNDS(slot, g.nP, kSiteMatchQuery)) g.fb_rows[slot] = r;
+      }
     }
   }
 
@@ -587,12 +594,12 @@ int sm_count() {
 
 template <int KS, int QT>
 cudaError_t launch_tc(const TcLayout &L, const float *FP, int nP, const float *FQ, int nQ, int *nn, float *d1,
-                      int *fb_count, int *err, float *d2, cudaStream_t s) {
+                      int *fb_count, int *err, float *d2, const TcFault &f, cudaStream_t s) {
   using C = Cfg<KS, QT>;
   const int nU = (int)lsr_div_up(nP, C::UnitQ), nNT = (int)lsr_div_up(nQ, kTcN);
   LSR_CUDA_TRY(cudaFuncSetAttribute(k_match_tc<KS, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SmemBytes));
   TcArgs g{L.A, L.B, L.aa, L.eta, L.maxes, L.maxes + 1, FP, FQ, nP, nQ, nU, nNT,
-           nn, d1, L.fb_rows, fb_count, err, d2};
+           nn, d1, L.fb_rows, fb_count, err, d2, f.wait_ns ? f.wait_ns : kWaitNs, f.stall};
   const int slots = sm_count() * C::CtasPerSm;
   const int grid = nU < slots ? nU : slots;
   LSR_LAUNCH(k_match_tc<KS, QT><<<grid, C::Threads, C::SmemBytes, s>>>(g));
@@ -601,7 +608,7 @@ cudaError_t launch_tc(const TcLayout &L, const float *FP, int nP, const float *F
 
 template <int KS>
 cudaError_t run_tc(const float *FP, int nP, const float *FQ, int nQ, int qt, char *ws, int *nn, float *d1,
-                   int *fb_count, int *err, float *d2, cudaStream_t s) {
+                   int *fb_count, int *err, float *d2, const TcFault &f, cudaStream_t s) {
   TcLayout L = tc_layout<KS>(ws, nP, nQ);
   const int nNT = (int)lsr_div_up(nQ, kTcN);
   LSR_CUDA_TRY(cudaMemsetAsync(L.maxes, 0, 2 * sizeof(unsigned), s));
@@ -614,9 +621,9 @@ cudaError_t run_tc(const float *FP, int nP, const float *FQ, int nQ, int qt, cha
   LSR_LAUNCH(k_prep_tiles<KS><<<(int)lsr_div_up(rowsA, 256), 256, 0, s>>>(FP, nP, rowsA, true, L.center, pa));
   LSR_LAUNCH(k_prep_tiles<KS><<<(int)lsr_div_up(rowsB, 256), 256, 0, s>>>(FQ, nQ, rowsB, false, L.center, pb));
   if (qt == 1)
-    LSR_CUDA_TRY((launch_tc<KS, 1>(L, FP, nP, FQ, nQ, nn, d1, fb_count, err, d2, s)));
+    LSR_CUDA_TRY((launch_tc<KS, 1>(L, FP, nP, FQ, nQ, nn, d1, fb_count, err, d2, f, s)));
   else
-    LSR_CUDA_TRY((launch_tc<KS, 2>(L, FP, nP, FQ, nQ, nn, d1, fb_count, err, d2, s)));
+    LSR_CUDA_TRY((launch_tc<KS, 2>(L, FP, nP, FQ, nQ, nn, d1, fb_count, err, d2, f, s)));
   if (!d2) LSR_CUDA_TRY(launch_match_fp32_rows(FP, nP, FQ, nQ, L.fb_rows, fb_count, L.packed, nn, d1, s));
   return cudaGetLastError();
 }
@@ -624,6 +631,8 @@ cudaError_t run_tc(const float *FP, int nP, const float *FQ, int nQ, int qt, cha
 constexpr int kKsPlain = 3, kKsSplit = 7;
 
 }  // namespace
+
+LSR_CHECK_READER(match_tc)
 
 size_t tc_workspace_bytes(int nP, int nQ, bool split) {
   return split ? tc_layout<kKsSplit>(nullptr, nP, nQ).bytes : tc_layout<kKsPlain>(nullptr, nP, nQ).bytes;
@@ -634,11 +643,11 @@ int tc_score_cols(int nQ) { return (int)lsr_div_up(nQ, kTcN) * kTcN; }
 int tc_default_tile(int nP) { return lsr_div_up(nP, 2 * kTcM) >= kSms ? 2 : 1; }
 
 cudaError_t launch_match_bf16(const float *FP, int nP, const float *FQ, int nQ, bool split, int qt, char *ws, int *nn,
-                              float *d1, int *fb_count, int *err, float *d2, cudaStream_t s) {
+                              float *d1, int *fb_count, int *err, float *d2, cudaStream_t s, TcFault f) {
   if (nP < 1 || nQ < 1 || (qt != 0 && qt != 1 && qt != 2)) return cudaErrorInvalidValue;
   if (qt == 0) qt = tc_default_tile(nP);
-  return split ? run_tc<kKsSplit>(FP, nP, FQ, nQ, qt, ws, nn, d1, fb_count, err, d2, s)
-               : run_tc<kKsPlain>(FP, nP, FQ, nQ, qt, ws, nn, d1, fb_count, err, d2, s);
+  return split ? run_tc<kKsSplit>(FP, nP, FQ, nQ, qt, ws, nn, d1, fb_count, err, d2, f, s)
+               : run_tc<kKsPlain>(FP, nP, FQ, nQ, qt, ws, nn, d1, fb_count, err, d2, f, s);
 }
 
 }  // namespace lsr

@@ -63,7 +63,9 @@ __device__ __forceinline__ bool hyp_pass(const HypIn &in, uint32_t h, int ii[4],
   float4 p[4], q[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
+    if (!LSR_IN_BOUNDS(idx[k], in.nP, kSiteHypSample)) return false;
     ii[k] = in.invP[idx[k]];
+    if (!LSR_IN_BOUNDS(ii[k], in.nP, kSiteHypSample)) return false;
     if (in.NP[ii[k]].w < 0.f) return false;
     jj[k] = in.nn[ii[k]];
     if (jj[k] < 0 || jj[k] >= in.nQ) return false;
@@ -85,7 +87,20 @@ constexpr int kHypThreads = 256;
 constexpr int kHypIters = 16;
 constexpr int kHypPerBlock = kHypThreads * kHypIters;
 
+#ifdef LSR_CHECKED
+// Test probe (lsr_debug_inject LSR_INJECT_CHECK): when armed, the first
+// thread of the next hypothesis count asks one out-of-range index question of
+// the check machinery -- no memory access follows it -- and disarms.
+static __device__ int g_check_probe;
+#endif
+
 __global__ void __launch_bounds__(kHypThreads) k_hyp_count(HypIn in, int64_t H, int *block_counts) {
+#ifdef LSR_CHECKED
+  if (blockIdx.x == 0 && threadIdx.x == 0 && g_check_probe) {
+    g_check_probe = 0;
+    (void)LSR_IN_BOUNDS(in.nP, in.nP, kSiteProbe);
+  }
+#endif
   int cnt = 0;
   int64_t base = (int64_t)blockIdx.x * kHypPerBlock;
   for (int it = 0; it < kHypIters; ++it) {
@@ -492,5 +507,18 @@ cudaError_t launch_select(const int *surv, const int *count, const unsigned long
   LSR_LAUNCH(k_select<<<1, 1024, 0, s>>>(surv, count, sum, ok, pose, nP, min_ratio, st));
   return cudaGetLastError();
 }
+
+// Arms the test probe on stream s (checked builds; else cudaErrorNotSupported).
+cudaError_t check_probe_arm(cudaStream_t s) {
+#ifdef LSR_CHECKED
+  static const int one = 1;
+  return cudaMemcpyToSymbolAsync(g_check_probe, &one, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+#else
+  (void)s;
+  return cudaErrorNotSupported;
+#endif
+}
+
+LSR_CHECK_READER(ransac)
 
 }  // namespace lsr

@@ -534,4 +534,6 @@ cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const
   return cudaGetLastError();
 }
 
+LSR_CHECK_READER(refine)
+
 }  // namespace lsr

@@ -14,7 +14,10 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblsr.so")
+# LSR_CHECKED=1 in the environment loads the checked build (device bounds
+# checks that report instead of trapping), built by _build.build(checked=True).
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib",
+                         "liblsr_checked.so" if os.environ.get("LSR_CHECKED") == "1" else "liblsr.so")
 _lib = None
 _lock = threading.Lock()
 
@@ -31,8 +34,11 @@ ABI_FUNCTIONS = (
     "lsr_stage_normals", "lsr_stage_spfh", "lsr_stage_fpfh", "lsr_stage_match", "lsr_stage_hypotheses",
     "lsr_stage_rigid4", "lsr_stage_consensus", "lsr_stage_refine", "lsr_objective_fwd", "lsr_objective_bwd",
     "lsr_consensus_static", "lsr_match_scores_bf16", "lsr_information_matrix", "lsr_surfel_correct",
-    "lsr_voxel_downsample",
+    "lsr_voxel_downsample", "lsr_debug_inject", "lsr_set_kernel_timing", "lsr_kernel_timing_count",
+    "lsr_kernel_timing_entry", "lsr_checked_build",
 )
+INJECT_NONE, INJECT_ALLOC, INJECT_MATCH_STALL, INJECT_CHECK = 0, 1, 2, 3
+LSR_E_CHECK = -7
 
 
 class LsrError(RuntimeError):
@@ -104,6 +110,12 @@ def lib():
             "lsr_information_matrix": (C.c_int, [vp, vp, i64, vp, i64, vp, f32, vp, vp]),
             "lsr_surfel_correct": (C.c_int, [vp, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
             "lsr_voxel_downsample": (C.c_int, [vp, vp, i64, f32, vp, i64, vp]),
+            "lsr_debug_inject": (C.c_int, [vp, i32, i32]),
+            "lsr_set_kernel_timing": (C.c_int, [vp, C.c_char_p]),
+            "lsr_checked_build": (C.c_int, []),
+            "lsr_kernel_timing_count": (i32, [vp]),
+            "lsr_kernel_timing_entry": (C.c_int, [vp, i32, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
+                                                  C.POINTER(C.c_double)]),
         }
         for name in ABI_FUNCTIONS:
             res, args = sig[name]
@@ -252,6 +264,26 @@ class Context:
 
     def set_profiling(self, on: bool = True):
         self._check(self._L.lsr_set_profiling(self._h, 1 if on else 0))
+
+    def debug_inject(self, kind: int, count: int = 1):
+        """Test hook (lsr_debug_inject): make the next `count` workspace
+        allocations fail (INJECT_ALLOC) or tensor-core matcher launches stall
+        into their bounded wait (INJECT_MATCH_STALL); INJECT_NONE clears."""
+        self._check(self._L.lsr_debug_inject(self._h, int(kind), int(count)))
+
+    def set_kernel_timing(self, prefix: str | None = ""):
+        """Time every launch whose kernel name starts with `prefix` ("" = all,
+        None = off) with CUDA events in later registrations; clears the table."""
+        self._check(self._L.lsr_set_kernel_timing(self._h, None if prefix is None else prefix.encode()))
+
+    def kernel_times(self) -> dict:
+        """{kernel name: (timed launches, total ms)} since set_kernel_timing."""
+        out = {}
+        for i in range(int(self._L.lsr_kernel_timing_count(self._h))):
+            nm, n, ms = C.c_char_p(), C.c_int64(), C.c_double()
+            self._check(self._L.lsr_kernel_timing_entry(self._h, i, C.byref(nm), C.byref(n), C.byref(ms)))
+            out[nm.value.decode()] = (int(n.value), float(ms.value))
+        return out
 
     def workspace_bytes(self) -> int:
         return int(self._L.lsr_workspace_bytes(self._h))
