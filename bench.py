@@ -176,6 +176,10 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     pk, _ = peaks()
     times, stages, last = [], np.zeros(8), None
+    # the dominant kernel is bracketed by two CUDA events on the context stream
+    # in every timed step (its only added work: two event records per step)
+    main_kernel = "k_match_fp32" if args.match == "fp32" else "k_match_tc"
+    ctx.set_kernel_timing(main_kernel)
     with ClockSampler(dev) as clk:
         l0 = lsr.launch_count()
         for _ in range(args.steps):
@@ -188,6 +192,8 @@ def run_ours(args, rank, world):
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         launches = lsr.launch_count() - l0
+    main_times = ctx.kernel_times()
+    ctx.set_kernel_timing(None)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -196,6 +202,7 @@ def run_ours(args, rank, world):
     # per-stage device times (and the FP32 matcher's term count) from profiled
     # runs after the timed region: stage events and the counting matcher
     ctx.set_profiling(True)
+    ctx.set_kernel_timing("")
     n_prof = min(args.steps, 3)
     for _ in range(n_prof):
         with torch.cuda.stream(stream):
@@ -203,6 +210,8 @@ def run_ours(args, rank, world):
         prof = ctx.register_pair(P, Q, fp.vpP, fp.vpQ)
         stages += np.array(prof.stage_ms)
     ctx.set_profiling(False)
+    kernel_times = ctx.kernel_times()
+    ctx.set_kernel_timing(None)
     stage_ms = stages / n_prof
 
     # end to end through the public API from pinned host memory
@@ -254,6 +263,7 @@ def run_ours(args, rank, world):
         vox_ms.append((time.perf_counter() - t0) * 1e3)
     h2d, d2h = lsr.transfer_bytes(nP, nQ)
     info = dict(fp=fp, nP=nP, nQ=nQ, last=last, prof=prof, stage_ms=stage_ms, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d,
+                main_kernel=main_kernel, main_times=main_times, kernel_times=kernel_times, n_prof=n_prof,
                 d2h=d2h, launches=launches, clocks=clk.summary(pk.get("sm_max_mhz")), peaks=pk,
                 information={"ms": float(np.median(info_ms)), "correspondences": int(n_corr), "eps": 0.05},
                 voxel={"ms": float(np.median(vox_ms)), "points": nP, "voxels": len(vox), "leaf": 0.05,
@@ -275,6 +285,8 @@ def run_ours(args, rank, world):
             vctx.set_profiling(True)
             for _ in range(args.warmup):
                 vctx.register_pair(P, Q, fp.vpP, fp.vpQ)
+            vkern = "k_match_fp32" if name == "fp32" else "k_match_tc"
+            vctx.set_kernel_timing(vkern)
             vt, vst, vl = [], np.zeros(8), None
             for _ in range(args.steps):
                 with torch.cuda.stream(stream):
@@ -286,12 +298,38 @@ def run_ours(args, rank, world):
                 e1.synchronize()
                 vt.append(e0.elapsed_time(e1))
                 vst += np.array(vl.stage_ms)
+            vtimes = vctx.kernel_times()
             vctx.close()
             info["variants"][name] = {
                 "value": args.steps / (sum(vt) * 1e-3), "unit": "pairs/s", "ms_per_step": sum(vt) / args.steps,
                 "match_ms": float(vst[3] / args.steps), "match_fallbacks": vl.match_fallbacks,
-                "identical_pose": bool(np.array_equal(vl.T, last.T)) and vl.inliers == last.inliers}
+                "identical_pose": bool(np.array_equal(vl.T, last.T)) and vl.inliers == last.inliers,
+                "kernel_times": vtimes}
     return info
+
+
+# ---------------------------------------------------------------- oracle poses
+GOLDEN = os.path.join(ROOT, "tests", "golden", "registrations.json")
+
+
+def golden_entries():
+    """Complete FP64 oracle registrations stored by tests/golden/make_registrations.py."""
+    try:
+        with open(GOLDEN) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def golden_error(config: int, pair: int, pair_id: int, T):
+    """(deg, m) between a pose and the oracle's registration of the same pair
+    and RNG key, or None if that registration is not stored."""
+    from synth import pose_error
+    e = golden_entries().get(f"c{config}_p{pair}_k{pair_id}")
+    if e is None:
+        return None
+    ang, tr = pose_error(np.asarray(T), np.array(e["T"]).reshape(4, 4))
+    return {"deg": ang, "mm": tr * 1e3, "within_0.05deg_0.5mm": bool(ang < 0.05 and tr < 5e-4)}
 
 
 # ---------------------------------------------------------------- configs 2-4
@@ -394,6 +432,67 @@ def run_batch(args, rank, world, pairs):
                           "peak_source": "MEASURED_PEAKS.json bf16 burst (cuBLAS)"})
 
 
+def run_headline(dev, pairs, steps=2):
+    """The headline comparison on config 2's 256 uneven room pairs: the batched
+    tensor-core path (one lsr_register_batch per step: BF16 matching with FP32
+    re-rank, concurrent streams, one CUDA graph, autotuned tiles) against the
+    plain FP32 path registering the same pairs one lsr_register_pair after
+    another, both timed with CUDA events on resident inputs in this run. Parity:
+    the two paths' poses must be identical, and the poses of the pairs that have
+    a stored FP64 oracle registration are compared with it."""
+    import torch
+
+    import paper_1801_01572_gb300 as lsr
+    P = [torch.from_numpy(p[0]).cuda() for p in pairs]
+    Q = [torch.from_numpy(p[1]).cuda() for p in pairs]
+    vp = np.concatenate([np.concatenate([p[2], p[3]]) for p in pairs]).astype(np.float32)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    bctx = lsr.Context(dev, stream=stream.cuda_stream, match_precision=MATCH_MODES["bf16"], batch_graph=1)
+    for _ in range(3):  # tunes tiles and streams, captures the graph, replays once
+        bctx.register_batch(P, Q, vp)
+    bt = []
+    for _ in range(steps):
+        ms, res = _timed(stream, flush, lambda: bctx.register_batch(P, Q, vp))
+        bt.append(ms)
+    bctx.close()
+    sctx = lsr.Context(dev, stream=stream.cuda_stream)
+    sctx.register_pair(P[0], Q[0], pairs[0][2], pairs[0][3])
+
+    def singles():
+        out = []
+        for i in range(len(pairs)):
+            sctx.set_params(pair_id=i)
+            out.append(sctx.register_pair(P[i], Q[i], pairs[i][2], pairs[i][3]))
+        return out
+    single_ms, single = _timed(stream, flush, singles)
+    sctx.close()
+    n = len(pairs)
+    identical = all(np.array_equal(single[i].T, res[i].T) and single[i].inliers == res[i].inliers for i in range(n))
+    errs = {}
+    for i in range(n):
+        g = golden_error(2, i, i, res[i].T)
+        if g is not None:
+            errs[f"pair {i} ({len(pairs[i][0])} + {len(pairs[i][1])} points)"] = g
+    batched = n * steps / (sum(bt) * 1e-3)
+    single_rate = n / (single_ms * 1e-3)
+    return {"workload": WORKLOADS[2], "pairs": n, "points": int(sum(len(p[0]) + len(p[1]) for p in pairs)),
+            "batched_bf16": {"value": batched, "unit": "pairs/s", "ms_per_batch": sum(bt) / steps, "steps": steps},
+            "fp32_single_pair": {"value": single_rate, "unit": "pairs/s", "ms_all_pairs": single_ms},
+            "speedup": batched / single_rate,
+            "identical_poses_all_pairs": bool(identical),
+            "aligned": int(sum(r.status == 0 for r in res)),
+            "oracle_pose_error": {"pairs_compared": len(errs),
+                                  "max_deg": max((e["deg"] for e in errs.values()), default=None),
+                                  "max_mm": max((e["mm"] for e in errs.values()), default=None),
+                                  "all_within_0.05deg_0.5mm": all(e["within_0.05deg_0.5mm"] for e in errs.values())
+                                  if errs else None,
+                                  "per_pair": errs,
+                                  "reference": "complete FP64 oracle registrations of the same pairs and RNG keys "
+                                               "(tests/golden/registrations.json)"},
+            "l2": "flushed before each timed call by a 256 MB write outside the timed events"}
+
+
 def run_objective(args, rank, world, pairs):
     """Config 4: one batched forward + backward of the robust alignment objective
     over all pairs per step (RobustAlignBatch), nearest neighbours recomputed in
@@ -455,60 +554,140 @@ def run_objective(args, rank, world, pairs):
                 clocks=clk.summary(pk.get("sm_max_mhz")), h2d=12 * npts, d2h=12 * npts + 8 * n)
 
 
+def _kernel_avg_ms(times: dict, prefix: str):
+    """(launches, average ms) of the timed kernels whose name starts with prefix."""
+    n = sum(v[0] for k, v in times.items() if k.startswith(prefix))
+    ms = sum(v[1] for k, v in times.items() if k.startswith(prefix))
+    return n, (ms / n if n else None)
+
+
+def fp32_alu_peak(sm_mhz: float) -> float:
+    """Issue peak of the matcher's instruction mix, TFLOP/s: one FADD and one
+    FFMA per term (3 flop in 2 issue slots, 1.5 flop per lane per cycle)."""
+    return N_SM * FP32_LANES_PER_SM * 1.5 * sm_mhz * 1e6 / 1e12
+
+
 def roofline(info):
-    """Roofline of the kernel that dominates the step (from the stage timers)."""
+    """Roofline of the kernel that dominates the step, from its CUDA-event
+    durations in the timed steps (events on the context stream around each of
+    its launches)."""
     pk, src = peaks()
-    st = info["stage_ms"]
-    nP, nQ, last = info["nP"], info["nQ"], info["last"]
-    names = ["grids", "normals", "features", "matching", "hypotheses", "consensus", "refinement"]
-    k = int(np.argmax(st[:7]))
+    nP, nQ = info["nP"], info["nQ"]
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # FFMA TFLOP/s
-    if names[k] == "matching" and info["match"] != "fp32":
-        # tensor-core contraction: 2 flop per multiply-add over K = 112 (hi/lo
-        # split) or 48 (plain) operand columns, for every (query, database row)
+    n, avg = _kernel_avg_ms(info["main_times"], info["main_kernel"])
+    if info["main_kernel"] == "k_match_tc":
         K = 112 if info["match"] == "bf16" else 48
         flops = 2.0 * float(nP) * float(nQ) * K
-        ach = flops / (st[k] * 1e-3) / 1e12
+        ach = flops / (avg * 1e-3) / 1e12
         peak = float(pk["bf16_tflops"])
         return {"kernel": "k_match_tc", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "peak_source": f"{src} bf16 burst (cuBLAS)",
-                "work": f"2*nP*nQ*{K} flop (stage time incl. operand preparation, re-rank and exact fallback)"}
-    if names[k] == "matching":
-        # brute-force FP32 NN: per (query, candidate) pair 33 terms of one subtract and
-        # one fused multiply-add (3 flop, 2 issue slots: the mix's peak is 1.5 flop per
-        # lane per cycle). The exact early exit skips most terms, so the dense
-        # definition's rate can exceed the pipe; executed_frac is the executed terms'
-        # share of the pipe (terms counted by the profiled matcher launch).
-        dense = float(nP) * float(nQ) * 33
-        ach = dense * 3 / (st[k] * 1e-3) / 1e12
-        peak = N_SM * FP32_LANES_PER_SM * 1.5 * sm_mhz * 1e6 / 1e12
-        terms = float(info["prof"].match_terms)
-        # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
-        # (profiles/k_match_fp32_room150k_dram.md)
-        traffic = 43850752 + 2816 if (nP, nQ) == (150000, 150000) else None
-        return {"kernel": "k_match_fp32", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": traffic,
-                "executed_terms": terms, "executed_share": terms / dense,
-                "executed_frac": terms * 3 / (st[k] * 1e-3) / 1e12 / peak,
-                "note": "frac counts the dense definition's work; the exact early exits skip most terms, so it "
-                        "exceeds 1 by design; executed_frac is the pipe share of the terms actually evaluated",
-                "peak_source": f"152 SMs x 128 FP32 lanes x 1.5 flop x {sm_mhz:.0f} MHz (FADD+FFMA issue peak)",
-                "work": "nP*nQ*33 terms x 3 flop (dense definition)"}
-    if names[k] == "consensus":
-        # per (hypothesis, point) query: the rigid transform (9 FMA) and the
-        # squared-distance test of the points within eps (counted at one candidate)
-        q = float(last.n_normal_ok) * nP
-        flops = q * (18 + 8)
-        ach = flops / (st[k] * 1e-3) / 1e12
-        return {"kernel": "k_consensus", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None, "queries": q,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz", "work": "queries*26 flop"}
-    # other stages: report HBM against the algorithmic bytes of the stage's inputs and outputs
-    bytes_ = float(nP + nQ) * (12 + 16 * 4 + 2 * 144)
-    ach = bytes_ / (st[k] * 1e-3) / 1e9
-    return {"kernel": names[k], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": src}
+                "frac": ach / peak, "traffic": None, "launch_ms": avg, "launches_timed": n,
+                "peak_source": f"{src} bf16 burst (cuBLAS), of measured",
+                "work": f"2*nP*nQ*{K} flop per launch (the contraction the kernel executes)"}
+    # FP32 matcher: the terms it evaluates (counted by the profiled launch; the
+    # count does not depend on timing), one subtract and one fused multiply-add
+    # each, against the issue peak of that mix
+    terms = float(info["prof"].match_terms)
+    dense = float(nP) * float(nQ) * 33
+    peak = fp32_alu_peak(sm_mhz)
+    ach = terms * 3 / (avg * 1e-3) / 1e12
+    # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
+    # (profiles/k_match_fp32_room150k_dram.md)
+    traffic = 43850752 + 2816 if (nP, nQ) == (150000, 150000) else None
+    return {"kernel": "k_match_fp32", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": traffic, "launch_ms": avg, "launches_timed": n,
+            "algorithmic_bytes": 144.0 * (nP + nQ) + 8.0 * nP,
+            "executed_terms": terms, "executed_share": terms / dense,
+            "dense_equivalent": {"achieved": dense * 3 / (avg * 1e-3) / 1e12, "unit": "TFLOP/s",
+                                 "note": "rate of the definition's nP*nQ*33 terms; the exact early exits skip "
+                                         f"{100 * (1 - terms / dense):.1f}% of them, so it is no roofline fraction"},
+            "peak_source": f"152 SMs x 128 FP32 lanes x 1.5 flop x {sm_mhz:.0f} MHz (FADD+FFMA issue peak)",
+            "work": "executed terms x 3 flop (subtract + fused multiply-add), terms counted by the profiled launch"}
+
+
+def roofline_tc(info):
+    """Tensor-pipe roofline of the BF16 matcher from the bf16 variant's timed
+    steps: the contraction at the configuration's padded K = 48 and at the
+    K = 112 the hi/lo operand split executes, against the measured BF16 peak."""
+    v = info.get("variants", {}).get("bf16")
+    if not v or "kernel_times" not in v:
+        return None
+    pk, src = peaks()
+    n, avg = _kernel_avg_ms(v["kernel_times"], "k_match_tc")
+    if not avg:
+        return None
+    nP, nQ = float(info["nP"]), float(info["nQ"])
+    peak = float(pk["bf16_tflops"])
+    a48 = 2 * nP * nQ * 48 / (avg * 1e-3) / 1e12
+    a112 = 2 * nP * nQ * 112 / (avg * 1e-3) / 1e12
+    return {"kernel": "k_match_tc", "bound": "tensor", "launch_ms": avg, "launches_timed": n, "peak": peak,
+            "unit": "TFLOP/s", "peak_source": f"{src} bf16 burst (cuBLAS), of measured",
+            "padded_k48": {"achieved": a48, "frac": a48 / peak, "work": "2*nP*nQ*48 flop (the configuration's "
+                                                                        "descriptors zero-padded to 48)"},
+            "executed_k112": {"achieved": a112, "frac": a112 / peak, "work": "2*nP*nQ*112 flop (hi/lo BF16 split "
+                                                                            "the kernel executes)"},
+            "match_fallbacks": v.get("match_fallbacks"), "traffic": None}
+
+
+# Algorithmic HBM bytes (or flops) of one registration step per kernel family,
+# from the arrays each kernel reads and writes once (the work column of the
+# kernel table in the design notes); both clouds together.
+def _kernel_work(name, nP, nQ, res, prm, terms):
+    N = nP + nQ
+    S, n_ok, H = res.survivors, res.n_normal_ok, int(prm.n_hypotheses)
+    table = [
+        ("k_match_fp32", "alu", 3.0 * terms, "flop", "executed terms x 3 flop"),
+        ("k_match_tc", "tensor", 2.0 * nP * nQ * 112, "flop", "2*nP*nQ*112 flop"),
+        ("k_normals", "hbm", 48.0 * N, "B", "16 B point + 16 B grid copy in, 16 B normal out"),
+        ("k_spfh", "hbm", 176.0 * N, "B", "16 B point + 16 B normal in, 144 B SPFH row out"),
+        ("k_fpfh", "hbm", 320.0 * N, "B", "16 B point + 16 B normal + 144 B SPFH row in, 144 B FPFH row out"),
+        ("k_tile_bounds", "hbm", 144.0 * nQ + 288.0 * nQ / 64, "B", "144 B FPFH row in, 288 B per 64-row tile out"),
+        ("k_prep_tiles", "hbm", (144.0 + 224.0) * N, "B", "144 B FPFH row in, 224 B BF16 operand row out"),
+        ("k_hyp_count", "hbm", 36.0 * N, "B", "unique bytes of the sampled arrays (points, normals, nn)"),
+        ("k_hyp_write", "hbm", 36.0 * N + 4.0 * S, "B", "as k_hyp_count + 4 B per survivor id"),
+        ("k_rigid_survivors", "hbm", 321.0 * S, "B", "per survivor 4 x (P, Q points and normals, nn) in, 49 B out"),
+        ("k_consensus_count<true>", "hbm", 16.0 * nP + 56.0 * n_ok, "B",
+         "16 B per P point, 56 B per normal-checked pose (L1/L2-resident table lookups dominate)"),
+        ("k_pack", "hbm", 28.0 * N, "B", "12 B xyz in, 16 B float4 out"),
+        ("k_bbox_partial", "hbm", 12.0 * N, "B", "12 B xyz in"),
+    ]
+    for pre, bound, work, unit, what in table:
+        if name.startswith(pre):
+            return bound, work, unit, what
+    return None
+
+
+def kernel_table(info):
+    """Every kernel of the profiled steps: launches per step, average duration,
+    share of the summed kernel time, and, where the work is defined, the
+    achieved rate against the relevant peak."""
+    pk, src = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    steps = info["n_prof"]
+    kt = info["kernel_times"]
+    tot = sum(v[1] for v in kt.values()) or 1.0
+    rows = []
+    for name, (n, ms) in sorted(kt.items(), key=lambda x: -x[1][1]):
+        row = {"kernel": name, "launches_per_step": n / steps, "avg_us": 1e3 * ms / n, "share": ms / tot}
+        w = _kernel_work(name, info["nP"], info["nQ"], info["prof"], info["params"],
+                         float(info["prof"].match_terms))
+        if w is not None:
+            bound, work, unit, what = w
+            per_step_s = ms / steps * 1e-3
+            if unit == "B":
+                ach = work / per_step_s / 1e9
+                row.update(bound=bound, work_per_step=work, achieved=ach, unit="GB/s", peak=pk["hbm_gbs"],
+                           frac=ach / pk["hbm_gbs"], work=what)
+            else:
+                ach = work / per_step_s / 1e12
+                peak = fp32_alu_peak(sm_mhz) if bound == "alu" else float(pk["bf16_tflops"])
+                row.update(bound=bound, work_per_step=work, achieved=ach, unit="TFLOP/s", peak=peak,
+                           frac=ach / peak, work=what)
+        rows.append(row)
+    return {"source": f"CUDA events around every launch of {steps} profiled registrations after the timed steps "
+                      "(same resident inputs); shares are of the summed kernel time",
+            "peak_source": f"{src} (HBM, BF16); FP32 issue peak derived from 152 SMs x 128 lanes x {sm_mhz:.0f} MHz",
+            "kernels": rows}
 
 
 # ---------------------------------------------------------------- oracle timing
@@ -562,22 +741,54 @@ def cpu_sample(fp, n_ok: int, iters: int, H: int, budget: float = 1.0):
     return t_total, parts
 
 
-def cpu_baseline_line(fp, n_ok, iters, H, budget=1.0):
+CPU_SAMPLE = ("FP64 C oracle (pthreads): normals of all points; SPFH/FPFH of {pct:.0f}% of the points; descriptor "
+              "NN of {mq} queries; pre-rejection of {hs} hypotheses; consensus of {npose} poses (1 in 8 the true one); "
+              "2 refinement steps; each stage's time scaled by full size / sample size ({n_ok} normal-checked "
+              "hypotheses, {iters} refinement steps) and summed")
+
+
+def _sample_text(budget, n_ok, iters):
+    return CPU_SAMPLE.format(pct=2 * budget, mq=max(16, int(100 * budget)), hs=max(10_000, int(200_000 * budget)),
+                             npose=max(8, int(8 * budget)), n_ok=n_ok, iters=iters)
+
+
+def oracle_full_config0():
+    """Seconds of one complete oracle registration of the config-0 pair (5k + 5k
+    points): measured, not extrapolated."""
     import oracle
+    from synth import make_pair
+    fp = make_pair(0, 0)
+    t0 = time.perf_counter()
+    r = oracle.register(fp.P, fp.Q, fp.vpP, fp.vpQ, seed=0)
+    return time.perf_counter() - t0, r
+
+
+def cpu_baseline_line(fp, n_ok, iters, H, budget=4.0, config=1):
+    """The oracle on the host cores: the stage-sampled estimate for this
+    workload (the same sampling as --impl reference), and one complete
+    registration of the config-0 pair, measured."""
+    import oracle
+    oracle.build()
+    if config == 0:
+        secs, _ = oracle_full_config0()
+        return {"value": 1.0 / secs, "unit": "pairs/s", "cores": oracle.threads(), "kind": "oracle",
+                "estimate": False, "sample": "one complete FP64 oracle registration of the pair (5k + 5k points)"}
     secs, parts = cpu_sample(fp, n_ok, iters, H, budget)
-    return {"value": 1.0 / secs, "unit": "pairs/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": ("FP64 C oracle (pthreads): normals of all points; SPFH/FPFH of %.0f%% of the points; "
-                       "descriptor NN of %d queries; pre-rejection of %d hypotheses; consensus of %d poses; "
-                       "2 refinement steps; each scaled to the full pair (%d normal-checked hypotheses, "
-                       "%d refinement steps as the GPU run)") % (2 * budget, max(16, int(100 * budget)),
-                                                               max(10_000, int(200_000 * budget)),
-                                                               max(8, int(8 * budget)), n_ok, iters),
-            "stage_s": {k: round(v, 3) for k, v in parts.items()}}
+    c0, _ = oracle_full_config0()
+    return {"value": 1.0 / secs, "unit": "pairs/s", "cores": oracle.threads(), "kind": "oracle", "estimate": True,
+            "sample": _sample_text(budget, n_ok, iters), "formula": "1 / sum over stages (sample s x full / sample)",
+            "stage_s": {k: round(v, 3) for k, v in parts.items()},
+            "measured_config0": {"workload": WORKLOADS[0], "value": 1.0 / c0, "unit": "pairs/s", "seconds": c0,
+                                 "sample": "one complete FP64 oracle registration (not extrapolated)"}}
 
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
-    """The oracle on bounded samples of the workload, one sample per step."""
+    """The oracle on the host cores, one bounded sample of the workload per
+    step. On config 0 a step is one complete registration (measured); on the
+    larger configurations a step is the stage sample of cpu_sample, and its
+    value is the fraction of a pair the sample stands for over the step's wall
+    time (so steps x ms_per_step is the real duration of the run)."""
     if rank != 0:
         return None
     import oracle
@@ -587,23 +798,31 @@ def run_reference(args, rank, world):
     n_ok = {0: 6900, 1: 8700}.get(args.config, 8000)  # normal-checked hypotheses of the workload
     iters = 120
     H = 4_000_000
-    budget = 2.0
+    budget = 4.0
+    full = args.config == 0
     for _ in range(args.warmup):
-        cpu_sample(fp, n_ok, iters, H, budget=0.25)
-    secs = []
+        if not full:
+            cpu_sample(fp, n_ok, iters, H, budget=0.25)
+    walls, frac = [], []
     for _ in range(args.steps):
-        s, parts = cpu_sample(fp, n_ok, iters, H, budget=budget)
-        secs.append(s)
-    value = len(secs) / sum(secs)
+        t0 = time.perf_counter()
+        if full:
+            oracle_full_config0()
+            frac.append(1.0)
+        else:
+            est, _ = cpu_sample(fp, n_ok, iters, H, budget=budget)
+            frac.append((time.perf_counter() - t0) / est)
+        walls.append(time.perf_counter() - t0)
+    value = sum(frac) / sum(walls)
     cores = oracle.threads()
+    sample = "one complete FP64 oracle registration per step" if full else _sample_text(budget, n_ok, iters)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / len(walls),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.config], "parallelism": "host threads"},
-            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-                             "sample": "per step: normals of all points, 4% of SPFH/FPFH, 200 descriptor-NN "
-                                       "queries, 400k hypotheses, 16 consensus poses (1 in 8 the true one), "
-                                       "2 refinement steps, each scaled to the full pair"},
+            "pair_fraction_per_step": sum(frac) / len(frac),
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "estimate": not full},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return line
 
@@ -623,11 +842,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="do not also time the other descriptor matchers")
+    ap.add_argument("--no-headline", dest="headline", action="store_false",
+                    help="do not also time the batched BF16 path against the FP32 single-pair path on config 2")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", 1))
     rank = int(os.environ.get("RANK", 0))
     pairs = batch_pairs(args.config, rank) if args.config in BATCH_PAIRS and args.impl == "ours" else None
+    # the headline's 256 pairs are generated by host processes (spawned before
+    # any GPU work) while the single-pair workload runs
+    head_pool = head_async = None
+    if args.impl == "ours" and args.config in (0, 1) and args.headline and world == 1 and args.points is None:
+        import multiprocessing as mp
+        head_pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))
+        head_async = head_pool.map_async(_gen_pair, [(2, i) for i in rank_pair_ids(2, 0)], chunksize=2)
     if world > 1 and args.impl == "ours":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
@@ -697,17 +925,17 @@ def main():
                     "identical_pose": info["identical"]}},
                 "clocks": info["clocks"],
             }
-            if args.config == 3:
-                # pose error against the FP64 oracle on two pairs: the oracle's graduated
-                # refinement from the generator's pose reaches the fixed point the path converges to
-                import oracle
-                from synth import pose_error
-                errs = []
-                for i in (0, 1):
-                    T_ref, _ = oracle.refine_gnc(pairs[i][0], pairs[i][1], pairs[i][4], 0.0375, 1.0, levels=3, iters=50)
-                    errs.append(pose_error(info["res"][i].T, T_ref))
-                line["result"]["oracle_pose_error"] = {"deg": max(e[0] for e in errs), "m": max(e[1] for e in errs),
-                                                       "pairs": 2}
+            # pose error against complete FP64 oracle registrations of the pairs that have one
+            errs = {}
+            for i in range(N_BATCH):
+                g = golden_error(args.config, i, i, info["res"][i].T)
+                if g is not None:
+                    errs[f"pair {i}"] = g
+            line["result"]["oracle_pose_error"] = {
+                "pairs_compared": len(errs), "max_deg": max((e["deg"] for e in errs.values()), default=None),
+                "max_mm": max((e["mm"] for e in errs.values()), default=None),
+                "all_within_0.05deg_0.5mm": all(e["within_0.05deg_0.5mm"] for e in errs.values()) if errs else None,
+                "reference": "complete FP64 oracle registrations (tests/golden/registrations.json)"}
             print(json.dumps(line), flush=True)
         if world > 1:
             import torch
@@ -716,6 +944,13 @@ def main():
         return
 
     info = run_ours(args, rank, world)
+    headline = None
+    if head_async is not None:
+        head_pairs = head_async.get()
+        head_pool.close()
+        head_pool.join()
+        headline = run_headline(int(os.environ.get("LOCAL_RANK", 0)), head_pairs)
+        del head_pairs
     if rank == 0:
         K = args.steps
         value = job_rate(K, world, info["total_ms"])
@@ -737,8 +972,12 @@ def main():
                 ["grids", "normals", "features", "matching", "hypotheses", "consensus", "refinement", "total"],
                 info["stage_ms"])},
             "result": {"inliers": last.inliers, "survivors": last.survivors, "normal_ok": last.n_normal_ok,
-                       "refine_iters": last.refine_iters, "match_fallbacks": last.match_fallbacks},
+                       "refine_iters": last.refine_iters, "match_fallbacks": last.match_fallbacks,
+                       "oracle_pose_error": golden_error(args.config, rank, 0, last.T) if args.points is None
+                       else None},
             "roofline": roofline(info),
+            "roofline_tc": roofline_tc(info),
+            "kernels": kernel_table(info),
             "information_matrix": info["information"],
             "surfel_correction": info["surfels"],
             "voxel_downsample": info["voxel"],
@@ -748,9 +987,11 @@ def main():
             "variants": info["variants"],
             "clocks": info["clocks"],
         }
+        if headline is not None:
+            line["headline"] = headline
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_line(info["fp"], last.n_normal_ok, last.refine_iters,
-                                                     int(prm.n_hypotheses), budget=12.0)
+                                                     int(prm.n_hypotheses), budget=4.0, config=args.config)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch
