@@ -64,3 +64,33 @@ def test_static_scoring_matches_workspace_entry_point_twice():
         assert rc == lsr.LSR_E_TOO_LARGE
     finally:
         ctx.close()
+
+
+@gpu
+def test_static_scoring_with_host_arrays_on_a_caller_stream():
+    """Poses read from, and counts and sums written to, host arrays, with the
+    work ordered on a stream the caller created (the entry point copies the
+    host arrays itself and synchronises that stream before returning)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1801_01572_gb300 as lsr
+    L = lsr.lib()
+    rng = np.random.default_rng(47)
+    fp = make_pair(0, 2, n_p=3500, n_q=3000)
+    nh = 91
+    Rt = _poses(fp, rng, nh)
+    P = torch.from_numpy(fp.P).cuda()
+    Q = torch.from_numpy(fp.Q).cuda()
+    cnt = np.full(nh, -1, np.int32)
+    sd = np.full(nh, -1.0, np.float64)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    rc = L.lsr_consensus_static(C.c_void_p(P.data_ptr()), len(fp.P), C.c_void_p(Q.data_ptr()), len(fp.Q),
+                                C.c_void_p(Rt.ctypes.data), nh, C.c_float(0.0375), C.c_void_p(cnt.ctypes.data),
+                                C.c_void_p(sd.ctypes.data), C.c_void_p(stream.cuda_stream))
+    assert rc == lsr.LSR_OK, L.lsr_error_string(rc)
+    with lsr.Context(0) as ctx:
+        ref_cnt, ref_sd = ctx.stage_consensus(fp.P, fp.Q, Rt, 0.0375)
+    assert np.array_equal(cnt, ref_cnt)
+    assert np.allclose(sd, ref_sd, rtol=1e-9, atol=1e-12)
