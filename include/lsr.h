@@ -93,8 +93,20 @@ typedef struct {
                              parameters) is registered again; 0 (default) = launch directly */
   int32_t match_tile;     /* tensor-core matcher work unit: 1 or 2 query tiles of 128 per CTA; 0 (default) =
                              chosen per cloud size by the autotuner */
-  int32_t reserved_;
+  int32_t nn_mode;        /* inlier test of the consensus: LSR_NN_EXACT (default: the nearest Q point over every
+                             grid cell the eps-ball overlaps) or LSR_NN_SINGLE_CELL (the O(1) lookup of eq. (1):
+                             only the query's own cell of edge eps, centred on Q's centroid; approximate, it can
+                             only miss inliers) */
+  int32_t normal_mode;    /* normal check: LSR_NORMALS_SAMPLES (default: the 4 sampled pairs of a hypothesis) or
+                             LSR_NORMALS_INLIERS (every inlier instead: a point counts only if its nearest Q
+                             point's normal agrees with its rotated normal, cos >= cos_normal) */
+  int32_t reserved_[2];
 } lsr_params;
+
+#define LSR_NN_EXACT 0
+#define LSR_NN_SINGLE_CELL 1
+#define LSR_NORMALS_SAMPLES 0
+#define LSR_NORMALS_INLIERS 1
 
 /* Result of one registration. */
 typedef struct {
@@ -304,6 +316,35 @@ LSR_API int lsr_stage_consensus(lsr_ctx *ctx, const float *P, int64_t nP, const 
 LSR_API int lsr_consensus_static(const float *P, int64_t nP, const float *Q, int64_t nQ, const float *Rt, int64_t nh,
                                  float eps, int32_t *count, double *sumd2, void *cuda_stream);
 
+/* Consensus with the variant modes of lsr_params (nn_mode, normal_mode), on
+ * caller-supplied inputs: for each pose Rt (nh x 12, row-major [R | t]),
+ * count[k] = points p of P whose nearest Q point q -- exact (LSR_NN_EXACT) or
+ * in p's own cell of the eps lattice through Q's centroid
+ * (LSR_NN_SINGLE_CELL, eq. (1)) -- is closer than eps and, with
+ * LSR_NORMALS_INLIERS, whose rotated normal R n_p agrees with n_q
+ * (cos >= cos_normal, both normals non-zero); sumd2[k] = the sum of their
+ * squared distances. NP (nP x 3), NQ (nQ x 3): normals in the caller's order
+ * (zero = invalid), needed only with LSR_NORMALS_INLIERS. Every array may be
+ * device or host. The registration pipeline runs the same kernels when the
+ * context's modes are not the defaults. */
+LSR_API int lsr_stage_consensus_modes(lsr_ctx *ctx, const float *P, const float *NP, int64_t nP, const float *Q,
+                                      const float *NQ, int64_t nQ, const float *Rt, int64_t nh, float eps,
+                                      int32_t nn_mode, int32_t normal_mode, float cos_normal, int32_t *count,
+                                      double *sumd2);
+
+/* Nearest neighbours of the consensus (eq. (1) and the inlier test of Alg.
+ * 1): for every query x (X: nX x 3 float32), the nearest point of Q (nQ x 3
+ * float32), both device or host. mode LSR_NN_EXACT: the nearest Q point
+ * within r over every grid cell the r-ball overlaps (ties to the smaller
+ * index). mode LSR_NN_SINGLE_CELL: the O(1) lookup of eq. (1): Q binned into
+ * cells of edge r on a lattice through Q's centroid c (cell index
+ * floor((x - c) / r) per axis, evaluated in FP32), and the nearest point of
+ * the query's own cell, at any distance. nn (nX int32, device or host): the Q
+ * index or -1 (none within r / empty cell); d2 (nX float32, may be NULL): its
+ * squared distance or +inf. */
+LSR_API int lsr_stage_nn(lsr_ctx *ctx, const float *Q, int64_t nQ, const float *X, int64_t nX, float r, int32_t mode,
+                         int32_t *nn, float *d2);
+
 /* Graduated robust refinement from T_in (host, 4x4 row-major double). Level
  * l = 0..levels-1 iterates Geman-McClure IRLS (at most iters steps) with exact
  * NN within r_l = eps * 2^(levels-1-l), mu_l = mu_scale * r_l^2, on the points
@@ -346,6 +387,32 @@ LSR_API int lsr_objective_bwd(lsr_ctx *ctx, int32_t n, const float *const *P, co
  * pointers, sizes outside [1, 2^26], eps outside (0, 10] or a non-finite T. */
 LSR_API int lsr_information_matrix(lsr_ctx *ctx, const float *P, int64_t nP, const float *Q, int64_t nQ,
                                    const double *T, float eps, double *info, int64_t *n_corr);
+
+/* Gradient of the refined pose with respect to the points (implicit
+ * differentiation of the robust alignment of eq. (3)-(4) at its optimum; the
+ * pose perturbation of eq. (5)). At the refined pose T (the pose
+ * lsr_stage_refine or lsr_register_pair returns), the held pairs are the
+ * points p of P whose nearest Q point q lies within eps under T (the finest
+ * refinement level's correspondences, recomputed here), rho(s) = mu s /
+ * (mu + s). The optimality condition g(T) = 0 of E = sum rho(|T p - q|^2)
+ * makes T a function of the points; for a loss L with gradient dL_dT
+ * (host, 16 doubles, row-major d L / d T; the last row is ignored), it gives
+ *   lambda = H^-1 dL/dxi,  dL/dp = -R^T d(lambda . g_p)/dz,  dL/dq = -d(lambda . g_p)/dq,
+ * with xi = (w, v) the left perturbation T(xi) = [Exp(w) | v] T, g_p the pair's
+ * term of the gradient of E in xi and H its exact Hessian (rho'' and the
+ * second-order term of Exp included).
+ * P: nP x 3, Q: nQ x 3 float32 (device or host). T: 16 doubles (host).
+ * dP (nP x 3) and dQ (nQ x 3) float32: both device or both host, written
+ * (points without a pair get 0; a Q point sums the terms of every pair it
+ * closes). grad (6), hess (36, row-major), lambda (6): host doubles, each may
+ * be NULL: g, H and lambda at T. n_corr (host, may be NULL): held pairs. The
+ * terms are evaluated and summed in FP64 (fixed order over blocks), the
+ * neighbours found in FP32, dQ scattered with FP32 atomics. Errors: LSR_E_ARG
+ * for null pointers, sizes outside [1, 2^26], eps outside (0, 10], mu <= 0, a
+ * non-finite T or dL_dT, or a singular H (too few pairs). */
+LSR_API int lsr_pose_implicit_grad(lsr_ctx *ctx, const float *P, int64_t nP, const float *Q, int64_t nQ,
+                                   const double *T, float eps, float mu, const double *dL_dT, float *dP, float *dQ,
+                                   double *grad, double *hess, double *lambda, int64_t *n_corr);
 
 /* Voxel downsampling (Algorithm 1, first line): one point per occupied voxel
  * of edge leaf, the mean of the points in it. Voxels are aligned to the

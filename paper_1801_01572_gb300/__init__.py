@@ -9,7 +9,7 @@ from __future__ import annotations
 
 from .lsr import (DESC_DIM, LSR_E_ARG, LSR_E_CUDA, LSR_E_OOM, LSR_E_STATE, LSR_E_TIMEOUT, LSR_E_TOO_LARGE,  # noqa: F401
                   LSR_OK,
-                  MATCH_BF16, MATCH_BF16_PLAIN, MATCH_FP32, STATUS_ALIGNED, STATUS_NO_ALIGNMENT, ABI_FUNCTIONS, Context, LsrError,
+                  MATCH_BF16, MATCH_BF16_PLAIN, MATCH_FP32, NN_EXACT, NN_SINGLE_CELL, NORMALS_INLIERS, NORMALS_SAMPLES, STATUS_ALIGNED, STATUS_NO_ALIGNMENT, ABI_FUNCTIONS, Context, LsrError,
                   Params, Registration, context, default_params, launch_count, lib, library_path, register_pair,
                   transfer_bytes, INJECT_ALLOC, INJECT_CHECK, INJECT_MATCH_STALL, INJECT_NONE, LSR_E_CHECK)
 
@@ -64,6 +64,53 @@ class RobustAlignBatch:
     @classmethod
     def apply(cls, xis, T0s, eps, mu, lctx, *clouds):
         return cls.function().apply(xis, T0s, eps, mu, lctx, *clouds)
+
+
+class RefinedPose:
+    """T* = the graduated robust refinement of T0 (lsr_stage_refine: the
+    Geman-McClure IRLS of eq. (3)-(5)), differentiable in the points.
+
+    ``apply(P, Q, T0, eps, mu_scale, levels, iters, lctx)`` with P, Q CUDA
+    float32 (N, 3) tensors and T0 a (4, 4) float64 tensor; returns T* (4, 4)
+    float64. The backward differentiates the optimality condition at T*
+    (lsr_pose_implicit_grad, on the finest level's pairs, recomputed): the
+    gradient reaches P and Q; T0 gets none (the optimum does not move with the
+    start inside its basin)."""
+
+    _fn = None
+
+    @classmethod
+    def function(cls):
+        if cls._fn is None:
+            torch = _torch()
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(fctx, P, Q, T0, eps, mu_scale, levels, iters, lctx):
+                    T, _ = lctx.stage_refine(P.detach(), Q.detach(), T0.detach().cpu().numpy(), eps, mu_scale,
+                                             levels, iters)
+                    Tt = torch.as_tensor(T, dtype=torch.float64, device=T0.device)
+                    fctx.save_for_backward(P, Q, Tt)
+                    fctx.eps, fctx.mu, fctx.lctx = eps, mu_scale * eps * eps, lctx
+                    return Tt
+
+                @staticmethod
+                def backward(fctx, gT):
+                    P, Q, Tt = fctx.saved_tensors
+                    dP = torch.empty(P.shape, dtype=torch.float32, device=P.device)
+                    dQ = torch.empty(Q.shape, dtype=torch.float32, device=Q.device)
+                    fctx.lctx.pose_implicit_grad(P.detach().contiguous(), Q.detach().contiguous(),
+                                                 Tt.detach().cpu().numpy(), gT.detach().cpu().numpy(), fctx.eps,
+                                                 fctx.mu, dP, dQ)
+                    return dP.to(P.dtype), dQ.to(Q.dtype), None, None, None, None, None, None
+
+            cls._fn = _F
+        return cls._fn
+
+    @classmethod
+    def apply(cls, P, Q, T0, eps=0.0375, mu_scale=1.0, levels=3, iters=50, lctx=None):
+        lctx = lctx or context(P.device.index or 0)
+        return cls.function().apply(P, Q, T0, eps, mu_scale, levels, iters, lctx)
 
 
 def robust_align(P, Q, xi, T0, eps: float = 0.0375, mu: float | None = None, lctx: Context | None = None):

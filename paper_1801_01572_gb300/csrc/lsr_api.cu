@@ -301,6 +301,11 @@ struct PairLayout {
   uint8_t *tie = nullptr;    // those tied at the maximum exact count
   int *amb = nullptr;        // points in undecided voxels per hypothesis
   int *count2 = nullptr;     // exact counts of the reaching hypotheses
+  // single-cell lattice of Q (lsr_params.nn_mode = LSR_NN_SINGLE_CELL)
+  int cap_s = 0;
+  GridParams *gs = nullptr;
+  int *start_s = nullptr;
+  float4 *Xs = nullptr;
 };
 
 int surv_cap_for(int64_t H) { return (int)std::min<int64_t>(H, (int64_t)1 << 22); }
@@ -339,6 +344,10 @@ void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int leve
   L.count2 = a.take<int>(L.surv_cap);
   L.tc_ws = a.take<char>(precision != LSR_MATCH_FP32 ? tc_workspace_bytes(nP, nQ, precision == LSR_MATCH_BF16)
                                                       : fp32_workspace_bytes(nQ));
+  L.cap_s = L.Q.cap_e;
+  L.gs = a.take<GridParams>(1);
+  L.start_s = a.take<int>((size_t)L.cap_s + 1);
+  L.Xs = a.take<float4>(nQ);
 }
 
 int set_err(lsr_ctx *c, int code, const char *msg) {
@@ -370,12 +379,15 @@ int cuda_err(lsr_ctx *c, cudaError_t e, const char *where) {
 int check_report(lsr_ctx *c) {
   static cudaError_t (*const readers[])(CheckReport *) = {check_read_features, check_read_match,
                                                           check_read_match_tc, check_read_ransac,
-                                                          check_read_classify, check_read_refine};
-  static const char *const units[] = {"features", "match", "match_tc", "ransac", "classify", "refine"};
+                                                          check_read_classify, check_read_refine,
+                                                          check_read_nn,       check_read_implicit};
+  static const char *const units[] = {"features", "match", "match_tc", "ransac",
+                                      "classify", "refine", "nn",       "implicit"};
+  constexpr int kUnits = (int)(sizeof(units) / sizeof(units[0]));
   static const char *const sites[] = {"?", "grid row", "grid cell", "grid point", "hypothesis sample",
                                       "hypothesis match", "matcher row", "matcher query", "probe"};
   int rc = LSR_OK;
-  for (int u = 0; u < 6; ++u) {
+  for (int u = 0; u < kUnits; ++u) {
     CheckReport r{0, 0, 0};
     cudaError_t e = readers[u](&r);
     if (e != cudaSuccess) return cuda_err(c, e, "check words");
@@ -485,6 +497,9 @@ int check_params(const lsr_params *p) {
   if (p->eps_inlier > 10.f) return LSR_E_ARG;  // fixed-point inlier sums assume eps^2 * |P| << 2^23
   if (p->batch_streams < 0 || p->batch_streams > 16 || (p->batch_graph != 0 && p->batch_graph != 1) ||
       p->match_tile < 0 || p->match_tile > 2)
+    return LSR_E_ARG;
+  if ((p->nn_mode != LSR_NN_EXACT && p->nn_mode != LSR_NN_SINGLE_CELL) ||
+      (p->normal_mode != LSR_NORMALS_SAMPLES && p->normal_mode != LSR_NORMALS_INLIERS))
     return LSR_E_ARG;
   return LSR_OK;
 }
@@ -662,43 +677,68 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
                              pair_id, p.tau, L.blk_cnt, L.blk_off, L.blk_scan, L.surv, L.surv_cap, L.st, s),
            "hypotheses");
   tm.mark();
+  // with the per-inlier normal check the sampled pairs are not checked (a
+  // cosine threshold below -1 passes every hypothesis)
+  const bool inlier_normals = p.normal_mode == LSR_NORMALS_INLIERS;
   TRY_CUDA(c,
            launch_rigid_survivors(Pc.X, Pc.inv, Pc.N, nP, Qc.X, Qc.N, L.nn, L.surv, L.st, p.seed, pair_id,
-                                  p.cos_normal, L.pose, L.ok, &L.st->n_normal_ok, s),
+                                  inlier_normals ? -2.f : p.cos_normal, L.pose, L.ok, &L.st->n_normal_ok, s),
            "rigid");
-  // Inlier-count bounds of every survivor from the voxel classification of Q;
-  // exact counts of the 32 largest upper bounds give C; exact counts of the
-  // others whose upper bound reaches C; distance sums of the top ties. No
-  // survivor left out can be selected. P is read in normal-grid order (5 cm
-  // cells): the counts and fixed-point sums do not depend on the order, and
-  // a warp's points then land on fewer table words.
-  TRY_CUDA(c, launch_cls_build(Qc.box, p.eps_inlier, Qc.X, nQ, L.cls, L.in_bits, L.near_bits, s), "classify");
-  TRY_CUDA(c, cudaMemsetAsync(L.count, 0, sizeof(int) * L.surv_cap, s), "memset count");
-  TRY_CUDA(c, cudaMemsetAsync(L.amb, 0, sizeof(int) * L.surv_cap, s), "memset count");
-  TRY_CUDA(c, cudaMemsetAsync(L.count2, 0, sizeof(int) * L.surv_cap, s), "memset count");
-  TRY_CUDA(c, cudaMemsetAsync(L.sum, 0, sizeof(unsigned long long) * L.surv_cap, s), "memset sum");
-  TRY_CUDA(c,
-           launch_consensus_bounds(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, L.pose, L.ok, &L.st->n_surv, L.count,
-                                   L.amb, s),
-           "consensus bounds");
-  TRY_CUDA(c, launch_top_upper(L.count, L.amb, L.ok, &L.st->n_surv, 32, L.sel, s), "top");
-  TRY_CUDA(c,
-           launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.sel,
-                                  &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
-           "consensus top");
-  TRY_CUDA(c, launch_reach_rest(L.count, L.amb, L.count2, L.sel, L.ok, &L.st->n_surv, L.rest, L.reach, s), "reach");
-  TRY_CUDA(c,
-           launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.rest,
-                                  &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
-           "consensus reach");
-  TRY_CUDA(c, launch_reach_mask(L.count2, nullptr, L.reach, &L.st->n_surv, L.tie, s), "ties");
-  // (the exact kernel adds its counts too: into amb, no longer needed)
-  TRY_CUDA(c,
-           launch_consensus(Pc.Xn, nP, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.tie, &L.st->n_surv, 0, p.eps_inlier,
-                            L.amb, L.sum, s, c->cons_lanes),
-           "consensus sums");
-  tm.mark();
-  TRY_CUDA(c, launch_select(L.surv, L.count2, L.sum, L.reach, L.pose, nP, p.min_inlier_ratio, L.st, s), "select");
+  if (p.nn_mode != LSR_NN_EXACT || inlier_normals) {
+    // variant consensus: every ok survivor counted with the single-cell lookup
+    // and/or the per-inlier normal check (no classification bounds)
+    const bool single = p.nn_mode == LSR_NN_SINGLE_CELL;
+    const GridParams *g = Qc.ge;
+    const int *gstart = Qc.start_e;
+    const float4 *gx = Qc.Xe;
+    if (single) {
+      TRY_CUDA(c, launch_cell_grid_params(Qc.box, p.eps_inlier, nQ, L.cap_s, L.gs, s), "single-cell grid");
+      TRY_CUDA(c, build_grid_f4(Qc.X, nQ, L.gs, L.cap_s, L.start_s, L.Xs, L.sc.g, s), "single-cell grid");
+      g = L.gs, gstart = L.start_s, gx = L.Xs;
+    }
+    TRY_CUDA(c, cudaMemsetAsync(L.count, 0, sizeof(int) * L.surv_cap, s), "memset count");
+    TRY_CUDA(c, cudaMemsetAsync(L.sum, 0, sizeof(unsigned long long) * L.surv_cap, s), "memset sum");
+    TRY_CUDA(c,
+             launch_consensus_variant(Pc.Xn, nP, Pc.N, g, gstart, gx, Qc.N, nQ, L.pose, L.ok, &L.st->n_surv,
+                                      p.eps_inlier, single, inlier_normals, p.cos_normal, L.count, L.sum, s),
+             "consensus variant");
+    tm.mark();
+    TRY_CUDA(c, launch_select(L.surv, L.count, L.sum, L.ok, L.pose, nP, p.min_inlier_ratio, L.st, s), "select");
+  } else {
+    // Inlier-count bounds of every survivor from the voxel classification of Q;
+    // exact counts of the 32 largest upper bounds give C; exact counts of the
+    // others whose upper bound reaches C; distance sums of the top ties. No
+    // survivor left out can be selected. P is read in normal-grid order (5 cm
+    // cells): the counts and fixed-point sums do not depend on the order, and
+    // a warp's points then land on fewer table words.
+    TRY_CUDA(c, launch_cls_build(Qc.box, p.eps_inlier, Qc.X, nQ, L.cls, L.in_bits, L.near_bits, s), "classify");
+    TRY_CUDA(c, cudaMemsetAsync(L.count, 0, sizeof(int) * L.surv_cap, s), "memset count");
+    TRY_CUDA(c, cudaMemsetAsync(L.amb, 0, sizeof(int) * L.surv_cap, s), "memset count");
+    TRY_CUDA(c, cudaMemsetAsync(L.count2, 0, sizeof(int) * L.surv_cap, s), "memset count");
+    TRY_CUDA(c, cudaMemsetAsync(L.sum, 0, sizeof(unsigned long long) * L.surv_cap, s), "memset sum");
+    TRY_CUDA(c,
+             launch_consensus_bounds(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, L.pose, L.ok, &L.st->n_surv, L.count,
+                                     L.amb, s),
+             "consensus bounds");
+    TRY_CUDA(c, launch_top_upper(L.count, L.amb, L.ok, &L.st->n_surv, 32, L.sel, s), "top");
+    TRY_CUDA(c,
+             launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.sel,
+                                    &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
+             "consensus top");
+    TRY_CUDA(c, launch_reach_rest(L.count, L.amb, L.count2, L.sel, L.ok, &L.st->n_surv, L.rest, L.reach, s), "reach");
+    TRY_CUDA(c,
+             launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.rest,
+                                    &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
+             "consensus reach");
+    TRY_CUDA(c, launch_reach_mask(L.count2, nullptr, L.reach, &L.st->n_surv, L.tie, s), "ties");
+    // (the exact kernel adds its counts too: into amb, no longer needed)
+    TRY_CUDA(c,
+             launch_consensus(Pc.Xn, nP, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.tie, &L.st->n_surv, 0, p.eps_inlier,
+                              L.amb, L.sum, s, c->cons_lanes),
+             "consensus sums");
+    tm.mark();
+    TRY_CUDA(c, launch_select(L.surv, L.count2, L.sum, L.reach, L.pose, nP, p.min_inlier_ratio, L.st, s), "select");
+  }
   TRY_CUDA(c, launch_refine_init(L.st, Pc.box, nullptr, s), "refine init");
   float eps = p.eps_inlier;
   TRY_CUDA(c,
@@ -1852,6 +1892,219 @@ int lsr_information_matrix(lsr_ctx *c, const float *P, int64_t nP, const float *
   SYNC_CHECKED(c, s);
   for (int k = 0; k < 36; ++k) info[k] = host[k];
   if (n_corr) *n_corr = (int64_t)host[36];
+  return LSR_OK;
+}
+
+int lsr_stage_consensus_modes(lsr_ctx *c, const float *P, const float *NP, int64_t nP, const float *Q, const float *NQ,
+                              int64_t nQ, const float *Rt, int64_t nh, float eps, int32_t nn_mode, int32_t normal_mode,
+                              float cos_normal, int32_t *count, double *sumd2) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!P || !Q || !Rt || !count || !sumd2 || nP < 1 || nQ < 1 || nP > kMaxPoints || nQ > kMaxPoints || nh < 1 ||
+      nh > ((int64_t)1 << 26) || !(eps > 0.f && eps <= 10.f))
+    return set_err(c, LSR_E_ARG, "bad argument");
+  if ((nn_mode != LSR_NN_EXACT && nn_mode != LSR_NN_SINGLE_CELL) ||
+      (normal_mode != LSR_NORMALS_SAMPLES && normal_mode != LSR_NORMALS_INLIERS))
+    return set_err(c, LSR_E_ARG, "bad mode");
+  const bool normals = normal_mode == LSR_NORMALS_INLIERS, single = nn_mode == LSR_NN_SINGLE_CELL;
+  if (normals && (!NP || !NQ || !(cos_normal >= -1.f && cos_normal <= 1.f)))
+    return set_err(c, LSR_E_ARG, "the per-inlier normal check needs both normal arrays and a cosine in [-1, 1]");
+  struct Bufs {
+    float *p, *pose, *np, *nq;
+    float4 *XP, *XQ, *NP4, *NQ4;
+    CloudLayout Cq;
+    ScratchLayout S;
+    int *cnt;
+    unsigned long long *sum;
+    double *sd;
+    int *nrows;
+  };
+  auto plan = [&](Arena &a, Bufs &b) {
+    b.p = a.take<float>(3 * nP);
+    b.XP = a.take<float4>(nP);
+    b.np = a.take<float>(normals ? 3 * nP : 1);
+    b.nq = a.take<float>(normals ? 3 * nQ : 1);
+    b.NP4 = a.take<float4>(normals ? nP : 1);
+    b.NQ4 = a.take<float4>(normals ? nQ : 1);
+    b.XQ = a.take<float4>(normals ? nQ : 1);
+    plan_cloud(a, (int)nQ, true, false, true, b.Cq);
+    plan_scratch(a, (int)nQ, b.Cq.cap_e, b.S);
+    b.pose = a.take<float>(12 * nh);
+    b.cnt = a.take<int>(nh);
+    b.sum = a.take<unsigned long long>(nh);
+    b.sd = a.take<double>(nh);
+    b.nrows = a.take<int>(1);
+  };
+  Arena m(nullptr);
+  Bufs bm;
+  plan(m, bm);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  Bufs b;
+  plan(a, b);
+  CloudLayout &Cq = b.Cq;
+  cudaStream_t s = c->stream;
+  TRY_CUDA(c, cudaMemcpyAsync(b.p, P, sizeof(float) * 3 * nP, cudaMemcpyDefault, s), "copy P");
+  const float *qsrc;
+  if ((rc = stage_input(c, Q, nQ, Cq.src, &qsrc))) return rc;
+  TRY_CUDA(c, cudaMemcpyAsync(b.pose, Rt, sizeof(float) * 12 * nh, cudaMemcpyDefault, s), "copy Rt");
+  LSR_LAUNCH(k_pack<<<nblk(nP), 256, 0, s>>>(b.p, (int)nP, b.XP));  // w = caller index
+  if (normals) {
+    TRY_CUDA(c, cudaMemcpyAsync(b.np, NP, sizeof(float) * 3 * nP, cudaMemcpyDefault, s), "copy NP");
+    TRY_CUDA(c, cudaMemcpyAsync(b.nq, NQ, sizeof(float) * 3 * nQ, cudaMemcpyDefault, s), "copy NQ");
+    LSR_LAUNCH(k_gather_normals<<<nblk(nP), 256, 0, s>>>(b.np, b.XP, (int)nP, b.NP4));
+    LSR_LAUNCH(k_pack<<<nblk(nQ), 256, 0, s>>>(qsrc, (int)nQ, b.XQ));
+    LSR_LAUNCH(k_gather_normals<<<nblk(nQ), 256, 0, s>>>(b.nq, b.XQ, (int)nQ, b.NQ4));
+  }
+  // Q's grid with caller indices in w (exact: cells of eps; single: the eps lattice through the centroid)
+  TRY_CUDA(c, launch_bbox_xyz(qsrc, Cq.n, Cq.box_part, bbox_blocks(Cq.n), Cq.box, s), "bbox");
+  if (single)
+    TRY_CUDA(c, launch_cell_grid_params(Cq.box, eps, Cq.n, Cq.cap_e, Cq.ge, s), "grid params");
+  else
+    TRY_CUDA(c, launch_grid_params(Cq.box, eps, Cq.n, Cq.cap_e, Cq.ge, s), "grid params");
+  TRY_CUDA(c, build_grid_xyz(qsrc, Cq.n, Cq.ge, Cq.cap_e, Cq.start_e, Cq.Xe, Cq.inv, b.S.g, s), "grid");
+  if (!single) TRY_CUDA(c, build_nbmask(Cq.ge, Cq.start_e, Cq.cap_e, Cq.mask_e, s), "mask");
+  TRY_CUDA(c, cudaMemsetAsync(b.cnt, 0, sizeof(int) * nh, s), "memset");
+  TRY_CUDA(c, cudaMemsetAsync(b.sum, 0, sizeof(unsigned long long) * nh, s), "memset");
+  const int nh32 = (int)nh;
+  TRY_CUDA(c, cudaMemcpyAsync(b.nrows, &nh32, sizeof(int), cudaMemcpyHostToDevice, s), "H2D");
+  TRY_CUDA(c,
+           launch_consensus_variant(b.XP, (int)nP, b.NP4, Cq.ge, Cq.start_e, Cq.Xe, b.NQ4, (int)nQ, b.pose, nullptr,
+                                    b.nrows, eps, single, normals, cos_normal, b.cnt, b.sum, s),
+           "consensus variant");
+  LSR_LAUNCH(k_sum_to_double<<<nblk(nh), 256, 0, s>>>(b.sum, (int)nh, b.sd));
+  if ((rc = copy_out(c, count, b.cnt, sizeof(int) * nh))) return rc;
+  if ((rc = copy_out(c, sumd2, b.sd, sizeof(double) * nh))) return rc;
+  SYNC_CHECKED(c, s);
+  return LSR_OK;
+}
+
+int lsr_stage_nn(lsr_ctx *c, const float *Q, int64_t nQ, const float *X, int64_t nX, float r, int32_t mode,
+                 int32_t *nn, float *d2) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!Q || !X || !nn || nQ < 1 || nX < 1 || nQ > kMaxPoints || nX > kMaxPoints || !(r > 0.f && r <= 10.f))
+    return set_err(c, LSR_E_ARG, "bad argument");
+  if (mode != LSR_NN_EXACT && mode != LSR_NN_SINGLE_CELL) return set_err(c, LSR_E_ARG, "bad mode");
+  struct Bufs {
+    float *x;
+    CloudLayout Cq;
+    ScratchLayout S;
+    int *nn;
+    float *d2;
+  };
+  auto plan = [&](Arena &a, Bufs &b) {
+    b.x = a.take<float>(3 * nX);
+    plan_cloud(a, (int)nQ, true, false, true, b.Cq);
+    plan_scratch(a, (int)nQ, b.Cq.cap_e, b.S);
+    b.nn = a.take<int>(nX);
+    b.d2 = a.take<float>(nX);
+  };
+  Arena m(nullptr);
+  Bufs bm;
+  plan(m, bm);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  Bufs b;
+  plan(a, b);
+  cudaStream_t s = c->stream;
+  const float *xsrc, *qsrc;
+  if ((rc = stage_input(c, X, nX, b.x, &xsrc))) return rc;
+  if ((rc = stage_input(c, Q, nQ, b.Cq.src, &qsrc))) return rc;
+  CloudLayout &Cq = b.Cq;
+  const bool single = mode == LSR_NN_SINGLE_CELL;
+  TRY_CUDA(c, launch_bbox_xyz(qsrc, Cq.n, Cq.box_part, bbox_blocks(Cq.n), Cq.box, s), "bbox");
+  if (single)
+    TRY_CUDA(c, launch_cell_grid_params(Cq.box, r, Cq.n, Cq.cap_e, Cq.ge, s), "grid params");
+  else
+    TRY_CUDA(c, launch_grid_params(Cq.box, r, Cq.n, Cq.cap_e, Cq.ge, s), "grid params");
+  TRY_CUDA(c, build_grid_xyz(qsrc, Cq.n, Cq.ge, Cq.cap_e, Cq.start_e, Cq.Xe, Cq.inv, b.S.g, s), "grid");
+  if (!single) TRY_CUDA(c, build_nbmask(Cq.ge, Cq.start_e, Cq.cap_e, Cq.mask_e, s), "mask");
+  TRY_CUDA(c, launch_nn_stage(xsrc, (int)nX, Cq.ge, Cq.start_e, Cq.Xe, r, single ? 1 : 0, b.nn, b.d2, s), "nn");
+  if ((rc = copy_out(c, nn, b.nn, sizeof(int) * nX))) return rc;
+  if (d2 && (rc = copy_out(c, d2, b.d2, sizeof(float) * nX))) return rc;
+  SYNC_CHECKED(c, s);
+  return LSR_OK;
+}
+
+int lsr_pose_implicit_grad(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int64_t nQ, const double *T,
+                           float eps, float mu, const double *dL_dT, float *dP, float *dQ, double *grad,
+                           double *hess, double *lambda, int64_t *n_corr) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!P || !Q || !T || !dL_dT || !dP || !dQ || nP < 1 || nQ < 1 || nP > kMaxPoints || nQ > kMaxPoints ||
+      !(eps > 0.f && eps <= 10.f) || !(mu > 0.f))
+    return set_err(c, LSR_E_ARG, "bad argument");
+  for (int k = 0; k < 16; ++k)
+    if (!std::isfinite(T[k]) || !std::isfinite(dL_dT[k])) return set_err(c, LSR_E_ARG, "non-finite pose or gradient");
+  // dL/dxi of the left perturbation T(xi) = [Exp(w) | v] T: with M = G_R R^T +
+  // G_t t^T (G = dL/dT), dL/dw = (M32 - M23, M13 - M31, M21 - M12), dL/dv = G_t
+  double M[3][3], dl[6];
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) {
+      double v = dL_dT[4 * r + 3] * T[4 * q + 3];
+      for (int k = 0; k < 3; ++k) v += dL_dT[4 * r + k] * T[4 * q + k];
+      M[r][q] = v;
+    }
+  dl[0] = M[2][1] - M[1][2], dl[1] = M[0][2] - M[2][0], dl[2] = M[1][0] - M[0][1];
+  for (int r = 0; r < 3; ++r) dl[3 + r] = dL_dT[4 * r + 3];
+  struct Bufs {
+    float *p, *gp, *gq;
+    CloudLayout Cq;
+    ScratchLayout S;
+    double *part, *out, *dl;
+  };
+  const bool dev_out = is_device_ptr(dP);
+  if (dev_out != is_device_ptr(dQ)) return set_err(c, LSR_E_ARG, "dP and dQ must both be device or both host");
+  auto plan = [&](Arena &a, Bufs &b) {
+    b.p = a.take<float>(3 * nP);
+    b.gp = dev_out ? nullptr : a.take<float>(3 * nP);
+    b.gq = dev_out ? nullptr : a.take<float>(3 * nQ);
+    plan_cloud(a, (int)nQ, true, false, true, b.Cq);
+    plan_scratch(a, (int)nQ, b.Cq.cap_f, b.S);
+    b.part = a.take<double>((size_t)implicit_partials((int)nP));
+    b.out = a.take<double>(50);
+    b.dl = a.take<double>(6);
+  };
+  Arena m(nullptr);
+  Bufs bm;
+  plan(m, bm);
+  if ((rc = ensure_ws(c, m.off))) return rc;
+  Arena a(c->ws);
+  Bufs b;
+  plan(a, b);
+  cudaStream_t s = c->stream;
+  const float *psrc, *qsrc;
+  if ((rc = stage_input(c, P, nP, b.p, &psrc))) return rc;
+  if ((rc = stage_input(c, Q, nQ, b.Cq.src, &qsrc))) return rc;
+  // eps grid of Q with caller indices in w (build_grid_xyz carries the caller order), so dQ is in caller order
+  CloudLayout &Cq = b.Cq;
+  TRY_CUDA(c, launch_bbox_xyz(qsrc, Cq.n, Cq.box_part, bbox_blocks(Cq.n), Cq.box, s), "bbox");
+  TRY_CUDA(c, launch_grid_params(Cq.box, eps, Cq.n, Cq.cap_e, Cq.ge, s), "grid params");
+  TRY_CUDA(c, build_grid_xyz(qsrc, Cq.n, Cq.ge, Cq.cap_e, Cq.start_e, Cq.Xe, Cq.inv, b.S.g, s), "grid");
+  TRY_CUDA(c, build_nbmask(Cq.ge, Cq.start_e, Cq.cap_e, Cq.mask_e, s), "mask");
+  TRY_CUDA(c, cudaMemcpyAsync(b.dl, dl, sizeof(dl), cudaMemcpyHostToDevice, s), "H2D");
+  float *gp = dev_out ? dP : b.gp, *gq = dev_out ? dQ : b.gq;
+  TRY_CUDA(c, cudaMemsetAsync(gq, 0, sizeof(float) * 3 * nQ, s), "memset dQ");
+  TRY_CUDA(c,
+           launch_implicit(psrc, (int)nP, b.Cq.ge, b.Cq.start_e, b.Cq.Xe, (int)nQ, T, eps, (double)mu, b.dl, b.part,
+                           b.out, gp, gq, s),
+           "implicit");
+  double host[50];
+  TRY_CUDA(c, cudaMemcpyAsync(host, b.out, sizeof(host), cudaMemcpyDeviceToHost, s), "D2H");
+  if (!dev_out) {
+    TRY_CUDA(c, cudaMemcpyAsync(dP, gp, sizeof(float) * 3 * nP, cudaMemcpyDeviceToHost, s), "D2H");
+    TRY_CUDA(c, cudaMemcpyAsync(dQ, gq, sizeof(float) * 3 * nQ, cudaMemcpyDeviceToHost, s), "D2H");
+  }
+  SYNC_CHECKED(c, s);
+  if (grad)
+    for (int k = 0; k < 6; ++k) grad[k] = host[k];
+  if (hess)
+    for (int k = 0; k < 36; ++k) hess[k] = host[6 + k];
+  if (lambda)
+    for (int k = 0; k < 6; ++k) lambda[k] = host[42 + k];
+  if (n_corr) *n_corr = (int64_t)host[48];
+  if (host[49] != 0.0) return set_err(c, LSR_E_ARG, "the Hessian of the held pairs is singular (too few pairs)");
   return LSR_OK;
 }
 

@@ -132,6 +132,8 @@ cudaError_t check_read_match_tc(CheckReport *r);
 cudaError_t check_read_ransac(CheckReport *r);
 cudaError_t check_read_classify(CheckReport *r);
 cudaError_t check_read_refine(CheckReport *r);
+cudaError_t check_read_nn(CheckReport *r);
+cudaError_t check_read_implicit(CheckReport *r);
 cudaError_t check_probe_arm(cudaStream_t s);
 
 // Kernel launches of this library, counted process-wide (lsr_launch_count).
@@ -582,6 +584,28 @@ int information_blocks(int nP);
 cudaError_t launch_information(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
                                const float *boxQ, const float R[9], const float t[3], float eps, double *partials,
                                double *out, cudaStream_t s);
+// Nearest-neighbour modes (lsr_nn.cu). The single-cell lattice: cell edge
+// exact, anchored at the centroid of the box (box[8..10]).
+cudaError_t launch_cell_grid_params(const float *box, float cell, int npts, int cap_cells, GridParams *g,
+                                    cudaStream_t s);
+// nn / d2 of every query (caller-order xyz): exact (nearest within r over the
+// grid of cell r) or single (own cell of the single-cell lattice).
+cudaError_t launch_nn_stage(const float *X, int nX, const GridParams *g, const int *start, const float4 *Xs, float r,
+                            int single, int *nn, float *d2, cudaStream_t s);
+// Consensus of the ok hypotheses with the single-cell lookup and/or the
+// per-inlier normal check (count / sum as launch_consensus).
+cudaError_t launch_consensus_variant(const float4 *XP, int nP, const float4 *NP, const GridParams *g,
+                                     const int *start, const float4 *Xs, const float4 *NQ, int nQ, const float *pose,
+                                     const uint8_t *ok, const int *n_dev, float eps, bool single, bool normals,
+                                     float cos_normal, int *count, unsigned long long *sum, cudaStream_t s);
+
+// Implicit gradient of the refined pose (lsr_implicit.cu): partials holds
+// implicit_partials(nP) doubles; out 50 doubles (g 6, H 36, lambda 6, count,
+// singular flag); dl_dev: dL/dxi (6 doubles, device); dQ must be zeroed.
+int implicit_partials(int nP);
+cudaError_t launch_implicit(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
+                            int nQ, const double T[16], float eps, double mu, const double *dl_dev,
+                            double *partials, double *out, float *dP, float *dQ, cudaStream_t s);
 cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
                              const float R[9], const float t[3], const float v[3], float eps, float mu, float scale,
                              int want_grad, double *partials, double *out7, float *dP, float *dQ, cudaStream_t s);

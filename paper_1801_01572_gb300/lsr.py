@@ -24,6 +24,8 @@ _lock = threading.Lock()
 LSR_OK, LSR_E_ARG, LSR_E_CUDA, LSR_E_OOM, LSR_E_TIMEOUT, LSR_E_STATE, LSR_E_TOO_LARGE = 0, -1, -2, -3, -4, -5, -6
 STATUS_ALIGNED, STATUS_NO_ALIGNMENT = 0, 1
 MATCH_FP32, MATCH_BF16, MATCH_BF16_PLAIN = 0, 1, 2
+NN_EXACT, NN_SINGLE_CELL = 0, 1
+NORMALS_SAMPLES, NORMALS_INLIERS = 0, 1
 DESC_DIM = 33
 
 # Names of every entry point declared in include/lsr.h (checked by the tests).
@@ -35,7 +37,8 @@ ABI_FUNCTIONS = (
     "lsr_stage_rigid4", "lsr_stage_consensus", "lsr_stage_refine", "lsr_objective_fwd", "lsr_objective_bwd",
     "lsr_consensus_static", "lsr_match_scores_bf16", "lsr_information_matrix", "lsr_surfel_correct",
     "lsr_voxel_downsample", "lsr_debug_inject", "lsr_set_kernel_timing", "lsr_kernel_timing_count",
-    "lsr_kernel_timing_entry", "lsr_checked_build",
+    "lsr_kernel_timing_entry", "lsr_checked_build", "lsr_pose_implicit_grad", "lsr_stage_nn",
+    "lsr_stage_consensus_modes",
 )
 INJECT_NONE, INJECT_ALLOC, INJECT_MATCH_STALL, INJECT_CHECK = 0, 1, 2, 3
 LSR_E_CHECK = -7
@@ -53,7 +56,7 @@ class Params(C.Structure):
                 ("refine_iters", C.c_int32), ("n_hypotheses", C.c_int64), ("seed", C.c_uint64),
                 ("pair_id", C.c_uint64), ("match_precision", C.c_int32), ("refine_levels", C.c_int32),
                 ("batch_streams", C.c_int32), ("batch_graph", C.c_int32), ("match_tile", C.c_int32),
-                ("reserved_", C.c_int32)]
+                ("nn_mode", C.c_int32), ("normal_mode", C.c_int32), ("reserved_", C.c_int32 * 2)]
 
 
 class Result(C.Structure):
@@ -113,6 +116,11 @@ def lib():
             "lsr_debug_inject": (C.c_int, [vp, i32, i32]),
             "lsr_set_kernel_timing": (C.c_int, [vp, C.c_char_p]),
             "lsr_checked_build": (C.c_int, []),
+            "lsr_stage_nn": (C.c_int, [vp, vp, i64, vp, i64, f32, i32, vp, vp]),
+            "lsr_stage_consensus_modes": (C.c_int, [vp, vp, vp, i64, vp, vp, i64, vp, i64, f32, i32, i32, f32, vp,
+                                                    vp]),
+            "lsr_pose_implicit_grad": (C.c_int, [vp, vp, i64, vp, i64, vp, f32, f32, vp, vp, vp, vp, vp, vp,
+                                                 C.POINTER(C.c_int64)]),
             "lsr_kernel_timing_count": (i32, [vp]),
             "lsr_kernel_timing_entry": (C.c_int, [vp, i32, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
                                                   C.POINTER(C.c_double)]),
@@ -405,6 +413,56 @@ class Context:
                                              C.c_float(mu_scale), int(levels), int(iters),
                                              C.c_void_p(Tout.ctypes.data), C.byref(it)))
         return Tout.reshape(4, 4), int(it.value)
+
+    def stage_consensus_modes(self, P, Q, Rt, eps=0.0375, nn_mode=NN_EXACT, normal_mode=NORMALS_SAMPLES,
+                              NP=None, NQ=None, cos_normal=0.8660254037844387):
+        """Consensus counts and squared-distance sums per pose with the variant
+        modes (lsr_stage_consensus_modes)."""
+        pP, kP, nP = _prep(P, np.float32, 3)
+        pQ, kQ, nQ = _prep(Q, np.float32, 3)
+        pR, kR, nh = _prep(Rt, np.float32, 12)
+        pNP = pNQ = None
+        if NP is not None:
+            pNP, kNP, _ = _prep(NP, np.float32, 3)
+            pNQ, kNQ, _ = _prep(NQ, np.float32, 3)
+        cnt = np.zeros(nh, np.int32)
+        sd = np.zeros(nh, np.float64)
+        self._check(self._L.lsr_stage_consensus_modes(self._h, pP, pNP, nP, pQ, pNQ, nQ, pR, nh, C.c_float(eps),
+                                                      int(nn_mode), int(normal_mode), C.c_float(cos_normal),
+                                                      C.c_void_p(cnt.ctypes.data), C.c_void_p(sd.ctypes.data)))
+        return cnt, sd
+
+    def stage_nn(self, Q, X, r, mode=NN_EXACT):
+        """Nearest Q point of every query (lsr_stage_nn): (nn int32, d2 float32)."""
+        pQ, kQ, nQ = _prep(Q, np.float32, 3)
+        pX, kX, nX = _prep(X, np.float32, 3)
+        nn = np.zeros(nX, np.int32)
+        d2 = np.zeros(nX, np.float32)
+        self._check(self._L.lsr_stage_nn(self._h, pQ, nQ, pX, nX, C.c_float(r), int(mode),
+                                         C.c_void_p(nn.ctypes.data), C.c_void_p(d2.ctypes.data)))
+        return nn, d2
+
+    def pose_implicit_grad(self, P, Q, T, dL_dT, eps=0.0375, mu=None, dP=None, dQ=None):
+        """Gradient of a loss of the refined pose T with respect to the points
+        (lsr_pose_implicit_grad). dL_dT: 4x4 gradient of the loss in T. dP, dQ:
+        optional output arrays (both torch CUDA tensors or both None for numpy).
+        Returns (dP, dQ, g (6), H (6x6), lambda (6), held pairs)."""
+        mu = eps * eps if mu is None else mu
+        pP, kP, nP = _prep(P, np.float32, 3)
+        pQ, kQ, nQ = _prep(Q, np.float32, 3)
+        Tin = np.ascontiguousarray(np.asarray(T, np.float64).reshape(16))
+        G = np.ascontiguousarray(np.asarray(dL_dT, np.float64).reshape(16))
+        if dP is None:
+            dP, dQ = np.zeros((nP, 3), np.float32), np.zeros((nQ, 3), np.float32)
+            pdP, pdQ = C.c_void_p(dP.ctypes.data), C.c_void_p(dQ.ctypes.data)
+        else:
+            pdP, pdQ = C.c_void_p(dP.data_ptr()), C.c_void_p(dQ.data_ptr())
+        g, H, lam, n = np.zeros(6), np.zeros(36), np.zeros(6), C.c_int64(0)
+        self._check(self._L.lsr_pose_implicit_grad(self._h, pP, nP, pQ, nQ, C.c_void_p(Tin.ctypes.data),
+                                                    C.c_float(eps), C.c_float(mu), C.c_void_p(G.ctypes.data), pdP, pdQ,
+                                                    C.c_void_p(g.ctypes.data), C.c_void_p(H.ctypes.data),
+                                                    C.c_void_p(lam.ctypes.data), C.byref(n)))
+        return dP, dQ, g, H.reshape(6, 6), lam, int(n.value)
 
     def information_matrix(self, P, Q, T, eps=0.05):
         """Information matrix of eq. (5)-(6) for the pose T (P into Q's frame):
