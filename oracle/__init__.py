@@ -371,6 +371,54 @@ def nn_single_cell(Q, X, cell):
     return nn, d2
 
 
+def consensus_single_cell(P, Q, Rs, ts, eps):
+    """Consensus of Alg. 1 with the single-cell lookup of eq. (1) as the
+    nearest-neighbour search (the paper's speed mode; cell edge = eps on the
+    lattice through Q's centroid): per pose [R | t], the points of P whose own
+    cell's nearest Q point is closer than eps, and the sum of their squared
+    distances. FP64."""
+    P, Q = _f64(P, 3), _f64(Q, 3)
+    Rs = _f64(Rs).reshape(-1, 3, 3)
+    ts = _f64(ts).reshape(-1, 3)
+    cnt, sd = np.zeros(len(Rs), np.int64), np.zeros(len(Rs))
+    for k, (R, t) in enumerate(zip(Rs, ts)):
+        _, d2 = nn_single_cell(Q, P @ R.T + t, eps)
+        inl = d2 < eps * eps
+        cnt[k], sd[k] = int(inl.sum()), float(d2[inl].sum())
+    return cnt, sd
+
+
+def consensus_normals(P, NP, Q, NQ, Rs, ts, eps, cos_normal, band=0.0):
+    """Consensus of Alg. 1 with the normal check applied to every inlier (the
+    alternative reading of "normal check moved into hypotheses testing",
+    Sec. IV): per pose [R | t], a point p of P counts if its nearest Q point q
+    (exact search, ties to the smaller index) is closer than eps and
+    cos(R n_p, n_q) >= cos_normal, both normals valid (non-zero). Returns
+    (count, sum of squared distances, ambiguous): ambiguous counts the points
+    an FP32 evaluation may decide the other way (distance within band of eps,
+    cosine within band of the threshold, or a runner-up within band of the
+    nearest). FP64."""
+    P, Q, NP, NQ = _f64(P, 3), _f64(Q, 3), _f64(NP, 3), _f64(NQ, 3)
+    Rs = _f64(Rs).reshape(-1, 3, 3)
+    ts = _f64(ts).reshape(-1, 3)
+    vP = np.abs(NP).sum(1) > 0
+    vQ = np.abs(NQ).sum(1) > 0
+    cnt, sd, amb = np.zeros(len(Rs), np.int64), np.zeros(len(Rs)), np.zeros(len(Rs), np.int64)
+    for k, (R, t) in enumerate(zip(Rs, ts)):
+        X = P @ R.T + t
+        j, d2 = nn_within(Q, X, eps + band)
+        has = j >= 0
+        jj = np.where(has, j, 0)
+        cs = ((NP @ R.T) * NQ[jj]).sum(1)
+        inl = has & (d2 < eps * eps) & vP & vQ[jj] & (cs >= cos_normal)
+        cnt[k], sd[k] = int(inl.sum()), float(d2[inl].sum())
+        if band > 0:
+            d = np.sqrt(np.where(has, d2, np.inf))
+            near = has & ((np.abs(d - eps) < band) | (np.abs(cs - cos_normal) < band))
+            amb[k] = int(near.sum())
+    return cnt, sd, amb
+
+
 def _gm(s, mu):
     """Geman-McClure rho(s) = mu s / (mu + s) of eq. (4) and its first two
     derivatives in s."""
