@@ -288,6 +288,7 @@ struct PairLayout {
   int *count = nullptr;
   unsigned long long *sum = nullptr;
   double *ref_part = nullptr;
+  int *seeds = nullptr;      // refinement: each point's neighbour of the previous step
   float *fpose = nullptr;
   int *fcount = nullptr;
   unsigned long long *fsum = nullptr;
@@ -329,6 +330,7 @@ void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int leve
   L.count = a.take<int>(L.surv_cap);
   L.sum = a.take<unsigned long long>(L.surv_cap);
   L.ref_part = a.take<double>((size_t)kRefAcc * refine_blocks(nP));
+  L.seeds = a.take<int>(nP);
   L.fpose = a.take<float>(12);
   L.fcount = a.take<int>(1);
   L.fsum = a.take<unsigned long long>(1);
@@ -587,8 +589,8 @@ cudaError_t build_cloud(const float *xyz, CloudLayout &c, float r_f, float r_n, 
 // xyz on the device; (ge, start_e, Xe): Q's eps grid for the finest level.
 cudaError_t enqueue_refine(const float4 *XP, const float *P, int nP, const float *Q, int nQ, const float *boxQ,
                            const GridParams *ge, const int *start_e, const float4 *Xe, const LevelLayout &V, float eps,
-                           float mu_scale, int iters, RansacState *st, double *part, const ScratchLayout &sc,
-                           cudaStream_t s) {
+                           float mu_scale, int iters, RansacState *st, double *part, int *seeds,
+                           const ScratchLayout &sc, cudaStream_t s) {
   int L = V.levels;
   for (int l = 0; l < L; ++l) {
     float e = eps * (float)(1 << (L - 1 - l));
@@ -611,8 +613,9 @@ cudaError_t enqueue_refine(const float4 *XP, const float *P, int nP, const float
       g = V.g[l], st0 = V.start[l], xs = V.Xs[l];
     }
     LSR_CUDA_TRY(launch_refine_level_begin(st, s));
+    LSR_CUDA_TRY(cudaMemsetAsync(seeds, 0xff, sizeof(int) * (size_t)np, s));  // no neighbour yet at this level
     for (int it = 0; it < iters; ++it)
-      LSR_CUDA_TRY(launch_refine_step(xp, np, 1, g, st0, xs, e, mu, iters, st, part, s));
+      LSR_CUDA_TRY(launch_refine_step(xp, np, 1, g, st0, xs, e, mu, iters, st, part, seeds, s));
   }
   return cudaSuccess;
 }
@@ -743,7 +746,7 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
   float eps = p.eps_inlier;
   TRY_CUDA(c,
            enqueue_refine(Pc.X, P, nP, Q, nQ, Qc.box, Qc.ge, Qc.start_e, Qc.Xe, L.lv, eps, p.mu_scale, p.refine_iters,
-                          L.st, L.ref_part, L.sc, s),
+                          L.st, L.ref_part, L.seeds, L.sc, s),
            "refine");
   TRY_CUDA(c, launch_final_pose(L.st, L.fpose, s), "final pose");
   TRY_CUDA(c, cudaMemsetAsync(L.fcount, 0, sizeof(int), s), "memset fcount");
@@ -1792,8 +1795,10 @@ int lsr_stage_refine(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int
     return set_err(c, LSR_E_ARG, "bad argument");
   float *boxP = nullptr;
   double *boxP_part = nullptr;
+  int *seeds = nullptr;
   auto plan = [&](Arena &a, float *&p, float4 *&XP, CloudLayout &Cq, LevelLayout &V, ScratchLayout &S, double *&part,
                   double *&Td, RansacState *&st) {
+    seeds = a.take<int>(nP);
     p = a.take<float>(3 * nP);
     XP = a.take<float4>(nP);
     boxP = a.take<float>(kBox);
@@ -1836,7 +1841,7 @@ int lsr_stage_refine(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int
   TRY_CUDA(c, launch_refine_init(st, boxP, Td, s), "init");
   TRY_CUDA(c,
            enqueue_refine(XP, p, (int)nP, qsrc, (int)nQ, Cq.box, Cq.ge, Cq.start_e, Cq.Xe, V, eps, mu_scale, iters, st,
-                          part, S, s),
+                          part, seeds, S, s),
            "refine");
   RansacState h;
   TRY_CUDA(c, cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H");

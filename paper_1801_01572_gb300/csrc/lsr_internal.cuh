@@ -243,14 +243,31 @@ __device__ __forceinline__ void grid_ranges(const GridParams &g, const int *__re
 // rounding of cell coordinates) can still reach the group's best so far. A
 // skipped cell holds no point at or below that best, so the result is the
 // one of the full walk. (Grids with wrapped storage walk all cells.)
+//
+// seed (optional, >= 0): an index into Xe known to be a candidate (the
+// previous refinement step's neighbour of the same point). Its distance,
+// computed exactly as the walk computes distances, starts the search when it
+// is below eps2, so cells beyond it are skipped; the result is the walk's
+// result without a seed (the nearest point wins either way, ties to the
+// smaller carried index).
+__device__ __forceinline__ float nn_d2(float4 q, float x, float y, float z) {
+  float dx = q.x - x, dy = q.y - y, dz = q.z - z;
+  return dx * dx + dy * dy + dz * dz;
+}
+
 template <int G>
 __device__ __forceinline__ void group_nn(const GridParams &g, const int *__restrict__ start,
                                          const float4 *__restrict__ Xe, float x, float y, float z, float eps2,
-                                         float &best, int &bt, int &bidx) {
+                                         float &best, int &bt, int &bidx, int seed = -1) {
   int sub = threadIdx.x & (G - 1);
   best = eps2;
   bt = -1;
   bidx = 0x7fffffff;
+  if (seed >= 0 && LSR_IN_BOUNDS(seed, g.npts, kSiteGridPoint)) {
+    const float4 q = Xe[seed];
+    const float d2 = nn_d2(q, x, y, z);
+    if (d2 < eps2) best = d2, bt = seed, bidx = __float_as_int(q.w);
+  }
   int next = sub, base = 0;
   auto scan = [&](int b, int e) {
     int len = e - b;
@@ -268,8 +285,7 @@ __device__ __forceinline__ void group_nn(const GridParams &g, const int *__restr
       float4 q[4] = {Xe[t], Xe[t + G], Xe[t + 2 * G], Xe[t + 3 * G]};
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        float dx = q[k].x - x, dy = q[k].y - y, dz = q[k].z - z;
-        float d2 = dx * dx + dy * dy + dz * dz;
+        float d2 = nn_d2(q[k], x, y, z);
         int qi = __float_as_int(q[k].w);
         if (d2 < best || (d2 == best && qi < bidx)) best = d2, bt = t + k * G, bidx = qi;
       }
@@ -277,8 +293,7 @@ __device__ __forceinline__ void group_nn(const GridParams &g, const int *__restr
     for (; next < base + len; next += G) {
       int t = b + next - base;
       float4 q = Xe[t];
-      float dx = q.x - x, dy = q.y - y, dz = q.z - z;
-      float d2 = dx * dx + dy * dy + dz * dz;
+      float d2 = nn_d2(q, x, y, z);
       int qi = __float_as_int(q.w);
       if (d2 < best || (d2 == best && qi < bidx)) best = d2, bt = t, bidx = qi;
     }
@@ -310,7 +325,7 @@ __device__ __forceinline__ void group_nn(const GridParams &g, const int *__restr
       const float gyl = gsq((fy - (float)cy) * g.cell), gyh = gsq(((float)cy + 1.f - fy) * g.cell);
       const float gzl = gsq((fz - (float)cz) * g.cell), gzh = gsq(((float)cz + 1.f - fz) * g.cell);
       constexpr float kShrink = 1.f - 1e-6f;  // the FP32 rounding of d^2 itself
-      float gb = eps2;
+      float gb = best;  // eps2, or the seed's distance (the same on every lane of the group)
 #pragma unroll 1
       for (int k = 0; k < 9; ++k) {
         // rows: own, then the four edge neighbours, then the four corners
@@ -541,10 +556,12 @@ constexpr int kMaxLevels = 8;
 int gnc_stride(int64_t n, int level, int levels);
 cudaError_t launch_refine_level_begin(RansacState *st, cudaStream_t s);
 // One IRLS step on the points of P (internal order, w = caller index) whose
-// caller index is a multiple of strideP, against the given grid of Q.
+// caller index is a multiple of strideP, against the given grid of Q. seeds
+// (nP ints, -1 = none; set to -1 at the start of a level): each point's
+// neighbour of the previous step, read as the search's start and rewritten.
 cudaError_t launch_refine_step(const float4 *XP, int nP, int strideP, const GridParams *ge, const int *start_e,
                                const float4 *Xe, float eps_r, float mu, int max_iters, RansacState *st,
-                               double *partials, cudaStream_t s);
+                               double *partials, int *seeds, cudaStream_t s);
 // out[m] = (Q[m * stride], m) for m < ceil(n / stride); Q caller-order xyz.
 cudaError_t launch_subsample(const float *xyz, int n, int stride, float4 *out, cudaStream_t s);
 cudaError_t launch_final_pose(RansacState *st, float *pose, cudaStream_t s);

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
                                                              const GridParams *gep, const int *__restrict__ start,
                                                              const float4 *__restrict__ Xe, float eps2, float mu,
                                                              RansacState *st, double *partials, int max_iters,
-                                                             double tol) {
+                                                             double tol, int *__restrict__ seeds) {
   __shared__ int s_last;
   __shared__ double tot[kNAcc];
   if (!st->active) return;
@@ -175,7 +175,12 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
     float x = xc0 + c[0], y = xc1 + c[1], z = xc2 + c[2];
     float best;
     int bt, bidx;
-    group_nn<G>(g, start, Xe, x, y, z, eps2, best, bt, bidx);
+    // the previous step's neighbour of this point starts the search (an exact
+    // search either way; the pose moves little between steps, so most cells
+    // beyond it are skipped)
+    const int seed = valid ? seeds[i] : -1;
+    group_nn<G>(g, start, Xe, x, y, z, eps2, best, bt, bidx, seed);
+    if (valid && sub == 0) seeds[i] = bt;
     if (!valid || bt < 0) continue;
     float4 q = Xe[bt];
     float r[3] = {x - q.x, y - q.y, z - q.z};
@@ -478,10 +483,10 @@ cudaError_t launch_subsample(const float *xyz, int n, int stride, float4 *out, c
 
 cudaError_t launch_refine_step(const float4 *XP, int nP, int strideP, const GridParams *ge, const int *start_e,
                                const float4 *Xe, float eps_r, float mu, int max_iters, RansacState *st,
-                               double *partials, cudaStream_t s) {
+                               double *partials, int *seeds, cudaStream_t s) {
   int nb = refine_blocks((int)lsr_div_up(nP, strideP));
   LSR_LAUNCH(k_refine_step<<<nb, kRefThreads, 0, s>>>(XP, nP, strideP, ge, start_e, Xe, eps_r * eps_r, mu, st, partials,
-                                           max_iters, 1e-6));
+                                           max_iters, 1e-6, seeds));
   return cudaGetLastError();
 }
 

@@ -11,6 +11,8 @@ the GPU's gradient, Hessian, lambda and point gradients must equal the
 oracle's up to FP64 summation order and the FP32 rounding of the outputs.
 Then the gradient is checked against central differences of re-optimised
 poses (oracle.pose_optimum on the held pairs) for a few coordinates.
+
+The library takes mu as a float32, so the oracle is given that same value.
 """
 import numpy as np
 import pytest
@@ -49,17 +51,6 @@ def dl_dxi(G, T):
     return np.r_[M[2, 1] - M[1, 2], M[0, 2] - M[2, 0], M[1, 0] - M[0, 1], G[:3, 3]]
 
 
-def xi_of(Ta, Tb):
-    """The left perturbation xi with Ta = [Exp(w) | v] Tb (first order enough
-    for differences of nearby poses, exact for the rotation log)."""
-    D = Ta @ np.linalg.inv(Tb)
-    R = D[:3, :3]
-    c = np.clip((np.trace(R) - 1) / 2, -1, 1)
-    th = np.arccos(c)
-    w = np.array([R[2, 1] - R[1, 2], R[0, 2] - R[2, 0], R[1, 0] - R[0, 1]]) * (0.5 if th < 1e-12 else th / (2 * np.sin(th)))
-    return np.r_[w, D[:3, 3]]
-
-
 @pytest.mark.parametrize("case", ["objects5k", "room50k"])
 @gpu
 def test_implicit_gradient_matches_oracle(lsr, case):
@@ -75,7 +66,7 @@ def test_implicit_gradient_matches_oracle(lsr, case):
     if namb:
         pytest.skip(f"{namb} pairs within the FP32 band: the held sets may differ")
     X, Y = fp.P[held].astype(np.float64), fp.Q[nn[held]].astype(np.float64)
-    mu = EPS * EPS
+    mu = float(np.float32(EPS * EPS))
     _, g_ref, H_ref = oracle.pose_grad_hess(X, Y, T, mu)
     hs = np.abs(H_ref).max()
     assert np.abs(H - H_ref).max() <= 1e-9 * hs
@@ -103,7 +94,7 @@ def test_implicit_gradient_against_reoptimised_poses(lsr):
         held, nn, namb = held_pairs(fp.P, fp.Q, T, EPS)
         if namb:
             pytest.skip("pairs within the FP32 band")
-        mu = EPS * EPS
+        mu = float(np.float32(EPS * EPS))
         X, Y = fp.P[held].astype(np.float64), fp.Q[nn[held]].astype(np.float64)
         T0, _ = oracle.pose_optimum(X, Y, T, mu)
         rng = np.random.default_rng(11)

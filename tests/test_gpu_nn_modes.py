@@ -106,10 +106,11 @@ def test_single_cell_nn_matches_oracle(ctx, config, n):
     assert np.array_equal(nn[sure], ref[sure])
     has = sure & (ref >= 0)
     assert np.allclose(d2[has], rd2[has], rtol=1e-5, atol=1e-9)
-    # the single cell only ever loses neighbours: never closer than the exact search
+    # the single cell only ever loses neighbours: never closer than the exact
+    # search (the two kernels may round the same distance one unit apart)
     ex, exd2 = ctx.stage_nn(fp.Q, X, 10 * EPS)
     found = nn >= 0
-    assert np.all(d2[found] >= exd2[found] - 1e-12)
+    assert np.all(d2[found] >= exd2[found] * (1 - 1e-6))
 
 
 def _poses(fp, rng, n):
