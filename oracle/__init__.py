@@ -504,7 +504,7 @@ def pose_implicit_grad(X, Y, T, mu, dL_dxi):
     return -(dz @ T[:3, :3]), -dy
 
 
-def surfel_correct(pos, nrm, t0, tu, T_old, T_new, t_kf, cam):
+def surfel_correct(pos, nrm, t0, tu, T_old, T_new, t_kf, cam, band=None):
     """Dense model correction of eq. (7), in FP64 with numpy.
 
     For each surfel (position p, normal n, time stamps t0 < tu), F is the set
@@ -517,7 +517,11 @@ def surfel_correct(pos, nrm, t0, tu, T_old, T_new, t_kf, cam):
         n' = normalize((1/k) sum_f R_f_new R_f_old^-1 n),
     and a surfel with k = 0 is removed (keep = False; p, n returned unchanged).
     T_old, T_new: m x 4 x 4 camera-to-world poses; t_kf: m time stamps.
-    Returns (p', n', keep)."""
+    Returns (p', n', keep); with band = (metres, pixels) also a fourth array,
+    border: surfels for which some keyframe of their time window decides
+    visibility within that band of a limit (depth 0 or the maximum, an image
+    edge), so that an FP32 evaluation may decide it the other way (reporting
+    only)."""
     pos, nrm = np.asarray(pos, np.float64), np.asarray(nrm, np.float64)
     t0, tu = np.asarray(t0, np.float64), np.asarray(tu, np.float64)
     T_old, T_new = np.asarray(T_old, np.float64), np.asarray(T_new, np.float64)
@@ -525,6 +529,7 @@ def surfel_correct(pos, nrm, t0, tu, T_old, T_new, t_kf, cam):
     sp = np.zeros_like(pos)
     sn = np.zeros_like(nrm)
     k = np.zeros(len(pos), np.int64)
+    border = np.zeros(len(pos), bool)
     for f in range(len(T_old)):
         inv = np.linalg.inv(T_old[f])
         M = T_new[f] @ inv
@@ -534,6 +539,13 @@ def surfel_correct(pos, nrm, t0, tu, T_old, T_new, t_kf, cam):
             u = fx * xc[:, 0] / z + cx
             v = fy * xc[:, 1] / z + cy
         seen = (t0 < t_kf[f]) & (t_kf[f] < tu) & (z > 0) & (z <= dmax) & (u >= 0) & (u < W) & (v >= 0) & (v < H)
+        if band is not None:
+            bm, bp = band
+            win = (t0 < t_kf[f]) & (t_kf[f] < tu)
+            with np.errstate(invalid="ignore"):
+                near = (np.abs(z) < bm) | (np.abs(z - dmax) < bm) | (np.abs(u) < bp) | (np.abs(u - W) < bp) | \
+                    (np.abs(v) < bp) | (np.abs(v - H) < bp)
+            border |= win & near
         k += seen
         sp[seen] += pos[seen] @ M[:3, :3].T + M[:3, 3]
         sn[seen] += nrm[seen] @ M[:3, :3].T
@@ -542,6 +554,8 @@ def surfel_correct(pos, nrm, t0, tu, T_old, T_new, t_kf, cam):
     p_out[keep] = sp[keep] / k[keep, None]
     m = sn[keep] / k[keep, None]
     n_out[keep] = m / np.linalg.norm(m, axis=1, keepdims=True)
+    if band is not None:
+        return p_out, n_out, keep, border
     return p_out, n_out, keep
 
 

@@ -3,10 +3,11 @@ FP64 oracle, on a seeded room-sized surfel map and a keyframe loop with a
 drift correction growing to 1.5 deg / 6 cm.
 
 Which keyframes observe a surfel is decided in FP32 on the device and in FP64
-in the oracle; a surfel projecting within rounding of an image edge or at the
-maximum depth may be decided differently (a rare event, bounded below). Where
-both keep a surfel, position and normal agree to FP32 rounding (1e-5) for all
-but the surfels whose keyframe sets differ by such a boundary case.
+in the oracle. The oracle reports the surfels for which some keyframe of their
+time window decides visibility within 1e-5 m of a depth limit or 1e-3 pixels of
+an image edge (the FP32 transform and projection err by less); only those may
+differ. Every other surfel is kept or removed by both, and where kept its
+position and normal agree to FP32 rounding (1e-5).
 """
 import numpy as np
 import pytest
@@ -37,14 +38,16 @@ def smap():
 def test_surfel_correction_matches_oracle(ctx, smap):
     S = smap
     p, n, keep, kept = ctx.surfel_correct(S.pos, S.nrm, S.t0, S.tu, S.T_old, S.T_new, S.t_kf, S.cam)
-    pr, nr, keepr = oracle.surfel_correct(S.pos, S.nrm, S.t0, S.tu, S.T_old, S.T_new, S.t_kf, S.cam)
+    pr, nr, keepr, border = oracle.surfel_correct(S.pos, S.nrm, S.t0, S.tu, S.T_old, S.T_new, S.t_kf, S.cam,
+                                                  band=(1e-5, 1e-3))
     keep = keep.astype(bool)
     assert kept == keep.sum() and 0.1 < keep.mean() < 0.9
-    assert (keep != keepr).mean() < 1e-4
-    both = keep & keepr
+    assert border.mean() < 1e-3
+    assert np.array_equal(keep[~border], keepr[~border])
+    both = keep & keepr & ~border
     ep = np.linalg.norm(p[both] - pr[both], axis=1)
     en = np.linalg.norm(n[both] - nr[both], axis=1)
-    assert (ep > 1e-5).mean() < 1e-3 and (en > 1e-5).mean() < 1e-3, (np.quantile(ep, 0.999), np.quantile(en, 0.999))
+    assert ep.max() <= 1e-5 and en.max() <= 1e-5, (ep.max(), en.max())
     assert np.median(ep) < 2e-6
     # removed surfels come back unchanged
     assert np.array_equal(p[~keep], S.pos[~keep]) and np.array_equal(n[~keep], S.nrm[~keep])

@@ -76,3 +76,23 @@ def test_average_of_two_corrections():
     B[:3, 3] = [0.0, 0.04, 0.0]
     p, _, keep = _one([[0.1, -0.1, 1.5]], -1.0, 5.0, [I, I], [A, B], [0.0, 1.0])
     assert keep[0] and np.allclose(p[0], [0.11, -0.08, 1.5], atol=1e-12)
+
+
+def test_border_report_flags_only_limit_cases():
+    """The band report flags a surfel whose projection sits on an image edge
+    or at the maximum depth of a keyframe in its window, and nothing else; it
+    changes no result."""
+    cam = np.array([525.0, 525.0, 320.0, 240.0, 640.0, 480.0, 4.0])
+    T = np.eye(4)[None]  # one camera at the origin looking along +z
+    z = 2.0
+    x_edge = (0.0 - 320.0) * z / 525.0  # u = 0 exactly
+    pos = np.array([[0.0, 0.0, z], [x_edge, 0.0, z], [0.0, 0.0, 4.0], [0.1, 0.05, 3.0]])
+    nrm = np.tile([0.0, 0.0, -1.0], (4, 1))
+    t0, tu, tk = np.full(4, -1.0), np.full(4, 1.0), np.zeros(1)
+    p, n, keep, border = oracle.surfel_correct(pos, nrm, t0, tu, T, T, tk, cam, band=(1e-5, 1e-3))
+    assert border.tolist() == [False, True, True, False]
+    p2, n2, keep2 = oracle.surfel_correct(pos, nrm, t0, tu, T, T, tk, cam)
+    assert np.array_equal(keep, keep2) and np.array_equal(p, p2)
+    # outside the time window nothing is a border case
+    _, _, _, b3 = oracle.surfel_correct(pos, nrm, np.full(4, 0.5), tu, T, T, tk, cam, band=(1e-5, 1e-3))
+    assert not b3.any()
