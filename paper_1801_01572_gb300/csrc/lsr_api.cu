@@ -2347,12 +2347,7 @@ static int objective_impl(lsr_ctx *c, int32_t n, const float *const *P, const in
         for (int k = 0; k < 4; ++k) acc += M[4 * r + k] * T[4 * k + q];
         Tm[4 * r + q] = acc;
       }
-    float Rf[9], tf[3], vf[3];
-    for (int r = 0; r < 3; ++r) {
-      for (int q = 0; q < 3; ++q) Rf[3 * r + q] = (float)Tm[4 * r + q];
-      tf[r] = (float)Tm[4 * r + 3];
-      vf[r] = (float)w[3 + r];
-    }
+    const double vd[3] = {w[3], w[4], w[5]};
     // eps grid of Q with caller indices (build_grid_xyz carries caller order)
     TRY_CUDA(c, launch_bbox_xyz(Q[i], Cq.n, Cq.box_part, bbox_blocks(Cq.n), Cq.box, s), "bbox");
     TRY_CUDA(c, launch_grid_params(Cq.box, eps, Cq.n, Cq.cap_e, Cq.ge, s), "grid params");
@@ -2360,8 +2355,8 @@ static int objective_impl(lsr_ctx *c, int32_t n, const float *const *P, const in
     TRY_CUDA(c, build_nbmask(Cq.ge, Cq.start_e, Cq.cap_e, Cq.mask_e, s), "mask");
     if (grad) TRY_CUDA(c, cudaMemsetAsync(dQ[i], 0, sizeof(float) * 3 * nQ[i], s), "memset dQ");
     TRY_CUDA(c,
-             launch_objective(P[i], (int)nP[i], Cq.ge, Cq.start_e, Cq.Xe, Rf, tf, vf, eps, mu,
-                              grad ? (float)dE[i] : 1.f, grad ? 1 : 0, part, out7 + 7 * i, grad ? dP[i] : nullptr,
+             launch_objective(P[i], (int)nP[i], Cq.ge, Cq.start_e, Cq.Xe, Tm, vd, eps, mu,
+                              grad ? dE[i] : 1.0, grad ? 1 : 0, part, out7 + 7 * i, grad ? dP[i] : nullptr,
                               grad ? dQ[i] : nullptr, s),
              "objective");
   }

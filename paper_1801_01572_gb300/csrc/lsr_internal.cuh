@@ -624,7 +624,7 @@ cudaError_t launch_implicit(const float *P, int nP, const GridParams *ge, const 
                             int nQ, const double T[16], float eps, double mu, const double *dl_dev,
                             double *partials, double *out, float *dP, float *dQ, cudaStream_t s);
 cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
-                             const float R[9], const float t[3], const float v[3], float eps, float mu, float scale,
+                             const double T[16], const double v[3], float eps, float mu, double scale,
                              int want_grad, double *partials, double *out7, float *dP, float *dQ, cudaStream_t s);
 
 }  // namespace lsr

@@ -59,72 +59,102 @@ __device__ void exp_so3(const double w[3], double R[9]) {
     }
 }
 
-// Solve A d = -b (Cholesky, FP64) from the summed partials and left-multiply
-// the pose by the update about the centre c used for this step:
-// x' = Exp(d_w)(x - c) + c + d_v. The next step's centre is the weighted
-// centroid of this step's correspondences.
-__device__ void refine_solve(const double *acc, RansacState *st, int max_iters, double tol) {
-  double A[36];
-  int k = 0;
-  for (int a = 0; a < 6; ++a)
-    for (int b = a; b < 6; ++b) {
-      A[6 * a + b] = A[6 * b + a] = acc[k++];
+// Per-step sums of the IRLS normal equations. With J = [-[xc]_x | I] (xc the
+// moved point about the step's centre c), w the line-process weight of eq. (4)
+// and r the residual, J^T W J and J^T W r need only these 17 sums:
+//   [0] count  [1] sum w  [2..4] sum w xc  [5..10] sum w xc_a xc_b (00 01 02 11 12 22)
+//   [11..16] b = sum w J^T r = (sum w xc x r, sum w r)
+constexpr int kNSum = 17;
+static_assert(kNSum <= kNAcc, "refinement partial layout");
+
+// Solve A d = -b in FP64 from the summed partials (LDL^T: one division per
+// pivot, no square root) and left-multiply the pose by the update about the
+// centre c used for this step: x' = Exp(d_w)(x - c) + c + d_v. The next step's
+// centre is the weighted centroid of this step's correspondences.
+__device__ void refine_solve(const double *S, RansacState *st, int max_iters, double tol) {
+  const double *xx = S + 5, *b = S + 11;
+  const double sw = S[1], sx0 = S[2], sx1 = S[3], sx2 = S[4];
+  double A[6][6] = {{xx[3] + xx[5], -xx[1], -xx[2], 0.0, -sx2, sx1},
+                    {0.0, xx[0] + xx[5], -xx[4], sx2, 0.0, -sx0},
+                    {0.0, 0.0, xx[0] + xx[3], -sx1, sx0, 0.0},
+                    {0.0, 0.0, 0.0, sw, 0.0, 0.0},
+                    {0.0, 0.0, 0.0, 0.0, sw, 0.0},
+                    {0.0, 0.0, 0.0, 0.0, 0.0, sw}};
+  for (int i = 1; i < 6; ++i)
+    for (int j = 0; j < i; ++j) A[i][j] = A[j][i];
+  double L[6][6], D[6], iD[6];
+  bool pd = S[0] >= 3.0;
+  for (int j = 0; j < 6 && pd; ++j) {
+    double dj = A[j][j];
+    for (int k = 0; k < j; ++k) dj -= L[j][k] * L[j][k] * D[k];
+    if (!(dj > 0.0)) {
+      pd = false;
+      break;
     }
-  double L[36];
-  for (int i = 0; i < 36; ++i) L[i] = 0.0;
-  bool pd = acc[27] >= 3.0;
-  for (int i = 0; i < 6 && pd; ++i)
-    for (int j = 0; j <= i; ++j) {
-      double s = A[6 * i + j];
-      for (int q = 0; q < j; ++q) s -= L[6 * i + q] * L[6 * j + q];
-      if (i == j) {
-        if (!(s > 0.0)) {
-          pd = false;
-          break;
-        }
-        L[6 * i + i] = sqrt(s);
-      } else {
-        L[6 * i + j] = s / L[6 * j + j];
-      }
+    D[j] = dj;
+    iD[j] = 1.0 / dj;
+    for (int i = j + 1; i < 6; ++i) {
+      double v = A[i][j];
+      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k] * D[k];
+      L[i][j] = v * iD[j];
     }
+  }
   if (!pd) {
     st->active = 0;
     return;
   }
   double y[6], d[6];
   for (int i = 0; i < 6; ++i) {
-    double s = -acc[21 + i];
-    for (int q = 0; q < i; ++q) s -= L[6 * i + q] * y[q];
-    y[i] = s / L[6 * i + i];
+    double v = -b[i];
+    for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
+    y[i] = v;
   }
   for (int i = 5; i >= 0; --i) {
-    double s = y[i];
-    for (int q = i + 1; q < 6; ++q) s -= L[6 * q + i] * d[q];
-    d[i] = s / L[6 * i + i];
+    double v = y[i] * iD[i];
+    for (int k = i + 1; k < 6; ++k) v -= L[k][i] * d[k];
+    d[i] = v;
   }
+  // Exp of the rotation part: the series of sin(t)/t and (1 - cos t)/t^2 to
+  // the t^8 term below t = 0.01 (the next term is below 1e-21), else sin/cos
   double Rd[9];
-  exp_so3(d, Rd);
+  {
+    const double th2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double a, bb;
+    if (th2 < 1e-4) {
+      a = 1.0 - th2 / 6.0 * (1.0 - th2 / 20.0 * (1.0 - th2 / 42.0 * (1.0 - th2 / 72.0)));
+      bb = 0.5 * (1.0 - th2 / 12.0 * (1.0 - th2 / 30.0 * (1.0 - th2 / 56.0 * (1.0 - th2 / 90.0))));
+    } else {
+      const double th = sqrt(th2);
+      a = sin(th) / th;
+      bb = (1.0 - cos(th)) / th2;
+    }
+    const double K[9] = {0, -d[2], d[1], d[2], 0, -d[0], -d[1], d[0], 0};
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        const double k2 = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+        Rd[3 * r + c] = (r == c ? 1.0 : 0.0) + a * K[3 * r + c] + bb * k2;
+      }
+  }
   const double *c = st->center;
   double v[3];
   for (int r = 0; r < 3; ++r) v[r] = c[r] - (Rd[3 * r] * c[0] + Rd[3 * r + 1] * c[1] + Rd[3 * r + 2] * c[2]) + d[3 + r];
-  double M[16] = {Rd[0], Rd[1], Rd[2], v[0], Rd[3], Rd[4], Rd[5], v[1], Rd[6], Rd[7], Rd[8], v[2], 0, 0, 0, 1};
-  double Tn[16];
-  for (int r = 0; r < 4; ++r)
-    for (int q = 0; q < 4; ++q) {
-      double s = 0.0;
-      for (int m = 0; m < 4; ++m) s += M[4 * r + m] * st->T[4 * m + q];
-      Tn[4 * r + q] = s;
-    }
-  for (int i = 0; i < 16; ++i) st->T[i] = Tn[i];
-  if (acc[28] > 0.0)
-    for (int r = 0; r < 3; ++r) st->center[r] = acc[29 + r] / acc[28];
-  double nd = 0.0;
-  for (int i = 0; i < 6; ++i) nd += d[i] * d[i];
-  nd = sqrt(nd);
-  st->last_step = nd;
+  double Tn[12];
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 4; ++q)
+      Tn[4 * r + q] = Rd[3 * r] * st->T[q] + Rd[3 * r + 1] * st->T[4 + q] + Rd[3 * r + 2] * st->T[8 + q] +
+                      (q == 3 ? v[r] : 0.0);
+  for (int i = 0; i < 12; ++i) st->T[i] = Tn[i];
+  if (sw > 0.0) {
+    const double iw = 1.0 / sw;
+    const double cn[3] = {c[0] + sx0 * iw, c[1] + sx1 * iw, c[2] + sx2 * iw};
+    for (int r = 0; r < 3; ++r) st->center[r] = cn[r];
+  }
+  double nd2 = 0.0;
+  for (int i = 0; i < 6; ++i) nd2 += d[i] * d[i];
+  st->last_step = sqrt(nd2);
   st->iters_done += 1;
   st->level_iters += 1;
-  if (nd < tol || st->level_iters >= max_iters) st->active = 0;
+  if (nd2 < tol * tol || st->level_iters >= max_iters) st->active = 0;
 }
 
 // One IRLS step. Every block accumulates its points; the last block to
@@ -135,7 +165,7 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
                                                              RansacState *st, double *partials, int max_iters,
                                                              double tol, int *__restrict__ seeds) {
   __shared__ int s_last;
-  __shared__ double tot[kNAcc];
+  __shared__ double tot[kNSum];
   if (!st->active) return;
   const GridParams g = *gep;
   const double *T = st->T;
@@ -145,23 +175,11 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
     c[r] = (float)st->center[r];
     tc[r] = (float)(T[4 * r + 3] - st->center[r]);
   }
-  // every lane of a point group holds the same correspondence after the
-  // group search: lane sub accumulates the sums U sub .. U sub + U - 1 of the
-  // 32 (the 21 entries of J^T W J, the 6 of J^T W r, count, sum w, sum w x)
-  constexpr int G = kRefG, GPB = kRefThreads / G, U = kNAcc / G;
-  static_assert(U * G == kNAcc && G <= 32, "sums per lane of a point group");
-  int grp = threadIdx.x / G, sub = threadIdx.x & (G - 1);
-  int qa[U], qb[U];  // the (a, b) column pair of a J^T W J entry, or -1
+  constexpr int G = kRefG, GPB = kRefThreads / G;
+  const int grp = threadIdx.x / G, sub = threadIdx.x & (G - 1);
+  float acc[kNSum];
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    int k = U * sub + u, a = 0;
-    while (a < 6 && k >= 6 - a) k -= 6 - a, ++a;  // k-th entry of the row-major upper triangle
-    qa[u] = a < 6 ? a : -1;
-    qb[u] = a < 6 ? a + k : -1;
-  }
-  float acc[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) acc[u] = 0.f;
+  for (int u = 0; u < kNSum; ++u) acc[u] = 0.f;
   // block-uniform trip count: every lane reaches the group shuffles
   for (int r0 = blockIdx.x * GPB; r0 < nP; r0 += gridDim.x * GPB) {
     int i = r0 + grp;
@@ -169,59 +187,44 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
     float4 p = valid ? XP[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid && strideP > 1 && __float_as_int(p.w) % strideP != 0) valid = false;
     if (!valid) p.x = __int_as_float(0x7fc00000);  // NaN: the query visits no cell
-    float xc0 = fmaf(R[0], p.x, fmaf(R[1], p.y, fmaf(R[2], p.z, tc[0])));
-    float xc1 = fmaf(R[3], p.x, fmaf(R[4], p.y, fmaf(R[5], p.z, tc[1])));
-    float xc2 = fmaf(R[6], p.x, fmaf(R[7], p.y, fmaf(R[8], p.z, tc[2])));
-    float x = xc0 + c[0], y = xc1 + c[1], z = xc2 + c[2];
+    const float xc0 = fmaf(R[0], p.x, fmaf(R[1], p.y, fmaf(R[2], p.z, tc[0])));
+    const float xc1 = fmaf(R[3], p.x, fmaf(R[4], p.y, fmaf(R[5], p.z, tc[1])));
+    const float xc2 = fmaf(R[6], p.x, fmaf(R[7], p.y, fmaf(R[8], p.z, tc[2])));
+    const float x = xc0 + c[0], y = xc1 + c[1], z = xc2 + c[2];
     float best;
     int bt, bidx;
     // the previous step's neighbour of this point starts the search (an exact
-    // search either way; the pose moves little between steps, so most cells
-    // beyond it are skipped)
+    // search either way)
     const int seed = valid ? seeds[i] : -1;
     group_nn<G>(g, start, Xe, x, y, z, eps2, best, bt, bidx, seed);
     if (valid && sub == 0) seeds[i] = bt;
-    if (!valid || bt < 0) continue;
-    float4 q = Xe[bt];
-    float r[3] = {x - q.x, y - q.y, z - q.z};
-    float s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-    float l = mu / (mu + s);
-    float w = l * l;
-    // J = [-[xc]_x | I] (rows: x, y, z; columns: alpha, beta, gamma, tx, ty, tz)
-    auto col = [&](int a, float (&v)[3]) {
-      v[0] = a == 1 ? xc2 : (a == 2 ? -xc1 : (a == 3 ? 1.f : 0.f));
-      v[1] = a == 0 ? -xc2 : (a == 2 ? xc0 : (a == 4 ? 1.f : 0.f));
-      v[2] = a == 0 ? xc1 : (a == 1 ? -xc0 : (a == 5 ? 1.f : 0.f));
-    };
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = U * sub + u;
-      float va[3], vb[3];
-      if (qa[u] >= 0) {
-        col(qa[u], va);
-        col(qb[u], vb);
-        acc[u] += w * (va[0] * vb[0] + va[1] * vb[1] + va[2] * vb[2]);
-      } else if (k < 27) {
-        col(k - 21, va);
-        acc[u] += w * (va[0] * r[0] + va[1] * r[1] + va[2] * r[2]);
-      } else {
-        acc[u] += k == 27 ? 1.f : (k == 28 ? w : w * (k == 29 ? x : (k == 30 ? y : z)));
-      }
-    }
+    if (!valid || bt < 0 || sub != 0) continue;
+    const float4 q = Xe[bt];
+    const float e0 = x - q.x, e1 = y - q.y, e2 = z - q.z;  // the residual
+    const float s = e0 * e0 + e1 * e1 + e2 * e2;
+    const float l = mu / (mu + s);
+    const float w = l * l;
+    const float w0 = w * xc0, w1 = w * xc1, w2 = w * xc2;
+    acc[0] += 1.f;
+    acc[1] += w;
+    acc[2] += w0, acc[3] += w1, acc[4] += w2;
+    acc[5] += w0 * xc0, acc[6] += w0 * xc1, acc[7] += w0 * xc2;
+    acc[8] += w1 * xc1, acc[9] += w1 * xc2, acc[10] += w2 * xc2;
+    acc[11] += w * (xc1 * e2 - xc2 * e1);
+    acc[12] += w * (xc2 * e0 - xc0 * e2);
+    acc[13] += w * (xc0 * e1 - xc1 * e0);
+    acc[14] += w * e0, acc[15] += w * e1, acc[16] += w * e2;
   }
   {
-    // the lanes sub, sub + G, ... of a warp hold the same sums
-    __shared__ float sm[kRefThreads / 32][kNAcc];
+    __shared__ float sm[kRefThreads / 32][kNSum];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
-    for (int off = 16; off >= G; off >>= 1)
-#pragma unroll
-      for (int u = 0; u < U; ++u) acc[u] += __shfl_down_sync(0xffffffffu, acc[u], off);
-    if (lane < G)
-#pragma unroll
-      for (int u = 0; u < U; ++u) sm[wp][U * lane + u] = acc[u];
+    for (int u = 0; u < kNSum; ++u) {
+      const float v = warp_sum(acc[u]);
+      if (lane == 0) sm[wp][u] = v;
+    }
     __syncthreads();
-    if (threadIdx.x < kNAcc) {
+    if (threadIdx.x < kNSum) {
       double t = 0.0;
       for (int k = 0; k < kRefThreads / 32; ++k) t += (double)sm[k][threadIdx.x];
       partials[(size_t)blockIdx.x * kNAcc + threadIdx.x] = t;
@@ -234,16 +237,18 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
   if (!s_last) return;
   __threadfence();
   {
-    // all threads: quantity k = t % 32 over the blocks t / 32, t / 32 + 8, ...,
-    // then the 8 segments in order (a fixed order: the sums are deterministic)
-    constexpr int kSeg = kRefThreads / kNAcc;
-    __shared__ double seg[kSeg][kNAcc];
-    const int k = threadIdx.x % kNAcc, sg = threadIdx.x / kNAcc;
-    double sum = 0.0;
-    for (unsigned b = sg; b < gridDim.x; b += kSeg) sum += __ldcg(partials + (size_t)b * kNAcc + k);
-    seg[sg][k] = sum;
+    // sum k = t % 17 over the blocks t / 17, t / 17 + 15, ..., then the 15
+    // segments in order (a fixed order: the sums are deterministic)
+    constexpr int kSeg = kRefThreads / kNSum;
+    __shared__ double seg[kSeg][kNSum];
+    const int k = threadIdx.x % kNSum, sg = threadIdx.x / kNSum;
+    if (sg < kSeg) {
+      double sum = 0.0;
+      for (unsigned b = sg; b < gridDim.x; b += kSeg) sum += __ldcg(partials + (size_t)b * kNAcc + k);
+      seg[sg][k] = sum;
+    }
     __syncthreads();
-    if (threadIdx.x < kNAcc) {
+    if (threadIdx.x < kNSum) {
       double t = 0.0;
       for (int q = 0; q < kSeg; ++q) t += seg[q][threadIdx.x];
       tot[threadIdx.x] = t;
@@ -383,11 +388,22 @@ __global__ void k_info_final(const double *__restrict__ partials, int nb, const 
 // Forward and backward share this kernel; the backward also writes
 // dP_i = 2 rho'(s) R^T r_i, scatters dQ_j -= 2 rho'(s) r_i, and reduces
 // g_v = sum 2 rho' r_i and g_w = sum z_i x (2 rho' r_i) with z_i = x_i - v.
-// dxi = (J_l(w)^T g_w, g_v) is finished on the host.
+// dxi = (J_l(w)^T g_w, g_v) is finished on the host. The nearest neighbour is
+// found in FP32 (the pose rounded to FP32); the residual of the pair, the
+// terms and their sums are evaluated in FP64 from the FP32 coordinates: a
+// residual of a few millimetres between points metres from the origin would
+// otherwise carry the 2^-24 rounding of the coordinates (about 1e-7 m).
 struct ObjArgs {
-  float R[9], t[3], v[3];
-  float eps2, mu, rho_eps, scale;
+  float Rf[9], tf[3];    // the pose in FP32, for the neighbour search
+  double R[9], t[3], v[3];
+  float eps2;
+  double mu, rho_eps, scale;
 };
+
+__device__ __forceinline__ double warp_sum_dbl(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
 
 __global__ void __launch_bounds__(kRefThreads) k_objective(const float *__restrict__ P, int nP, const GridParams *gep,
                                                            const int *__restrict__ start,
@@ -395,7 +411,7 @@ __global__ void __launch_bounds__(kRefThreads) k_objective(const float *__restri
                                                            double *partials, float *__restrict__ dP,
                                                            float *__restrict__ dQ) {
   const GridParams g = *gep;
-  float acc[7] = {0, 0, 0, 0, 0, 0, 0};  // E, g_v (3), g_w (3)
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};  // E, g_v (3), g_w (3)
   constexpr int G = kObjG, GPB = kRefThreads / G;
   int grp = threadIdx.x / G, sub = threadIdx.x & (G - 1);
   for (int rb = blockIdx.x * GPB; rb < nP; rb += gridDim.x * GPB) {
@@ -403,9 +419,9 @@ __global__ void __launch_bounds__(kRefThreads) k_objective(const float *__restri
     bool valid = i < nP;
     float px = valid ? P[3 * i] : __int_as_float(0x7fc00000), py = valid ? P[3 * i + 1] : 0.f,
           pz = valid ? P[3 * i + 2] : 0.f;
-    float x = fmaf(a.R[0], px, fmaf(a.R[1], py, fmaf(a.R[2], pz, a.t[0])));
-    float y = fmaf(a.R[3], px, fmaf(a.R[4], py, fmaf(a.R[5], pz, a.t[1])));
-    float z = fmaf(a.R[6], px, fmaf(a.R[7], py, fmaf(a.R[8], pz, a.t[2])));
+    float x = fmaf(a.Rf[0], px, fmaf(a.Rf[1], py, fmaf(a.Rf[2], pz, a.tf[0])));
+    float y = fmaf(a.Rf[3], px, fmaf(a.Rf[4], py, fmaf(a.Rf[5], pz, a.tf[1])));
+    float z = fmaf(a.Rf[6], px, fmaf(a.Rf[7], py, fmaf(a.Rf[8], pz, a.tf[2])));
     float best;
     int bt, bidx;
     group_nn<G>(g, start, Xe, x, y, z, a.eps2, best, bt, bidx);
@@ -414,29 +430,46 @@ __global__ void __launch_bounds__(kRefThreads) k_objective(const float *__restri
       if (want_grad) dP[3 * i] = dP[3 * i + 1] = dP[3 * i + 2] = 0.f;
       continue;
     }
-    float4 q = Xe[bt];
-    float r0 = x - q.x, r1 = y - q.y, r2 = z - q.z;
-    float s = r0 * r0 + r1 * r1 + r2 * r2;
-    float den = a.mu + s;
+    const float4 q = Xe[bt];
+    const double p[3] = {px, py, pz};
+    double zd[3], r[3];
+    for (int k = 0; k < 3; ++k) {
+      zd[k] = a.R[3 * k] * p[0] + a.R[3 * k + 1] * p[1] + a.R[3 * k + 2] * p[2] + a.t[k];
+      r[k] = zd[k] - (double)(k == 0 ? q.x : (k == 1 ? q.y : q.z));
+    }
+    const double s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    const double den = a.mu + s;
     acc[0] += a.mu * s / den - a.rho_eps;
     if (want_grad) {
-      float k2 = 2.f * a.mu * a.mu / (den * den);
-      float g0 = k2 * r0, g1 = k2 * r1, g2 = k2 * r2;
-      dP[3 * i + 0] = a.scale * (a.R[0] * g0 + a.R[3] * g1 + a.R[6] * g2);
-      dP[3 * i + 1] = a.scale * (a.R[1] * g0 + a.R[4] * g1 + a.R[7] * g2);
-      dP[3 * i + 2] = a.scale * (a.R[2] * g0 + a.R[5] * g1 + a.R[8] * g2);
-      int j = __float_as_int(q.w);
-      atomicAdd(&dQ[3 * j + 0], -a.scale * g0);
-      atomicAdd(&dQ[3 * j + 1], -a.scale * g1);
-      atomicAdd(&dQ[3 * j + 2], -a.scale * g2);
-      float zx = x - a.v[0], zy = y - a.v[1], zz = z - a.v[2];
+      const double k2 = 2.0 * a.mu * a.mu / (den * den);
+      const double g0 = k2 * r[0], g1 = k2 * r[1], g2 = k2 * r[2];
+      dP[3 * i + 0] = (float)(a.scale * (a.R[0] * g0 + a.R[3] * g1 + a.R[6] * g2));
+      dP[3 * i + 1] = (float)(a.scale * (a.R[1] * g0 + a.R[4] * g1 + a.R[7] * g2));
+      dP[3 * i + 2] = (float)(a.scale * (a.R[2] * g0 + a.R[5] * g1 + a.R[8] * g2));
+      const int j = __float_as_int(q.w);
+      atomicAdd(&dQ[3 * j + 0], (float)(-a.scale * g0));
+      atomicAdd(&dQ[3 * j + 1], (float)(-a.scale * g1));
+      atomicAdd(&dQ[3 * j + 2], (float)(-a.scale * g2));
+      const double zx = zd[0] - a.v[0], zy = zd[1] - a.v[1], zz = zd[2] - a.v[2];
       acc[1] += g0, acc[2] += g1, acc[3] += g2;
       acc[4] += zy * g2 - zz * g1;
       acc[5] += zz * g0 - zx * g2;
       acc[6] += zx * g1 - zy * g0;
     }
   }
-  block_reduce_to<7>(acc, partials + (size_t)blockIdx.x * 7);
+  __shared__ double sm[kRefThreads / 32][7];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const double v = warp_sum_dbl(acc[k]);
+    if (lane == 0) sm[wp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double t = 0.0;
+    for (int k = 0; k < kRefThreads / 32; ++k) t += sm[k][threadIdx.x];
+    partials[(size_t)blockIdx.x * 7 + threadIdx.x] = t;
+  }
 }
 
 __global__ void k_objective_sum(const double *partials, int nblocks, double *out) {
@@ -524,14 +557,17 @@ int objective_blocks(int nP) {
 }
 
 cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
-                             const float R[9], const float t[3], const float v[3], float eps, float mu, float scale,
+                             const double T[16], const double v[3], float eps, float mu, double scale,
                              int want_grad, double *partials, double *out7, float *dP, float *dQ, cudaStream_t s) {
   ObjArgs a;
-  for (int k = 0; k < 9; ++k) a.R[k] = R[k];
-  for (int k = 0; k < 3; ++k) a.t[k] = t[k], a.v[k] = v[k];
+  for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 3; ++q) a.R[3 * r + q] = T[4 * r + q], a.Rf[3 * r + q] = (float)T[4 * r + q];
+    a.t[r] = T[4 * r + 3], a.tf[r] = (float)T[4 * r + 3], a.v[r] = v[r];
+  }
   a.eps2 = eps * eps;
   a.mu = mu;
-  a.rho_eps = mu * a.eps2 / (mu + a.eps2);
+  const double e2 = (double)eps * (double)eps;
+  a.rho_eps = a.mu * e2 / (a.mu + e2);
   a.scale = scale;
   int nb = objective_blocks(nP);
   LSR_LAUNCH(k_objective<<<nb, kRefThreads, 0, s>>>(P, nP, ge, start_e, Xe, a, want_grad, partials, dP, dQ));

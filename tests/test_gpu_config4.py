@@ -11,7 +11,8 @@ differences are taken of the objective with the correspondences of the base
 pose held (the function the analytic gradient differentiates), evaluated in
 FP64 from the oracle's neighbours and pose update; every component must agree
 at relative 1e-4 (plus 1e-6 of the largest component, for components near
-zero). Point gradients are checked against the oracle's and against FP64
+zero, plus the terms of the few points whose pair an FP32 search may form
+differently: each such pair moves the sum by its own term). Point gradients are checked against the oracle's and against FP64
 central differences of the held objective in the point coordinates (a seeded
 1% of them), excluding only the points whose nearest neighbour an FP32 search
 may pick differently: a runner-up within 1e-6 m of the nearest, or a distance
@@ -70,14 +71,34 @@ def test_config4_objective_and_pose_gradient(run4, i):
     assert abs(run4["E"][i] - E_ref) <= 1e-5 * abs(E_ref)
     g = run4["dxi"][i]
     scale = np.abs(dxi_ref).max()
-    assert np.all(np.abs(g - dxi_ref) <= 1e-4 * np.abs(dxi_ref) + 1e-6 * scale), (g, dxi_ref)
+    # the pairs an FP32 search may form differently each move dxi by their own
+    # term (or their term with the runner-up neighbour): that is added to the bound
+    slack = ambiguous_dxi(P, Q, xi, T0)
+    assert np.all(np.abs(g - dxi_ref) <= 1e-4 * np.abs(dxi_ref) + 1e-6 * scale + slack), (g, dxi_ref, slack)
     h = 1e-6
     for k in range(6):
         e = np.zeros(6)
         e[k] = h
         fd = (held_objective(P, Q, nn, xi + e, T0) - held_objective(P, Q, nn, xi - e, T0)) / (2 * h)
-        assert abs(g[k] - fd) <= 1e-4 * abs(fd) + 1e-6 * scale, (k, g[k], fd)
+        assert abs(g[k] - fd) <= 1e-4 * abs(fd) + 1e-6 * scale + slack[k], (k, g[k], fd)
     assert abs(held_objective(P, Q, nn, xi, T0) - E_ref) <= 1e-9 * abs(E_ref)
+
+
+def ambiguous_dxi(P, Q, xi, T0):
+    """Per component, the sum over the FP32-ambiguous points of the absolute
+    dxi terms they contribute with their nearest and with their runner-up
+    neighbour (oracle, FP64)."""
+    spatial = pytest.importorskip("scipy.spatial")
+    T = oracle.apply_xi(xi, T0)
+    Z = P @ T[:3, :3].T + T[:3, 3]
+    d, j = spatial.cKDTree(Q).query(Z, k=2)
+    amb = np.nonzero((np.abs(d[:, 0] - EPS) < 1e-6) | ((d[:, 0] < EPS + 1e-6) & (d[:, 1] - d[:, 0] < 1e-6)))[0]
+    slack = np.zeros(6)
+    for a in amb:
+        for q in j[a]:
+            _, _, _, dx, _ = oracle.objective(P[a:a + 1], Q[q:q + 1], xi, T0, EPS, MU)
+            slack += np.abs(dx)
+    return slack
 
 
 def ambiguous_points(P, Q, xi, T0):
