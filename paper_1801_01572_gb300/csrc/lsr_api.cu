@@ -302,6 +302,7 @@ struct PairLayout {
   uint8_t *tie = nullptr;    // those tied at the maximum exact count
   int *amb = nullptr;        // points in undecided voxels per hypothesis
   int *count2 = nullptr;     // exact counts of the reaching hypotheses
+  int *tie_list = nullptr;   // the survivor slots tied at the top
   // single-cell lattice of Q (lsr_params.nn_mode = LSR_NN_SINGLE_CELL)
   int cap_s = 0;
   GridParams *gs = nullptr;
@@ -344,6 +345,7 @@ void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int leve
   L.tie = a.take<uint8_t>(L.surv_cap);
   L.amb = a.take<int>(L.surv_cap);
   L.count2 = a.take<int>(L.surv_cap);
+  L.tie_list = a.take<int>(L.surv_cap);
   L.tc_ws = a.take<char>(precision != LSR_MATCH_FP32 ? tc_workspace_bytes(nP, nQ, precision == LSR_MATCH_BF16)
                                                       : fp32_workspace_bytes(nQ));
   L.cap_s = L.Q.cap_e;
@@ -733,11 +735,12 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
              launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.rest,
                                     &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
              "consensus reach");
-    TRY_CUDA(c, launch_reach_mask(L.count2, nullptr, L.reach, &L.st->n_surv, L.tie, s), "ties");
+    TRY_CUDA(c, launch_reach_mask(L.count2, nullptr, L.reach, &L.st->n_surv, L.tie, &L.st->n_tie, L.tie_list, s),
+             "ties");
     // (the exact kernel adds its counts too: into amb, no longer needed)
     TRY_CUDA(c,
-             launch_consensus(Pc.Xn, nP, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.tie, &L.st->n_surv, 0, p.eps_inlier,
-                              L.amb, L.sum, s, c->cons_lanes),
+             launch_consensus(Pc.Xn, nP, Qc.ge, Qc.start_e, Qc.Xe, L.pose, nullptr, &L.st->n_tie, 0, p.eps_inlier,
+                              L.amb, L.sum, s, c->cons_lanes, L.tie_list),
              "consensus sums");
     tm.mark();
     TRY_CUDA(c, launch_select(L.surv, L.count2, L.sum, L.reach, L.pose, nP, p.min_inlier_ratio, L.st, s), "select");

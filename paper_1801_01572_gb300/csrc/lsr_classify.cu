@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(kClsThreads, kClsMinBlocks) k_consensus_count(
 // mask[k] = ok[k] && lo[k] + extra[k] >= L (extra == null: 0), if L > 0.
 __global__ void __launch_bounds__(1024) k_reach_mask(const int *__restrict__ lo, const int *__restrict__ extra,
                                                      const uint8_t *__restrict__ ok, const int *n_dev,
-                                                     uint8_t *__restrict__ mask) {
+                                                     uint8_t *__restrict__ mask, int *__restrict__ n_mask,
+                                                     int *__restrict__ list) {
   __shared__ int s_max[32];
   const int n = *n_dev;
   int mx = 0;
@@ -243,9 +244,23 @@ __global__ void __launch_bounds__(1024) k_reach_mask(const int *__restrict__ lo,
   }
   __syncthreads();
   mx = s_max[0];
+  __shared__ int s_set;
+  if (threadIdx.x == 0) s_set = 0;
+  __syncthreads();
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const int up = lo[k] + (extra ? extra[k] : 0);
-    mask[k] = ((!ok || ok[k]) && (mx == 0 ? extra != nullptr : up >= mx)) ? 1 : 0;
+    const bool m = (!ok || ok[k]) && (mx == 0 ? extra != nullptr : up >= mx);
+    mask[k] = m ? 1 : 0;
+    // the set entries are also listed (in no particular order) for the kernels
+    // that visit only them
+    if (m && (list || n_mask)) {
+      const int slot = atomicAdd(&s_set, 1);
+      if (list) list[slot] = k;
+    }
+  }
+  if (n_mask) {
+    __syncthreads();
+    if (threadIdx.x == 0) *n_mask = s_set;
   }
 }
 
@@ -254,31 +269,52 @@ __global__ void __launch_bounds__(1024) k_reach_mask(const int *__restrict__ lo,
 __global__ void __launch_bounds__(1024) k_top_upper(const int *__restrict__ lo, const int *__restrict__ extra,
                                                     const uint8_t *__restrict__ ok, const int *n_dev, int K,
                                                     uint8_t *__restrict__ sel) {
-  __shared__ long long s_best[32];
+  // key: upper bound in the high word, complemented index in the low word,
+  // so keys are distinct and a larger key wins (ties to the smaller index).
+  // The K-th largest key T is found by radix selection, eight bits at a time
+  // from the top; the K keys >= T are then marked.
+  __shared__ unsigned hist[256];
+  __shared__ unsigned long long s_prefix, s_mask;
+  __shared__ unsigned s_need, s_nok;
   const int n = *n_dev;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) sel[k] = 0;
+  auto key_of = [&](int k) {
+    return ((unsigned long long)(unsigned)(lo[k] + extra[k]) << 32) | (unsigned)(0x7fffffff - k);
+  };
+  if (threadIdx.x == 0) s_nok = 0, s_prefix = 0ull, s_mask = 0ull, s_need = (unsigned)K;
   __syncthreads();
-  for (int round = 0; round < K; ++round) {
-    // key: upper bound in the high word, complemented index in the low word
-    long long best = -1;
+  unsigned mine = 0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) mine += (!ok || ok[k]) ? 1u : 0u;
+  atomicAdd(&s_nok, mine);
+  __syncthreads();
+  if (s_nok <= (unsigned)K) {  // every candidate is selected
+    for (int k = threadIdx.x; k < n; k += blockDim.x) sel[k] = (!ok || ok[k]) ? 1 : 0;
+    return;
+  }
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[d] = 0u;
+    __syncthreads();
+    const unsigned long long prefix = s_prefix, mask = s_mask;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      if ((ok && !ok[k]) || sel[k]) continue;
-      long long key = ((long long)(lo[k] + extra[k]) << 32) | (unsigned)(0x7fffffff - k);
-      best = key > best ? key : best;
+      if (ok && !ok[k]) continue;
+      const unsigned long long key = key_of(k);
+      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      long long o = __shfl_xor_sync(0xffffffffu, best, off);
-      best = o > best ? o : best;
-    }
-    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
-      long long b = -1;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = s_best[w] > b ? s_best[w] : b;
-      if (b >= 0) sel[0x7fffffff - (int)(b & 0xffffffff)] = 1;
+      unsigned need = s_need, above = 0u;
+      int d = 255;
+      for (; d > 0; --d) {
+        if (above + hist[d] >= need) break;
+        above += hist[d];
+      }
+      s_need = need - above;
+      s_prefix = prefix | ((unsigned long long)d << shift);
+      s_mask = mask | (255ull << shift);
     }
     __syncthreads();
   }
+  const unsigned long long T = s_prefix;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) sel[k] = ((!ok || ok[k]) && key_of(k) >= T) ? 1 : 0;
 }
 
 // One block: C = the maximum exact count among sel; then
@@ -351,9 +387,10 @@ cudaError_t launch_reach_rest(const int *lo, const int *extra, const int *exact,
   return cudaGetLastError();
 }
 
-cudaError_t launch_reach_mask(const int *lo, const int *extra, const uint8_t *ok, const int *n_dev, uint8_t *mask,
+cudaError_t launch_reach_mask(const int *lo, const int *extra, const uint8_t *ok, const int *n_dev, uint8_t *mask, int *n_mask,
+                              int *list,
                               cudaStream_t s) {
-  LSR_LAUNCH(k_reach_mask<<<1, 1024, 0, s>>>(lo, extra, ok, n_dev, mask));
+  LSR_LAUNCH(k_reach_mask<<<1, 1024, 0, s>>>(lo, extra, ok, n_dev, mask, n_mask, list));
   return cudaGetLastError();
 }
 

@@ -127,11 +127,11 @@ __global__ void __launch_bounds__(kImpThreads) k_implicit_sums(const float *__re
 // out: g (6), H (36, row-major), lambda (6), count, singular flag.
 __global__ void k_implicit_solve(const double *__restrict__ partials, int nb, const double *__restrict__ dl,
                                  double *__restrict__ out) {
+  __shared__ double seg[256], tot[kImpSums];
+  block_sum_partials(partials, nb, kImpSums, kImpSums, seg, tot);
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double S[kImpSums];
-  for (int k = 0; k < kImpSums; ++k) S[k] = 0.0;
-  for (int b = 0; b < nb; ++b)
-    for (int k = 0; k < kImpSums; ++k) S[k] += partials[(size_t)b * kImpSums + k];
+  for (int k = 0; k < kImpSums; ++k) S[k] = tot[k];
   double H[6][6], A[6][7];
   int k = 6;
   for (int u = 0; u < 6; ++u)
@@ -239,7 +239,7 @@ cudaError_t launch_implicit(const float *P, int nP, const GridParams *ge, const 
   a.mu = mu;
   const int nb = implicit_blocks(nP);
   LSR_LAUNCH(k_implicit_sums<<<nb, kImpThreads, 0, s>>>(P, nP, ge, start_e, Xe, a, partials));
-  LSR_LAUNCH(k_implicit_solve<<<1, 32, 0, s>>>(partials, nb, dl_dev, out));
+  LSR_LAUNCH(k_implicit_solve<<<1, 256, 0, s>>>(partials, nb, dl_dev, out));
   LSR_LAUNCH(k_implicit_grad<<<nb, kImpThreads, 0, s>>>(P, nP, ge, start_e, Xe, a, out, nQ, dP, dQ));
   return cudaGetLastError();
 }

@@ -380,6 +380,37 @@ struct Rigid12 {
   }
 };
 
+// Sums nq per-block partials (partials[b * stride + k], b < nb) with the whole
+// block: thread t adds quantity t % nq over the blocks t / nq, t / nq + S, ...
+// (S = blockDim.x / nq segments, eight loads in flight), then threads k < nq add
+// the S segment sums in order. The order is fixed, so the sums are
+// deterministic. seg: shared scratch of at least blockDim.x doubles; out[k] for
+// k < nq is valid after the call (which ends with a barrier).
+__device__ __forceinline__ void block_sum_partials(const double *__restrict__ partials, int nb, int nq, int stride,
+                                                   double *seg, double *out) {
+  const int S = (int)blockDim.x / nq, k = (int)threadIdx.x % nq, sg = (int)threadIdx.x / nq;
+  if (sg < S) {
+    double sum = 0.0;
+    int b = sg;
+    for (; b + 7 * S < nb; b += 8 * S) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(partials + (size_t)(b + u * S) * stride + k);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sum += v[u];
+    }
+    for (; b < nb; b += S) sum += __ldcg(partials + (size_t)b * stride + k);
+    seg[sg * nq + k] = sum;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nq) {
+    double t = 0.0;
+    for (int q = 0; q < S; ++q) t += seg[q * nq + threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
@@ -481,7 +512,7 @@ struct RansacState {
   unsigned ticket;     // blocks finished in the current refinement step
   int match_fallbacks; // BF16 matcher: queries re-scanned exactly in FP32
   int match_err;       // BF16 matcher: a CTA gave up waiting (result invalid)
-  int pad_;
+  int n_tie;           // hypotheses tied at the top exact count (their sums are computed)
   unsigned long long match_terms;  // FP32 matcher, counting launch: terms evaluated
   double final_sumd2;
   double T[16];        // current pose (refinement), row-major
@@ -504,9 +535,12 @@ cudaError_t launch_rigid_survivors(const float4 *XP, const int *invP, const floa
 cudaError_t launch_rigid4(const float *ps, const float *qs, int nh, float *pose, cudaStream_t s);
 // Consensus: for every pose k < *n_dev (or n_host if n_dev is null) with ok[k] (or ok == null),
 // count[k] / sum[k] (fixed point, 2^-40 m^2 units) over all P points.
+// list (optional, device): count only the poses list[0 .. *n_dev) (ok is then
+// ignored); few poses get P split into smaller chunks so that every block works.
 cudaError_t launch_consensus(const float4 *XP, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
                              const float *pose, const uint8_t *ok, const int *n_dev, int n_host, float eps,
-                             int *count, unsigned long long *sum, cudaStream_t s, int lanes = 1);
+                             int *count, unsigned long long *sum, cudaStream_t s, int lanes = 1,
+                             const int *list = nullptr);
 cudaError_t launch_select(const int *surv, const int *count, const unsigned long long *sum, const uint8_t *ok,
                           const float *pose, int nP, float min_ratio, RansacState *st, cudaStream_t s);
 
@@ -541,7 +575,9 @@ cudaError_t launch_reach_rest(const int *lo, const int *extra, const int *exact,
                               const int *n_dev, uint8_t *rest, uint8_t *all, cudaStream_t s);
 // With L = max over ok of lo: mask[k] = ok[k] && lo[k] + extra[k] >= L. If L is
 // 0: every ok hypothesis when extra is given, none otherwise.
-cudaError_t launch_reach_mask(const int *lo, const int *extra, const uint8_t *ok, const int *n_dev, uint8_t *mask,
+// n_mask, list (optional, device): the number of set entries and their indices.
+cudaError_t launch_reach_mask(const int *lo, const int *extra, const uint8_t *ok, const int *n_dev, uint8_t *mask, int *n_mask,
+                              int *list,
                               cudaStream_t s);
 constexpr double kFixScale = 1099511627776.0;  // 2^40
 

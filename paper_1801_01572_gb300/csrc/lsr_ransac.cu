@@ -345,23 +345,33 @@ __global__ void __launch_bounds__(kConsThreads) k_consensus(const float4 *__rest
                                                             const int *__restrict__ start,
                                                             const float4 *__restrict__ Xe, const float *__restrict__ pose,
                                                             const uint8_t *__restrict__ ok, const int *n_dev, int n_host,
-                                                            float eps2, int *count, unsigned long long *sum) {
+                                                            float eps2, int *count, unsigned long long *sum,
+                                                            const int *list) {
   constexpr int GPB = kConsThreads / G;
   const GridParams g = *gep;
   int nh = n_dev ? *n_dev : n_host;
-  int chunks = (nP + kConsChunk - 1) / kConsChunk;
+  // few poses (the top ties, the refined pose): smaller chunks of P so that
+  // every block of the grid gets work (the counts and fixed-point sums do not
+  // depend on the split)
+  int chunk = kConsChunk;
+  while (chunk > 256 && (int64_t)nh * ((nP + chunk - 1) / chunk) < (int64_t)gridDim.x) chunk >>= 1;
+  int chunks = (nP + chunk - 1) / chunk;
   int64_t items = (int64_t)nh * chunks;
   int grp = threadIdx.x / G, sub = threadIdx.x & (G - 1);
   __shared__ int s_cnt[kConsThreads / 32];
   __shared__ unsigned long long s_sum[kConsThreads / 32];
   for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
     int s = (int)(item / chunks), c = (int)(item - (int64_t)s * chunks);
-    if (ok && !ok[s]) continue;
+    if (list) {
+      s = list[s];
+    } else if (ok && !ok[s]) {
+      continue;
+    }
     Rigid12 T;
     T.load(pose + (size_t)s * 12);
     int cnt = 0;
     unsigned long long acc = 0ull;
-    int i0 = c * kConsChunk, i1 = (c + 1) * kConsChunk < nP ? (c + 1) * kConsChunk : nP;
+    int i0 = c * chunk, i1 = (c + 1) * chunk < nP ? (c + 1) * chunk : nP;
     // block-uniform trip count: every lane reaches the group shuffles
     for (int r = i0; r < i1; r += GPB) {
       int i = r + grp;
@@ -486,11 +496,11 @@ cudaError_t launch_rigid4(const float *ps, const float *qs, int nh, float *pose,
 
 cudaError_t launch_consensus(const float4 *XP, int nP, const GridParams *ge, const int *start_e, const float4 *Xe,
                              const float *pose, const uint8_t *ok, const int *n_dev, int n_host, float eps, int *count,
-                             unsigned long long *sum, cudaStream_t s, int lanes) {
+                             unsigned long long *sum, cudaStream_t s, int lanes, const int *list) {
   float e2 = eps * eps;
 #define LSR_CONS(G)                                                                                            \
   LSR_LAUNCH(k_consensus<G><<<kSms * 8, kConsThreads, 0, s>>>(XP, nP, ge, start_e, Xe, pose, ok, n_dev, n_host, e2, \
-                                                             count, sum))
+                                                             count, sum, list))
   switch (lanes) {
     case 2: LSR_CONS(2); break;
     case 4: LSR_CONS(4); break;

@@ -243,8 +243,17 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
     __shared__ double seg[kSeg][kNSum];
     const int k = threadIdx.x % kNSum, sg = threadIdx.x / kNSum;
     if (sg < kSeg) {
+      // eight loads in flight, added in block order (the same order as one at a time)
       double sum = 0.0;
-      for (unsigned b = sg; b < gridDim.x; b += kSeg) sum += __ldcg(partials + (size_t)b * kNAcc + k);
+      unsigned b = sg;
+      for (; b + 7 * kSeg < gridDim.x; b += 8 * kSeg) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(partials + (size_t)(b + u * kSeg) * kNAcc + k);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sum += v[u];
+      }
+      for (; b < gridDim.x; b += kSeg) sum += __ldcg(partials + (size_t)b * kNAcc + k);
       seg[sg][k] = sum;
     }
     __syncthreads();
@@ -356,10 +365,11 @@ __global__ void __launch_bounds__(kRefThreads) k_info_sums(const float *__restri
 
 __global__ void k_info_final(const double *__restrict__ partials, int nb, const float *__restrict__ boxQ,
                              double *__restrict__ out) {
+  __shared__ double seg[256], tot[10];
+  block_sum_partials(partials, nb, 10, 10, seg, tot);
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double S[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = 0; b < nb; ++b)
-    for (int k = 0; k < 10; ++k) S[k] += partials[(size_t)b * 10 + k];
+  double S[10];
+  for (int k = 0; k < 10; ++k) S[k] = tot[k];
   const double c[3] = {0.5 * ((double)boxQ[0] + (double)boxQ[3]), 0.5 * ((double)boxQ[1] + (double)boxQ[4]),
                        0.5 * ((double)boxQ[2] + (double)boxQ[5])};
   const double n = S[0];
@@ -473,11 +483,9 @@ __global__ void __launch_bounds__(kRefThreads) k_objective(const float *__restri
 }
 
 __global__ void k_objective_sum(const double *partials, int nblocks, double *out) {
-  if (threadIdx.x < 7) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * 7 + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
+  __shared__ double seg[256], tot[7];
+  block_sum_partials(partials, nblocks, 7, 7, seg, tot);
+  if (threadIdx.x < 7) out[threadIdx.x] = tot[threadIdx.x];
 }
 
 }  // namespace
@@ -547,7 +555,7 @@ cudaError_t launch_information(const float *P, int nP, const GridParams *ge, con
   a.eps2 = eps * eps;
   const int nb = information_blocks(nP);
   LSR_LAUNCH(k_info_sums<<<nb, kRefThreads, 0, s>>>(P, nP, ge, start_e, Xe, boxQ, a, partials));
-  LSR_LAUNCH(k_info_final<<<1, 32, 0, s>>>(partials, nb, boxQ, out));
+  LSR_LAUNCH(k_info_final<<<1, 256, 0, s>>>(partials, nb, boxQ, out));
   return cudaGetLastError();
 }
 
@@ -571,7 +579,7 @@ cudaError_t launch_objective(const float *P, int nP, const GridParams *ge, const
   a.scale = scale;
   int nb = objective_blocks(nP);
   LSR_LAUNCH(k_objective<<<nb, kRefThreads, 0, s>>>(P, nP, ge, start_e, Xe, a, want_grad, partials, dP, dQ));
-  LSR_LAUNCH(k_objective_sum<<<1, 32, 0, s>>>(partials, nb, out7));
+  LSR_LAUNCH(k_objective_sum<<<1, 256, 0, s>>>(partials, nb, out7));
   return cudaGetLastError();
 }
 
