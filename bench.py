@@ -178,7 +178,7 @@ def run_ours(args, rank, world):
     times, stages, last = [], np.zeros(8), None
     # the dominant kernel is bracketed by two CUDA events on the context stream
     # in every timed step (its only added work: two event records per step)
-    main_kernel = "k_match_fp32" if args.match == "fp32" else "k_match_tc"
+    main_kernel = "k_match_win" if args.match == "fp32" else "k_match_tc"
     ctx.set_kernel_timing(main_kernel)
     with ClockSampler(dev) as clk:
         l0 = lsr.launch_count()
@@ -296,7 +296,7 @@ def run_ours(args, rank, world):
             vctx.set_profiling(True)
             for _ in range(args.warmup):
                 vctx.register_pair(P, Q, fp.vpP, fp.vpQ)
-            vkern = "k_match_fp32" if name == "fp32" else "k_match_tc"
+            vkern = "k_match_win" if name == "fp32" else "k_match_tc"
             vctx.set_kernel_timing(vkern)
             vt, vst, vl = [], np.zeros(8), None
             for _ in range(args.steps):
@@ -651,15 +651,16 @@ def roofline(info):
     dense = float(nP) * float(nQ) * 33
     peak = fp32_alu_peak(sm_mhz)
     ach = terms * 3 / (avg * 1e-3) / 1e12
-    # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
-    # (profiles/k_match_fp32_room150k_dram.md)
-    traffic = 43850752 + 2816 if (nP, nQ) == (150000, 150000) else None
-    return {"kernel": "k_match_fp32", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+    # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one full-size
+    # launch, from an ncu capture of the current kernel (none yet: null)
+    traffic = None
+    return {"kernel": "k_match_win", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak, "traffic": traffic, "launch_ms": avg, "launches_timed": n,
             "algorithmic_bytes": 144.0 * (nP + nQ) + 8.0 * nP,
             "executed_terms": terms, "executed_share": terms / dense,
             "dense_equivalent": {"achieved": dense * 3 / (avg * 1e-3) / 1e12, "unit": "TFLOP/s",
-                                 "note": "rate of the definition's nP*nQ*33 terms; the exact early exits skip "
+                                 "note": "rate of the definition's nP*nQ*33 terms; the projection window and the "
+                                         "exact early exits skip "
                                          f"{100 * (1 - terms / dense):.1f}% of them, so it is no roofline fraction"},
             "peak_source": f"152 SMs x 128 FP32 lanes x 1.5 flop x {sm_mhz:.0f} MHz (FADD+FFMA issue peak)",
             "work": "executed terms x 3 flop (subtract + fused multiply-add), terms counted by the profiled launch"}
@@ -696,12 +697,14 @@ def _kernel_work(name, nP, nQ, res, prm, terms):
     N = nP + nQ
     S, n_ok, H = res.survivors, res.n_normal_ok, int(prm.n_hypotheses)
     table = [
-        ("k_match_fp32", "alu", 3.0 * terms, "flop", "executed terms x 3 flop"),
+        ("k_match_win", "alu", 3.0 * terms, "flop", "executed terms x 3 flop"),
         ("k_match_tc", "tensor", 2.0 * nP * nQ * 112, "flop", "2*nP*nQ*112 flop"),
         ("k_normals", "hbm", 48.0 * N, "B", "16 B point + 16 B grid copy in, 16 B normal out"),
         ("k_spfh", "hbm", 176.0 * N, "B", "16 B point + 16 B normal in, 144 B SPFH row out"),
         ("k_fpfh", "hbm", 320.0 * N, "B", "16 B point + 16 B normal + 144 B SPFH row in, 144 B FPFH row out"),
-        ("k_tile_bounds", "hbm", 144.0 * nQ + 288.0 * nQ / 64, "B", "144 B FPFH row in, 288 B per 64-row tile out"),
+        ("k_proj", "hbm", 152.0 * N, "B", "144 B FPFH row in, 8 B projection and bound out"),
+        ("k_gather_db", "hbm", 300.0 * nQ, "B", "4 B order + 8 B projection + 144 B row in, 144 B row out "
+                                                "(Q: the database)"),
         ("k_prep_tiles", "hbm", (144.0 + 224.0) * N, "B", "144 B FPFH row in, 224 B BF16 operand row out"),
         ("k_hyp_count", "hbm", 36.0 * N, "B", "unique bytes of the sampled arrays (points, normals, nn)"),
         ("k_hyp_write", "hbm", 36.0 * N + 4.0 * S, "B", "as k_hyp_count + 4 B per survivor id"),

@@ -347,7 +347,7 @@ void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int leve
   L.count2 = a.take<int>(L.surv_cap);
   L.tie_list = a.take<int>(L.surv_cap);
   L.tc_ws = a.take<char>(precision != LSR_MATCH_FP32 ? tc_workspace_bytes(nP, nQ, precision == LSR_MATCH_BF16)
-                                                      : fp32_workspace_bytes(nQ));
+                                                      : fp32_workspace_bytes(nP, nQ));
   L.cap_s = L.Q.cap_e;
   L.gs = a.take<GridParams>(1);
   L.start_s = a.take<int>((size_t)L.cap_s + 1);
@@ -1541,7 +1541,7 @@ int lsr_stage_match(lsr_ctx *c, const float *FP, int64_t nP, const float *FQ, in
     dn = a.take<int>(nP);
     dd = a.take<float>(nP);
     flags = a.take<int>(2);
-    tws = a.take<char>(tc ? tc_workspace_bytes((int)nP, (int)nQ, split) : fp32_workspace_bytes((int)nQ));
+    tws = a.take<char>(tc ? tc_workspace_bytes((int)nP, (int)nQ, split) : fp32_workspace_bytes((int)nP, (int)nQ));
   };
   Arena m(nullptr);
   float *x1, *x2, *x3, *x4, *x6;

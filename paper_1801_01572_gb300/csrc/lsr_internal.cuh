@@ -465,9 +465,10 @@ cudaError_t launch_fpfh(const float4 *X, const float4 *N, const float *spfh, int
                         const int *start_f, float r, float *fpfh, cudaStream_t s);
 
 // ----------------------------------------------------------------- matching (lsr_match.cu)
-// ws: fp32_workspace_bytes(nQ) of device memory (per-tile bin bounds);
+// ws: fp32_workspace_bytes(nP, nQ) of device memory, 256-byte aligned (the
+// projection order: a copy of FQ in that order and per-tile bounds);
 // terms (optional): add the number of descriptor terms evaluated (profiling)
-size_t fp32_workspace_bytes(int nQ);
+size_t fp32_workspace_bytes(int nP, int nQ);
 cudaError_t launch_match_fp32(const float *FP, int nP, const float *FQ, int nQ, void *ws, int *nn, float *d1,
                               cudaStream_t s, unsigned long long *terms = nullptr);
 // Exact FP32 scan of the queries rows[0..*nrows) (count read on the device),
