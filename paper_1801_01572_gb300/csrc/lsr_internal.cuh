@@ -469,6 +469,8 @@ cudaError_t launch_fpfh(const float4 *X, const float4 *N, const float *spfh, int
 // projection order: a copy of FQ in that order and per-tile bounds);
 // terms (optional): add the number of descriptor terms evaluated (profiling)
 size_t fp32_workspace_bytes(int nP, int nQ);
+// SMs of the current device (148 if the query fails).
+int device_sm_count();
 cudaError_t launch_match_fp32(const float *FP, int nP, const float *FQ, int nQ, void *ws, int *nn, float *d1,
                               cudaStream_t s, unsigned long long *terms = nullptr);
 // Exact FP32 scan of the queries rows[0..*nrows) (count read on the device),

@@ -6,24 +6,28 @@
 // desc_order (central bins first). What is exact is the result; the search
 // visits only the database rows that could change it.
 //
-// Projection window. Both sets are ordered by their projection p = u . x on
-// one unit direction u (the principal axis of a sample of the database,
-// found by power iteration; any unit vector gives the same result, a good
-// one visits fewer rows). By Cauchy-Schwarz |u . (a - b)| <= |u| |a - b|, so
-// a database row whose projection lies farther than sqrt(best) from the
-// query's cannot be nearer than the current best. One block takes 128
-// consecutive queries of the projection order and scans database tiles of
-// that order outward from its own projection, alternately to the right and
-// to the left; a side ends once no query of the block can find a row there.
-// The FP32 rounding of the projections (a bound per row from the error of an
-// fma chain), of |u| and of the distance itself is taken into the test by
-// directed rounding, so a row or a side is left out only when every
-// computed distance in it exceeds the query's computed best: the nearest
-// row and its ties are always scanned, and ties go to the smaller original
-// index whatever the scan order. Ordering is a counting sort into as many
-// buckets as points over the projections' range; the order within a bucket
-// is arbitrary, so the per-tile projection bounds are made monotone by a
-// suffix minimum (right side) and a prefix maximum (left side).
+// Projection window. Both sets are ordered by their projections p1 = u1 . x
+// and p2 = u2 . x on the first two principal axes of a sample of the
+// database (power iteration; any pair of directions gives the same result,
+// good ones visit fewer rows): by p1, then, inside slabs of 1024 consecutive
+// rows, by p2. For the stored FP32 axes U = [u1 u2], |U^T (a - b)|^2 <=
+// lambda |a - b|^2 with lambda bounding the Gram matrix's largest
+// eigenvalue, so a database row whose projections lie farther than
+// sqrt(lambda * best) from the query's, in the plane of the two axes, cannot
+// be nearer than the current best. One block takes 128 consecutive queries
+// of that order (one query slab: close in p1 and in p2) and visits database
+// slabs outward from its own p1, alternately to the right and to the left,
+// and in each slab its tiles outward from its own p2; a side ends once no
+// query of the block can find a row there. The FP32 rounding of the
+// projections (a bound per row from the error of an fma chain), of the axes
+// and of the distance itself is taken into the test by directed rounding,
+// so a row, a tile or a slab is left out only when every computed distance
+// in it exceeds the query's computed best: the nearest row and its ties are
+// always scanned, and ties go to the smaller original index whatever the
+// scan order. Each ordering is a counting sort into as many buckets as rows
+// over the projections' range; the order within a bucket is arbitrary, so
+// the bounds that end a side are made monotone by suffix minima (right) and
+// prefix maxima (left).
 //
 // Inside the window each thread keeps one query descriptor in registers;
 // tiles of database descriptors are staged in shared memory in desc_order
@@ -47,18 +51,22 @@ constexpr int kQR = 2;     // queries per thread, listed rows (k_match_rows_chun
 constexpr int kTile = 64;  // database rows per shared-memory tile
 constexpr int kStageThreads = 9 * (kMT / 9);  // staging threads: one float4 column each
 static_assert(kTile * 9 > kStageThreads, "staging covers the tile in several passes");
-constexpr int kPcThreads = 256;  // k_pc1 block
-constexpr int kPcSamples = 1024; // database rows sampled for the principal axis (in shared memory)
-constexpr int kPcIters = 10;     // power iterations (the second axis of FPFH sets holds ~0.1 of the first's variance)
-constexpr int kScanThreadsT = 1024;  // k_tile_scan block
+constexpr int kSlab = 1024;      // rows of a slab: consecutive in p1, ordered by p2 inside
+constexpr int kTilesPerSlab = kSlab / kTile;
+static_assert(kSlab % kTile == 0 && kSlab % kMT == 0, "tiles and query blocks do not straddle slabs");
+constexpr int kPcThreads = 256;  // k_pc block
+constexpr int kPcSamples = 1024; // database rows sampled for the principal axes (in shared memory)
+constexpr int kPcIters = 10;     // power iterations per axis (FPFH sets: variance ratios ~0.1 and ~0.4)
+constexpr int kScanThreadsT = 1024;  // k_bound_scan block
 
-// Direction and range of the projection order (one per matcher call).
+// Directions and ranges of the projection order (one per matcher call).
 struct ProjParams {
-  float u[kD];       // unit direction, column order
-  float fac;         // lower-bound factor of a squared projection gap (k_pc1)
-  unsigned key_min;  // f2key of the smallest / largest finite projection
-  unsigned key_max;
-  int ntot;          // nQ + nP (read by the scan)
+  float u[2][kD];       // the two unit directions, column order
+  float fac;            // lower-bound factor of a sum of squared projection gaps (k_pc)
+  unsigned key_min[2];  // f2key of the smallest / largest finite projection per direction
+  unsigned key_max[2];
+  int ntot;             // nQ + nP (read by the first sort's scan)
+  int ncap2;            // buckets of the second sort (read by its scan)
 };
 
 // Database rows [base, base + kTile) (zero past lim) into the tile, bin
@@ -167,16 +175,55 @@ __device__ __forceinline__ void pc_block_sum(float (*wred)[kD], const float (&w)
   __syncthreads();
 }
 
-// Principal axis of up to kPcSamples evenly spaced database rows (staged in
-// shared memory, centred on their mean): kPcIters power iterations
-// v <- sum_r c_r (c_r . v), normalised in FP32. Writes u, the factor
-// fac = (1 - 6e-6) / |u|^2 (|u|^2 rounded up, the quotient down) by which a
-// squared projection gap bounds a computed distance from below, and the
-// initial keys of the projections' range.
-__global__ void __launch_bounds__(kPcThreads) k_pc1(const float *__restrict__ FQ, int nQ, int nP, ProjParams *pp) {
+// kPcIters power iterations v <- sum_r c_r (c_r . v) over the centred
+// samples cs (m x kD, shared), removing the component along `away` (unit,
+// or null) after each product; v is normalised in FP32, and kept when an
+// update is zero or not finite.
+__device__ void pc_power(const float *cs, int m, float (*wred)[kD], float *v, float *nv, const float *away) {
+  for (int it = 0; it < kPcIters; ++it) {
+    float w[kD];
+#pragma unroll
+    for (int k = 0; k < kD; ++k) w[k] = 0.f;
+    for (int i = threadIdx.x; i < m; i += kPcThreads) {
+      const float *c = cs + i * kD;
+      float d = 0.f;
+#pragma unroll
+      for (int k = 0; k < kD; ++k) d = fmaf(c[k], v[k], d);
+#pragma unroll
+      for (int k = 0; k < kD; ++k) w[k] = fmaf(d, c[k], w[k]);
+    }
+    pc_block_sum(wred, w, nv);
+    if (threadIdx.x == 0) {
+      if (away) {
+        float d = 0.f;
+        for (int k = 0; k < kD; ++k) d = fmaf(nv[k], away[k], d);
+        for (int k = 0; k < kD; ++k) nv[k] = fmaf(-d, away[k], nv[k]);
+      }
+      float n2 = 0.f;
+      for (int k = 0; k < kD; ++k) n2 = fmaf(nv[k], nv[k], n2);
+      if (n2 > 0.f && n2 <= FLT_MAX) {
+        const float inv = rsqrtf(n2);
+        for (int k = 0; k < kD; ++k) v[k] = nv[k] * inv;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The first two principal axes u1, u2 of up to kPcSamples evenly spaced
+// database rows (staged in shared memory, centred on their mean), by power
+// iteration (u2 kept orthogonal to u1). Writes both, the factor fac by which
+// the sum of the two squared projection gaps bounds a computed distance from
+// below, the initial keys of the two projections' ranges and the sizes the
+// sorts read. fac = (1 - 6e-6) / lambda, lambda >= the largest eigenvalue of
+// the 2 x 2 Gram matrix of the stored FP32 axes (max |u_i|^2 + |u1 . u2|,
+// Gershgorin, all rounded up): |U^T x|^2 <= lambda |x|^2 for U = [u1 u2],
+// and a computed distance is >= (1 - 35 * 2^-24) |a - b|^2.
+__global__ void __launch_bounds__(kPcThreads) k_pc(const float *__restrict__ FQ, int nQ, int nP, int ncap2,
+                                                   ProjParams *pp) {
   extern __shared__ float xs[];  // kPcSamples x kD
   __shared__ float wred[kPcThreads / 32][kD];
-  __shared__ float mean[kD], v[kD], nv[kD];
+  __shared__ float mean[kD], v1[kD], v2[kD], nv[kD];
   const int m = nQ < kPcSamples ? nQ : kPcSamples;
   float w[kD];
 #pragma unroll
@@ -193,166 +240,218 @@ __global__ void __launch_bounds__(kPcThreads) k_pc1(const float *__restrict__ FQ
   pc_block_sum(wred, w, mean);
   if (threadIdx.x < kD) {
     mean[threadIdx.x] = m > 0 ? mean[threadIdx.x] / (float)m : 0.f;
-    // start away from any particular axis
-    v[threadIdx.x] = 1.f + 0.25f * (float)((threadIdx.x * 7) % 5);
+    // starts away from any particular axis and from each other
+    v1[threadIdx.x] = 1.f + 0.25f * (float)((threadIdx.x * 7) % 5);
+    v2[threadIdx.x] = (threadIdx.x & 1) ? 1.f : -0.75f - 0.125f * (float)(threadIdx.x % 3);
   }
   __syncthreads();
+  // each thread centres its own rows, which it alone reads until the first block sum
   for (int i = threadIdx.x; i < m; i += kPcThreads)
 #pragma unroll
     for (int k = 0; k < kD; ++k) xs[i * kD + k] -= mean[k];
-  // (each thread reads back only its own rows until the first block sum)
-  for (int it = 0; it < kPcIters; ++it) {
-#pragma unroll
-    for (int k = 0; k < kD; ++k) w[k] = 0.f;
-    for (int i = threadIdx.x; i < m; i += kPcThreads) {
-      const float *c = xs + i * kD;
-      float d = 0.f;
-#pragma unroll
-      for (int k = 0; k < kD; ++k) d = fmaf(c[k], v[k], d);
-#pragma unroll
-      for (int k = 0; k < kD; ++k) w[k] = fmaf(d, c[k], w[k]);
-    }
-    pc_block_sum(wred, w, nv);
-    if (threadIdx.x == 0) {
-      float n2 = 0.f;
-      for (int k = 0; k < kD; ++k) n2 = fmaf(nv[k], nv[k], n2);
-      // a zero or non-finite update (identical rows) keeps the current axis
-      if (n2 > 0.f && n2 <= FLT_MAX) {
-        const float inv = rsqrtf(n2);
-        for (int k = 0; k < kD; ++k) v[k] = nv[k] * inv;
-      }
-    }
-    __syncthreads();
-  }
+  pc_power(xs, m, wred, v1, nv, nullptr);
   if (threadIdx.x == 0) {
+    // v1 as stored (normalised, or the first coordinate axis when no
+    // iteration produced a direction)
     float n2 = 0.f;
-    for (int k = 0; k < kD; ++k) n2 = fmaf(v[k], v[k], n2);
+    for (int k = 0; k < kD; ++k) n2 = fmaf(v1[k], v1[k], n2);
     const bool ok = n2 > 0.f && n2 <= FLT_MAX;
     const float inv = ok ? rsqrtf(n2) : 0.f;
-    float r2 = 0.f;
+    for (int k = 0; k < kD; ++k) v1[k] = ok ? v1[k] * inv : (k == 0 ? 1.f : 0.f);
+  }
+  __syncthreads();
+  pc_power(xs, m, wred, v2, nv, v1);
+  if (threadIdx.x == 0) {
+    // final re-orthogonalisation and normalisation of u2 (the second
+    // coordinate axis when nothing is left)
+    float d = 0.f;
+    for (int k = 0; k < kD; ++k) d = fmaf(v2[k], v1[k], d);
+    for (int k = 0; k < kD; ++k) v2[k] = fmaf(-d, v1[k], v2[k]);
+    float n2 = 0.f;
+    for (int k = 0; k < kD; ++k) n2 = fmaf(v2[k], v2[k], n2);
+    const bool ok = n2 > 1e-12f && n2 <= FLT_MAX;
+    const float inv = ok ? rsqrtf(n2) : 0.f;
+    float r1 = 0.f, r2 = 0.f, c = 0.f;
     for (int k = 0; k < kD; ++k) {
-      const float uk = ok ? v[k] * inv : (k == 0 ? 1.f : 0.f);
-      pp->u[k] = uk;
-      r2 = __fmaf_ru(uk, uk, r2);
+      const float a = v1[k], b = ok ? v2[k] * inv : (k == 1 ? 1.f : 0.f);
+      pp->u[0][k] = a;
+      pp->u[1][k] = b;
+      r1 = __fmaf_ru(a, a, r1);
+      r2 = __fmaf_ru(b, b, r2);
+      c = fmaf(a, b, c);
     }
-    // s >= (1 - 35 * 2^-24) |a - b|^2 for the fma chain of a distance, and
-    // |a - b|^2 >= (u . (a - b))^2 / |u|^2
-    pp->fac = __fdiv_rd(0.999994f, r2);
-    pp->key_min = 0xFFFFFFFFu;
-    pp->key_max = 0u;
+    // |u1 . u2| <= |c| + gamma_33 |u1| |u2| (both norms below 1 + 1e-6)
+    const float lam = __fadd_ru(fmaxf(r1, r2), __fadd_ru(fabsf(c), 2.1e-6f));
+    pp->fac = __fdiv_rd(0.999994f, lam);
+    pp->key_min[0] = pp->key_min[1] = 0xFFFFFFFFu;
+    pp->key_max[0] = pp->key_max[1] = 0u;
     pp->ntot = nQ + nP;
+    pp->ncap2 = ncap2;
   }
 }
 
-// Projection p = u . x (fma chain over the 33 bins in column order) and a
-// bound e >= |p - u . x| (gamma_33 = 33 * 2^-24 / (1 - 33 * 2^-24) < 2e-6 of
-// sum |u_k x_k|, rounded up) for every database row (elements 0..nQ) and
-// every query (elements nQ..nQ+nP); the range of the finite projections.
+// Projections p_j = u_j . x (fma chains over the 33 bins in column order)
+// and bounds e_j >= |p_j - u_j . x| (gamma_33 = 33 * 2^-24 / (1 - 33 * 2^-24)
+// < 2e-6 of sum |u_jk x_k|, rounded up) for every database row (elements
+// 0..nQ) and every query (elements nQ..nQ+nP), as (p1, e1, p2, e2); the
+// ranges of the finite projections.
 __global__ void k_proj(const float *__restrict__ FP, int nP, const float *__restrict__ FQ, int nQ,
-                       ProjParams *pp, float2 *__restrict__ pe) {
-  __shared__ float su[kD];
-  if (threadIdx.x < kD) su[threadIdx.x] = pp->u[threadIdx.x];
+                       ProjParams *pp, float4 *__restrict__ pe) {
+  __shared__ float su[2][kD];
+  if (threadIdx.x < 2 * kD) su[threadIdx.x / kD][threadIdx.x % kD] = pp->u[threadIdx.x / kD][threadIdx.x % kD];
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned kmin = 0xFFFFFFFFu, kmax = 0u;
+  unsigned kmin[2] = {0xFFFFFFFFu, 0xFFFFFFFFu}, kmax[2] = {0u, 0u};
   if (i < nQ + nP) {
     const float *row = i < nQ ? FQ + (size_t)i * kDS : FP + (size_t)(i - nQ) * kDS;
-    float p = 0.f, S = 0.f;
+    float p[2] = {0.f, 0.f}, S[2] = {0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < kD; ++k) {
       const float x = row[k];
-      p = fmaf(su[k], x, p);
-      S = __fmaf_ru(fabsf(su[k]), fabsf(x), S);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        p[j] = fmaf(su[j][k], x, p[j]);
+        S[j] = __fmaf_ru(fabsf(su[j][k]), fabsf(x), S[j]);
+      }
     }
-    pe[i] = make_float2(p, __fmaf_ru(S, 2.0e-6f, 1e-37f));
-    if (isfinite(p)) kmin = kmax = f2key(p);
+    pe[i] = make_float4(p[0], __fmaf_ru(S[0], 2.0e-6f, 1e-37f), p[1], __fmaf_ru(S[1], 2.0e-6f, 1e-37f));
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+      if (isfinite(p[j])) kmin[j] = kmax[j] = f2key(p[j]);
   }
-  kmin = __reduce_min_sync(0xffffffffu, kmin);
-  kmax = __reduce_max_sync(0xffffffffu, kmax);
-  if ((threadIdx.x & 31) == 0 && kmin <= kmax) {
-    atomicMin(&pp->key_min, kmin);
-    atomicMax(&pp->key_max, kmax);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const unsigned lo = __reduce_min_sync(0xffffffffu, kmin[j]), hi = __reduce_max_sync(0xffffffffu, kmax[j]);
+    if ((threadIdx.x & 31) == 0 && lo <= hi) {
+      atomicMin(&pp->key_min[j], lo);
+      atomicMax(&pp->key_max[j], hi);
+    }
   }
 }
 
-// Bucket of every element: as many buckets per set as the set has elements,
-// spread evenly over the projections' range (non-finite ones last); counts
+// Bucket in [0, nb) of a projection over the range of direction j (non-finite
+// values last).
+__device__ __forceinline__ int proj_bucket(float p, const ProjParams *pp, int j, int nb) {
+  const unsigned k0 = pp->key_min[j], k1 = pp->key_max[j];
+  if (!(k0 <= k1) || !isfinite(p)) return nb - 1;
+  const float lo = key2f(k0), hi = key2f(k1);
+  const float inv = hi > lo ? (float)nb / (hi - lo) : 0.f;
+  const float f = (p - lo) * inv;
+  const int b = f < (float)nb ? (int)f : nb - 1;
+  return b < 0 ? 0 : b;
+}
+
+// First sort, by p1: as many buckets per set as the set has elements; counts
 // of the database's buckets first, then the queries'.
-__global__ void k_bucket_count(const float2 *__restrict__ pe, int nQ, int nP, const ProjParams *pp,
-                               int *__restrict__ slot, int *__restrict__ counts) {
+__global__ void k_bucket1(const float4 *__restrict__ pe, int nQ, int nP, const ProjParams *pp,
+                          int *__restrict__ slot, int *__restrict__ counts) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nQ + nP) return;
   const bool db = i < nQ;
-  const int nb = db ? nQ : nP, off = db ? 0 : nQ;
-  const unsigned k0 = pp->key_min, k1 = pp->key_max;
-  const float lo = k0 <= k1 ? key2f(k0) : 0.f, hi = k0 <= k1 ? key2f(k1) : 0.f;
-  const float inv = hi > lo ? (float)nb / (hi - lo) : 0.f;
-  const float p = pe[i].x;
-  int b = nb - 1;
-  if (isfinite(p)) {
-    const float f = (p - lo) * inv;
-    b = f < (float)nb ? (int)f : nb - 1;
-    b = b < 0 ? 0 : b;
-  }
-  slot[i] = off + b;
-  atomicAdd(counts + off + b, 1);
+  const int s = (db ? 0 : nQ) + proj_bucket(pe[i].x, pp, 0, db ? nQ : nP);
+  slot[i] = s;
+  atomicAdd(counts + s, 1);
 }
 
-// order[pos] = element at position pos of its set's bucket order (database
-// positions 0..nQ, query positions nQ..nQ+nP); start is consumed as cursor.
-__global__ void k_bucket_scatter(int n, const int *__restrict__ slot, int *start, int *__restrict__ order) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int pos = atomicAdd(start + slot[i], 1);
-  if (LSR_IN_BOUNDS(pos, n, kSiteMatchRow)) order[pos] = i;
+// Second sort: position pos of the p1 order lies in slab pos / kSlab of its
+// set; inside the slab, kSlab buckets of p2. Database slabs first (capD
+// buckets), then the queries'.
+__global__ void k_bucket2(const float4 *__restrict__ pe, const int *__restrict__ order1, int nQ, int nP, int capD,
+                          const ProjParams *pp, int *__restrict__ slot, int *__restrict__ counts) {
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= nQ + nP) return;
+  const bool db = pos < nQ;
+  const int r = db ? pos : pos - nQ;
+  const int i = order1[pos];
+  const int s = (db ? 0 : capD) + (r / kSlab) * kSlab + proj_bucket(pe[i].z, pp, 1, kSlab);
+  slot[pos] = s;
+  atomicAdd(counts + s, 1);
 }
 
-// One block of kTile threads per database tile: the tile's rows in
-// projection order (FQs), their original indices (dorig), and the tile's
-// bounds lo <= p - e and hi >= p + e over its finite projections.
+// out[start[slot[j]]++] = src ? src[j] : j (start is consumed as cursor).
+__global__ void k_bucket_scatter(int n, const int *__restrict__ slot, int *start, const int *__restrict__ src,
+                                 int *__restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int pos = atomicAdd(start + slot[j], 1);
+  if (LSR_IN_BOUNDS(pos, n, kSiteMatchRow)) out[pos] = src ? src[j] : j;
+}
+
+// One block of kTile threads per database tile: the tile's rows in the final
+// order (FQs: per tile, float4 chunk c of row j at c * kTile + j, bins in
+// desc_order, zeros in slots 33..35), their original indices (dorig), and the tile's box of the
+// projection intervals, (lo1, hi1, lo2, hi2) with lo <= p - e and hi >= p + e
+// over its finite projections (empty: +inf, -inf).
 __global__ void __launch_bounds__(kTile) k_gather_db(const float *__restrict__ FQ, int nQ, const int *__restrict__ order,
-                                                     const float2 *__restrict__ pe, float *__restrict__ FQs,
-                                                     int *__restrict__ dorig, float *__restrict__ tlo,
-                                                     float *__restrict__ thi) {
-  __shared__ float slo[kTile / 32], shi[kTile / 32];
+                                                     const float4 *__restrict__ pe, float *__restrict__ FQs,
+                                                     int *__restrict__ dorig, float4 *__restrict__ tbox) {
+  __shared__ float4 sb[kTile / 32];
   const int pos = blockIdx.x * kTile + threadIdx.x;
-  float lo = INFINITY, hi = -INFINITY;
+  float lo1 = INFINITY, hi1 = -INFINITY, lo2 = INFINITY, hi2 = -INFINITY;
   if (pos < nQ) {
     int i = order[pos];
     if (!LSR_IN_BOUNDS(i, nQ, kSiteMatchRow)) i = 0;
-    const float4 *src = reinterpret_cast<const float4 *>(FQ + (size_t)i * kDS);
-    float4 *dst = reinterpret_cast<float4 *>(FQs + (size_t)pos * kDS);
+    const float *src = FQ + (size_t)i * kDS;
+    float4 *dst = reinterpret_cast<float4 *>(FQs) + (size_t)blockIdx.x * (9 * kTile) + threadIdx.x;
 #pragma unroll
-    for (int c = 0; c < kDS / 4; ++c) dst[c] = src[c];
+    for (int c = 0; c < kDS / 4; ++c) {
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = 4 * c + e < kD ? src[desc_order(4 * c + e)] : 0.f;
+      dst[c * kTile] = make_float4(v[0], v[1], v[2], v[3]);
+    }
     dorig[pos] = i;
-    const float2 v = pe[i];
-    if (isfinite(v.x)) lo = __fsub_rd(v.x, v.y), hi = __fadd_ru(v.x, v.y);
+    const float4 v = pe[i];
+    if (isfinite(v.x)) lo1 = __fsub_rd(v.x, v.y), hi1 = __fadd_ru(v.x, v.y);
+    if (isfinite(v.z)) lo2 = __fsub_rd(v.z, v.w), hi2 = __fadd_ru(v.z, v.w);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+    hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+    lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
+    hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
   }
-  if ((threadIdx.x & 31) == 0) slo[threadIdx.x >> 5] = lo, shi[threadIdx.x >> 5] = hi;
+  if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = make_float4(lo1, hi1, lo2, hi2);
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < kTile / 32; ++w) lo = fminf(lo, slo[w]), hi = fmaxf(hi, shi[w]);
-    tlo[blockIdx.x] = lo;
-    thi[blockIdx.x] = hi;
+    for (int w = 1; w < kTile / 32; ++w)
+      lo1 = fminf(lo1, sb[w].x), hi1 = fmaxf(hi1, sb[w].y), lo2 = fminf(lo2, sb[w].z), hi2 = fmaxf(hi2, sb[w].w);
+    tbox[blockIdx.x] = make_float4(lo1, hi1, lo2, hi2);
   }
 }
 
-// smin[t] = min over tiles t' >= t of tlo, hmax[t] = max over tiles t' <= t
-// of thi: bounds that only grow to the right (shrink to the left), so a side
-// of the window that no query needs stays unneeded.
-__global__ void __launch_bounds__(kScanThreadsT) k_tile_scan(const float *__restrict__ tlo,
-                                                             const float *__restrict__ thi, int nt,
-                                                             float *__restrict__ smin, float *__restrict__ hmax) {
+// One thread per database slab: the slab's p1 interval (slo1, shi1) and,
+// over its tiles in order, the suffix minimum of lo2 (smin2) and the prefix
+// maximum of hi2 (hmax2): p2 bounds that only grow to the right (shrink to
+// the left) within the slab.
+__global__ void k_slab_bounds(const float4 *__restrict__ tbox, int nt, int ns, float *__restrict__ slo1,
+                              float *__restrict__ shi1, float *__restrict__ smin2, float *__restrict__ hmax2) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const int a = s * kTilesPerSlab, b = min(nt, a + kTilesPerSlab);
+  float lo = INFINITY, hi = -INFINITY, run = -INFINITY;
+  for (int t = a; t < b; ++t) {
+    const float4 x = tbox[t];
+    lo = fminf(lo, x.x), hi = fmaxf(hi, x.y);
+    run = fmaxf(run, x.w), hmax2[t] = run;
+  }
+  run = INFINITY;
+  for (int t = b - 1; t >= a; --t) run = fminf(run, tbox[t].z), smin2[t] = run;
+  slo1[s] = lo;
+  shi1[s] = hi;
+}
+
+// smin[t] = min over entries t' >= t of lo, hmax[t] = max over t' <= t of
+// hi (one block): bounds that only grow to the right (shrink to the left).
+__global__ void __launch_bounds__(kScanThreadsT) k_bound_scan(const float *__restrict__ lo_in,
+                                                              const float *__restrict__ hi_in, int nt,
+                                                              float *__restrict__ smin, float *__restrict__ hmax) {
   __shared__ float a[kScanThreadsT], b[kScanThreadsT];
   const int per = (nt + kScanThreadsT - 1) / kScanThreadsT;
   const int t0 = threadIdx.x * per, t1 = min(nt, t0 + per);
   float lo = INFINITY, hi = -INFINITY;
-  for (int t = t0; t < t1; ++t) lo = fminf(lo, tlo[t]), hi = fmaxf(hi, thi[t]);
+  for (int t = t0; t < t1; ++t) lo = fminf(lo, lo_in[t]), hi = fmaxf(hi, hi_in[t]);
   a[threadIdx.x] = lo, b[threadIdx.x] = hi;
   __syncthreads();
   // inclusive scans over the threads' segments: a from the right, b from the left
@@ -366,105 +465,221 @@ __global__ void __launch_bounds__(kScanThreadsT) k_tile_scan(const float *__rest
   }
   float run_lo = threadIdx.x + 1 < kScanThreadsT ? a[threadIdx.x + 1] : INFINITY;
   float run_hi = threadIdx.x > 0 ? b[threadIdx.x - 1] : -INFINITY;
-  for (int t = t1 - 1; t >= t0; --t) run_lo = fminf(run_lo, tlo[t]), smin[t] = run_lo;
-  for (int t = t0; t < t1; ++t) run_hi = fmaxf(run_hi, thi[t]), hmax[t] = run_hi;
+  for (int t = t1 - 1; t >= t0; --t) run_lo = fminf(run_lo, lo_in[t]), smin[t] = run_lo;
+  for (int t = t0; t < t1; ++t) run_hi = fmaxf(run_hi, hi_in[t]), hmax[t] = run_hi;
 }
 
-// Squared projection gap g^2 (g rounded down, then the product and the
-// factor) that bounds every computed distance on that side from below; 0 for
-// gaps below 1e-18 (where subnormal terms of a distance lose their relative
-// rounding bound) and for non-finite gaps other than +inf.
-__device__ __forceinline__ float gap_bound(float g, float fac) {
-  return g > 1e-18f ? __fmul_rd(__fmul_rd(g, g), fac) : 0.f;
+// Lower bound of every computed distance from a query whose projection
+// intervals are separated by gaps g1, g2 (rounded down, >= 0) from those of
+// the rows: (g1^2 + g2^2) * fac, rounded down. Gaps below 1e-18 count as 0
+// (subnormal terms of a distance lose their relative rounding bound); +inf
+// gives +inf.
+__device__ __forceinline__ float gap_bound(float g1, float g2, float fac) {
+  const float a = g1 > 1e-18f ? __fmul_rd(g1, g1) : 0.f, b = g2 > 1e-18f ? __fmul_rd(g2, g2) : 0.f;
+  return __fmul_rd(__fadd_rd(a, b), fac);
 }
 
-// One block: the 128 queries at projection positions 128 b .. 128 b + 127.
-// The window starts at the tile where the block's middle projection falls
-// and grows alternately to the right and to the left; a side ends when no
-// query of the block needs its next tile (the monotone bounds make that
-// final), a warp scans a staged tile only if one of its queries needs it.
-// kCount: also add the number of terms (a_k - b_k)^2 evaluated for the valid
-// queries to *terms (a separate instantiation, used when profiling).
+// Gap, rounded down and >= 0, between the query's interval [ql, qh] and [lo, hi].
+__device__ __forceinline__ float interval_gap(float lo, float hi, float ql, float qh) {
+  return fmaxf(fmaxf(__fsub_rd(lo, qh), __fsub_rd(ql, hi)), 0.f);
+}
+
+// Scan the m rows of database tile t (final order, chunk-major: float4 chunk
+// c of row j at T4[c * kTile + j], bins in desc_order) for this lane's query
+// a, with the same partial-sum exits as scan_tile. The rows are read through
+// L1 as warp broadcasts; consecutive rows share the cache lines of a chunk,
+// the next row's first chunk is loaded ahead, and the lines of the first
+// two chunks eight rows ahead are prefetched into L1. best is the lane's
+// pruning bound (its own best or a smaller one another warp published); a
+// row is taken when its distance is smaller, or equal with a smaller index
+// than a row already taken (bj = -2: the bound came from elsewhere, so an
+// equal row is taken and the atomic minimum of the published pairs decides);
+// taken marks that there is a pair to publish.
+template <bool kCount>
+__device__ __forceinline__ void scan_rows(const float4 *__restrict__ T4, const int *__restrict__ ids, int m,
+                                          const float (&a)[kD], float &best, int &bj, bool &taken, unsigned &terms) {
+  float4 nxt = __ldg(T4);
+  for (int j = 0; j < m; ++j) {
+    float4 b = nxt;
+    if (j + 1 < m) nxt = __ldg(T4 + j + 1);
+    if ((j & 7) == 0 && j + 8 < m) {
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(T4 + j + 8));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(T4 + kTile + j + 8));
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c >= 1) {
+        if (c <= 4 || c == 6)
+          if (__all_sync(0xffffffffu, s > best)) break;
+        b = __ldg(T4 + c * kTile + j);
+      }
+      if (kCount) terms += c == 7 ? 5 : 4;
+      const float t0 = a[4 * c] - b.x, t1 = a[4 * c + 1] - b.y, t2 = a[4 * c + 2] - b.z, t3 = a[4 * c + 3] - b.w;
+      s = fmaf(t0, t0, s);
+      s = fmaf(t1, t1, s);
+      s = fmaf(t2, t2, s);
+      s = fmaf(t3, t3, s);
+      if (c == 7) {
+        const float t = a[32] - __ldg(reinterpret_cast<const float *>(T4 + 8 * kTile + j));
+        s = fmaf(t, t, s);
+        if (s < best || (s == best && bj != -1)) {
+          const int id = __ldg(ids + j);
+          if (s < best || (unsigned)id < (unsigned)bj) best = s, bj = id, taken = true;
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long pack_pair(float d, int j) {
+  return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)j;
+}
+
+// One warp per work unit: the 32 queries at positions 32 g .. 32 g + 31 of
+// the final query order (one query slab, close in p1 and in p2) and one
+// quarter of their window: units 4 g and 4 g + 1 the even and the odd
+// database slabs from the one where the group's middle p1 falls to the
+// right, units 4 g + 2 and 4 g + 3 the even and odd ones to its left. Units
+// are taken from a counter (persistent warps), so the four quarters of a
+// group run at once on different warps and a long window does not hold back
+// a block.
+// Each lane publishes its best (distance, index) with a 64-bit atomic
+// minimum and prunes with the smallest published distance: rows, tiles and
+// slabs are left out only when their bound exceeds a distance some row
+// really has, so the minimum over the published pairs is the exact result.
+// Outer loop: slabs outward, ending when no lane's p1 bound reaches the next
+// (monotone over slabs); inner loop, in a slab: its tiles outward from the
+// one where the middle p2 falls, alternately right and left, a side ending
+// when no lane's bound from the slab's p1 gap and the side's monotone p2 gap
+// reaches the next tile. kCount: also add the number of terms (a_k - b_k)^2
+// evaluated for the valid queries to *terms (a separate instantiation, used
+// when profiling).
 template <bool kCount>
 __global__ void __launch_bounds__(kMT) k_match_win(const float *__restrict__ FP, int nP,
                                                    const float *__restrict__ FQs, const int *__restrict__ dorig,
                                                    int nQ, const int *__restrict__ order,
-                                                   const float2 *__restrict__ pe, const float *__restrict__ smin,
-                                                   const float *__restrict__ hmax, const ProjParams *pp,
-                                                   int *__restrict__ nn, float *__restrict__ d1,
+                                                   const float4 *__restrict__ pe, const float *__restrict__ slo1,
+                                                   const float *__restrict__ shi1, const float *__restrict__ smin1,
+                                                   const float *__restrict__ hmax1, const float *__restrict__ smin2,
+                                                   const float *__restrict__ hmax2, const ProjParams *pp,
+                                                   unsigned long long *packed, unsigned *work,
                                                    unsigned long long *__restrict__ terms) {
-  __shared__ float4 tile[kTile][9];
-  __shared__ int ids[kTile];
-  const int nt = (int)lsr_div_up(nQ, kTile);
-  const int k = blockIdx.x * kMT + threadIdx.x;
-  const bool valid = k < nP;
-  int qo = 0;
-  if (valid) {
-    qo = order[nQ + k] - nQ;
-    if (!LSR_IN_BOUNDS(qo, nP, kSiteMatchQuery)) qo = 0;
-  }
-  float a[1][kD];
-  {
-    const float *row = FP + (size_t)qo * kDS;
-#pragma unroll
-    for (int j = 0; j < kD; ++j) a[0][j] = row[desc_order(j)];
-  }
-  const float2 q = pe[nQ + qo];
+  const int lane = threadIdx.x & 31;
+  const int nt = (int)lsr_div_up(nQ, kTile), ns = (int)lsr_div_up(nQ, kSlab);
+  const int nunits = 4 * (int)lsr_div_up(nP, 32);
+  const float4 *F4 = reinterpret_cast<const float4 *>(FQs);
   const float fac = pp->fac;
-  // invalid lanes: best below any distance, so they never hold a warp back
-  float best[1] = {valid ? FLT_MAX : -1.f};
-  int bj[1] = {-1};
-  int rk[4];
-  stage_ranks(rk);
-  // start tile: the last one whose suffix minimum does not exceed the block's
-  // middle projection (0 when it is not finite)
-  int t0 = 0;
-  {
-    const int mid = min(blockIdx.x * kMT + kMT / 2, nP - 1);
-    const float pm = pe[order[nQ + mid]].x;
-    if (isfinite(pm) && nt > 0) {
-      int lo = 0, hi = nt;  // first t with smin[t] > pm
+  unsigned long long nterm = 0;
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = (int)atomicAdd(work, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= nunits) break;
+    const int g = u >> 2;
+    const bool to_right = (u & 2) == 0;
+    const int par = u & 1;
+    const int k = g * 32 + lane;
+    const bool valid = k < nP;
+    int qo = 0;
+    if (valid) {
+      qo = order[nQ + k] - nQ;
+      if (!LSR_IN_BOUNDS(qo, nP, kSiteMatchQuery)) qo = 0;
+    }
+    float a[kD];
+    {
+      const float *row = FP + (size_t)qo * kDS;
+#pragma unroll
+      for (int j = 0; j < kD; ++j) a[j] = row[desc_order(j)];
+    }
+    float ql1, qh1, ql2, qh2;
+    {
+      const float4 q = pe[nQ + qo];
+      ql1 = __fsub_rd(q.x, q.y), qh1 = __fadd_ru(q.x, q.y), ql2 = __fsub_rd(q.z, q.w), qh2 = __fadd_ru(q.z, q.w);
+    }
+    // invalid lanes: bound below any distance, so they never hold the warp back
+    float best = valid ? FLT_MAX : -1.f;
+    int bj = -1;
+    bool taken = false;
+    unsigned uterm = 0;  // terms of this unit (at most 33 per database row)
+    // the group's middle projections (warp-uniform)
+    float m1, m2;
+    {
+      const int mid = min(g * 32 + 16, nP - 1);
+      const float4 q = pe[order[nQ + mid]];
+      m1 = q.x, m2 = q.z;
+    }
+    // start slab: the last whose suffix minimum of lo1 does not exceed m1 (0 if m1 is not finite)
+    int s0 = 0;
+    if (isfinite(m1)) {
+      int lo = 0, hi = ns;
       while (lo < hi) {
         const int md = (lo + hi) >> 1;
-        if (smin[md] > pm) hi = md; else lo = md + 1;
+        if (smin1[md] > m1) hi = md; else lo = md + 1;
       }
-      t0 = lo > 0 ? lo - 1 : 0;
+      s0 = lo > 0 ? lo - 1 : 0;
     }
-  }
-  unsigned nterm = 0;
-  int r = t0, l = t0 - 1;
-  bool rgo = r < nt, lgo = l >= 0, right_turn = true;
-  while (rgo || lgo) {
-    const bool right = rgo && (right_turn || !lgo);
-    right_turn = !right;
-    const int t = right ? r : l;
-    const float g = right ? __fsub_rd(__fsub_rd(smin[t], q.x), q.y) : __fsub_rd(__fsub_rd(q.x, hmax[t]), q.y);
-    const bool need = valid && !(gap_bound(g, fac) > best[0]);
-    const bool wneed = __any_sync(0xffffffffu, need);
-    // (also the barrier after the previous tile's scan)
-    if (!__syncthreads_or(need)) {
-      (right ? rgo : lgo) = false;
-      continue;
+    for (int s = to_right ? s0 + par : s0 - 1 - par; s >= 0 && s < ns; s += to_right ? 2 : -2) {
+      if (valid) {
+        // the smallest distance published for this query so far
+        const float pb = __uint_as_float((unsigned)(__ldcg(packed + qo) >> 32));
+        if (pb < best) best = pb, bj = -2;
+      }
+      const float gs = to_right ? fmaxf(__fsub_rd(smin1[s], qh1), 0.f) : fmaxf(__fsub_rd(ql1, hmax1[s]), 0.f);
+      if (!__any_sync(0xffffffffu, valid && !(gap_bound(gs, 0.f, fac) > best))) break;
+      const float g1 = interval_gap(slo1[s], shi1[s], ql1, qh1);
+      const int ta = s * kTilesPerSlab, tb = min(nt, ta + kTilesPerSlab);
+      // start tile: the last of the slab whose suffix minimum of lo2 does not exceed m2
+      int t0 = ta;
+      if (isfinite(m2)) {
+        int lo = ta, hi = tb;
+        while (lo < hi) {
+          const int md = (lo + hi) >> 1;
+          if (smin2[md] > m2) hi = md; else lo = md + 1;
+        }
+        t0 = lo > ta ? lo - 1 : ta;
+      }
+      int r = t0, l = t0 - 1;
+      bool rgo = true, lgo = l >= ta, turn = true;
+      while (rgo || lgo) {
+        const bool right = rgo && (turn || !lgo);
+        turn = !right;
+        const int t = right ? r : l;
+        const float g2 = right ? fmaxf(__fsub_rd(smin2[t], qh2), 0.f) : fmaxf(__fsub_rd(ql2, hmax2[t]), 0.f);
+        if (!__any_sync(0xffffffffu, valid && !(gap_bound(g1, g2, fac) > best))) {
+          (right ? rgo : lgo) = false;
+          continue;
+        }
+        if (right) rgo = ++r < tb;
+        else lgo = --l >= ta;
+        const int base = t * kTile;
+        scan_rows<kCount>(F4 + (size_t)t * (9 * kTile), dorig + base, nQ - base < kTile ? nQ - base : kTile, a,
+                          best, bj, taken, uterm);
+      }
+      if (valid && taken && LSR_IN_BOUNDS(qo, nP, kSiteMatchQuery)) {
+        atomicMin(packed + qo, pack_pair(best, bj));
+        taken = false;
+      }
     }
-    if (right) rgo = ++r < nt;
-    else lgo = --l >= 0;
-    const int base = t * kTile, m = nQ - base < kTile ? nQ - base : kTile;
-    stage_tile(tile, FQs, base, nQ, rk);
-    if (threadIdx.x < kTile) ids[threadIdx.x] = threadIdx.x < m ? dorig[base + threadIdx.x] : 0x7FFFFFFF;
-    __syncthreads();
-    if (wneed) scan_tile<1, kCount>(tile, m, base, ids, a, best, bj, &nterm);
-  }
-  if (valid && LSR_IN_BOUNDS(qo, nP, kSiteMatchQuery)) {
-    nn[qo] = bj[0];
-    if (d1) d1[qo] = bj[0] >= 0 ? best[0] : FLT_MAX;
+    if (kCount && valid) nterm += uterm;
   }
   if (kCount) {
-    // nterm <= nQ * 33 < 2^32 (at most 2^26 points per cloud)
-    unsigned long long mine = valid ? (unsigned long long)nterm : 0ull;
+    unsigned long long mine = nterm;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(terms, mine);
+    if (lane == 0) atomicAdd(terms, mine);
   }
+}
+
+// nn / d1 from the published minimum of every query (none: -1 / FLT_MAX).
+__global__ void k_win_finish(const unsigned long long *__restrict__ packed, int nP, int *__restrict__ nn,
+                             float *__restrict__ d1) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nP) return;
+  const unsigned long long v = packed[q];
+  const bool none = v == ~0ull;
+  nn[q] = none ? -1 : (int)(unsigned)(v & 0xFFFFFFFFu);
+  if (d1) d1[q] = none ? FLT_MAX : __uint_as_float((unsigned)(v >> 32));
 }
 
 // Exact FP32 scan of the queries rows[0..*nrows), split over database chunks
@@ -540,17 +755,23 @@ namespace {
 
 struct Fp32Layout {
   ProjParams *pp;
-  float2 *pe;                      // (p, e) of the nQ database rows, then the nP queries
-  int *slot, *counts, *start, *order, *scan;
-  float *FQs;                      // database rows in projection order
-  int *dorig;                      // their original indices
-  float *tlo, *thi, *smin, *hmax;  // per tile
+  float4 *pe;                         // (p1, e1, p2, e2) of the nQ database rows, then the nP queries
+  int *slot1, *counts1, *start1, *order1;
+  int *slot2, *counts2, *start2, *order, *scan;
+  float *FQs;                         // database rows in the final order, chunk-major per tile
+  int *dorig;                         // their original indices
+  float4 *tbox;                       // per tile
+  float *smin2, *hmax2;               // per tile, within its slab
+  float *slo1, *shi1, *smin1, *hmax1; // per slab
+  unsigned long long *packed;         // per query: published (distance bits << 32 | index) minimum
+  unsigned *work;                     // work-unit counter
+  int capD, ncap2;
   size_t bytes;
 };
 
 Fp32Layout fp32_layout(char *base, int nP, int nQ) {
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-  const size_t n = (size_t)nP + (size_t)nQ, nt = (size_t)lsr_div_up(nQ, kTile);
+  const size_t n = (size_t)nP + (size_t)nQ, nt = (size_t)lsr_div_up(nQ, kTile), ns = (size_t)lsr_div_up(nQ, kSlab);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     char *p = base ? base + off : nullptr;
@@ -558,22 +779,37 @@ Fp32Layout fp32_layout(char *base, int nP, int nQ) {
     return p;
   };
   Fp32Layout L;
+  L.capD = (int)(ns * kSlab);
+  L.ncap2 = L.capD + (int)(lsr_div_up(nP, kSlab) * kSlab);
+  const size_t n2 = (size_t)L.ncap2;
   L.pp = reinterpret_cast<ProjParams *>(take(sizeof(ProjParams)));
-  L.pe = reinterpret_cast<float2 *>(take(sizeof(float2) * n));
-  L.slot = reinterpret_cast<int *>(take(sizeof(int) * n));
-  L.counts = reinterpret_cast<int *>(take(sizeof(int) * (n + 1)));
-  L.start = reinterpret_cast<int *>(take(sizeof(int) * (n + 1)));
+  L.pe = reinterpret_cast<float4 *>(take(sizeof(float4) * n));
+  L.slot1 = reinterpret_cast<int *>(take(sizeof(int) * n));
+  L.counts1 = reinterpret_cast<int *>(take(sizeof(int) * (n + 1)));
+  L.start1 = reinterpret_cast<int *>(take(sizeof(int) * (n + 1)));
+  L.order1 = reinterpret_cast<int *>(take(sizeof(int) * n));
+  L.slot2 = reinterpret_cast<int *>(take(sizeof(int) * n));
+  L.counts2 = reinterpret_cast<int *>(take(sizeof(int) * (n2 + 1)));
+  L.start2 = reinterpret_cast<int *>(take(sizeof(int) * (n2 + 1)));
   L.order = reinterpret_cast<int *>(take(sizeof(int) * n));
-  L.scan = reinterpret_cast<int *>(take(sizeof(int) * (size_t)scan_scratch_ints((int64_t)n)));
-  L.FQs = reinterpret_cast<float *>(take(sizeof(float) * kDS * (size_t)nQ));
+  L.scan = reinterpret_cast<int *>(take(sizeof(int) * (size_t)scan_scratch_ints((int64_t)(n2 > n ? n2 : n))));
+  // whole tiles: chunk c of the last tile's rows lies at c * kTile within it
+  L.FQs = reinterpret_cast<float *>(take(sizeof(float) * kDS * kTile * nt));
   L.dorig = reinterpret_cast<int *>(take(sizeof(int) * (size_t)nQ));
-  L.tlo = reinterpret_cast<float *>(take(sizeof(float) * nt));
-  L.thi = reinterpret_cast<float *>(take(sizeof(float) * nt));
-  L.smin = reinterpret_cast<float *>(take(sizeof(float) * nt));
-  L.hmax = reinterpret_cast<float *>(take(sizeof(float) * nt));
+  L.tbox = reinterpret_cast<float4 *>(take(sizeof(float4) * nt));
+  L.smin2 = reinterpret_cast<float *>(take(sizeof(float) * nt));
+  L.hmax2 = reinterpret_cast<float *>(take(sizeof(float) * nt));
+  L.slo1 = reinterpret_cast<float *>(take(sizeof(float) * ns));
+  L.shi1 = reinterpret_cast<float *>(take(sizeof(float) * ns));
+  L.smin1 = reinterpret_cast<float *>(take(sizeof(float) * ns));
+  L.hmax1 = reinterpret_cast<float *>(take(sizeof(float) * ns));
+  L.packed = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long) * (size_t)nP));
+  L.work = reinterpret_cast<unsigned *>(take(sizeof(unsigned)));
   L.bytes = off;
   return L;
 }
+
+int *pp_field(ProjParams *pp, size_t offset) { return reinterpret_cast<int *>(reinterpret_cast<char *>(pp) + offset); }
 
 }  // namespace
 
@@ -583,29 +819,46 @@ cudaError_t launch_match_fp32(const float *FP, int nP, const float *FQ, int nQ, 
                               cudaStream_t s, unsigned long long *terms) {
   if (nP < 1) return cudaSuccess;
   Fp32Layout L = fp32_layout(static_cast<char *>(ws), nP, nQ);
-  const int n = nP + nQ, nt = (int)lsr_div_up(nQ, kTile);
-  LSR_CUDA_TRY(cudaMemsetAsync(L.counts, 0, sizeof(int) * ((size_t)n + 1), s));
-  constexpr int kPcSmem = kPcSamples * kD * (int)sizeof(float);
-  LSR_CUDA_TRY(cudaFuncSetAttribute(k_pc1, cudaFuncAttributeMaxDynamicSharedMemorySize, kPcSmem));
-  LSR_LAUNCH(k_pc1<<<1, kPcThreads, kPcSmem, s>>>(FQ, nQ, nP, L.pp));
+  const int n = nP + nQ, nt = (int)lsr_div_up(nQ, kTile), ns = (int)lsr_div_up(nQ, kSlab);
   const int eb = (int)lsr_div_up(n, 256);
+  LSR_CUDA_TRY(cudaMemsetAsync(L.counts1, 0, sizeof(int) * ((size_t)n + 1), s));
+  LSR_CUDA_TRY(cudaMemsetAsync(L.counts2, 0, sizeof(int) * ((size_t)L.ncap2 + 1), s));
+  constexpr int kPcSmem = kPcSamples * kD * (int)sizeof(float);
+  LSR_CUDA_TRY(cudaFuncSetAttribute(k_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, kPcSmem));
+  LSR_LAUNCH(k_pc<<<1, kPcThreads, kPcSmem, s>>>(FQ, nQ, nP, L.ncap2, L.pp));
   LSR_LAUNCH(k_proj<<<eb, 256, 0, s>>>(FP, nP, FQ, nQ, L.pp, L.pe));
-  LSR_LAUNCH(k_bucket_count<<<eb, 256, 0, s>>>(L.pe, nQ, nP, L.pp, L.slot, L.counts));
-  LSR_CUDA_TRY(scan_exclusive(L.counts, L.start,
-                                  reinterpret_cast<int *>(reinterpret_cast<char *>(L.pp) + offsetof(ProjParams, ntot)),
-                                  n, L.scan, s));
-  LSR_LAUNCH(k_bucket_scatter<<<eb, 256, 0, s>>>(n, L.slot, L.start, L.order));
+  // by p1, then by p2 inside slabs of kSlab consecutive positions
+  LSR_LAUNCH(k_bucket1<<<eb, 256, 0, s>>>(L.pe, nQ, nP, L.pp, L.slot1, L.counts1));
+  LSR_CUDA_TRY(scan_exclusive(L.counts1, L.start1, pp_field(L.pp, offsetof(ProjParams, ntot)), n, L.scan, s));
+  LSR_LAUNCH(k_bucket_scatter<<<eb, 256, 0, s>>>(n, L.slot1, L.start1, nullptr, L.order1));
+  LSR_LAUNCH(k_bucket2<<<eb, 256, 0, s>>>(L.pe, L.order1, nQ, nP, L.capD, L.pp, L.slot2, L.counts2));
+  LSR_CUDA_TRY(scan_exclusive(L.counts2, L.start2, pp_field(L.pp, offsetof(ProjParams, ncap2)), L.ncap2, L.scan, s));
+  LSR_LAUNCH(k_bucket_scatter<<<eb, 256, 0, s>>>(n, L.slot2, L.start2, L.order1, L.order));
   if (nt > 0) {
-    LSR_LAUNCH(k_gather_db<<<nt, kTile, 0, s>>>(FQ, nQ, L.order, L.pe, L.FQs, L.dorig, L.tlo, L.thi));
-    LSR_LAUNCH(k_tile_scan<<<1, kScanThreadsT, 0, s>>>(L.tlo, L.thi, nt, L.smin, L.hmax));
+    LSR_LAUNCH(k_gather_db<<<nt, kTile, 0, s>>>(FQ, nQ, L.order, L.pe, L.FQs, L.dorig, L.tbox));
+    LSR_LAUNCH(k_slab_bounds<<<(int)lsr_div_up(ns, 128), 128, 0, s>>>(L.tbox, nt, ns, L.slo1, L.shi1, L.smin2,
+                                                                       L.hmax2));
+    LSR_LAUNCH(k_bound_scan<<<1, kScanThreadsT, 0, s>>>(L.slo1, L.shi1, ns, L.smin1, L.hmax1));
   }
-  const int blocks = (int)lsr_div_up(nP, kMT);
+  LSR_CUDA_TRY(cudaMemsetAsync(L.packed, 0xFF, sizeof(unsigned long long) * (size_t)nP, s));
+  LSR_CUDA_TRY(cudaMemsetAsync(L.work, 0, sizeof(unsigned), s));
+  // persistent warps: as many blocks as fit on the GPU at once, or fewer
+  const int units = 2 * (int)lsr_div_up(nP, 32);
+  int per_sm = 0;
+  LSR_CUDA_TRY(terms ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_win<true>, kMT, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_win<false>, kMT, 0));
+  int blocks = (int)lsr_div_up(units, kMT / 32);
+  const int resident = (per_sm > 0 ? per_sm : 1) * device_sm_count();
+  if (blocks > resident) blocks = resident;
   if (terms)
-    LSR_LAUNCH(k_match_win<true><<<blocks, kMT, 0, s>>>(FP, nP, L.FQs, L.dorig, nQ, L.order, L.pe, L.smin, L.hmax,
-                                                        L.pp, nn, d1, terms));
+    LSR_LAUNCH(k_match_win<true><<<blocks, kMT, 0, s>>>(FP, nP, L.FQs, L.dorig, nQ, L.order, L.pe, L.slo1, L.shi1,
+                                                        L.smin1, L.hmax1, L.smin2, L.hmax2, L.pp, L.packed, L.work,
+                                                        terms));
   else
-    LSR_LAUNCH(k_match_win<false><<<blocks, kMT, 0, s>>>(FP, nP, L.FQs, L.dorig, nQ, L.order, L.pe, L.smin, L.hmax,
-                                                         L.pp, nn, d1, nullptr));
+    LSR_LAUNCH(k_match_win<false><<<blocks, kMT, 0, s>>>(FP, nP, L.FQs, L.dorig, nQ, L.order, L.pe, L.slo1, L.shi1,
+                                                         L.smin1, L.hmax1, L.smin2, L.hmax2, L.pp, L.packed, L.work,
+                                                         nullptr));
+  LSR_LAUNCH(k_win_finish<<<(int)lsr_div_up(nP, 256), 256, 0, s>>>(L.packed, nP, nn, d1));
   return cudaGetLastError();
 }
 

@@ -650,4 +650,6 @@ cudaError_t launch_match_bf16(const float *FP, int nP, const float *FQ, int nQ, 
                : run_tc<kKsPlain>(FP, nP, FQ, nQ, qt, ws, nn, d1, fb_count, err, d2, f, s);
 }
 
+int device_sm_count() { return sm_count(); }
+
 }  // namespace lsr
