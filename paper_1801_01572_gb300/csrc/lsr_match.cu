@@ -58,6 +58,7 @@ constexpr int kPcThreads = 256;  // k_pc block
 constexpr int kPcSamples = 1024; // database rows sampled for the principal axes (in shared memory)
 constexpr int kPcIters = 10;     // power iterations per axis (FPFH sets: variance ratios ~0.1 and ~0.4)
 constexpr int kScanThreadsT = 1024;  // k_bound_scan block
+constexpr int kItemRun = 2;          // matcher work items taken per counter increment (more: later slabs overtake nearer ones)
 
 // Directions and ranges of the projection order (one per matcher call).
 struct ProjParams {
@@ -536,100 +537,140 @@ __device__ __forceinline__ unsigned long long pack_pair(float d, int j) {
   return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)j;
 }
 
-// One warp per work unit: the 32 queries at positions 32 g .. 32 g + 31 of
+// Queries in the final order: desc_order rows (FPs, zeros in slots 33..35)
+// and their original indices (qorig); one thread per query position.
+__global__ void k_gather_q(const float *__restrict__ FP, int nP, int nQ, const int *__restrict__ order,
+                           float *__restrict__ FPs, int *__restrict__ qorig) {
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= nP) return;
+  int i = order[nQ + pos] - nQ;
+  if (!LSR_IN_BOUNDS(i, nP, kSiteMatchQuery)) i = 0;
+  const float *src = FP + (size_t)i * kDS;
+  float4 *dst = reinterpret_cast<float4 *>(FPs + (size_t)pos * kDS);
+#pragma unroll
+  for (int c = 0; c < kDS / 4; ++c) {
+    float v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = 4 * c + e < kD ? src[desc_order(4 * c + e)] : 0.f;
+    dst[c] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  qorig[pos] = i;
+}
+
+// Per query group (32 consecutive query positions): the slab where its
+// middle p1 falls (the last whose suffix minimum of lo1 does not exceed it;
+// 0 when it is not finite) and its middle p2.
+__global__ void k_group_start(const float4 *__restrict__ pe, const int *__restrict__ qorig, int nP, int nQ,
+                              const float *__restrict__ smin1, int *__restrict__ gs0, float *__restrict__ gm2) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int G = (int)lsr_div_up(nP, 32), ns = (int)lsr_div_up(nQ, kSlab);
+  if (g >= G) return;
+  const float4 q = pe[nQ + qorig[min(g * 32 + 16, nP - 1)]];
+  int s0 = 0;
+  if (isfinite(q.x)) {
+    int lo = 0, hi = ns;
+    while (lo < hi) {
+      const int md = (lo + hi) >> 1;
+      if (smin1[md] > q.x) hi = md; else lo = md + 1;
+    }
+    s0 = lo > 0 ? lo - 1 : 0;
+  }
+  gs0[g] = s0;
+  gm2[g] = q.z;
+}
+
+// One warp per work item: the 32 queries at positions 32 g .. 32 g + 31 of
 // the final query order (one query slab, close in p1 and in p2) and one
-// quarter of their window: units 4 g and 4 g + 1 the even and the odd
-// database slabs from the one where the group's middle p1 falls to the
-// right, units 4 g + 2 and 4 g + 3 the even and odd ones to its left. Units
-// are taken from a counter (persistent warps), so the four quarters of a
-// group run at once on different warps and a long window does not hold back
-// a block.
-// Each lane publishes its best (distance, index) with a 64-bit atomic
-// minimum and prunes with the smallest published distance: rows, tiles and
-// slabs are left out only when their bound exceeds a distance some row
-// really has, so the minimum over the published pairs is the exact result.
-// Outer loop: slabs outward, ending when no lane's p1 bound reaches the next
-// (monotone over slabs); inner loop, in a slab: its tiles outward from the
-// one where the middle p2 falls, alternately right and left, a side ending
-// when no lane's bound from the slab's p1 gap and the side's monotone p2 gap
-// reaches the next tile. kCount: also add the number of terms (a_k - b_k)^2
-// evaluated for the valid queries to *terms (a separate instantiation, used
-// when profiling).
+// database slab of their window. Item u = k * G + g (G groups) takes the
+// k-th slab of the group's window in the order s0, s0 - 1, s0 + 1, s0 - 2,
+// ... (s0: the slab where the group's middle p1 falls; even k to the right,
+// odd k to the left), so all groups' nearest slabs are scanned before any
+// group's farther ones. Items are taken from a counter in runs of
+// kItemRun consecutive groups at the same k (neighbouring groups read the
+// same tiles, so they share L1). Each lane publishes its best (distance,
+// index) with a 64-bit atomic minimum and prunes with the smallest
+// published distance: rows, tiles and slabs are left out only when their
+// bound exceeds a distance some row really has, so the minimum over the
+// published pairs is the exact result. A slab that no lane's p1 bound
+// reaches ends its side for the group from that slab on (the bound is
+// monotone over slabs): done keeps the smallest such offset per side, and
+// items of that side at or beyond it return at once (nearer ones still run,
+// as another warp may have ended the side while they wait). In a
+// slab: its tiles outward from the one where the group's middle p2 falls,
+// alternately right and left, a side ending when no lane's bound from the
+// slab's p1 gap and the side's monotone p2 gap reaches the next tile.
+// kCount: also add the number of terms (a_k - b_k)^2 evaluated for the
+// valid queries to *terms (a separate instantiation, used when profiling).
 template <bool kCount>
-__global__ void __launch_bounds__(kMT) k_match_win(const float *__restrict__ FP, int nP,
-                                                   const float *__restrict__ FQs, const int *__restrict__ dorig,
-                                                   int nQ, const int *__restrict__ order,
+__global__ void __launch_bounds__(kMT) k_match_win(const float *__restrict__ FPs, const int *__restrict__ qorig,
+                                                   int nP, const float *__restrict__ FQs,
+                                                   const int *__restrict__ dorig, int nQ,
                                                    const float4 *__restrict__ pe, const float *__restrict__ slo1,
                                                    const float *__restrict__ shi1, const float *__restrict__ smin1,
                                                    const float *__restrict__ hmax1, const float *__restrict__ smin2,
-                                                   const float *__restrict__ hmax2, const ProjParams *pp,
-                                                   unsigned long long *packed, unsigned *work,
+                                                   const float *__restrict__ hmax2, const int *__restrict__ gs0,
+                                                   const float *__restrict__ gm2, int *done,
+                                                   const ProjParams *pp, unsigned long long *packed, unsigned long long *work,
                                                    unsigned long long *__restrict__ terms) {
   const int lane = threadIdx.x & 31;
   const int nt = (int)lsr_div_up(nQ, kTile), ns = (int)lsr_div_up(nQ, kSlab);
-  const int nunits = 4 * (int)lsr_div_up(nP, 32);
+  const int G = (int)lsr_div_up(nP, 32);
+  const long long nitems = 2ll * ns * G;
   const float4 *F4 = reinterpret_cast<const float4 *>(FQs);
   const float fac = pp->fac;
   unsigned long long nterm = 0;
   for (;;) {
-    int u = 0;
-    if (lane == 0) u = (int)atomicAdd(work, 1u);
-    u = __shfl_sync(0xffffffffu, u, 0);
-    if (u >= nunits) break;
-    const int g = u >> 2;
-    const bool to_right = (u & 2) == 0;
-    const int par = u & 1;
-    const int k = g * 32 + lane;
-    const bool valid = k < nP;
-    int qo = 0;
-    if (valid) {
-      qo = order[nQ + k] - nQ;
-      if (!LSR_IN_BOUNDS(qo, nP, kSiteMatchQuery)) qo = 0;
-    }
-    float a[kD];
-    {
-      const float *row = FP + (size_t)qo * kDS;
-#pragma unroll
-      for (int j = 0; j < kD; ++j) a[j] = row[desc_order(j)];
-    }
-    float ql1, qh1, ql2, qh2;
-    {
-      const float4 q = pe[nQ + qo];
-      ql1 = __fsub_rd(q.x, q.y), qh1 = __fadd_ru(q.x, q.y), ql2 = __fsub_rd(q.z, q.w), qh2 = __fadd_ru(q.z, q.w);
-    }
-    // invalid lanes: bound below any distance, so they never hold the warp back
-    float best = valid ? FLT_MAX : -1.f;
-    int bj = -1;
-    bool taken = false;
-    unsigned uterm = 0;  // terms of this unit (at most 33 per database row)
-    // the group's middle projections (warp-uniform)
-    float m1, m2;
-    {
-      const int mid = min(g * 32 + 16, nP - 1);
-      const float4 q = pe[order[nQ + mid]];
-      m1 = q.x, m2 = q.z;
-    }
-    // start slab: the last whose suffix minimum of lo1 does not exceed m1 (0 if m1 is not finite)
-    int s0 = 0;
-    if (isfinite(m1)) {
-      int lo = 0, hi = ns;
-      while (lo < hi) {
-        const int md = (lo + hi) >> 1;
-        if (smin1[md] > m1) hi = md; else lo = md + 1;
+    long long u0 = 0;
+    if (lane == 0) u0 = (long long)atomicAdd(work, (unsigned long long)kItemRun);
+    u0 = __shfl_sync(0xffffffffu, u0, 0);
+    if (u0 >= nitems) break;
+    for (long long u = u0; u < u0 + kItemRun && u < nitems; ++u) {
+      const int kk = (int)(u / G), g = (int)(u % G);
+      const bool to_right = (kk & 1) == 0;
+      const int s = to_right ? gs0[g] + (kk >> 1) : gs0[g] - 1 - (kk >> 1);
+      if (s < 0 || s >= ns) continue;
+      // (one lane reads what other warps record, so the warp takes one decision)
+      int end_off = 0;
+      if (lane == 0) end_off = *reinterpret_cast<volatile int *>(done + 2 * g + (to_right ? 0 : 1));
+      if ((kk >> 1) >= __shfl_sync(0xffffffffu, end_off, 0)) continue;
+      const int k = g * 32 + lane;
+      const bool valid = k < nP;
+      const int kq = valid ? k : 0;
+      float ql1, qh1, ql2, qh2;
+      {
+        const float4 q = pe[nQ + qorig[kq]];
+        ql1 = __fsub_rd(q.x, q.y), qh1 = __fadd_ru(q.x, q.y), ql2 = __fsub_rd(q.z, q.w), qh2 = __fadd_ru(q.z, q.w);
       }
-      s0 = lo > 0 ? lo - 1 : 0;
-    }
-    for (int s = to_right ? s0 + par : s0 - 1 - par; s >= 0 && s < ns; s += to_right ? 2 : -2) {
+      // invalid lanes: bound below any distance, so they never hold the warp
+      // back; valid ones start from the smallest distance published so far
+      float best = -1.f;
+      int bj = -1;
       if (valid) {
-        // the smallest distance published for this query so far
-        const float pb = __uint_as_float((unsigned)(__ldcg(packed + qo) >> 32));
-        if (pb < best) best = pb, bj = -2;
+        const unsigned long long pv = __ldcg(packed + qorig[kq]);
+        best = pv == ~0ull ? FLT_MAX : __uint_as_float((unsigned)(pv >> 32));
+        bj = pv == ~0ull ? -1 : -2;
       }
       const float gs = to_right ? fmaxf(__fsub_rd(smin1[s], qh1), 0.f) : fmaxf(__fsub_rd(ql1, hmax1[s]), 0.f);
-      if (!__any_sync(0xffffffffu, valid && !(gap_bound(gs, 0.f, fac) > best))) break;
+      if (!__any_sync(0xffffffffu, valid && !(gap_bound(gs, 0.f, fac) > best))) {
+        if (lane == 0) atomicMin(done + 2 * g + (to_right ? 0 : 1), kk >> 1);
+        continue;
+      }
+      float a[kD];
+      {
+        const float4 *row = reinterpret_cast<const float4 *>(FPs + (size_t)kq * kDS);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float4 v = __ldg(row + c);
+          a[4 * c] = v.x, a[4 * c + 1] = v.y, a[4 * c + 2] = v.z, a[4 * c + 3] = v.w;
+        }
+        a[32] = __ldg(reinterpret_cast<const float *>(row + 8));
+      }
+      bool taken = false;
+      unsigned uterm = 0;  // terms of this item (at most 33 per database row)
       const float g1 = interval_gap(slo1[s], shi1[s], ql1, qh1);
       const int ta = s * kTilesPerSlab, tb = min(nt, ta + kTilesPerSlab);
       // start tile: the last of the slab whose suffix minimum of lo2 does not exceed m2
+      const float m2 = gm2[g];
       int t0 = ta;
       if (isfinite(m2)) {
         int lo = ta, hi = tb;
@@ -656,12 +697,12 @@ __global__ void __launch_bounds__(kMT) k_match_win(const float *__restrict__ FP,
         scan_rows<kCount>(F4 + (size_t)t * (9 * kTile), dorig + base, nQ - base < kTile ? nQ - base : kTile, a,
                           best, bj, taken, uterm);
       }
-      if (valid && taken && LSR_IN_BOUNDS(qo, nP, kSiteMatchQuery)) {
-        atomicMin(packed + qo, pack_pair(best, bj));
-        taken = false;
+      if (valid && taken) {
+        const int qo = qorig[kq];
+        if (LSR_IN_BOUNDS(qo, nP, kSiteMatchQuery)) atomicMin(packed + qo, pack_pair(best, bj));
       }
+      if (kCount && valid) nterm += uterm;
     }
-    if (kCount && valid) nterm += uterm;
   }
   if (kCount) {
     unsigned long long mine = nterm;
@@ -764,7 +805,12 @@ struct Fp32Layout {
   float *smin2, *hmax2;               // per tile, within its slab
   float *slo1, *shi1, *smin1, *hmax1; // per slab
   unsigned long long *packed;         // per query: published (distance bits << 32 | index) minimum
-  unsigned *work;                     // work-unit counter
+  unsigned long long *work;           // work-item counter
+  float *FPs;                         // queries in the final order (desc_order rows)
+  int *qorig;                         // their original indices
+  int *gs0;                           // per query group: start slab
+  float *gm2;                         // per query group: middle p2
+  int *done;                          // per query group and side: offset from which no slab is needed
   int capD, ncap2;
   size_t bytes;
 };
@@ -804,7 +850,13 @@ Fp32Layout fp32_layout(char *base, int nP, int nQ) {
   L.smin1 = reinterpret_cast<float *>(take(sizeof(float) * ns));
   L.hmax1 = reinterpret_cast<float *>(take(sizeof(float) * ns));
   L.packed = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long) * (size_t)nP));
-  L.work = reinterpret_cast<unsigned *>(take(sizeof(unsigned)));
+  L.work = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long)));
+  const size_t G = (size_t)lsr_div_up(nP, 32);
+  L.FPs = reinterpret_cast<float *>(take(sizeof(float) * kDS * (size_t)nP));
+  L.qorig = reinterpret_cast<int *>(take(sizeof(int) * (size_t)nP));
+  L.gs0 = reinterpret_cast<int *>(take(sizeof(int) * G));
+  L.gm2 = reinterpret_cast<float *>(take(sizeof(float) * G));
+  L.done = reinterpret_cast<int *>(take(sizeof(int) * 2 * G));
   L.bytes = off;
   return L;
 }
@@ -841,23 +893,30 @@ cudaError_t launch_match_fp32(const float *FP, int nP, const float *FQ, int nQ, 
     LSR_LAUNCH(k_bound_scan<<<1, kScanThreadsT, 0, s>>>(L.slo1, L.shi1, ns, L.smin1, L.hmax1));
   }
   LSR_CUDA_TRY(cudaMemsetAsync(L.packed, 0xFF, sizeof(unsigned long long) * (size_t)nP, s));
-  LSR_CUDA_TRY(cudaMemsetAsync(L.work, 0, sizeof(unsigned), s));
-  // persistent warps: as many blocks as fit on the GPU at once, or fewer
-  const int units = 2 * (int)lsr_div_up(nP, 32);
-  int per_sm = 0;
-  LSR_CUDA_TRY(terms ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_win<true>, kMT, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_win<false>, kMT, 0));
-  int blocks = (int)lsr_div_up(units, kMT / 32);
-  const int resident = (per_sm > 0 ? per_sm : 1) * device_sm_count();
-  if (blocks > resident) blocks = resident;
-  if (terms)
-    LSR_LAUNCH(k_match_win<true><<<blocks, kMT, 0, s>>>(FP, nP, L.FQs, L.dorig, nQ, L.order, L.pe, L.slo1, L.shi1,
-                                                        L.smin1, L.hmax1, L.smin2, L.hmax2, L.pp, L.packed, L.work,
-                                                        terms));
-  else
-    LSR_LAUNCH(k_match_win<false><<<blocks, kMT, 0, s>>>(FP, nP, L.FQs, L.dorig, nQ, L.order, L.pe, L.slo1, L.shi1,
-                                                         L.smin1, L.hmax1, L.smin2, L.hmax2, L.pp, L.packed, L.work,
-                                                         nullptr));
+  LSR_CUDA_TRY(cudaMemsetAsync(L.work, 0, sizeof(unsigned long long), s));
+  const int G = (int)lsr_div_up(nP, 32);
+  // 0x7F7F7F7F: no side has ended yet
+  LSR_CUDA_TRY(cudaMemsetAsync(L.done, 0x7F, sizeof(int) * 2 * (size_t)G, s));
+  LSR_LAUNCH(k_gather_q<<<(int)lsr_div_up(nP, 256), 256, 0, s>>>(FP, nP, nQ, L.order, L.FPs, L.qorig));
+  if (nt > 0) {
+    LSR_LAUNCH(k_group_start<<<(int)lsr_div_up(G, 256), 256, 0, s>>>(L.pe, L.qorig, nP, nQ, L.smin1, L.gs0, L.gm2));
+    // persistent warps: as many blocks as fit on the GPU at once, or fewer
+    int per_sm = 0;
+    LSR_CUDA_TRY(terms ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_win<true>, kMT, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_win<false>, kMT, 0));
+    const long long items = 2ll * ns * G;
+    long long blocks = lsr_div_up(lsr_div_up(items, kItemRun), kMT / 32);
+    const long long resident = (long long)(per_sm > 0 ? per_sm : 1) * device_sm_count();
+    if (blocks > resident) blocks = resident;
+    if (terms)
+      LSR_LAUNCH(k_match_win<true><<<(int)blocks, kMT, 0, s>>>(L.FPs, L.qorig, nP, L.FQs, L.dorig, nQ, L.pe, L.slo1,
+                                                               L.shi1, L.smin1, L.hmax1, L.smin2, L.hmax2, L.gs0,
+                                                               L.gm2, L.done, L.pp, L.packed, L.work, terms));
+    else
+      LSR_LAUNCH(k_match_win<false><<<(int)blocks, kMT, 0, s>>>(L.FPs, L.qorig, nP, L.FQs, L.dorig, nQ, L.pe, L.slo1,
+                                                                L.shi1, L.smin1, L.hmax1, L.smin2, L.hmax2, L.gs0,
+                                                                L.gm2, L.done, L.pp, L.packed, L.work, nullptr));
+  }
   LSR_LAUNCH(k_win_finish<<<(int)lsr_div_up(nP, 256), 256, 0, s>>>(L.packed, nP, nn, d1));
   return cudaGetLastError();
 }
