@@ -89,6 +89,15 @@ thread_local KernelTimer *g_ktimer = nullptr;
 
 static std::string kernel_name_of(const char *expr) {
   const char *p = expr;
+  // a programmatic-dependent launch: pdl_launch(kernel, ...)
+  if (const char *k = strstr(p, "pdl_launch(")) {
+    p = k + strlen("pdl_launch(");
+    const char *q = strchr(p, ',');
+    std::string out;
+    for (const char *c = p; *c && c != q; ++c)
+      if (*c != ' ' && *c != '\n') out.push_back(*c);
+    return out;
+  }
   while (*p == ' ' || *p == '(' || *p == '\n') ++p;
   const char *q = strstr(p, "<<<");
   std::string n = q ? std::string(p, q) : std::string(p);
@@ -617,7 +626,7 @@ cudaError_t enqueue_refine(const float4 *XP, const float *P, int nP, const float
     LSR_CUDA_TRY(launch_refine_level_begin(st, s));
     LSR_CUDA_TRY(cudaMemsetAsync(seeds, 0xff, sizeof(int) * (size_t)np, s));  // no neighbour yet at this level
     for (int it = 0; it < iters; ++it)
-      LSR_CUDA_TRY(launch_refine_step(xp, np, 1, g, st0, xs, e, mu, iters, st, part, seeds, s));
+      LSR_CUDA_TRY(launch_refine_step(xp, np, 1, g, st0, xs, e, mu, iters, st, part, seeds, it > 0, s));
   }
   return cudaSuccess;
 }

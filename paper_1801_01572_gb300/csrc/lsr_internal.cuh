@@ -151,6 +151,25 @@ void ktimer_mark(const char *launch_expr, bool after);
   (::lsr::count_launch(), ::lsr::g_ktimer ? ::lsr::ktimer_mark(#__VA_ARGS__, false) : void(), \
    __VA_ARGS__, ::lsr::g_ktimer ? ::lsr::ktimer_mark(#__VA_ARGS__, true) : void())
 
+// Launch with programmatic stream serialisation: the kernel may be scheduled
+// before the previous kernel in the stream has finished (that kernel allows
+// it with griddepcontrol.launch_dependents) and must execute
+// griddepcontrol.wait before it touches anything the previous kernel writes.
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 #define LSR_CUDA_TRY(call)                         \
   do {                                             \
     cudaError_t e_ = (call);                       \
@@ -598,9 +617,11 @@ cudaError_t launch_refine_level_begin(RansacState *st, cudaStream_t s);
 // caller index is a multiple of strideP, against the given grid of Q. seeds
 // (nP ints, -1 = none; set to -1 at the start of a level): each point's
 // neighbour of the previous step, read as the search's start and rewritten.
+// chained: launched as a programmatic dependent of the previous step, which
+// must be the kernel directly before it in s.
 cudaError_t launch_refine_step(const float4 *XP, int nP, int strideP, const GridParams *ge, const int *start_e,
                                const float4 *Xe, float eps_r, float mu, int max_iters, RansacState *st,
-                               double *partials, int *seeds, cudaStream_t s);
+                               double *partials, int *seeds, bool chained, cudaStream_t s);
 // out[m] = (Q[m * stride], m) for m < ceil(n / stride); Q caller-order xyz.
 cudaError_t launch_subsample(const float *xyz, int n, int stride, float4 *out, cudaStream_t s);
 cudaError_t launch_final_pose(RansacState *st, float *pose, cudaStream_t s);

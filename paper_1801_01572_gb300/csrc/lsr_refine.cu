@@ -67,94 +67,144 @@ __device__ void exp_so3(const double w[3], double R[9]) {
 constexpr int kNSum = 17;
 static_assert(kNSum <= kNAcc, "refinement partial layout");
 
-// Solve A d = -b in FP64 from the summed partials (LDL^T: one division per
+// The state one step reads, copied to shared memory by the closing block
+// while it sums the partials (its loads then overlap instead of queueing
+// behind each other in the single solving thread).
+struct StepState {
+  double T[12];
+  double center[3];
+  int iters_done;
+  int level_iters;
+};
+
+// 1 / x in FP64 for a positive x: the FP32 reciprocal refined by two Newton-
+// Raphson steps r <- r + r (1 - x r) (each doubles the correct bits: 24 ->
+// 48 -> 96, so the result is within an ulp of 1 / x); outside the FP32 range
+// the FP64 division. A division costs far more FP64 latency on this part
+// than the four fused multiply-adds.
+__device__ __forceinline__ double recip_pos(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+
+// Solve A d = -b in FP64 from the summed partials (LDL^T: one reciprocal per
 // pivot, no square root) and left-multiply the pose by the update about the
 // centre c used for this step: x' = Exp(d_w)(x - c) + c + d_v. The next step's
-// centre is the weighted centroid of this step's correspondences.
-__device__ void refine_solve(const double *S, RansacState *st, int max_iters, double tol) {
+// centre is the weighted centroid of this step's correspondences. Reads the
+// state from ss, writes it to st. Run by warps 0 and 1 of the closing block
+// (every thread of the block reaches its barrier): each value is computed by
+// one lane with the same operations in the same order as a single thread
+// would, so the result does not depend on the split. LDL^T: for pivot j,
+// lanes j..5 form v_i = A_ij - sum_k L_ik L_jk D_k at once (v_j is D_j);
+// the substitutions and Exp's two coefficients run on lane 0, the twelve
+// pose entries on lanes 0..11; the next centre on warp 1 meanwhile, and the
+// step length and the state on warp 1 after the pose.
+__device__ void refine_solve(const double *S, const StepState &ss, RansacState *st, int max_iters, double tol) {
+  __shared__ double sA[6][6], sL[6][6], sD[6], siD[6], sd[6], scoef[2], scn[3];
+  __shared__ int spd;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double *xx = S + 5, *b = S + 11;
   const double sw = S[1], sx0 = S[2], sx1 = S[3], sx2 = S[4];
-  double A[6][6] = {{xx[3] + xx[5], -xx[1], -xx[2], 0.0, -sx2, sx1},
-                    {0.0, xx[0] + xx[5], -xx[4], sx2, 0.0, -sx0},
-                    {0.0, 0.0, xx[0] + xx[3], -sx1, sx0, 0.0},
-                    {0.0, 0.0, 0.0, sw, 0.0, 0.0},
-                    {0.0, 0.0, 0.0, 0.0, sw, 0.0},
-                    {0.0, 0.0, 0.0, 0.0, 0.0, sw}};
-  for (int i = 1; i < 6; ++i)
-    for (int j = 0; j < i; ++j) A[i][j] = A[j][i];
-  double L[6][6], D[6], iD[6];
   bool pd = S[0] >= 3.0;
-  for (int j = 0; j < 6 && pd; ++j) {
-    double dj = A[j][j];
-    for (int k = 0; k < j; ++k) dj -= L[j][k] * L[j][k] * D[k];
-    if (!(dj > 0.0)) {
-      pd = false;
-      break;
-    }
-    D[j] = dj;
-    iD[j] = 1.0 / dj;
-    for (int i = j + 1; i < 6; ++i) {
-      double v = A[i][j];
-      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k] * D[k];
-      L[i][j] = v * iD[j];
-    }
+  if (warp == 0 && lane == 0) {
+    const double A[6][6] = {{xx[3] + xx[5], -xx[1], -xx[2], 0.0, -sx2, sx1},
+                            {0.0, xx[0] + xx[5], -xx[4], sx2, 0.0, -sx0},
+                            {0.0, 0.0, xx[0] + xx[3], -sx1, sx0, 0.0},
+                            {0.0, 0.0, 0.0, sw, 0.0, 0.0},
+                            {0.0, 0.0, 0.0, 0.0, sw, 0.0},
+                            {0.0, 0.0, 0.0, 0.0, 0.0, sw}};
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) sA[i][j] = j >= i ? A[i][j] : A[j][i];
+  } else if (warp == 1 && lane == 0 && sw > 0.0) {
+    const double iw = recip_pos(sw);
+    const double *c = ss.center;
+    scn[0] = c[0] + sx0 * iw, scn[1] = c[1] + sx1 * iw, scn[2] = c[2] + sx2 * iw;
   }
-  if (!pd) {
-    st->active = 0;
-    return;
-  }
-  double y[6], d[6];
-  for (int i = 0; i < 6; ++i) {
-    double v = -b[i];
-    for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
-    y[i] = v;
-  }
-  for (int i = 5; i >= 0; --i) {
-    double v = y[i] * iD[i];
-    for (int k = i + 1; k < 6; ++k) v -= L[k][i] * d[k];
-    d[i] = v;
-  }
-  // Exp of the rotation part: the series of sin(t)/t and (1 - cos t)/t^2 to
-  // the t^8 term below t = 0.01 (the next term is below 1e-21), else sin/cos
-  double Rd[9];
-  {
-    const double th2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    double a, bb;
-    if (th2 < 1e-4) {
-      a = 1.0 - th2 / 6.0 * (1.0 - th2 / 20.0 * (1.0 - th2 / 42.0 * (1.0 - th2 / 72.0)));
-      bb = 0.5 * (1.0 - th2 / 12.0 * (1.0 - th2 / 30.0 * (1.0 - th2 / 56.0 * (1.0 - th2 / 90.0))));
-    } else {
-      const double th = sqrt(th2);
-      a = sin(th) / th;
-      bb = (1.0 - cos(th)) / th2;
-    }
-    const double K[9] = {0, -d[2], d[1], d[2], 0, -d[0], -d[1], d[0], 0};
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) {
-        const double k2 = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
-        Rd[3 * r + c] = (r == c ? 1.0 : 0.0) + a * K[3 * r + c] + bb * k2;
+  if (warp == 0) {
+    __syncwarp();
+    for (int j = 0; j < 6 && pd; ++j) {
+      double v = 0.0;
+      if (lane >= j && lane < 6) {
+        v = sA[lane][j];
+        for (int k = 0; k < j; ++k) v -= sL[lane][k] * sL[j][k] * sD[k];
       }
+      const double dj = __shfl_sync(0xffffffffu, v, j);
+      if (!(dj > 0.0)) {
+        pd = false;
+        break;
+      }
+      const double idj = recip_pos(dj);
+      if (lane == j) sD[j] = dj, siD[j] = idj;
+      if (lane > j && lane < 6) sL[lane][j] = v * idj;
+      __syncwarp();
+    }
+    if (pd && lane == 0) {
+      double y[6], d[6];
+      for (int i = 0; i < 6; ++i) {
+        double v = -b[i];
+        for (int k = 0; k < i; ++k) v -= sL[i][k] * y[k];
+        y[i] = v;
+      }
+      for (int i = 5; i >= 0; --i) {
+        double v = y[i] * siD[i];
+        for (int k = i + 1; k < 6; ++k) v -= sL[k][i] * d[k];
+        d[i] = v;
+      }
+      for (int i = 0; i < 6; ++i) sd[i] = d[i];
+    }
+    __syncwarp();
+    if (pd && lane == 0) {
+      // Exp of the rotation part: the series of sin(t)/t and (1 - cos t)/t^2 to
+      // the t^8 term below t = 0.01 (the next term is below 1e-21; the
+      // coefficients' reciprocals are FP64 constants), else sin/cos
+      const double th2 = sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2];
+      if (th2 < 1e-4) {
+        scoef[0] = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0) * (1.0 - th2 * (1.0 / 72.0))));
+        scoef[1] = 0.5 * (1.0 - th2 * (1.0 / 12.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0) * (1.0 - th2 * (1.0 / 90.0)))));
+      } else {
+        const double th = sqrt(th2);
+        scoef[0] = sin(th) / th;
+        scoef[1] = (1.0 - cos(th)) / th2;
+      }
+    }
+    if (lane == 0) spd = pd;
+    __syncwarp();
   }
-  const double *c = st->center;
-  double v[3];
-  for (int r = 0; r < 3; ++r) v[r] = c[r] - (Rd[3 * r] * c[0] + Rd[3 * r + 1] * c[1] + Rd[3 * r + 2] * c[2]) + d[3 + r];
-  double Tn[12];
-  for (int r = 0; r < 3; ++r)
-    for (int q = 0; q < 4; ++q)
-      Tn[4 * r + q] = Rd[3 * r] * st->T[q] + Rd[3 * r + 1] * st->T[4 + q] + Rd[3 * r + 2] * st->T[8 + q] +
-                      (q == 3 ? v[r] : 0.0);
-  for (int i = 0; i < 12; ++i) st->T[i] = Tn[i];
-  if (sw > 0.0) {
-    const double iw = 1.0 / sw;
-    const double cn[3] = {c[0] + sx0 * iw, c[1] + sx1 * iw, c[2] + sx2 * iw};
-    for (int r = 0; r < 3; ++r) st->center[r] = cn[r];
+  __syncthreads();  // spd, sd, scoef (warp 0) and scn (warp 1)
+  pd = spd != 0;
+  if (warp == 1 && lane == 0) {
+    if (!pd) {
+      st->active = 0;
+      return;
+    }
+    if (sw > 0.0)
+      for (int r = 0; r < 3; ++r) st->center[r] = scn[r];
+    double nd2 = 0.0;
+    for (int i = 0; i < 6; ++i) nd2 += sd[i] * sd[i];
+    st->last_step = sqrt(nd2);
+    st->iters_done = ss.iters_done + 1;
+    st->level_iters = ss.level_iters + 1;
+    if (nd2 < tol * tol || ss.level_iters + 1 >= max_iters) st->active = 0;
   }
-  double nd2 = 0.0;
-  for (int i = 0; i < 6; ++i) nd2 += d[i] * d[i];
-  st->last_step = sqrt(nd2);
-  st->iters_done += 1;
-  st->level_iters += 1;
-  if (nd2 < tol * tol || st->level_iters >= max_iters) st->active = 0;
+  if (warp != 0 || !pd) return;
+  if (lane < 12) {
+    // pose entry (r, q): row r of Rd (its three entries), then row r of Rd T
+    const int r = lane >> 2, q = lane & 3;
+    const double *d = sd;
+    const double a = scoef[0], bb = scoef[1];
+    const double K[9] = {0, -d[2], d[1], d[2], 0, -d[0], -d[1], d[0], 0};
+    double Rd[3];
+    for (int cc = 0; cc < 3; ++cc) {
+      const double k2 = K[3 * r] * K[cc] + K[3 * r + 1] * K[3 + cc] + K[3 * r + 2] * K[6 + cc];
+      Rd[cc] = (r == cc ? 1.0 : 0.0) + a * K[3 * r + cc] + bb * k2;
+    }
+    const double *c = ss.center;
+    const double vr = c[r] - (Rd[0] * c[0] + Rd[1] * c[1] + Rd[2] * c[2]) + d[3 + r];
+    st->T[lane] = Rd[0] * ss.T[q] + Rd[1] * ss.T[4 + q] + Rd[2] * ss.T[8 + q] + (q == 3 ? vr : 0.0);
+  }
 }
 
 // One IRLS step. Every block accumulates its points; the last block to
@@ -166,6 +216,11 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
                                                              double tol, int *__restrict__ seeds) {
   __shared__ int s_last;
   __shared__ double tot[kNSum];
+  // the next step may be scheduled now (launched as a programmatic dependent,
+  // it waits below for this one to finish); this step reads the pose, the
+  // state and the seeds the previous step wrote
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (!st->active) return;
   const GridParams g = *gep;
   const double *T = st->T;
@@ -236,6 +291,11 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  __shared__ StepState ss;
+  if (threadIdx.x < 12) ss.T[threadIdx.x] = __ldcg(st->T + threadIdx.x);
+  else if (threadIdx.x < 15) ss.center[threadIdx.x - 12] = __ldcg(st->center + threadIdx.x - 12);
+  else if (threadIdx.x == 15) ss.iters_done = __ldcg(&st->iters_done);
+  else if (threadIdx.x == 16) ss.level_iters = __ldcg(&st->level_iters);
   {
     // sum k = t % 17 over the blocks t / 17, t / 17 + 15, ..., then the 15
     // segments in order (a fixed order: the sums are deterministic)
@@ -264,10 +324,8 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    refine_solve(tot, st, max_iters, tol);
-    st->ticket = 0u;
-  }
+  if (threadIdx.x == 0) st->ticket = 0u;
+  refine_solve(tot, ss, st, max_iters, tol);
 }
 
 __global__ void k_refine_level_begin(RansacState *st) {
@@ -524,10 +582,18 @@ cudaError_t launch_subsample(const float *xyz, int n, int stride, float4 *out, c
 
 cudaError_t launch_refine_step(const float4 *XP, int nP, int strideP, const GridParams *ge, const int *start_e,
                                const float4 *Xe, float eps_r, float mu, int max_iters, RansacState *st,
-                               double *partials, int *seeds, cudaStream_t s) {
+                               double *partials, int *seeds, bool chained, cudaStream_t s) {
   int nb = refine_blocks((int)lsr_div_up(nP, strideP));
-  LSR_LAUNCH(k_refine_step<<<nb, kRefThreads, 0, s>>>(XP, nP, strideP, ge, start_e, Xe, eps_r * eps_r, mu, st, partials,
-                                           max_iters, 1e-6, seeds));
+  if (chained) {
+    // directly after the previous step: scheduled while it closes
+    cudaError_t e = cudaSuccess;
+    LSR_LAUNCH(e = pdl_launch(k_refine_step, dim3(nb), dim3(kRefThreads), s, XP, nP, strideP, ge, start_e, Xe,
+                              eps_r * eps_r, mu, st, partials, max_iters, 1e-6, seeds));
+    LSR_CUDA_TRY(e);
+  } else {
+    LSR_LAUNCH(k_refine_step<<<nb, kRefThreads, 0, s>>>(XP, nP, strideP, ge, start_e, Xe, eps_r * eps_r, mu, st,
+                                                        partials, max_iters, 1e-6, seeds));
+  }
   return cudaGetLastError();
 }
 
