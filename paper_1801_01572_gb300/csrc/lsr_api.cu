@@ -196,6 +196,11 @@ struct Arena {
 
 int cap_cells_for(int n) { return std::max(8 * n, 1 << 20); }
 
+// Consensus: clouds of P from this size on take the estimate pre-pass (every
+// kConsensusPrepassStride-th point) before the full bounds pass.
+constexpr int kConsensusPrepassMin = 16384;
+constexpr int kConsensusPrepassStride = 16;
+
 struct CloudLayout {
   int n = 0, cap_f = 0, cap_n = 0, cap_e = 0;
   float *src = nullptr;  // staged copy of host input (or null)
@@ -312,6 +317,8 @@ struct PairLayout {
   int *amb = nullptr;        // points in undecided voxels per hypothesis
   int *count2 = nullptr;     // exact counts of the reaching hypotheses
   int *tie_list = nullptr;   // the survivor slots tied at the top
+  unsigned long long *prog = nullptr;  // per survivor: bounds progress (points done << 32 | IN + undecided)
+  int *c0 = nullptr;         // an exact count reached by some survivor (the bounds pass's bar)
   // single-cell lattice of Q (lsr_params.nn_mode = LSR_NN_SINGLE_CELL)
   int cap_s = 0;
   GridParams *gs = nullptr;
@@ -355,6 +362,8 @@ void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int leve
   L.amb = a.take<int>(L.surv_cap);
   L.count2 = a.take<int>(L.surv_cap);
   L.tie_list = a.take<int>(L.surv_cap);
+  L.prog = a.take<unsigned long long>(L.surv_cap);
+  L.c0 = a.take<int>(1);
   L.tc_ws = a.take<char>(precision != LSR_MATCH_FP32 ? tc_workspace_bytes(nP, nQ, precision == LSR_MATCH_BF16)
                                                       : fp32_workspace_bytes(nP, nQ));
   L.cap_s = L.Q.cap_e;
@@ -720,9 +729,9 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
     TRY_CUDA(c, launch_select(L.surv, L.count, L.sum, L.ok, L.pose, nP, p.min_inlier_ratio, L.st, s), "select");
   } else {
     // Inlier-count bounds of every survivor from the voxel classification of Q;
-    // exact counts of the 32 largest upper bounds give C; exact counts of the
-    // others whose upper bound reaches C; distance sums of the top ties. No
-    // survivor left out can be selected. P is read in normal-grid order (5 cm
+    // exact counts of the 32 largest upper bounds (on a subsample of P for a
+    // large P) give C; exact counts of the others whose upper bound reaches C;
+    // distance sums of the top ties. No survivor left out can be selected. P is read in normal-grid order (5 cm
     // cells): the counts and fixed-point sums do not depend on the order, and
     // a warp's points then land on fewer table words.
     TRY_CUDA(c, launch_cls_build(Qc.box, p.eps_inlier, Qc.X, nQ, L.cls, L.in_bits, L.near_bits, s), "classify");
@@ -730,15 +739,37 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
     TRY_CUDA(c, cudaMemsetAsync(L.amb, 0, sizeof(int) * L.surv_cap, s), "memset count");
     TRY_CUDA(c, cudaMemsetAsync(L.count2, 0, sizeof(int) * L.surv_cap, s), "memset count");
     TRY_CUDA(c, cudaMemsetAsync(L.sum, 0, sizeof(unsigned long long) * L.surv_cap, s), "memset sum");
+    // Large P: the 32 largest upper bounds on every 16th point pick the
+    // hypotheses counted exactly first; their best count c0 then lets the
+    // full bounds pass leave out every hypothesis whose upper bound falls
+    // below c0 part-way (it can neither win nor tie).
+    const bool prepass = nP >= kConsensusPrepassMin;
+    if (prepass) {
+      TRY_CUDA(c,
+               launch_consensus_bounds(Pc.Xn, nP, kConsensusPrepassStride, L.cls, L.in_bits, L.near_bits, L.pose, L.ok,
+                                       &L.st->n_surv, L.count, L.amb, nullptr, nullptr, s),
+               "consensus estimate");
+      TRY_CUDA(c, launch_top_upper(L.count, L.amb, L.ok, &L.st->n_surv, 32, L.sel, s), "top");
+      TRY_CUDA(c,
+               launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose,
+                                      L.sel, &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
+               "consensus top");
+      TRY_CUDA(c, launch_sel_max(L.count2, L.sel, &L.st->n_surv, L.c0, s), "consensus bar");
+      TRY_CUDA(c, cudaMemsetAsync(L.count, 0, sizeof(int) * L.surv_cap, s), "memset count");
+      TRY_CUDA(c, cudaMemsetAsync(L.amb, 0, sizeof(int) * L.surv_cap, s), "memset count");
+      TRY_CUDA(c, cudaMemsetAsync(L.prog, 0, sizeof(unsigned long long) * L.surv_cap, s), "memset count");
+    }
     TRY_CUDA(c,
-             launch_consensus_bounds(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, L.pose, L.ok, &L.st->n_surv, L.count,
-                                     L.amb, s),
+             launch_consensus_bounds(Pc.Xn, nP, 1, L.cls, L.in_bits, L.near_bits, L.pose, L.ok, &L.st->n_surv, L.count,
+                                     L.amb, prepass ? L.c0 : nullptr, prepass ? L.prog : nullptr, s),
              "consensus bounds");
-    TRY_CUDA(c, launch_top_upper(L.count, L.amb, L.ok, &L.st->n_surv, 32, L.sel, s), "top");
-    TRY_CUDA(c,
-             launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.sel,
-                                    &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
-             "consensus top");
+    if (!prepass) {
+      TRY_CUDA(c, launch_top_upper(L.count, L.amb, L.ok, &L.st->n_surv, 32, L.sel, s), "top");
+      TRY_CUDA(c,
+               launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose,
+                                      L.sel, &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
+               "consensus top");
+    }
     TRY_CUDA(c, launch_reach_rest(L.count, L.amb, L.count2, L.sel, L.ok, &L.st->n_surv, L.rest, L.reach, s), "reach");
     TRY_CUDA(c,
              launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.rest,

@@ -152,33 +152,58 @@ __device__ __forceinline__ bool warp_any_within(const GridParams &g, const int *
 // One thread block per (hypothesis, chunk of P), as the exact kernel; a lane
 // per point. kBounds: count IN points into count and undecided ones into amb.
 // Otherwise the undecided lanes are resolved by the whole warp, one at a time,
-// and count receives the exact inlier count.
+// and count receives the exact inlier count. The points are XP[v * stride]
+// for v < ceil(nP / stride).
+// Bounds with c0 (a device count no larger than the winning count, e.g. the
+// exact count of some hypothesis): items run chunk-major, so each hypothesis's
+// chunks come in order, and prog[s] accumulates (points done << 32 | IN +
+// undecided) in one 64-bit word, read as one consistent pair. A chunk whose
+// hypothesis already has IN + undecided + points not yet done < c0 is left
+// out: that upper bound only falls as chunks finish, so the hypothesis can
+// neither win nor tie. (k_bounds_finish then adds the points left out to amb,
+// keeping IN + amb an upper bound.)
 template <bool kBounds>
 __global__ void __launch_bounds__(kClsThreads, kClsMinBlocks) k_consensus_count(
-    const float4 *__restrict__ XP, int nP, const ClsParams *__restrict__ cpp, const unsigned *__restrict__ in_bits,
-    const unsigned *__restrict__ near_bits, const GridParams *__restrict__ gep, const int *__restrict__ start,
-    const float4 *__restrict__ Xe, const float *__restrict__ pose, const uint8_t *__restrict__ ok, const int *n_dev,
-    int n_host, float eps2, int *__restrict__ count, int *__restrict__ amb_count) {
+    const float4 *__restrict__ XP, int nP, int stride, const ClsParams *__restrict__ cpp,
+    const unsigned *__restrict__ in_bits, const unsigned *__restrict__ near_bits, const GridParams *__restrict__ gep,
+    const int *__restrict__ start, const float4 *__restrict__ Xe, const float *__restrict__ pose,
+    const uint8_t *__restrict__ ok, const int *n_dev, int n_host, float eps2, int *__restrict__ count,
+    int *__restrict__ amb_count, const int *c0, unsigned long long *prog) {
   const ClsParams c = *cpp;
   const GridParams g = kBounds ? GridParams{} : *gep;
   const int nh = n_dev ? *n_dev : n_host;
-  const int chunks = (nP + kClsChunk - 1) / kClsChunk;
+  const int nv = (nP + stride - 1) / stride;
+  const int chunks = (nv + kClsChunk - 1) / kClsChunk;
   const int64_t items = (int64_t)nh * chunks;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __shared__ int s_cnt[kClsThreads / 32], s_amb[kClsThreads / 32];
+  const bool abandon = kBounds && c0 != nullptr;
+  const int cbar = abandon ? *c0 : 0;
+  __shared__ int s_cnt[kClsThreads / 32], s_amb[kClsThreads / 32], s_skip;
   for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
-    const int s = (int)(item / chunks), ch = (int)(item - (int64_t)s * chunks);
+    const int s = abandon ? (int)(item % nh) : (int)(item / chunks);
+    const int ch = abandon ? (int)(item / nh) : (int)(item - (int64_t)s * chunks);
     if (ok && !ok[s]) continue;
+    if (abandon) {
+      // (one thread reads the pair, so the whole block takes one decision)
+      if (threadIdx.x == 0) {
+        const unsigned long long pv = __ldcg(prog + s);
+        s_skip = (long long)(unsigned)pv + ((long long)nP - (long long)(pv >> 32)) < (long long)cbar;
+      }
+      __syncthreads();
+      const bool skip = s_skip != 0;
+      __syncthreads();
+      if (skip) continue;
+    }
     Rigid12 T;
     T.load(pose + (size_t)s * 12);
-    const int i0 = ch * kClsChunk, i1 = min(nP, (ch + 1) * kClsChunk);
+    const int i0 = ch * kClsChunk, i1 = min(nv, (ch + 1) * kClsChunk);
     int cnt = 0, namb = 0;
     for (int r = i0; r < i1; r += kClsThreads) {
       const int i = r + threadIdx.x;
       bool in = false, amb = false;
       float x = 0.f, y = 0.f, z = 0.f;
       if (i < i1) {
-        T.apply(XP[i], x, y, z);
+        T.apply(XP[(size_t)i * stride], x, y, z);
         if (c.all_amb) {
           amb = true;
         } else {
@@ -218,8 +243,40 @@ __global__ void __launch_bounds__(kClsThreads, kClsMinBlocks) k_consensus_count(
       for (int k = 0; k < kClsThreads / 32; ++k) tc += s_cnt[k], ta += s_amb[k];
       if (tc) atomicAdd(&count[s], tc);
       if (kBounds && ta) atomicAdd(&amb_count[s], ta);
+      if (abandon) atomicAdd(prog + s, ((unsigned long long)(i1 - i0) << 32) | (unsigned)(tc + ta));
     }
     __syncthreads();
+  }
+}
+
+// After bounds with abandonment: amb[s] += the points of s left out, so that
+// IN + amb stays an upper bound of the count (below c0 for those left out).
+__global__ void k_bounds_finish(const unsigned long long *__restrict__ prog, const uint8_t *__restrict__ ok,
+                                const int *n_dev, int nP, int *__restrict__ amb) {
+  const int n = *n_dev;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    if (ok && !ok[k]) continue;
+    const int done = (int)(prog[k] >> 32);
+    if (done < nP) amb[k] += nP - done;
+  }
+}
+
+// out = the largest exact[k] over sel[k] (0 if none): a count some hypothesis
+// reaches, so no smaller upper bound can win.
+__global__ void __launch_bounds__(1024) k_sel_max(const int *__restrict__ exact, const uint8_t *__restrict__ sel,
+                                                  const int *n_dev, int *out) {
+  __shared__ int s_max[32];
+  const int n = *n_dev;
+  int mx = 0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    if (sel[k]) mx = max(mx, exact[k]);
+  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_max[w]);
+    *out = m;
   }
 }
 
@@ -360,18 +417,25 @@ cudaError_t launch_consensus_count(const float4 *XP, int nP, const ClsParams *cp
                                    const unsigned *near_bits, const GridParams *ge, const int *start_e,
                                    const float4 *Xe, const float *pose, const uint8_t *ok, const int *n_dev,
                                    int n_host, float eps, int *count, cudaStream_t s) {
-  LSR_LAUNCH(k_consensus_count<false><<<kSms * 8, kClsThreads, 0, s>>>(XP, nP, cp, in_bits, near_bits, ge, start_e, Xe,
-                                                                       pose, ok, n_dev, n_host, eps * eps, count,
-                                                                       nullptr));
+  LSR_LAUNCH(k_consensus_count<false><<<kSms * 8, kClsThreads, 0, s>>>(XP, nP, 1, cp, in_bits, near_bits, ge, start_e,
+                                                                       Xe, pose, ok, n_dev, n_host, eps * eps, count,
+                                                                       nullptr, nullptr, nullptr));
   return cudaGetLastError();
 }
 
-cudaError_t launch_consensus_bounds(const float4 *XP, int nP, const ClsParams *cp, const unsigned *in_bits,
-                                    const unsigned *near_bits, const float *pose, const uint8_t *ok, const int *n_dev,
-                                    int *in_count, int *amb_count, cudaStream_t s) {
-  LSR_LAUNCH(k_consensus_count<true><<<kSms * 8, kClsThreads, 0, s>>>(XP, nP, cp, in_bits, near_bits, nullptr, nullptr,
-                                                                      nullptr, pose, ok, n_dev, 0, 0.f, in_count,
-                                                                      amb_count));
+cudaError_t launch_consensus_bounds(const float4 *XP, int nP, int stride, const ClsParams *cp,
+                                    const unsigned *in_bits, const unsigned *near_bits, const float *pose,
+                                    const uint8_t *ok, const int *n_dev, int *in_count, int *amb_count,
+                                    const int *c0, unsigned long long *prog, cudaStream_t s) {
+  LSR_LAUNCH(k_consensus_count<true><<<kSms * 8, kClsThreads, 0, s>>>(XP, nP, stride, cp, in_bits, near_bits, nullptr,
+                                                                      nullptr, nullptr, pose, ok, n_dev, 0, 0.f,
+                                                                      in_count, amb_count, c0, prog));
+  if (c0) LSR_LAUNCH(k_bounds_finish<<<kSms * 2, 256, 0, s>>>(prog, ok, n_dev, nP, amb_count));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sel_max(const int *exact, const uint8_t *sel, const int *n_dev, int *out, cudaStream_t s) {
+  LSR_LAUNCH(k_sel_max<<<1, 1024, 0, s>>>(exact, sel, n_dev, out));
   return cudaGetLastError();
 }
 

@@ -583,11 +583,18 @@ cudaError_t launch_consensus_count(const float4 *XP, int nP, const ClsParams *cp
                                    const unsigned *near_bits, const GridParams *ge, const int *start_e,
                                    const float4 *Xe, const float *pose, const uint8_t *ok, const int *n_dev,
                                    int n_host, float eps, int *count, cudaStream_t s);
-// Bounds without exact tests: in_count = points in IN voxels (a lower bound
-// of the inlier count), amb_count = points in undecided voxels.
-cudaError_t launch_consensus_bounds(const float4 *XP, int nP, const ClsParams *cp, const unsigned *in_bits,
-                                    const unsigned *near_bits, const float *pose, const uint8_t *ok, const int *n_dev,
-                                    int *in_count, int *amb_count, cudaStream_t s);
+// Bounds without exact tests over the points XP[v * stride]: in_count =
+// points in IN voxels (a lower bound of the inlier count), amb_count = points
+// in undecided voxels. With c0 (device; a count some hypothesis reaches) and
+// prog (device, one zeroed 64-bit word per hypothesis): a hypothesis whose
+// upper bound falls below c0 part-way is left out, its remaining points added
+// to amb_count (stride must be 1).
+cudaError_t launch_consensus_bounds(const float4 *XP, int nP, int stride, const ClsParams *cp,
+                                    const unsigned *in_bits, const unsigned *near_bits, const float *pose,
+                                    const uint8_t *ok, const int *n_dev, int *in_count, int *amb_count,
+                                    const int *c0, unsigned long long *prog, cudaStream_t s);
+// out (device) = max over sel of exact.
+cudaError_t launch_sel_max(const int *exact, const uint8_t *sel, const int *n_dev, int *out, cudaStream_t s);
 // sel: the K ok hypotheses with the largest lo + extra (ties to the smaller id).
 cudaError_t launch_top_upper(const int *lo, const int *extra, const uint8_t *ok, const int *n_dev, int K,
                              uint8_t *sel, cudaStream_t s);
