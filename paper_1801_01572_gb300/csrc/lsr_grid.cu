@@ -390,7 +390,10 @@ static cudaError_t build_grid_impl(const void *src, int n, const GridParams *g, 
   LSR_CUDA_TRY(scan_exclusive(sc.counts, start, ncells_dev, cap_cells, sc.scan, s));
   LSR_CUDA_TRY(cudaMemsetAsync(sc.counts, 0, sizeof(int) * (size_t)cap_cells, s));
   LSR_LAUNCH(k_scatter<<<grid_blocks(n), 256, 0, s>>>(n, sc.slot, start, sc.counts, sc.tmp));
-  LSR_LAUNCH(k_cell_order<kF4><<<grid_blocks(cap_cells * 32, 256), 256, 0, s>>>(src, g, start, sc.tmp, out, inv_out));
+  // warps stride over the cells (most are empty: a block per cell would spend
+  // the kernel on scheduling blocks)
+  const int cells_warps = cap_cells < kSms * 16 * 8 ? cap_cells : kSms * 16 * 8;
+  LSR_LAUNCH(k_cell_order<kF4><<<grid_blocks(cells_warps * 32, 256), 256, 0, s>>>(src, g, start, sc.tmp, out, inv_out));
   return cudaGetLastError();
 }
 
