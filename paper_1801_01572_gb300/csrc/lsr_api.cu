@@ -769,11 +769,15 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
                launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose,
                                       L.sel, &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
                "consensus top");
+      TRY_CUDA(c, launch_sel_max(L.count2, L.sel, &L.st->n_surv, L.c0, s), "consensus bar");
     }
     TRY_CUDA(c, launch_reach_rest(L.count, L.amb, L.count2, L.sel, L.ok, &L.st->n_surv, L.rest, L.reach, s), "reach");
+    // the others that may reach c0, each given up on once it no longer can
+    TRY_CUDA(c, cudaMemsetAsync(L.prog, 0, sizeof(unsigned long long) * L.surv_cap, s), "memset count");
     TRY_CUDA(c,
-             launch_consensus_count(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose, L.rest,
-                                    &L.st->n_surv, 0, p.eps_inlier, L.count2, s),
+             launch_consensus_count_bar(Pc.Xn, nP, L.cls, L.in_bits, L.near_bits, Qc.ge, Qc.start_e, Qc.Xe, L.pose,
+                                        L.rest, &L.st->n_surv, p.eps_inlier, L.count2, L.c0, L.count, L.amb, L.prog,
+                                        s),
              "consensus reach");
     TRY_CUDA(c, launch_reach_mask(L.count2, nullptr, L.reach, &L.st->n_surv, L.tie, &L.st->n_tie, L.tie_list, s),
              "ties");

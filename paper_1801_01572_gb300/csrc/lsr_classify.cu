@@ -162,13 +162,20 @@ __device__ __forceinline__ bool warp_any_within(const GridParams &g, const int *
 // out: that upper bound only falls as chunks finish, so the hypothesis can
 // neither win nor tie. (k_bounds_finish then adds the points left out to amb,
 // keeping IN + amb an upper bound.)
+// Exact counts with c0 and the upper bounds ub_lo + ub_extra of a bounds pass:
+// items run chunk-major too, prog[s] accumulates (IN + undecided of the chunks
+// done << 32 | their exact count), and a chunk whose hypothesis has exact so
+// far + (its upper bound - the upper bound of the chunks done) < c0 is left
+// out: its count can no longer reach c0, so it can neither win nor tie (its
+// count stays partial, below c0).
 template <bool kBounds>
 __global__ void __launch_bounds__(kClsThreads, kClsMinBlocks) k_consensus_count(
     const float4 *__restrict__ XP, int nP, int stride, const ClsParams *__restrict__ cpp,
     const unsigned *__restrict__ in_bits, const unsigned *__restrict__ near_bits, const GridParams *__restrict__ gep,
     const int *__restrict__ start, const float4 *__restrict__ Xe, const float *__restrict__ pose,
     const uint8_t *__restrict__ ok, const int *n_dev, int n_host, float eps2, int *__restrict__ count,
-    int *__restrict__ amb_count, const int *c0, unsigned long long *prog) {
+    int *__restrict__ amb_count, const int *c0, unsigned long long *prog, const int *__restrict__ ub_lo,
+    const int *__restrict__ ub_extra) {
   const ClsParams c = *cpp;
   const GridParams g = kBounds ? GridParams{} : *gep;
   const int nh = n_dev ? *n_dev : n_host;
@@ -176,18 +183,27 @@ __global__ void __launch_bounds__(kClsThreads, kClsMinBlocks) k_consensus_count(
   const int chunks = (nv + kClsChunk - 1) / kClsChunk;
   const int64_t items = (int64_t)nh * chunks;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const bool abandon = kBounds && c0 != nullptr;
+  const bool abandon = c0 != nullptr;
   const int cbar = abandon ? *c0 : 0;
-  __shared__ int s_cnt[kClsThreads / 32], s_amb[kClsThreads / 32], s_skip;
+  __shared__ int s_cnt[kClsThreads / 32], s_amb[kClsThreads / 32], s_in[kClsThreads / 32], s_skip;
+  // item = major * inner + minor (s-major: (s, chunk); chunk-major: (chunk, s)),
+  // stepped by gridDim.x without a 64-bit division per item
+  const int64_t inner = abandon ? nh : chunks;
+  if (inner <= 0) return;
+  int64_t major = (int64_t)blockIdx.x / inner, minor = (int64_t)blockIdx.x % inner;
+  const int64_t step_major = (int64_t)gridDim.x / inner, step_minor = (int64_t)gridDim.x % inner;
   for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
-    const int s = abandon ? (int)(item % nh) : (int)(item / chunks);
-    const int ch = abandon ? (int)(item / nh) : (int)(item - (int64_t)s * chunks);
+    const int s = (int)(abandon ? minor : major), ch = (int)(abandon ? major : minor);
+    major += step_major, minor += step_minor;
+    if (minor >= inner) minor -= inner, ++major;
     if (ok && !ok[s]) continue;
     if (abandon) {
       // (one thread reads the pair, so the whole block takes one decision)
       if (threadIdx.x == 0) {
         const unsigned long long pv = __ldcg(prog + s);
-        s_skip = (long long)(unsigned)pv + ((long long)nP - (long long)(pv >> 32)) < (long long)cbar;
+        const long long lo32 = (long long)(unsigned)pv, hi32 = (long long)(pv >> 32);
+        s_skip = kBounds ? lo32 + ((long long)nP - hi32) < (long long)cbar
+                         : lo32 + ((long long)ub_lo[s] + (long long)ub_extra[s] - hi32) < (long long)cbar;
       }
       __syncthreads();
       const bool skip = s_skip != 0;
@@ -197,7 +213,7 @@ __global__ void __launch_bounds__(kClsThreads, kClsMinBlocks) k_consensus_count(
     Rigid12 T;
     T.load(pose + (size_t)s * 12);
     const int i0 = ch * kClsChunk, i1 = min(nv, (ch + 1) * kClsChunk);
-    int cnt = 0, namb = 0;
+    int cnt = 0, namb = 0, nin = 0;
     for (int r = i0; r < i1; r += kClsThreads) {
       const int i = r + threadIdx.x;
       bool in = false, amb = false;
@@ -220,10 +236,9 @@ __global__ void __launch_bounds__(kClsThreads, kClsMinBlocks) k_consensus_count(
         }
       }
       cnt += in;
-      if (kBounds) {
-        namb += amb;
-        continue;
-      }
+      nin += in;
+      namb += amb;
+      if (kBounds) continue;
       unsigned pend = __ballot_sync(0xffffffffu, amb);
       while (pend) {
         const int src = __ffs(pend) - 1;
@@ -235,15 +250,18 @@ __global__ void __launch_bounds__(kClsThreads, kClsMinBlocks) k_consensus_count(
       }
     }
     cnt = warp_sum(cnt);
-    if (kBounds) namb = warp_sum(namb);
-    if (lane == 0) s_cnt[w] = cnt, s_amb[w] = namb;
+    namb = warp_sum(namb);
+    if (!kBounds) nin = warp_sum(nin);
+    if (lane == 0) s_cnt[w] = cnt, s_amb[w] = namb, s_in[w] = nin;
     __syncthreads();
     if (threadIdx.x == 0) {
-      int tc = 0, ta = 0;
-      for (int k = 0; k < kClsThreads / 32; ++k) tc += s_cnt[k], ta += s_amb[k];
+      int tc = 0, ta = 0, ti = 0;
+      for (int k = 0; k < kClsThreads / 32; ++k) tc += s_cnt[k], ta += s_amb[k], ti += s_in[k];
       if (tc) atomicAdd(&count[s], tc);
       if (kBounds && ta) atomicAdd(&amb_count[s], ta);
-      if (abandon) atomicAdd(prog + s, ((unsigned long long)(i1 - i0) << 32) | (unsigned)(tc + ta));
+      if (abandon)
+        atomicAdd(prog + s, kBounds ? ((unsigned long long)(i1 - i0) << 32) | (unsigned)(tc + ta)
+                                    : ((unsigned long long)(ti + ta) << 32) | (unsigned)tc);
     }
     __syncthreads();
   }
@@ -419,7 +437,18 @@ cudaError_t launch_consensus_count(const float4 *XP, int nP, const ClsParams *cp
                                    int n_host, float eps, int *count, cudaStream_t s) {
   LSR_LAUNCH(k_consensus_count<false><<<kSms * 8, kClsThreads, 0, s>>>(XP, nP, 1, cp, in_bits, near_bits, ge, start_e,
                                                                        Xe, pose, ok, n_dev, n_host, eps * eps, count,
-                                                                       nullptr, nullptr, nullptr));
+                                                                       nullptr, nullptr, nullptr, nullptr, nullptr));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_consensus_count_bar(const float4 *XP, int nP, const ClsParams *cp, const unsigned *in_bits,
+                                       const unsigned *near_bits, const GridParams *ge, const int *start_e,
+                                       const float4 *Xe, const float *pose, const uint8_t *ok, const int *n_dev,
+                                       float eps, int *count, const int *c0, const int *ub_lo, const int *ub_extra,
+                                       unsigned long long *prog, cudaStream_t s) {
+  LSR_LAUNCH(k_consensus_count<false><<<kSms * 8, kClsThreads, 0, s>>>(XP, nP, 1, cp, in_bits, near_bits, ge, start_e,
+                                                                       Xe, pose, ok, n_dev, 0, eps * eps, count,
+                                                                       nullptr, c0, prog, ub_lo, ub_extra));
   return cudaGetLastError();
 }
 
@@ -429,7 +458,7 @@ cudaError_t launch_consensus_bounds(const float4 *XP, int nP, int stride, const 
                                     const int *c0, unsigned long long *prog, cudaStream_t s) {
   LSR_LAUNCH(k_consensus_count<true><<<kSms * 8, kClsThreads, 0, s>>>(XP, nP, stride, cp, in_bits, near_bits, nullptr,
                                                                       nullptr, nullptr, pose, ok, n_dev, 0, 0.f,
-                                                                      in_count, amb_count, c0, prog));
+                                                                      in_count, amb_count, c0, prog, nullptr, nullptr));
   if (c0) LSR_LAUNCH(k_bounds_finish<<<kSms * 2, 256, 0, s>>>(prog, ok, n_dev, nP, amb_count));
   return cudaGetLastError();
 }

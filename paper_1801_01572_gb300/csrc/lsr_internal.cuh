@@ -593,6 +593,15 @@ cudaError_t launch_consensus_bounds(const float4 *XP, int nP, int stride, const 
                                     const unsigned *in_bits, const unsigned *near_bits, const float *pose,
                                     const uint8_t *ok, const int *n_dev, int *in_count, int *amb_count,
                                     const int *c0, unsigned long long *prog, cudaStream_t s);
+// Exact counts (count += ...) that give up on a hypothesis as soon as its
+// count can no longer reach c0 (device), from the upper bounds ub_lo + ub_extra
+// of a bounds pass; prog: one zeroed 64-bit word per hypothesis. A count given
+// up on stays partial and below c0.
+cudaError_t launch_consensus_count_bar(const float4 *XP, int nP, const ClsParams *cp, const unsigned *in_bits,
+                                       const unsigned *near_bits, const GridParams *ge, const int *start_e,
+                                       const float4 *Xe, const float *pose, const uint8_t *ok, const int *n_dev,
+                                       float eps, int *count, const int *c0, const int *ub_lo, const int *ub_extra,
+                                       unsigned long long *prog, cudaStream_t s);
 // out (device) = max over sel of exact.
 cudaError_t launch_sel_max(const int *exact, const uint8_t *sel, const int *n_dev, int *out, cudaStream_t s);
 // sel: the K ok hypotheses with the largest lo + extra (ties to the smaller id).
