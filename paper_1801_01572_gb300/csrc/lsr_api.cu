@@ -610,7 +610,7 @@ cudaError_t build_cloud(const float *xyz, CloudLayout &c, float r_f, float r_n, 
 cudaError_t enqueue_refine(const float4 *XP, const float *P, int nP, const float *Q, int nQ, const float *boxQ,
                            const GridParams *ge, const int *start_e, const float4 *Xe, const LevelLayout &V, float eps,
                            float mu_scale, int iters, RansacState *st, double *part, int *seeds,
-                           const ScratchLayout &sc, cudaStream_t s) {
+                           const ScratchLayout &sc, cudaStream_t s, bool chain) {
   int L = V.levels;
   for (int l = 0; l < L; ++l) {
     float e = eps * (float)(1 << (L - 1 - l));
@@ -635,7 +635,7 @@ cudaError_t enqueue_refine(const float4 *XP, const float *P, int nP, const float
     LSR_CUDA_TRY(launch_refine_level_begin(st, s));
     LSR_CUDA_TRY(cudaMemsetAsync(seeds, 0xff, sizeof(int) * (size_t)np, s));  // no neighbour yet at this level
     for (int it = 0; it < iters; ++it)
-      LSR_CUDA_TRY(launch_refine_step(xp, np, 1, g, st0, xs, e, mu, iters, st, part, seeds, it > 0, s));
+      LSR_CUDA_TRY(launch_refine_step(xp, np, 1, g, st0, xs, e, mu, iters, st, part, seeds, chain && it > 0, s));
   }
   return cudaSuccess;
 }
@@ -663,8 +663,11 @@ int match_tile_for(const lsr_ctx *c, int nP) {
 }
 
 // The registration of one pair, enqueued on stream s. Results stay in L.st.
+// chain: refinement steps as programmatic dependent launches (one stream at a
+// time only: with pairs on concurrent streams, steps waiting for their
+// predecessor would hold SM slots the other streams need).
 int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q, const float *vpP, const float *vpQ,
-                 uint64_t pair_id, Timer &tm, cudaStream_t s) {
+                 uint64_t pair_id, Timer &tm, cudaStream_t s, bool chain) {
   const lsr_params &p = c->prm;
   int nP = L.P.n, nQ = L.Q.n;
   tm.mark();
@@ -793,7 +796,7 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
   float eps = p.eps_inlier;
   TRY_CUDA(c,
            enqueue_refine(Pc.X, P, nP, Q, nQ, Qc.box, Qc.ge, Qc.start_e, Qc.Xe, L.lv, eps, p.mu_scale, p.refine_iters,
-                          L.st, L.ref_part, L.seeds, L.sc, s),
+                          L.st, L.ref_part, L.seeds, L.sc, s, chain),
            "refine");
   TRY_CUDA(c, launch_final_pose(L.st, L.fpose, s), "final pose");
   TRY_CUDA(c, cudaMemsetAsync(L.fcount, 0, sizeof(int), s), "memset fcount");
@@ -955,7 +958,7 @@ int enqueue_batch(lsr_ctx *c, const BatchIn &b, const std::vector<std::vector<in
       Timer t{c};
       t.k = 9;  // no per-stage timing inside batches
       if ((rc = enqueue_pair(c, L, dP, dQ, b.vp ? b.vp + 6 * i : nullptr, b.vp ? b.vp + 6 * i + 3 : nullptr,
-                             b.pair0 + i, t, s)))
+                             b.pair0 + i, t, s, false)))
         return rc;
       TRY_CUDA(c, cudaMemcpyAsync(&c->st_host[i], L.st, sizeof(RansacState), cudaMemcpyDeviceToHost, s), "D2H");
       TRY_CUDA(c,
@@ -1373,7 +1376,7 @@ static int register_many(lsr_ctx *c, int32_t n, const float *const *P, const int
       Timer &t = (n == 1) ? tm : t1;
       if (n != 1) t.k = 9;  // per-stage timing only for single pairs
       if ((rc = enqueue_pair(c, L, dP, dQ, vp ? vp + 6 * i : nullptr, vp ? vp + 6 * i + 3 : nullptr, pair0 + i, t,
-                             c->stream)))
+                             c->stream, true)))
         return rc;
       TRY_CUDA(c, cudaMemcpyAsync(&c->st_host[i], L.st, sizeof(RansacState), cudaMemcpyDeviceToHost, c->stream),
                "D2H");
@@ -1888,7 +1891,7 @@ int lsr_stage_refine(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int
   TRY_CUDA(c, launch_refine_init(st, boxP, Td, s), "init");
   TRY_CUDA(c,
            enqueue_refine(XP, p, (int)nP, qsrc, (int)nQ, Cq.box, Cq.ge, Cq.start_e, Cq.Xe, V, eps, mu_scale, iters, st,
-                          part, seeds, S, s),
+                          part, seeds, S, s, true),
            "refine");
   RansacState h;
   TRY_CUDA(c, cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H");
