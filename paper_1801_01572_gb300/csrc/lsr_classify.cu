@@ -58,12 +58,12 @@ __global__ void k_cls_params(const float *box, float eps, ClsParams *cp) {
         if (!(e < 1e9f)) fits = false;
         n[d] = fits ? (long long)e + 2 : 0;
       }
-      long long wx = (n[0] + 31) / 32;
-      if (!fits || wx * n[1] * n[2] > kClsCapWords) continue;
+      const long long sx = (n[0] + 7) / 8, sy = (n[1] + 7) / 8, sz = (n[2] + 3) / 4;
+      if (!fits || sx * sy * sz * 8 > kClsCapWords) continue;
       c.ox = lo[0] - pad, c.oy = lo[1] - pad, c.oz = lo[2] - pad;
       c.h = h;
       c.inv_h = 1.f / h;
-      c.nx = (int)n[0], c.ny = (int)n[1], c.nz = (int)n[2], c.wx = (int)wx;
+      c.nx = (int)n[0], c.ny = (int)n[1], c.nz = (int)n[2], c.wx = (int)sx, c.wy = (int)sy;
       float rho = 0.8660254f * h * (1.f + 1e-6f);
       float r_in = eps - rho - c.m;
       c.r_in2 = r_in > 0.f ? r_in * r_in * (1.f - 1e-6f) : -1.f;
@@ -77,9 +77,10 @@ __global__ void k_cls_params(const float *box, float eps, ClsParams *cp) {
 }
 
 // One thread per (Q point, voxel plane dz around it), looping over the rows
-// dy: the NEAR bits of a row are set over an interval widened beyond the ball
-// (a superset), the IN bits voxel by voxel after an explicit distance check
-// (a subset).
+// dy in the aligned groups of four that share a brick row: the NEAR bits of a
+// row are set over an interval widened beyond the ball (a superset), the IN
+// bits voxel by voxel after an explicit distance check (a subset); one atomic
+// per brick and bit-set collects the four rows.
 __global__ void k_cls_splat(const float4 *__restrict__ XQ, int nQ, const ClsParams *__restrict__ cpp,
                             unsigned *__restrict__ in_bits, unsigned *__restrict__ near_bits) {
   const ClsParams c = *cpp;
@@ -98,31 +99,47 @@ __global__ void k_cls_splat(const float4 *__restrict__ XQ, int nQ, const ClsPara
     const float ez = fmaf((float)iz + 0.5f, c.h, c.oz) - q.z;
     if (ez * ez > rn2) continue;
     const int iy0 = (int)floorf(fy);
-    for (int dy = -c.R; dy <= c.R; ++dy) {
-      const int iy = iy0 + dy;
-      if (iy < 0 || iy >= c.ny) continue;
-      const float ey = fmaf((float)iy + 0.5f, c.h, c.oy) - q.y;
-      const float rem = rn2 - ey * ey - ez * ez;
-      if (rem < 0.f) continue;
-      const float half = sqrtf(rem) * (1.f + 1e-5f) + c.m;
-      int x0 = (int)floorf(fx - half * c.inv_h - 0.5f) - 1, x1 = (int)ceilf(fx + half * c.inv_h - 0.5f) + 1;
-      x0 = x0 < 0 ? 0 : x0;
-      x1 = x1 >= c.nx ? c.nx - 1 : x1;
-      if (x0 > x1) continue;
-      const size_t row = ((size_t)iz * c.ny + iy) * c.wx;
-      const float eyz = fmaf(ey, ey, ez * ez);
-      for (int w = x0 >> 5; w <= (x1 >> 5); ++w) {
-        const int b0 = max(x0, w * 32) - w * 32, b1 = min(x1, w * 32 + 31) - w * 32;
-        const unsigned near = (b1 == 31 ? 0xffffffffu : ((1u << (b1 + 1)) - 1u)) & ~((1u << b0) - 1u);
-        unsigned in = 0u;
-        if (c.r_in2 > 0.f && eyz <= c.r_in2) {
-          for (int b = b0; b <= b1; ++b) {
-            const float ex = fmaf((float)(w * 32 + b) + 0.5f, c.h, c.ox) - q.x;
-            if (fmaf(ex, ex, eyz) <= c.r_in2) in |= 1u << b;
+    const int ylo = max(iy0 - c.R, 0), yhi = min(iy0 + c.R, c.ny - 1);
+    const int zsh = (iz & 1) << 4;
+    for (int gy = ylo >> 2; gy <= (yhi >> 2); ++gy) {
+      int x0r[4], x1r[4];
+      float eyzr[4];
+      int xmin = 0x7fffffff, xmax = -1;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        x0r[r] = 1, x1r[r] = 0, eyzr[r] = 0.f;
+        const int iy = 4 * gy + r;
+        if (iy < ylo || iy > yhi) continue;
+        const float ey = fmaf((float)iy + 0.5f, c.h, c.oy) - q.y;
+        const float rem = rn2 - ey * ey - ez * ez;
+        if (rem < 0.f) continue;
+        const float half = sqrtf(rem) * (1.f + 1e-5f) + c.m;
+        int x0 = (int)floorf(fx - half * c.inv_h - 0.5f) - 1, x1 = (int)ceilf(fx + half * c.inv_h - 0.5f) + 1;
+        x0 = x0 < 0 ? 0 : x0;
+        x1 = x1 >= c.nx ? c.nx - 1 : x1;
+        if (x0 > x1) continue;
+        x0r[r] = x0, x1r[r] = x1, eyzr[r] = fmaf(ey, ey, ez * ez);
+        xmin = min(xmin, x0), xmax = max(xmax, x1);
+      }
+      if (xmax < 0) continue;
+      for (int bx = xmin >> 2; bx <= (xmax >> 2); ++bx) {
+        unsigned near = 0u, in = 0u;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int b0 = max(x0r[r], 4 * bx), b1 = min(x1r[r], 4 * bx + 3);
+          if (b0 > b1) continue;
+          near |= ((((1u << (b1 - 4 * bx + 1)) - 1u) & ~((1u << (b0 - 4 * bx)) - 1u)) << (4 * r));
+          if (c.r_in2 > 0.f && eyzr[r] <= c.r_in2) {
+            for (int b = b0; b <= b1; ++b) {
+              const float ex = fmaf((float)b + 0.5f, c.h, c.ox) - q.x;
+              if (fmaf(ex, ex, eyzr[r]) <= c.r_in2) in |= 1u << ((b - 4 * bx) + 4 * r);
+            }
           }
         }
-        atomicOr(near_bits + row + w, near);
-        if (in) atomicOr(in_bits + row + w, in);
+        if (!near) continue;
+        const size_t word = cls_word(c, 4 * bx, 4 * gy, iz);
+        atomicOr(near_bits + word, near << zsh);
+        if (in) atomicOr(in_bits + word, in << zsh);
       }
     }
   }
@@ -226,8 +243,8 @@ __global__ void __launch_bounds__(kClsThreads, kClsMinBlocks) k_consensus_count(
           float fx = (x - c.ox) * c.inv_h, fy = (y - c.oy) * c.inv_h, fz = (z - c.oz) * c.inv_h;
           if (fx >= 0.f && fx < (float)c.nx && fy >= 0.f && fy < (float)c.ny && fz >= 0.f && fz < (float)c.nz) {
             int ix = (int)fx, iy = (int)fy, iz = (int)fz;
-            size_t word = ((size_t)iz * c.ny + iy) * c.wx + (ix >> 5);
-            unsigned bit = 1u << (ix & 31);
+            size_t word = cls_word(c, ix, iy, iz);
+            unsigned bit = 1u << cls_bit(ix, iy, iz);
             if (__ldg(in_bits + word) & bit)
               in = true;
             else

@@ -571,10 +571,20 @@ cudaError_t launch_select(const int *surv, const int *count, const unsigned long
 // point of the voxel has a Q point closer than eps, bit NEAR clear only if no
 // point of the voxel has one. Consensus counts then need the exact eps-grid
 // test only for voxels with NEAR set and IN clear.
+// Bits are stored in bricks: a 32-bit word holds 4 x 4 x 2 voxels (x, y, z),
+// and eight consecutive words (a 32-byte sector) a 2 x 2 x 2 block of bricks,
+// 8 x 8 x 4 voxels, so the nearby points of a warp read few sectors. wx, wy:
+// sectors along x and y.
 struct ClsParams {
   float ox, oy, oz, h, inv_h, r_in2, r_near, m;
-  int nx, ny, nz, wx, R, all_amb;
+  int nx, ny, nz, wx, wy, R, all_amb;
 };
+__host__ __device__ inline size_t cls_word(const ClsParams &c, int x, int y, int z) {
+  return ((((size_t)(z >> 2) * c.wy + (y >> 3)) * c.wx + (x >> 3)) << 3) | (size_t)((((z >> 1) & 1) << 2) |
+                                                                                    (((y >> 2) & 1) << 1) |
+                                                                                    ((x >> 2) & 1));
+}
+__host__ __device__ inline int cls_bit(int x, int y, int z) { return (x & 3) | ((y & 3) << 2) | ((z & 1) << 4); }
 constexpr int kClsCapWords = 1 << 23;  // words per bit-set (32 MB)
 cudaError_t launch_cls_build(const float *boxQ, float eps, const float4 *XQ, int nQ, ClsParams *cp, unsigned *in_bits,
                              unsigned *near_bits, cudaStream_t s);
