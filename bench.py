@@ -708,7 +708,7 @@ def _kernel_work(name, nP, nQ, res, prm, terms):
                                                 "(Q: the database)"),
         ("k_prep_tiles", "hbm", (144.0 + 224.0) * N, "B", "144 B FPFH row in, 224 B BF16 operand row out"),
         ("k_hyp_count", "hbm", 36.0 * N, "B", "unique bytes of the sampled arrays (points, normals, nn)"),
-        ("k_hyp_write", "hbm", 36.0 * N + 4.0 * S, "B", "as k_hyp_count + 4 B per survivor id"),
+        ("k_hyp_gather", "hbm", 8.0 * S, "B", "4 B per survivor id in, 4 B out"),
         ("k_rigid_survivors", "hbm", 321.0 * S, "B", "per survivor 4 x (P, Q points and normals, nn) in, 49 B out"),
         ("k_consensus_count<true>", "hbm", 16.0 * nP + 56.0 * n_ok, "B",
          "16 B per P point, 56 B per normal-checked pose (L1/L2-resident table lookups dominate)"),

@@ -295,6 +295,7 @@ struct PairLayout {
   float *d1 = nullptr;
   int nb = 0;
   int *blk_cnt = nullptr, *blk_off = nullptr, *blk_scan = nullptr;
+  int *hyp_local = nullptr;  // per hypothesis block: its survivors, before they are placed
   int surv_cap = 0;
   int *surv = nullptr;
   float *pose = nullptr;
@@ -340,6 +341,7 @@ void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int leve
   L.blk_cnt = a.take<int>((size_t)L.nb + 2);
   L.blk_off = a.take<int>((size_t)L.nb + 2);
   L.blk_scan = a.take<int>((size_t)scan_scratch_ints(L.nb));
+  L.hyp_local = a.take<int>((size_t)hyp_local_ints(H));
   L.surv_cap = surv_cap_for(H);
   L.surv = a.take<int>(L.surv_cap);
   L.pose = a.take<float>((size_t)12 * L.surv_cap);
@@ -700,7 +702,8 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
   tm.mark();
   TRY_CUDA(c,
            launch_hypotheses(Pc.X, Pc.inv, Pc.N, nP, Qc.X, Qc.N, nQ, L.nn, nullptr, nullptr, p.n_hypotheses, p.seed,
-                             pair_id, p.tau, L.blk_cnt, L.blk_off, L.blk_scan, L.surv, L.surv_cap, L.st, s),
+                             pair_id, p.tau, L.blk_cnt, L.blk_off, L.blk_scan, L.surv, L.surv_cap, L.st,
+                             L.hyp_local, s),
            "hypotheses");
   tm.mark();
   // with the per-inlier normal check the sampled pairs are not checked (a
@@ -1696,6 +1699,7 @@ int lsr_stage_hypotheses(lsr_ctx *c, const float *P, int64_t nP, const float *Q,
     L.blk_cnt = a.take<int>((size_t)L.nb + 2);
     L.blk_off = a.take<int>((size_t)L.nb + 2);
     L.blk_scan = a.take<int>((size_t)scan_scratch_ints(L.nb));
+    L.hyp_local = a.take<int>((size_t)hyp_local_ints(H));
     L.surv_cap = (int)std::min<int64_t>(H, (int64_t)1 << 26);
     L.surv = a.take<int>(L.surv_cap);
     L.st = a.take<RansacState>(1);
@@ -1729,7 +1733,7 @@ int lsr_stage_hypotheses(lsr_ctx *c, const float *P, int64_t nP, const float *Q,
   LSR_LAUNCH(k_valid_normals<<<nblk(nQ), 256, 0, s>>>(vq, (int)nQ, NQ));
   TRY_CUDA(c,
            launch_hypotheses(XP, inv, NP, (int)nP, XQ, NQ, (int)nQ, dnn, nullptr, nullptr, H, seed, pair_id, tau,
-                             L.blk_cnt, L.blk_off, L.blk_scan, L.surv, L.surv_cap, L.st, s),
+                             L.blk_cnt, L.blk_off, L.blk_scan, L.surv, L.surv_cap, L.st, L.hyp_local, s),
            "hypotheses");
   RansacState st;
   TRY_CUDA(c, cudaMemcpyAsync(&st, L.st, sizeof(st), cudaMemcpyDeviceToHost, s), "D2H");

@@ -545,10 +545,15 @@ struct RansacState {
 };
 
 int hyp_blocks(int64_t H);
+// ints of the per-block survivor regions (local) for H hypotheses
+int64_t hyp_local_ints(int64_t H);
+// local: hyp_local_ints(H) ints of scratch; survivors are written there while
+// they are counted and placed in order after the scan.
 cudaError_t launch_hypotheses(const float4 *XP, const int *invP, const float4 *NP, int nP, const float4 *XQ,
                               const float4 *NQ, int nQ, const int *nn, const uint8_t *vP_ext, const uint8_t *vQ_ext,
                               int64_t H, uint64_t seed, uint64_t pair, float tau, int *block_counts, int *block_offsets,
-                              int *scan_scratch, int *surv, int surv_cap, RansacState *st, cudaStream_t s);
+                              int *scan_scratch, int *surv, int surv_cap, RansacState *st, int *local,
+                              cudaStream_t s);
 // Pose of each survivor from its 4 pairs + the normal check. pose: cap x 12 floats, ok: cap bytes.
 cudaError_t launch_rigid_survivors(const float4 *XP, const int *invP, const float4 *NP, int nP, const float4 *XQ,
                                    const float4 *NQ, const int *nn, const int *surv, const RansacState *st,

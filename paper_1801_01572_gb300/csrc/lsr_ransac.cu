@@ -94,59 +94,52 @@ constexpr int kHypPerBlock = kHypThreads * kHypIters;
 static __device__ int g_check_probe;
 #endif
 
-__global__ void __launch_bounds__(kHypThreads) k_hyp_count(HypIn in, int64_t H, int *block_counts) {
+// Survivors of each block of kHypPerBlock hypotheses: counted into
+// block_counts and written in increasing hypothesis id (warp ballots and a
+// block prefix per iteration) to the block's own region of local
+// (kHypPerBlock ints a block), so that one gather after the scan places them
+// in order without testing the hypotheses again.
+__global__ void __launch_bounds__(kHypThreads) k_hyp_count(HypIn in, int64_t H, int *block_counts, int *local) {
 #ifdef LSR_CHECKED
   if (blockIdx.x == 0 && threadIdx.x == 0 && g_check_probe) {
     g_check_probe = 0;
     (void)LSR_IN_BOUNDS(in.nP, in.nP, kSiteProbe);
   }
 #endif
-  int cnt = 0;
-  int64_t base = (int64_t)blockIdx.x * kHypPerBlock;
-  for (int it = 0; it < kHypIters; ++it) {
-    int64_t h = base + it * kHypThreads + threadIdx.x;
-    int ii[4], jj[4];
-    if (h < H && hyp_pass(in, (uint32_t)h, ii, jj)) ++cnt;
-  }
-  cnt = warp_sum(cnt);
-  __shared__ int sm[kHypThreads / 32];
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = cnt;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int w = 0; w < kHypThreads / 32; ++w) t += sm[w];
-    block_counts[blockIdx.x] = t;
-  }
-}
-
-// Ordered compaction: each block writes its survivors at its scanned offset,
-// in increasing hypothesis id (warp ballots + a block prefix per iteration).
-__global__ void __launch_bounds__(kHypThreads) k_hyp_write(HypIn in, int64_t H, const int *block_offsets, int *surv,
-                                                           int cap) {
   __shared__ int warp_cnt[kHypThreads / 32];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int *mine = local + (size_t)blockIdx.x * kHypPerBlock;
+  int pos = 0;
   int64_t base = (int64_t)blockIdx.x * kHypPerBlock;
-  int pos = block_offsets[blockIdx.x];
   for (int it = 0; it < kHypIters; ++it) {
     int64_t h = base + it * kHypThreads + threadIdx.x;
     int ii[4], jj[4];
-    bool ok = h < H && hyp_pass(in, (uint32_t)h, ii, jj);
-    unsigned m = __ballot_sync(0xffffffffu, ok);
+    const bool ok = h < H && hyp_pass(in, (uint32_t)h, ii, jj);
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
     if (lane == 0) warp_cnt[w] = __popc(m);
     __syncthreads();
     int before = 0, total = 0;
     for (int k = 0; k < kHypThreads / 32; ++k) {
-      int c = warp_cnt[k];
+      const int c = warp_cnt[k];
       before += (k < w) ? c : 0;
       total += c;
     }
-    if (ok) {
-      int slot = pos + before + __popc(m & ((1u << lane) - 1u));
-      if (slot < cap) surv[slot] = (int)h;
-    }
+    if (ok) mine[pos + before + __popc(m & ((1u << lane) - 1u))] = (int)h;
     pos += total;
     __syncthreads();
   }
+  if (threadIdx.x == 0) block_counts[blockIdx.x] = pos;
+}
+
+// Block b's survivors from its region of local to their scanned offset.
+__global__ void __launch_bounds__(kHypThreads) k_hyp_gather(const int *__restrict__ local,
+                                                            const int *__restrict__ block_counts,
+                                                            const int *__restrict__ block_offsets, int *surv,
+                                                            int cap) {
+  const int n = block_counts[blockIdx.x], off = block_offsets[blockIdx.x];
+  const int *mine = local + (size_t)blockIdx.x * kHypPerBlock;
+  for (int j = threadIdx.x; j < n; j += kHypThreads)
+    if (off + j < cap) surv[off + j] = mine[j];
 }
 
 __global__ void k_set_int(int *p, int v) {
@@ -464,17 +457,20 @@ __global__ void __launch_bounds__(1024) k_select(const int *surv, const int *cou
 
 int hyp_blocks(int64_t H) { return (int)lsr_div_up(H > 0 ? H : 1, kHypPerBlock); }
 
+int64_t hyp_local_ints(int64_t H) { return (int64_t)hyp_blocks(H) * kHypPerBlock; }
+
 cudaError_t launch_hypotheses(const float4 *XP, const int *invP, const float4 *NP, int nP, const float4 *XQ,
                               const float4 *NQ, int nQ, const int *nn, const uint8_t *, const uint8_t *, int64_t H,
                               uint64_t seed, uint64_t pair, float tau, int *block_counts, int *block_offsets,
-                              int *scan_scratch, int *surv, int surv_cap, RansacState *st, cudaStream_t s) {
+                              int *scan_scratch, int *surv, int surv_cap, RansacState *st, int *local,
+                              cudaStream_t s) {
   HypIn in{XP, invP, NP, nP, XQ, NQ, nQ, nn, seed, pair, tau * tau};
   int nb = hyp_blocks(H);
-  LSR_LAUNCH(k_hyp_count<<<nb, kHypThreads, 0, s>>>(in, H, block_counts));
+  LSR_LAUNCH(k_hyp_count<<<nb, kHypThreads, 0, s>>>(in, H, block_counts, local));
   int *nb_dev = block_counts + nb;  // one spare int after the counts holds nb
   LSR_LAUNCH(k_set_int<<<1, 32, 0, s>>>(nb_dev, nb));
   LSR_CUDA_TRY(scan_exclusive(block_counts, block_offsets, nb_dev, nb, scan_scratch, s));
-  LSR_LAUNCH(k_hyp_write<<<nb, kHypThreads, 0, s>>>(in, H, block_offsets, surv, surv_cap));
+  LSR_LAUNCH(k_hyp_gather<<<nb, kHypThreads, 0, s>>>(local, block_counts, block_offsets, surv, surv_cap));
   LSR_LAUNCH(k_hyp_finish<<<1, 32, 0, s>>>(block_offsets, nb, surv_cap, st));
   return cudaGetLastError();
 }
