@@ -348,7 +348,7 @@ void plan_pair(Arena &a, int nP, int nQ, bool stP, bool stQ, int64_t H, int leve
   L.ok = a.take<uint8_t>(L.surv_cap);
   L.count = a.take<int>(L.surv_cap);
   L.sum = a.take<unsigned long long>(L.surv_cap);
-  L.ref_part = a.take<double>((size_t)kRefAcc * refine_blocks(nP));
+  L.ref_part = a.take<double>((size_t)refine_partial_doubles());
   L.seeds = a.take<int>(nP);
   L.fpose = a.take<float>(12);
   L.fcount = a.take<int>(1);
@@ -614,6 +614,7 @@ cudaError_t enqueue_refine(const float4 *XP, const float *P, int nP, const float
                            float mu_scale, int iters, RansacState *st, double *part, int *seeds,
                            const ScratchLayout &sc, cudaStream_t s, bool chain) {
   int L = V.levels;
+  LSR_CUDA_TRY(refine_reset_tickets(part, s));
   for (int l = 0; l < L; ++l) {
     float e = eps * (float)(1 << (L - 1 - l));
     float mu = mu_scale * e * e;
@@ -1860,7 +1861,7 @@ int lsr_stage_refine(lsr_ctx *c, const float *P, int64_t nP, const float *Q, int
     plan_cloud(a, (int)nQ, true, false, true, Cq);
     plan_levels(a, (int)nP, (int)nQ, levels, V);
     plan_scratch(a, (int)nQ, Cq.cap_f, S);
-    part = a.take<double>((size_t)kRefAcc * refine_blocks((int)nP));
+    part = a.take<double>((size_t)refine_partial_doubles());
     Td = a.take<double>(16);
     st = a.take<RansacState>(1);
   };

@@ -636,6 +636,10 @@ constexpr double kFixScale = 1099511627776.0;  // 2^40
 
 // ----------------------------------------------------------------- refinement (lsr_refine.cu)
 int refine_blocks(int nP);
+// Doubles of a refinement partial-sum buffer (block and group sums, then the
+// group tickets), and the reset of its tickets (before a refinement's first step).
+int64_t refine_partial_doubles();
+cudaError_t refine_reset_tickets(double *partials, cudaStream_t s);
 // Starting pose (T_in, or the selected hypothesis already in st) and the first
 // linearisation centre (the centroid of P, boxP[8..10], moved by that pose).
 cudaError_t launch_refine_init(RansacState *st, const float *boxP, const double *T_in, cudaStream_t s);

@@ -19,6 +19,9 @@ namespace {
 constexpr int kRefThreads = 256;
 constexpr int kRefG = 4;   // lanes per nearest-neighbour query in refinement (4 measured fastest of 4/8/16)
 constexpr int kRefBlocksPerSm = 4;  // resident refinement blocks per SM (64 registers a thread; 3 measured slower)
+constexpr int kRefMaxBlocks = kSms * kRefBlocksPerSm;  // refine_blocks' cap
+constexpr int kRefGroup = 16;                           // blocks per first-level closing sum
+constexpr int kRefMaxGroups = (kRefMaxBlocks + kRefGroup - 1) / kRefGroup;
 constexpr int kObjG = 8;   // lanes per query in the objective
 // 21 (upper triangle of A) + 6 (b) + count + sum w + sum w x (3)
 constexpr int kNAcc = kRefAcc;
@@ -285,9 +288,33 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
       partials[(size_t)blockIdx.x * kNAcc + threadIdx.x] = t;
     }
   }
+  // Two-level close: the last block of each group of kRefGroup blocks sums its
+  // group's partials in block order; the last group to close sums the group
+  // sums and solves (fewer dependent loads on the closing path).
+  double *gpart = partials + (size_t)kRefMaxBlocks * kNAcc;
+  unsigned *gticket = reinterpret_cast<unsigned *>(gpart + (size_t)kRefMaxGroups * kNAcc);
+  const unsigned cgrp = blockIdx.x / kRefGroup, ng = (gridDim.x + kRefGroup - 1) / kRefGroup;
+  const unsigned g0 = cgrp * kRefGroup, gsz = min((unsigned)kRefGroup, gridDim.x - g0);
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) s_last = atomicAdd(gticket + cgrp, 1u) == gsz - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < kNSum) {
+    double v[kRefGroup];
+#pragma unroll
+    for (int u = 0; u < kRefGroup; ++u)
+      v[u] = (unsigned)u < gsz ? __ldcg(partials + (size_t)(g0 + u) * kNAcc + threadIdx.x) : 0.0;
+    double t = 0.0;
+#pragma unroll
+    for (int u = 0; u < kRefGroup; ++u) t += v[u];
+    gpart[(size_t)cgrp * kNAcc + threadIdx.x] = t;
+  }
+  if (threadIdx.x == 0) gticket[cgrp] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->ticket, 1u) == ng - 1;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
@@ -297,23 +324,14 @@ __global__ void __launch_bounds__(kRefThreads, kRefBlocksPerSm) k_refine_step(co
   else if (threadIdx.x == 15) ss.iters_done = __ldcg(&st->iters_done);
   else if (threadIdx.x == 16) ss.level_iters = __ldcg(&st->level_iters);
   {
-    // sum k = t % 17 over the blocks t / 17, t / 17 + 15, ..., then the 15
+    // sum k = t % 17 over the groups t / 17, t / 17 + 15, ..., then the 15
     // segments in order (a fixed order: the sums are deterministic)
     constexpr int kSeg = kRefThreads / kNSum;
     __shared__ double seg[kSeg][kNSum];
     const int k = threadIdx.x % kNSum, sg = threadIdx.x / kNSum;
     if (sg < kSeg) {
-      // eight loads in flight, added in block order (the same order as one at a time)
       double sum = 0.0;
-      unsigned b = sg;
-      for (; b + 7 * kSeg < gridDim.x; b += 8 * kSeg) {
-        double v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldcg(partials + (size_t)(b + u * kSeg) * kNAcc + k);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) sum += v[u];
-      }
-      for (; b < gridDim.x; b += kSeg) sum += __ldcg(partials + (size_t)b * kNAcc + k);
+      for (unsigned b = sg; b < ng; b += kSeg) sum += __ldcg(gpart + (size_t)b * kNAcc + k);
       seg[sg][k] = sum;
     }
     __syncthreads();
@@ -550,6 +568,13 @@ __global__ void k_objective_sum(const double *partials, int nblocks, double *out
 
 // One query per group of kRefG lanes per round; at most two blocks per SM so
 // that the launch-closing block sums few partials.
+int64_t refine_partial_doubles() { return (int64_t)kNAcc * (kRefMaxBlocks + kRefMaxGroups) + kRefMaxGroups; }
+
+cudaError_t refine_reset_tickets(double *partials, cudaStream_t s) {
+  return cudaMemsetAsync(partials + (size_t)kNAcc * (kRefMaxBlocks + kRefMaxGroups), 0,
+                         sizeof(unsigned) * kRefMaxGroups, s);
+}
+
 int refine_blocks(int nP) {
   int64_t b = lsr_div_up((int64_t)(nP > 0 ? nP : 1) * kRefG, kRefThreads);
   return (int)(b < 1 ? 1 : (b > kSms * kRefBlocksPerSm ? kSms * kRefBlocksPerSm : b));  // all blocks resident
