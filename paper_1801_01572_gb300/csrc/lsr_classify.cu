@@ -79,8 +79,8 @@ __global__ void k_cls_params(const float *box, float eps, ClsParams *cp) {
 // One thread per (Q point, voxel plane dz around it), looping over the rows
 // dy in the aligned groups of four that share a brick row: the NEAR bits of a
 // row are set over an interval widened beyond the ball (a superset), the IN
-// bits voxel by voxel after an explicit distance check (a subset); one atomic
-// per brick and bit-set collects the four rows.
+// bits over the interval of voxels that pass an explicit distance check (a
+// subset); one atomic per brick and bit-set collects the four rows.
 __global__ void k_cls_splat(const float4 *__restrict__ XQ, int nQ, const ClsParams *__restrict__ cpp,
                             unsigned *__restrict__ in_bits, unsigned *__restrict__ near_bits) {
   const ClsParams c = *cpp;
@@ -102,12 +102,11 @@ __global__ void k_cls_splat(const float4 *__restrict__ XQ, int nQ, const ClsPara
     const int ylo = max(iy0 - c.R, 0), yhi = min(iy0 + c.R, c.ny - 1);
     const int zsh = (iz & 1) << 4;
     for (int gy = ylo >> 2; gy <= (yhi >> 2); ++gy) {
-      int x0r[4], x1r[4];
-      float eyzr[4];
+      int x0r[4], x1r[4], inl[4], inr[4];
       int xmin = 0x7fffffff, xmax = -1;
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        x0r[r] = 1, x1r[r] = 0, eyzr[r] = 0.f;
+        x0r[r] = 1, x1r[r] = 0, inl[r] = 1, inr[r] = 0;
         const int iy = 4 * gy + r;
         if (iy < ylo || iy > yhi) continue;
         const float ey = fmaf((float)iy + 0.5f, c.h, c.oy) - q.y;
@@ -118,8 +117,26 @@ __global__ void k_cls_splat(const float4 *__restrict__ XQ, int nQ, const ClsPara
         x0 = x0 < 0 ? 0 : x0;
         x1 = x1 >= c.nx ? c.nx - 1 : x1;
         if (x0 > x1) continue;
-        x0r[r] = x0, x1r[r] = x1, eyzr[r] = fmaf(ey, ey, ez * ez);
+        x0r[r] = x0, x1r[r] = x1;
         xmin = min(xmin, x0), xmax = max(xmax, x1);
+        // IN voxels of the row: those passing the explicit test, an interval
+        // (ex grows with the voxel index, the test is monotone in |ex|): an
+        // estimate from the ball, each end then settled by the test itself
+        const float eyz = fmaf(ey, ey, ez * ez);
+        if (c.r_in2 > 0.f && eyz <= c.r_in2) {
+          auto pass = [&](int b) {
+            const float ex = fmaf((float)b + 0.5f, c.h, c.ox) - q.x;
+            return fmaf(ex, ex, eyz) <= c.r_in2;
+          };
+          const float rr = sqrtf(c.r_in2 - eyz);
+          int lo = (int)floorf((q.x - rr - c.ox) * c.inv_h - 0.5f), hi = (int)ceilf((q.x + rr - c.ox) * c.inv_h - 0.5f);
+          lo = max(lo, x0), hi = min(hi, x1);
+          while (lo <= hi && !pass(lo)) ++lo;
+          while (lo <= hi && lo > x0 && pass(lo - 1)) --lo;
+          while (hi >= lo && !pass(hi)) --hi;
+          while (hi >= lo && hi < x1 && pass(hi + 1)) ++hi;
+          inl[r] = lo, inr[r] = hi;
+        }
       }
       if (xmax < 0) continue;
       for (int bx = xmin >> 2; bx <= (xmax >> 2); ++bx) {
@@ -129,12 +146,8 @@ __global__ void k_cls_splat(const float4 *__restrict__ XQ, int nQ, const ClsPara
           const int b0 = max(x0r[r], 4 * bx), b1 = min(x1r[r], 4 * bx + 3);
           if (b0 > b1) continue;
           near |= ((((1u << (b1 - 4 * bx + 1)) - 1u) & ~((1u << (b0 - 4 * bx)) - 1u)) << (4 * r));
-          if (c.r_in2 > 0.f && eyzr[r] <= c.r_in2) {
-            for (int b = b0; b <= b1; ++b) {
-              const float ex = fmaf((float)b + 0.5f, c.h, c.ox) - q.x;
-              if (fmaf(ex, ex, eyzr[r]) <= c.r_in2) in |= 1u << ((b - 4 * bx) + 4 * r);
-            }
-          }
+          const int i0 = max(inl[r], 4 * bx), i1 = min(inr[r], 4 * bx + 3);
+          if (i0 <= i1) in |= ((((1u << (i1 - 4 * bx + 1)) - 1u) & ~((1u << (i0 - 4 * bx)) - 1u)) << (4 * r));
         }
         if (!near) continue;
         const size_t word = cls_word(c, 4 * bx, 4 * gy, iz);
