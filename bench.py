@@ -654,7 +654,7 @@ def roofline(info):
     # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one full-size
     # launch of this kernel on the room pair, from an ncu capture (the two
     # descriptor tables read once; the tiles' rows re-read from L2)
-    traffic = 47621120 + 561920 if (nP, nQ) == (150000, 150000) else None
+    traffic = 47619328 + 600832 if (nP, nQ) == (150000, 150000) else None
     return {"kernel": "k_match_win", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak, "traffic": traffic, "launch_ms": avg, "launches_timed": n,
             "algorithmic_bytes": 144.0 * (nP + nQ) + 8.0 * nP,
