@@ -159,24 +159,64 @@ __global__ void k_cls_splat(const float4 *__restrict__ XQ, int nQ, const ClsPara
 }
 
 // Whether a Q point lies closer than eps to (x, y, z): all 32 lanes walk the
-// eps-grid candidates of the same query and stop at the first hit.
+// eps-grid candidates of the same query and stop at the first hit. Without
+// wrapped storage the nine row ranges (the x-adjacent cells of a row are one
+// range) are read at once, one row per lane, and then scanned in the order of
+// grid_ranges, 32 candidates at a time.
 __device__ __forceinline__ bool warp_any_within(const GridParams &g, const int *__restrict__ start,
                                                 const float4 *__restrict__ Xe, float x, float y, float z,
                                                 float eps2) {
   const int lane = threadIdx.x & 31;
-  bool hit = false;
-  grid_ranges(g, start, x, y, z, [&](int b, int e) {
-    if (hit) return;
-    for (int base = b; base < e; base += 32) {
-      int t = base + lane;
-      bool h = t < e && dist2(Xe[t], x, y, z) < eps2;
-      if (__any_sync(0xffffffffu, h)) {
-        hit = true;
-        return;
+  const bool wrapped = (g.wx != g.nx) | (g.wy != g.ny) | (g.wz != g.nz);
+  if (wrapped) {
+    bool hit = false;
+    grid_ranges(g, start, x, y, z, [&](int b, int e) {
+      if (hit) return;
+      for (int base = b; base < e; base += 32) {
+        int t = base + lane;
+        bool h = t < e && dist2(Xe[t], x, y, z) < eps2;
+        if (__any_sync(0xffffffffu, h)) {
+          hit = true;
+          return;
+        }
+      }
+    });
+    return hit;
+  }
+  const float fx = (x - g.ox) * g.inv_cell, fy = (y - g.oy) * g.inv_cell, fz = (z - g.oz) * g.inv_cell;
+  if (!(fx >= -1.f && fx < (float)g.nx + 1.f && fy >= -1.f && fy < (float)g.ny + 1.f && fz >= -1.f &&
+        fz < (float)g.nz + 1.f))
+    return false;
+  const int cx = __float2int_rd(fx), cy = __float2int_rd(fy), cz = __float2int_rd(fz);
+  const int x0 = cx - 1 < 0 ? 0 : cx - 1, x1 = cx + 1 > g.nx - 1 ? g.nx - 1 : cx + 1;
+  if (x0 > x1) return false;
+  if (g.nbmask && cx >= 0 && cx < g.nx && cy >= 0 && cy < g.ny && cz >= 0 && cz < g.nz) {
+    const int slot = (cz * g.wy + cy) * g.wx + cx;
+    if (!((__ldg(g.nbmask + (slot >> 5)) >> (slot & 31)) & 1u)) return false;
+  }
+  int b = 0, e = 0;
+  if (lane < 9) {
+    const int iz = cz + lane / 3 - 1, iy = cy + lane % 3 - 1;
+    if (iz >= 0 && iz < g.nz && iy >= 0 && iy < g.ny) {
+      const int row = (iz * g.wy + iy) * g.wx;
+      if (LSR_IN_BOUNDS(row + x1 + 1, g.ncells + 1, kSiteGridRow) && LSR_IN_BOUNDS(row + x0, g.ncells + 1, kSiteGridRow)) {
+        b = start[row + x0], e = start[row + x1 + 1];
+#ifdef LSR_CHECKED
+        if (e > b && (!LSR_IN_BOUNDS(e - 1, g.npts, kSiteGridPoint) || !LSR_IN_BOUNDS(b, g.npts, kSiteGridPoint)))
+          b = e = 0;
+#endif
       }
     }
-  });
-  return hit;
+  }
+  for (int k = 0; k < 9; ++k) {
+    const int bk = __shfl_sync(0xffffffffu, b, k), ek = __shfl_sync(0xffffffffu, e, k);
+    for (int base = bk; base < ek; base += 32) {
+      const int t = base + lane;
+      const bool h = t < ek && dist2(Xe[t], x, y, z) < eps2;
+      if (__any_sync(0xffffffffu, h)) return true;
+    }
+  }
+  return false;
 }
 
 // One thread block per (hypothesis, chunk of P), as the exact kernel; a lane
