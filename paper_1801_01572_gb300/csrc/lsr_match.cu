@@ -14,29 +14,32 @@
 // lambda |a - b|^2 with lambda bounding the Gram matrix's largest
 // eigenvalue, so a database row whose projections lie farther than
 // sqrt(lambda * best) from the query's, in the plane of the two axes, cannot
-// be nearer than the current best. One block takes 128 consecutive queries
-// of that order (one query slab: close in p1 and in p2) and visits database
-// slabs outward from its own p1, alternately to the right and to the left,
-// and in each slab its tiles outward from its own p2; a side ends once no
-// query of the block can find a row there. The FP32 rounding of the
-// projections (a bound per row from the error of an fma chain), of the axes
-// and of the distance itself is taken into the test by directed rounding,
-// so a row, a tile or a slab is left out only when every computed distance
-// in it exceeds the query's computed best: the nearest row and its ties are
-// always scanned, and ties go to the smaller original index whatever the
-// scan order. Each ordering is a counting sort into as many buckets as rows
-// over the projections' range; the order within a bucket is arbitrary, so
-// the bounds that end a side are made monotone by suffix minima (right) and
-// prefix maxima (left).
+// be nearer than the current best. A warp takes 32 consecutive queries of
+// that order (one query slab: close in p1 and in p2) and one database slab of
+// their window at a time (persistent warps, work items taken breadth-first:
+// every group's nearest slabs before any group's farther ones); in a slab it
+// visits the tiles outward from its own p2, and a side ends once no query of
+// the warp can find a row there. Best distances are shared between the warps
+// of a group by a 64-bit atomic minimum of (distance, index). The FP32
+// rounding of the projections (a bound per row from the error of an fma
+// chain), of the axes and of the distance itself is taken into the test by
+// directed rounding, so a row, a tile or a slab is left out only when every
+// computed distance in it exceeds a distance some row has: the nearest row
+// and its ties are always scanned, and ties go to the smaller original index
+// whatever the scan order. Each ordering is a counting sort into as many
+// buckets as rows over the projections' range; the order within a bucket is
+// arbitrary, so the bounds that end a side are made monotone by suffix minima
+// (right) and prefix maxima (left).
 //
-// Inside the window each thread keeps one query descriptor in registers;
-// tiles of database descriptors are staged in shared memory in desc_order
-// and read as broadcasts. The partial sums only grow (t^2 >= 0 and rounding
-// is monotone), so a row whose partial sum already exceeds every query's
+// Inside the window each thread keeps one query descriptor in registers and
+// reads the database rows (bins in desc_order, chunk-major per tile) through
+// L1 as warp broadcasts. The partial sums only grow (t^2 >= 0 and rounding is
+// monotone), so a row whose partial sum already exceeds every query's
 // current best in the warp can neither win nor tie: after 4, 8, 12, 16 and
 // 24 terms the warp tests that and skips the rest of the row (same result).
 // The 32 queries of a warp have nearly equal projections, and their best
-// distances fall together.
+// distances fall together. The listed-rows scan of the tensor-core path's
+// exact fallback (k_match_rows_chunked) stages tiles in shared memory.
 #include <float.h>
 #include <stddef.h>
 
