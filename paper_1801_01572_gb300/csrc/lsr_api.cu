@@ -684,8 +684,8 @@ int enqueue_pair(lsr_ctx *c, const PairLayout &L, const float *P, const float *Q
   TRY_CUDA(c, launch_normals(Pc.X, nP, Pc.gn, Pc.start_n, Pc.Xn, p.r_normal, vp_p, Pc.N, nullptr, s), "normals P");
   TRY_CUDA(c, launch_normals(Qc.X, nQ, Qc.gn, Qc.start_n, Qc.Xn, p.r_normal, vp_q, Qc.N, nullptr, s), "normals Q");
   tm.mark();
-  TRY_CUDA(c, launch_spfh(Pc.X, Pc.N, nP, Pc.gf, Pc.start_f, p.r_feature, Pc.S, nullptr, s), "spfh P");
-  TRY_CUDA(c, launch_spfh(Qc.X, Qc.N, nQ, Qc.gf, Qc.start_f, p.r_feature, Qc.S, nullptr, s), "spfh Q");
+  TRY_CUDA(c, launch_spfh(Pc.X, Pc.N, nP, Pc.gf, Pc.start_f, p.r_feature, Pc.S, nullptr, Pc.F, s), "spfh P");
+  TRY_CUDA(c, launch_spfh(Qc.X, Qc.N, nQ, Qc.gf, Qc.start_f, p.r_feature, Qc.S, nullptr, Qc.F, s), "spfh Q");
   TRY_CUDA(c, launch_fpfh(Pc.X, Pc.N, Pc.S, nP, Pc.gf, Pc.start_f, p.r_feature, Pc.F, s), "fpfh P");
   TRY_CUDA(c, launch_fpfh(Qc.X, Qc.N, Qc.S, nQ, Qc.gf, Qc.start_f, p.r_feature, Qc.F, s), "fpfh Q");
   tm.mark();
@@ -1548,7 +1548,7 @@ static int stage_desc_common(lsr_ctx *c, const float *P, const float *normals, c
   TRY_CUDA(c, build_cloud(src, C, r, r, r, false, false, S, s), "grids");
   LSR_LAUNCH(k_gather_normals<<<nblk(n), 256, 0, s>>>(nrm, C.X, (int)n, C.N));
   if (!spfh_in) {
-    TRY_CUDA(c, launch_spfh(C.X, C.N, (int)n, C.gf, C.start_f, r, C.S, kk, s), "spfh");
+    TRY_CUDA(c, launch_spfh(C.X, C.N, (int)n, C.gf, C.start_f, r, C.S, kk, C.F, s), "spfh");
     LSR_LAUNCH(k_scatter_rows<<<nblk(n * kD), 256, 0, s>>>(C.S, C.X, (int)n, o));
     if (k_out) LSR_LAUNCH(k_scatter_int<<<nblk(n), 256, 0, s>>>(kk, C.X, (int)n, ko));
   } else {

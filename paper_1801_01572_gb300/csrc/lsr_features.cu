@@ -118,11 +118,14 @@ __global__ void __launch_bounds__(kThreads) k_normals(const float4 *__restrict__
 // keep p); u = n_s, v = (u x e)/|u x e|, w = u x v; alpha = v.n_t, phi = u.e,
 // theta = atan2(w.n_t, u.n_t). A pair without a frame (|u x e|^2 < 1e-12) is
 // skipped. Bins: 11 per feature over [-1, 1], [-1, 1], [-pi, pi].
+// tie (optional): set when the two angles are equal, the one case in which
+// the features of (q, p) differ from those of (p, q).
 __device__ __forceinline__ bool pair_bins(float3 p, float3 np, float3 q, float3 nq, float d2, int &ba, int &bp,
-                                          int &bt) {
+                                          int &bt, bool *tie = nullptr) {
   float id = rsqrtf(d2);
   float3 e = make_float3((q.x - p.x) * id, (q.y - p.y) * id, (q.z - p.z) * id);
   float cs = fabsf(dot3(np, e)), ct = fabsf(dot3(nq, e));
+  if (tie) *tie = cs == ct;
   float3 u = np, nt = nq;
   if (cs < ct) {
     u = nq, nt = np;
@@ -141,12 +144,20 @@ __device__ __forceinline__ bool pair_bins(float3 p, float3 np, float3 q, float3 
   return true;
 }
 
-// SPFH: every lane counts its pairs into a private column of a per-warp
-// [bin][lane] histogram in shared memory (row stride 33 words, so both the
-// lane-private updates and the per-bin column sums avoid bank conflicts).
+// SPFH, each unordered pair once: the pair (p, t) with t after p in the grid
+// order is evaluated by p's warp only. Its features are those of (t, p) as well
+// (the source is the point whose normal makes the smaller angle with the
+// line, whichever is named first; only an exact tie of the two angles makes
+// them differ, and then (t, p) is evaluated too), so they count for both: into
+// p's private per-lane column of a per-warp [bin][lane] histogram in shared
+// memory (row stride 33 words, so both the lane-private updates and the
+// per-bin column sums avoid bank conflicts), and into t's counts H (n x 36
+// ints, bins then the pair count in column 33) by atomic adds. p's own sums
+// are added to H at the end of its warp; k_spfh_finish divides. Counts are
+// integers, so the result does not depend on the order of the adds.
 __global__ void __launch_bounds__(kThreads) k_spfh(const float4 *__restrict__ X, const float4 *__restrict__ N, int n,
                                                    const GridParams *gfp, const int *__restrict__ start, float r2,
-                                                   float *__restrict__ S, int *__restrict__ kout) {
+                                                   int *__restrict__ H) {
   __shared__ int hist[kWarps][kD * 33];
   const GridParams g = *gfp;
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -160,8 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_spfh(const float4 *__restrict__ X,
     if (np4.w >= 0.f) {
       float3 np = f3(np4);
       grid_ranges(g, start, p.x, p.y, p.z, [&](int b, int e) {
-        for (int t = b + lane; t < e; t += 32) {
-          if (t == i) continue;
+        for (int t = (b > i + 1 ? b : i + 1) + lane; t < e; t += 32) {
           float4 q4 = X[t];
           float dx = q4.x - p.x, dy = q4.y - p.y, dz = q4.z - p.z;
           float d2 = dx * dx + dy * dy + dz * dz;
@@ -169,30 +179,55 @@ __global__ void __launch_bounds__(kThreads) k_spfh(const float4 *__restrict__ X,
           float4 nq4 = N[t];
           if (nq4.w < 0.f) continue;
           int ba, bp, bt;
-          if (!pair_bins(p, np, f3(q4), f3(nq4), d2, ba, bp, bt)) continue;
-          h[ba * 33 + lane] += 1;
-          h[(kNB + bp) * 33 + lane] += 1;
-          h[(2 * kNB + bt) * 33 + lane] += 1;
-          ++kk;
+          bool tie = false;
+          const bool ok = pair_bins(p, np, f3(q4), f3(nq4), d2, ba, bp, bt, &tie);
+          if (ok) {
+            h[ba * 33 + lane] += 1;
+            h[(kNB + bp) * 33 + lane] += 1;
+            h[(2 * kNB + bt) * 33 + lane] += 1;
+            ++kk;
+          }
+          int *ht = H + (size_t)t * kDS;
+          if (tie) {
+            // t's own view of the pair
+            const float qx = -dx, qy = -dy, qz = -dz;
+            if (!pair_bins(f3(q4), f3(nq4), p, np, qx * qx + qy * qy + qz * qz, ba, bp, bt)) continue;
+          } else if (!ok) {
+            continue;
+          }
+          atomicAdd(ht + ba, 1);
+          atomicAdd(ht + kNB + bp, 1);
+          atomicAdd(ht + 2 * kNB + bt, 1);
+          atomicAdd(ht + kD, 1);
         }
       });
     }
     kk = warp_sum(kk);
     __syncwarp();
-    float inv = kk > 0 ? 1.f / (float)kk : 0.f;
-    float *row = S + (size_t)i * kDS;
+    int *hi = H + (size_t)i * kDS;
     int c = 0;
     for (int l = 0; l < 32; ++l) c += h[lane * 33 + l];
-    row[lane] = (float)c * inv;
+    if (c) atomicAdd(hi + lane, c);
     if (lane == 0) {
       int c2 = 0;
       for (int l = 0; l < 32; ++l) c2 += h[32 * 33 + l];
-      row[32] = (float)c2 * inv;
+      if (c2) atomicAdd(hi + 32, c2);
+      if (kk) atomicAdd(hi + kD, kk);
     }
-    if (lane >= 1 && lane <= 3) row[32 + lane] = 0.f;
-    if (lane == 0 && kout) kout[i] = kk;
     __syncwarp();
   }
+}
+
+// S = H / (pair count), one thread per (point, column); zeros in the padding;
+// kout (optional): the pair counts.
+__global__ void k_spfh_finish(const int *__restrict__ H, int n, float *__restrict__ S, int *__restrict__ kout) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * kDS) return;
+  const int i = (int)(t / kDS), b = (int)(t - (int64_t)i * kDS);
+  const int kk = H[(size_t)i * kDS + kD];
+  const float inv = kk > 0 ? 1.f / (float)kk : 0.f;
+  S[t] = b < kD ? (float)H[t] * inv : 0.f;
+  if (b == 0 && kout) kout[i] = kk;
 }
 
 // FPFH: every lane accumulates the distance-weighted SPFH rows of its
@@ -283,8 +318,11 @@ cudaError_t launch_normals(const float4 *X, int n, const GridParams *gn, const i
 }
 
 cudaError_t launch_spfh(const float4 *X, const float4 *N, int n, const GridParams *gf, const int *start_f, float r,
-                        float *spfh, int *k, cudaStream_t s) {
-  LSR_LAUNCH(k_spfh<<<blocks_for_warps(n), kThreads, 0, s>>>(X, N, n, gf, start_f, r * r, spfh, k));
+                        float *spfh, int *k, void *scratch, cudaStream_t s) {
+  int *H = static_cast<int *>(scratch);
+  LSR_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(int) * kDS * (size_t)n, s));
+  LSR_LAUNCH(k_spfh<<<blocks_for_warps(n), kThreads, 0, s>>>(X, N, n, gf, start_f, r * r, H));
+  LSR_LAUNCH(k_spfh_finish<<<(int)lsr_div_up((int64_t)n * kDS, 256), 256, 0, s>>>(H, n, spfh, k));
   return cudaGetLastError();
 }
 

@@ -478,8 +478,10 @@ cudaError_t scan_exclusive(const int *in, int *out, const int *n_dev, int cap, i
 // ----------------------------------------------------------------- features (lsr_features.cu)
 cudaError_t launch_normals(const float4 *X, int n, const GridParams *gn, const int *start_n, const float4 *Xn,
                            float r, float3 vp, float4 *N, int *count, cudaStream_t s);
+// scratch: n x 36 ints of device memory (the pair counts; the FPFH output
+// buffer may serve, as SPFH comes first).
 cudaError_t launch_spfh(const float4 *X, const float4 *N, int n, const GridParams *gf, const int *start_f, float r,
-                        float *spfh, int *k, cudaStream_t s);
+                        float *spfh, int *k, void *scratch, cudaStream_t s);
 cudaError_t launch_fpfh(const float4 *X, const float4 *N, const float *spfh, int n, const GridParams *gf,
                         const int *start_f, float r, float *fpfh, cudaStream_t s);
 
