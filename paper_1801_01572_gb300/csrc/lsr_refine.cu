@@ -8,7 +8,8 @@
 // weighted centroid of the current correspondences, so that FP32 stays exact
 // to the micrometre whatever the clouds' offset): FP32 per-thread and
 // per-block sums, then one launch-closing block sums the block partials in
-// FP64 in a fixed order, solves the 6x6 system by Cholesky and updates the
+// FP64 in a fixed order, solves the 6x6 system (Schur complement of its
+// translation block, then a 3x3 adjugate) and updates the
 // FP64 pose -- one kernel launch per iteration, no host round trip.
 #include "lsr_internal.cuh"
 
@@ -44,24 +45,6 @@ __device__ __forceinline__ void block_reduce_to(float (&v)[N], double *out) {
   }
 }
 
-__device__ void exp_so3(const double w[3], double R[9]) {
-  double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2], th = sqrt(th2);
-  double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
-  double a, b;
-  if (th < 1e-6) {
-    a = 1.0 - th2 / 6.0;
-    b = 0.5 - th2 / 24.0;
-  } else {
-    a = sin(th) / th;
-    b = (1.0 - cos(th)) / th2;
-  }
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) {
-      double k2 = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
-      R[3 * r + c] = (r == c ? 1.0 : 0.0) + a * K[3 * r + c] + b * k2;
-    }
-}
-
 // Per-step sums of the IRLS normal equations. With J = [-[xc]_x | I] (xc the
 // moved point about the step's centre c), w the line-process weight of eq. (4)
 // and r the residual, J^T W J and J^T W r need only these 17 sums:
@@ -93,71 +76,72 @@ __device__ __forceinline__ double recip_pos(double x) {
   return r;
 }
 
-// Solve A d = -b in FP64 from the summed partials (LDL^T: one reciprocal per
-// pivot, no square root) and left-multiply the pose by the update about the
-// centre c used for this step: x' = Exp(d_w)(x - c) + c + d_v. The next step's
-// centre is the weighted centroid of this step's correspondences. Reads the
-// state from ss, writes it to st. Run by warps 0 and 1 of the closing block
-// (every thread of the block reaches its barrier): each value is computed by
-// one lane with the same operations in the same order as a single thread
-// would, so the result does not depend on the split. LDL^T: for pivot j,
-// lanes j..5 form v_i = A_ij - sum_k L_ik L_jk D_k at once (v_j is D_j);
-// the substitutions and Exp's two coefficients run on lane 0, the twelve
-// pose entries on lanes 0..11; the next centre on warp 1 meanwhile, and the
-// step length and the state on warp 1 after the pose.
+// Solve A d = -b in FP64 from the summed partials and left-multiply the pose
+// by the update about the centre c used for this step: x' = Exp(d_w)(x - c) +
+// c + d_v. The next step's centre is the weighted centroid of this step's
+// correspondences. Reads the state from ss, writes it to st.
+//
+// With J = [-[xc]_x | I], A = [[M, [s]_x], [[s]_x^T, sw I]] where M is the
+// rotation block, s = sum w xc and sw = sum w. The translation block is a
+// multiple of I, so it is eliminated in closed form (Schur complement):
+//   M' = M - [s]_x [s]_x^T / sw = M - (|s|^2 I - s s^T) / sw,
+//   M' d_w = -b_w + (s x b_v) / sw,   d_v = -(b_v - s x d_w) / sw,
+// and the 3x3 system is solved by its adjugate (one reciprocal). A is
+// positive definite iff sw > 0 and M' is (its leading minors m00, m00 m11 -
+// m01^2 and det M' positive). This is the same solution as a 6x6 Cholesky in
+// exact arithmetic with a far shorter chain of dependent FP64 operations,
+// whose latency is long on this part.
+//
+// Run by warps 0 and 1 of the closing block (every thread of the block
+// reaches its barrier): the solve, the Exp coefficients and the twelve pose
+// entries (lanes 0..11) on warp 0; the next centre on warp 1 meanwhile, and
+// the step length and the state on warp 1 after the pose. Each value is
+// computed by one lane in a fixed order, so the result is deterministic.
 __device__ void refine_solve(const double *S, const StepState &ss, RansacState *st, int max_iters, double tol) {
-  __shared__ double sA[6][6], sL[6][6], sD[6], siD[6], sd[6], scoef[2], scn[3];
+  __shared__ double sd[6], scoef[2], scn[3];
   __shared__ int spd;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double *xx = S + 5, *b = S + 11;
   const double sw = S[1], sx0 = S[2], sx1 = S[3], sx2 = S[4];
-  bool pd = S[0] >= 3.0;
-  if (warp == 0 && lane == 0) {
-    const double A[6][6] = {{xx[3] + xx[5], -xx[1], -xx[2], 0.0, -sx2, sx1},
-                            {0.0, xx[0] + xx[5], -xx[4], sx2, 0.0, -sx0},
-                            {0.0, 0.0, xx[0] + xx[3], -sx1, sx0, 0.0},
-                            {0.0, 0.0, 0.0, sw, 0.0, 0.0},
-                            {0.0, 0.0, 0.0, 0.0, sw, 0.0},
-                            {0.0, 0.0, 0.0, 0.0, 0.0, sw}};
-    for (int i = 0; i < 6; ++i)
-      for (int j = 0; j < 6; ++j) sA[i][j] = j >= i ? A[i][j] : A[j][i];
-  } else if (warp == 1 && lane == 0 && sw > 0.0) {
+  bool pd = S[0] >= 3.0 && sw > 0.0;
+  if (warp == 1 && lane == 0 && sw > 0.0) {
     const double iw = recip_pos(sw);
     const double *c = ss.center;
     scn[0] = c[0] + sx0 * iw, scn[1] = c[1] + sx1 * iw, scn[2] = c[2] + sx2 * iw;
   }
   if (warp == 0) {
-    __syncwarp();
-    for (int j = 0; j < 6 && pd; ++j) {
-      double v = 0.0;
-      if (lane >= j && lane < 6) {
-        v = sA[lane][j];
-        for (int k = 0; k < j; ++k) v -= sL[lane][k] * sL[j][k] * sD[k];
+    if (lane == 0 && pd) {
+      const double iw = recip_pos(sw);
+      const double ss2 = sx0 * sx0 + sx1 * sx1 + sx2 * sx2;
+      // M' (symmetric; M from the weighted second moments of xc)
+      const double m00 = xx[3] + xx[5] - (ss2 - sx0 * sx0) * iw;
+      const double m11 = xx[0] + xx[5] - (ss2 - sx1 * sx1) * iw;
+      const double m22 = xx[0] + xx[3] - (ss2 - sx2 * sx2) * iw;
+      const double m01 = -xx[1] + sx0 * sx1 * iw;
+      const double m02 = -xx[2] + sx0 * sx2 * iw;
+      const double m12 = -xx[4] + sx1 * sx2 * iw;
+      // right-hand side -b_w + (s x b_v) / sw
+      const double r0 = -b[0] + (sx1 * b[5] - sx2 * b[4]) * iw;
+      const double r1 = -b[1] + (sx2 * b[3] - sx0 * b[5]) * iw;
+      const double r2 = -b[2] + (sx0 * b[4] - sx1 * b[3]) * iw;
+      // adjugate (cofactors) and determinant
+      const double c00 = m11 * m22 - m12 * m12, c01 = m02 * m12 - m01 * m22, c02 = m01 * m12 - m02 * m11;
+      const double c11 = m00 * m22 - m02 * m02, c12 = m01 * m02 - m00 * m12, c22 = m00 * m11 - m01 * m01;
+      const double det = m00 * c00 + m01 * c01 + m02 * c02;
+      pd = m00 > 0.0 && c22 > 0.0 && det > 0.0;
+      if (pd) {
+        const double idet = recip_pos(det);
+        const double w0 = (c00 * r0 + c01 * r1 + c02 * r2) * idet;
+        const double w1 = (c01 * r0 + c11 * r1 + c12 * r2) * idet;
+        const double w2 = (c02 * r0 + c12 * r1 + c22 * r2) * idet;
+        sd[0] = w0, sd[1] = w1, sd[2] = w2;
+        // d_v = -(b_v - s x d_w) / sw
+        sd[3] = -(b[3] - (sx1 * w2 - sx2 * w1)) * iw;
+        sd[4] = -(b[4] - (sx2 * w0 - sx0 * w2)) * iw;
+        sd[5] = -(b[5] - (sx0 * w1 - sx1 * w0)) * iw;
       }
-      const double dj = __shfl_sync(0xffffffffu, v, j);
-      if (!(dj > 0.0)) {
-        pd = false;
-        break;
-      }
-      const double idj = recip_pos(dj);
-      if (lane == j) sD[j] = dj, siD[j] = idj;
-      if (lane > j && lane < 6) sL[lane][j] = v * idj;
-      __syncwarp();
     }
-    if (pd && lane == 0) {
-      double y[6], d[6];
-      for (int i = 0; i < 6; ++i) {
-        double v = -b[i];
-        for (int k = 0; k < i; ++k) v -= sL[i][k] * y[k];
-        y[i] = v;
-      }
-      for (int i = 5; i >= 0; --i) {
-        double v = y[i] * siD[i];
-        for (int k = i + 1; k < 6; ++k) v -= sL[k][i] * d[k];
-        d[i] = v;
-      }
-      for (int i = 0; i < 6; ++i) sd[i] = d[i];
-    }
+    pd = __shfl_sync(0xffffffffu, pd, 0);
     __syncwarp();
     if (pd && lane == 0) {
       // Exp of the rotation part: the series of sin(t)/t and (1 - cos t)/t^2 to
