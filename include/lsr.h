@@ -6,7 +6,7 @@
  *
  * Given two fragments P and Q (float32 xyz, N x 3 row-major), the library
  * estimates T_QP (q ~ T p) with no initial pose: radius-PCA normals, FPFH
- * descriptors (Rusu et al. 2009, the descriptor of Alg. 1 line 2), the feature
+ * descriptors (Rusu et al. 2009, the descriptor of Alg. 1), the feature
  * pre-matching cache (Alg. 1, "Parallel FPFH feature pre-matching"), 4-point
  * hypotheses with polygon pre-rejection (Alg. 1, tau of Sec. IV), stream
  * compaction, consensus on a 3D grid (eq. (1)), selection, and a robust
@@ -229,7 +229,7 @@ LSR_API int lsr_register_batch(lsr_ctx *ctx, int32_t n, const float *const *P, c
  * stage can be checked on its own. Arrays are in the caller's point order.
  * ------------------------------------------------------------------------ */
 
-/* Normals (needed by FPFH, Alg. 1 line 2; radius of Sec. IV): eigenvector of
+/* Normals (needed by FPFH, Alg. 1; radius of Sec. IV): eigenvector of
  * the smallest eigenvalue of the covariance of the points within r (inclusive,
  * the point itself included), oriented toward vp; fewer than 3 neighbours give
  * a zero normal and curvature -1. normals: n x 3, count: n (neighbours),

@@ -341,7 +341,7 @@ static void jacobi3(const double A_in[9], double w[3], double V[9]) {
 void orc_eig3(const double A[9], double w[3], double V[9]) { jacobi3(A, w, V); }
 
 /* ------------------------------------------------------------------------ */
-/* Normals (needed by the FPFH of Alg. 1, line 2; radius r_n of Sec. IV).   */
+/* Normals (needed by the FPFH step of Alg. 1; radius r_n of Sec. IV).      */
 /* Reading: the paper does not state the method. The normal is the          */
 /* eigenvector of the smallest eigenvalue of the covariance of all points  */
 /* with ||q - p||^2 <= r^2 (p itself included), oriented so that            */
@@ -422,7 +422,7 @@ void orc_normals(const double *P, int64_t n, const double vp[3], double r, const
 
 /* ------------------------------------------------------------------------ */
 /* Point-pair features of FPFH (Rusu, Blodow, Beetz, ICRA 2009, cited by    */
-/* the paper as the descriptor of Alg. 1, line 2).                          */
+/* the paper as the descriptor of Alg. 1's FPFH step).                      */
 /* Source is the point whose normal makes the smaller angle with the line  */
 /* joining the two points (|n . e| larger; ties keep p as source).          */
 /* Darboux frame u = n_s, v = (u x e)/|u x e|, w = u x v, e = (p_t-p_s)/d.  */
@@ -1412,7 +1412,7 @@ int orc_register(const double *P, int64_t nP, const double *Q, int64_t nQ, const
   res->status = 1;
   res->best_h = -1;
   if (nP < 4 || nQ < 4) return -1;
-  /* Alg. 1 line 2: normals and FPFH of both clouds */
+  /* Alg. 1, FPFH step: normals and FPFH of both clouds */
   double *NP = malloc(sizeof(double) * 3 * nP), *NQ = malloc(sizeof(double) * 3 * nQ);
   double *cv = malloc(sizeof(double) * (nP > nQ ? nP : nQ)), *dg = malloc(sizeof(double) * 3 * (nP > nQ ? nP : nQ));
   int64_t *ct = malloc(sizeof(int64_t) * (nP > nQ ? nP : nQ));

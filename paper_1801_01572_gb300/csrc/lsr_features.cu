@@ -1,9 +1,10 @@
-// lsr_features.cu -- per-point normals, SPFH and FPFH (Algorithm 1, line 2:
-// "Compute FPFH features"; radii of Sec. IV).
+// lsr_features.cu -- per-point normals, SPFH and FPFH (Algorithm 1, the FPFH
+// computation; radii of Sec. IV).
 //
-// All three kernels are warp-per-point: the 32 lanes of a warp stride over the
+// Normals and SPFH are warp-per-point: the 32 lanes of a warp stride over the
 // contiguous sorted ranges of the neighbouring grid cells, so the neighbour
-// loads of a warp are coalesced and the work per point is split evenly.
+// loads of a warp are coalesced and the work per point is split evenly. FPFH
+// is lane-per-point over candidates staged in shared memory (see k_fpfh).
 #include <math_constants.h>
 
 #include "lsr_internal.cuh"
@@ -230,77 +231,171 @@ __global__ void k_spfh_finish(const int *__restrict__ H, int n, float *__restric
   if (b == 0 && kout) kout[i] = kk;
 }
 
-// FPFH: every lane accumulates the distance-weighted SPFH rows of its
-// neighbours in registers; the warp then sums the 33 bins through a [lane][bin]
-// shared-memory transpose, adds SPFH(p), and rescales each sub-histogram.
-__global__ void __launch_bounds__(kThreads) k_fpfh(const float4 *__restrict__ X, const float4 *__restrict__ N,
-                                                   const float *__restrict__ S, int n, const GridParams *gfp,
-                                                   const int *__restrict__ start, float r2, float *__restrict__ F) {
-  __shared__ float red[kWarps][32 * 33 + 33];
+// 16-byte global -> shared copy that completes asynchronously (cp.async).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// FPFH: one query per lane. A window of 32 consecutive points of the
+// cell-sorted array is taken by kFpParts warps of one block; the lanes whose
+// queries lie in the same grid cell (most of a window: a cell holds dozens of
+// points) walk that cell's 3 x 3 x 3 neighbourhood together, each warp the
+// rows of cells r with r % kFpParts equal to its part, 32 candidates at a
+// time: their positions, normal flags and SPFH rows (contiguous in the sorted
+// array) are copied to shared memory with coalesced asynchronous copies, then
+// every lane reads each candidate from there (a broadcast) and adds its row
+// weighted by 1/d when the candidate is its neighbour (0 < d <= r, not
+// itself, valid normal). A window spanning several cells walks once per
+// distinct cell. The parts' sums are then added in part order, SPFH(p) added
+// and each lane's three sub-histograms rescaled. Every sum runs in a fixed
+// order, so the result is deterministic.
+constexpr int kFpParts = 3;                      // warps per window
+constexpr int kFpWin = 2;                        // windows per block
+constexpr int kFpThreads = 32 * kFpParts * kFpWin;
+constexpr int kFpRowV = kDS / 4;                 // float4 per SPFH row
+// one staging buffer: 32 rows, 32 positions, 32 normal flags (float4 units)
+constexpr int kFpBufV = 32 * kFpRowV + 32 + 8;
+constexpr int kFpSmem = kFpParts * kFpWin * 2 * kFpBufV * 16;  // two buffers a warp
+static_assert(kFpRowV * 32 * 4 >= (kD + 1) * 32, "the staging buffer holds a part's sums");
+
+__global__ void __launch_bounds__(kFpThreads, 3) k_fpfh(const float4 *__restrict__ X, const float4 *__restrict__ N,
+                                                        const float *__restrict__ S, int n, const GridParams *gfp,
+                                                        const int *__restrict__ start, float r2,
+                                                        float *__restrict__ F) {
+  extern __shared__ float4 fp_smem[];
   const GridParams g = *gfp;
-  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  int warp = (blockIdx.x * kThreads + threadIdx.x) >> 5, nwarps = (gridDim.x * kThreads) >> 5;
-  float *sm = red[wl];
-  for (int i = warp; i < n; i += nwarps) {
-    float3 p = f3(X[i]);
-    bool valid = N[i].w >= 0.f;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int part = wl % kFpParts, wslot = wl / kFpParts;
+  float4 *const wbuf = fp_smem + (size_t)wl * 2 * kFpBufV;
+  // stage candidates c0 .. c0 + m - 1 into buffer bi
+  auto stage = [&](int c0, int m, int bi) {
+    float4 *bb = wbuf + bi * kFpBufV;
+    if (lane < m) {
+      cp_async16(bb + 32 * kFpRowV + lane, X + c0 + lane);
+      cp_async4(reinterpret_cast<float *>(bb + 32 * kFpRowV + 32) + lane, &N[c0 + lane].w);
+    }
+    const float4 *src = reinterpret_cast<const float4 *>(S + (size_t)c0 * kDS);
+#pragma unroll
+    for (int u = 0; u < kFpRowV; ++u) {
+      const int k = lane + 32 * u;
+      if (k < kFpRowV * m) cp_async16(bb + k, src + k);
+    }
+    cp_async_commit();
+  };
+  const int nwin = (n + 31) / 32;
+  // block-uniform trip count (the block meets at its barriers every window)
+  for (int wb = blockIdx.x * kFpWin; wb < nwin; wb += gridDim.x * kFpWin) {
+    const int i0 = (wb + wslot) * 32;
+    const int i = i0 + lane;
+    const bool in = i < n;
+    const float4 p4 = in ? X[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool valid = in && N[i].w >= 0.f;
+    // the cell as the grid walk computes it (the grouping key)
+    const int cx = __float2int_rd((p4.x - g.ox) * g.inv_cell), cy = __float2int_rd((p4.y - g.oy) * g.inv_cell),
+              cz = __float2int_rd((p4.z - g.oz) * g.inv_cell);
     float acc[kD];
 #pragma unroll
     for (int b = 0; b < kD; ++b) acc[b] = 0.f;
     int kk = 0;
-    if (valid) {
-      grid_ranges(g, start, p.x, p.y, p.z, [&](int b, int e) {
-        for (int t = b + lane; t < e; t += 32) {
-          if (t == i) continue;
-          float4 q4 = X[t];
-          float dx = q4.x - p.x, dy = q4.y - p.y, dz = q4.z - p.z;
-          float d2 = dx * dx + dy * dy + dz * dz;
-          if (d2 > r2 || d2 == 0.f) continue;
-          if (N[t].w < 0.f) continue;
-          float w = rsqrtf(d2);
-          const float4 *srow = reinterpret_cast<const float4 *>(S + (size_t)t * kDS);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            float4 v = srow[q];
-            acc[4 * q + 0] += w * v.x;
-            acc[4 * q + 1] += w * v.y;
-            acc[4 * q + 2] += w * v.z;
-            acc[4 * q + 3] += w * v.w;
+    unsigned todo = __ballot_sync(0xffffffffu, valid);
+    while (todo) {
+      const int lead = __ffs(todo) - 1;
+      const int lx = __shfl_sync(0xffffffffu, cx, lead), ly = __shfl_sync(0xffffffffu, cy, lead),
+                lz = __shfl_sync(0xffffffffu, cz, lead);
+      const bool mine = valid && cx == lx && cy == ly && cz == lz && ((todo >> lane) & 1u);
+      todo &= ~__ballot_sync(0xffffffffu, mine);
+      // the leader's position gives the cell's ranges (the same for every
+      // lane of the group and every part); every lane runs the uniform loop
+      const float px = __shfl_sync(0xffffffffu, p4.x, lead), py = __shfl_sync(0xffffffffu, p4.y, lead),
+                  pz = __shfl_sync(0xffffffffu, p4.z, lead);
+      int ri = 0;
+      grid_ranges(g, start, px, py, pz, [&](int b, int e) {
+        if (ri++ % kFpParts != part || b >= e) return;
+        stage(b, e - b < 32 ? e - b : 32, 0);
+        int bi = 0;
+#pragma unroll 1
+        for (int c0 = b; c0 < e; c0 += 32, bi ^= 1) {
+          const int m = e - c0 < 32 ? e - c0 : 32;
+          // the next chunk's copies run while this one is summed
+          if (c0 + 32 < e) {
+            stage(c0 + 32, e - c0 - 32 < 32 ? e - c0 - 32 : 32, bi ^ 1);
+            cp_async_wait_group<1>();
+          } else {
+            cp_async_wait_group<0>();
           }
-          acc[32] += w * S[(size_t)t * kDS + 32];
-          ++kk;
+          __syncwarp();
+          const float4 *rows = wbuf + bi * kFpBufV, *pos = rows + 32 * kFpRowV;
+          const float *nw = reinterpret_cast<const float *>(pos + 32);
+#pragma unroll 1
+          for (int j = 0; j < m; ++j) {
+            const float4 q4 = pos[j];
+            const float dx = q4.x - p4.x, dy = q4.y - p4.y, dz = q4.z - p4.z;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            const bool acc_t = mine && c0 + j != i && d2 <= r2 && d2 != 0.f && nw[j] >= 0.f;
+            if (!__any_sync(0xffffffffu, acc_t)) continue;
+            const float w = acc_t ? rsqrtf(d2) : 0.f;
+            kk += acc_t ? 1 : 0;
+            const float4 *rj = rows + kFpRowV * j;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float4 v = rj[q];
+              acc[4 * q + 0] += w * v.x;
+              acc[4 * q + 1] += w * v.y;
+              acc[4 * q + 2] += w * v.z;
+              acc[4 * q + 3] += w * v.w;
+            }
+            acc[32] += w * rj[8].x;
+          }
+          __syncwarp();  // this buffer is refilled two chunks on
         }
       });
     }
-    kk = warp_sum(kk);
+    // the parts' sums meet in the staging buffers ([bin][lane], then counts)
+    float *cb = reinterpret_cast<float *>(wbuf);
 #pragma unroll
-    for (int b = 0; b < kD; ++b) sm[lane * 33 + b] = acc[b];
-    __syncwarp();
-    float tot = 0.f, tot32 = 0.f;
-    for (int l = 0; l < 32; ++l) tot += sm[l * 33 + lane];
-    if (lane == 0)
-      for (int l = 0; l < 32; ++l) tot32 += sm[l * 33 + 32];
-    __syncwarp();
-    const float *srow_i = S + (size_t)i * kDS;
-    float ik = kk > 0 ? 1.f / (float)kk : 0.f;
-    float f = valid ? srow_i[lane] + tot * ik : 0.f;
-    float f32 = valid ? srow_i[32] + tot32 * ik : 0.f;
-    // sub-histogram sums: bins 0..10, 11..21, 22..32
-    float *fb = sm + 32 * 33;  // 33 spare words
-    fb[lane] = f;
-    if (lane == 0) fb[32] = f32;
-    __syncwarp();
-    int grp = lane / kNB;
-    float gs = 0.f;
-    for (int b = 0; b < kNB; ++b) gs += fb[grp * kNB + b];
-    float g2 = 0.f;
-    if (lane == 0)
-      for (int b = 0; b < kNB; ++b) g2 += fb[2 * kNB + b];
-    float *row = F + (size_t)i * kDS;
-    row[lane] = gs > 0.f ? f / gs : 0.f;
-    if (lane == 0) row[32] = g2 > 0.f ? f32 / g2 : 0.f;
-    if (lane >= 1 && lane <= 3) row[32 + lane] = 0.f;
-    __syncwarp();
+    for (int b = 0; b < kD; ++b) cb[b * 32 + lane] = acc[b];
+    cb[kD * 32 + lane] = __int_as_float(kk);
+    __syncthreads();
+    if (part == 0 && in) {
+      kk = 0;
+#pragma unroll
+      for (int b = 0; b < kD; ++b) acc[b] = 0.f;
+      for (int pp = 0; pp < kFpParts; ++pp) {
+        const float *ob = reinterpret_cast<const float *>(fp_smem + (size_t)(wslot * kFpParts + pp) * 2 * kFpBufV);
+#pragma unroll
+        for (int b = 0; b < kD; ++b) acc[b] += ob[b * 32 + lane];
+        kk += __float_as_int(ob[kD * 32 + lane]);
+      }
+      float f[kD];
+      const float ik = kk > 0 ? 1.f / (float)kk : 0.f;
+      const float *srow_i = S + (size_t)i * kDS;
+#pragma unroll
+      for (int b = 0; b < kD; ++b) f[b] = valid ? srow_i[b] + acc[b] * ik : 0.f;
+      // sub-histograms: bins 0..10, 11..21, 22..32
+      float gs[3];
+#pragma unroll
+      for (int h = 0; h < 3; ++h) {
+        float t = 0.f;
+#pragma unroll
+        for (int b = 0; b < kNB; ++b) t += f[h * kNB + b];
+        gs[h] = t;
+      }
+      float *row = F + (size_t)i * kDS;
+#pragma unroll
+      for (int b = 0; b < kD; ++b) row[b] = gs[b / kNB] > 0.f ? f[b] / gs[b / kNB] : 0.f;
+#pragma unroll
+      for (int b = kD; b < kDS; ++b) row[b] = 0.f;
+    }
+    __syncthreads();  // the buffers are reused by the next window
   }
 }
 
@@ -328,7 +423,11 @@ cudaError_t launch_spfh(const float4 *X, const float4 *N, int n, const GridParam
 
 cudaError_t launch_fpfh(const float4 *X, const float4 *N, const float *spfh, int n, const GridParams *gf,
                         const int *start_f, float r, float *fpfh, cudaStream_t s) {
-  LSR_LAUNCH(k_fpfh<<<blocks_for_warps(n), kThreads, 0, s>>>(X, N, spfh, n, gf, start_f, r * r, fpfh));
+  const int64_t nb = lsr_div_up(lsr_div_up(n > 0 ? n : 1, 32), kFpWin);
+  // dynamic shared memory above the default 48 KB
+  LSR_CUDA_TRY(cudaFuncSetAttribute(k_fpfh, cudaFuncAttributeMaxDynamicSharedMemorySize, kFpSmem));
+  LSR_LAUNCH(k_fpfh<<<(int)(nb < kSms * 64 ? nb : kSms * 64), kFpThreads, kFpSmem, s>>>(X, N, spfh, n, gf, start_f,
+                                                                                        r * r, fpfh));
   return cudaGetLastError();
 }
 
