@@ -248,24 +248,35 @@ __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.w
 // FPFH: one query per lane. A window of 32 consecutive points of the
 // cell-sorted array is taken by kFpParts warps of one block; the lanes whose
 // queries lie in the same grid cell (most of a window: a cell holds dozens of
-// points) walk that cell's 3 x 3 x 3 neighbourhood together, each warp the
-// rows of cells r with r % kFpParts equal to its part, 32 candidates at a
-// time: their positions, normal flags and SPFH rows (contiguous in the sorted
-// array) are copied to shared memory with coalesced asynchronous copies, then
-// every lane reads each candidate from there (a broadcast) and adds its row
-// weighted by 1/d when the candidate is its neighbour (0 < d <= r, not
-// itself, valid normal). A window spanning several cells walks once per
-// distinct cell. The parts' sums are then added in part order, SPFH(p) added
-// and each lane's three sub-histograms rescaled. Every sum runs in a fixed
-// order, so the result is deterministic.
+// points) walk that cell's 3 x 3 x 3 neighbourhood together. The cell's
+// candidate ranges are listed, cut into chunks of 32 candidates and dealt out
+// to the window's warps round robin; a warp copies its next chunk's positions,
+// normal flags and SPFH rows (contiguous in the sorted array) to shared memory
+// with coalesced asynchronous copies while it sums the current one, every lane
+// reading each candidate from there (a broadcast) and adding its row weighted
+// by 1/d when the candidate is its neighbour (0 < d <= r, not itself, valid
+// normal). A window spanning several cells walks once per distinct cell. The
+// parts' sums are then added in part order (the window's warps meet at a named
+// barrier of their own), SPFH(p) added and each lane's three sub-histograms
+// rescaled. Every sum runs in a fixed order, so the result is deterministic.
 constexpr int kFpParts = 3;                      // warps per window
 constexpr int kFpWin = 2;                        // windows per block
 constexpr int kFpThreads = 32 * kFpParts * kFpWin;
 constexpr int kFpRowV = kDS / 4;                 // float4 per SPFH row
 // one staging buffer: 32 rows, 32 positions, 32 normal flags (float4 units)
 constexpr int kFpBufV = 32 * kFpRowV + 32 + 8;
-constexpr int kFpSmem = kFpParts * kFpWin * 2 * kFpBufV * 16;  // two buffers a warp
+constexpr int kFpWarpV = 2 * kFpBufV + 14;    // two buffers and the range list (27 pairs) a warp
+constexpr int kFpSmem = kFpParts * kFpWin * kFpWarpV * 16;
 static_assert(kFpRowV * 32 * 4 >= (kD + 1) * 32, "the staging buffer holds a part's sums");
+
+// barrier of the kFpParts warps of one window (named barrier 1 + window slot)
+__device__ __forceinline__ void window_sync(int wslot) {
+  static_assert(kFpWin == 2, "one named barrier per window slot");
+  if (wslot == 0)
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kFpParts) : "memory");
+  else
+    asm volatile("bar.sync 2, %0;" ::"n"(32 * kFpParts) : "memory");
+}
 
 __global__ void __launch_bounds__(kFpThreads, 3) k_fpfh(const float4 *__restrict__ X, const float4 *__restrict__ N,
                                                         const float *__restrict__ S, int n, const GridParams *gfp,
@@ -275,7 +286,7 @@ __global__ void __launch_bounds__(kFpThreads, 3) k_fpfh(const float4 *__restrict
   const GridParams g = *gfp;
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int part = wl % kFpParts, wslot = wl / kFpParts;
-  float4 *const wbuf = fp_smem + (size_t)wl * 2 * kFpBufV;
+  float4 *const wbuf = fp_smem + (size_t)wl * kFpWarpV;
   // stage candidates c0 .. c0 + m - 1 into buffer bi
   auto stage = [&](int c0, int m, int bi) {
     float4 *bb = wbuf + bi * kFpBufV;
@@ -292,7 +303,8 @@ __global__ void __launch_bounds__(kFpThreads, 3) k_fpfh(const float4 *__restrict
     cp_async_commit();
   };
   const int nwin = (n + 31) / 32;
-  // block-uniform trip count (the block meets at its barriers every window)
+  // the window's warps meet at its barrier twice a window (the trip count is
+  // the same for the whole block)
   for (int wb = blockIdx.x * kFpWin; wb < nwin; wb += gridDim.x * kFpWin) {
     const int i0 = (wb + wslot) * 32;
     const int i = i0 + lane;
@@ -317,60 +329,91 @@ __global__ void __launch_bounds__(kFpThreads, 3) k_fpfh(const float4 *__restrict
       // lane of the group and every part); every lane runs the uniform loop
       const float px = __shfl_sync(0xffffffffu, p4.x, lead), py = __shfl_sync(0xffffffffu, p4.y, lead),
                   pz = __shfl_sync(0xffffffffu, p4.z, lead);
-      int ri = 0;
+      // the cell's candidate ranges, listed first (uniform), then dealt out
+      // to the window's warps 32 candidates at a time, round robin
+      int *rl = reinterpret_cast<int *>(wbuf + 2 * kFpBufV);
+      int nr = 0;
       grid_ranges(g, start, px, py, pz, [&](int b, int e) {
-        if (ri++ % kFpParts != part || b >= e) return;
-        stage(b, e - b < 32 ? e - b : 32, 0);
-        int bi = 0;
-#pragma unroll 1
-        for (int c0 = b; c0 < e; c0 += 32, bi ^= 1) {
-          const int m = e - c0 < 32 ? e - c0 : 32;
-          // the next chunk's copies run while this one is summed
-          if (c0 + 32 < e) {
-            stage(c0 + 32, e - c0 - 32 < 32 ? e - c0 - 32 : 32, bi ^ 1);
-            cp_async_wait_group<1>();
-          } else {
-            cp_async_wait_group<0>();
-          }
-          __syncwarp();
-          const float4 *rows = wbuf + bi * kFpBufV, *pos = rows + 32 * kFpRowV;
-          const float *nw = reinterpret_cast<const float *>(pos + 32);
-#pragma unroll 1
-          for (int j = 0; j < m; ++j) {
-            const float4 q4 = pos[j];
-            const float dx = q4.x - p4.x, dy = q4.y - p4.y, dz = q4.z - p4.z;
-            const float d2 = dx * dx + dy * dy + dz * dz;
-            const bool acc_t = mine && c0 + j != i && d2 <= r2 && d2 != 0.f && nw[j] >= 0.f;
-            if (!__any_sync(0xffffffffu, acc_t)) continue;
-            const float w = acc_t ? rsqrtf(d2) : 0.f;
-            kk += acc_t ? 1 : 0;
-            const float4 *rj = rows + kFpRowV * j;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const float4 v = rj[q];
-              acc[4 * q + 0] += w * v.x;
-              acc[4 * q + 1] += w * v.y;
-              acc[4 * q + 2] += w * v.z;
-              acc[4 * q + 3] += w * v.w;
-            }
-            acc[32] += w * rj[8].x;
-          }
-          __syncwarp();  // this buffer is refilled two chunks on
-        }
+        if (b >= e) return;
+        if (lane == 0) rl[2 * nr] = b, rl[2 * nr + 1] = e;
+        ++nr;
       });
+      __syncwarp();
+      // (r, k): chunk k of range r; advance past the ends of ranges
+      auto settle = [&](int &r, int &k) {
+        while (r < nr) {
+          const int nk = (rl[2 * r + 1] - rl[2 * r] + 31) >> 5;
+          if (k < nk) break;
+          k -= nk;
+          ++r;
+        }
+      };
+      auto chunk = [&](int r, int k, int &c0, int &m) {
+        c0 = rl[2 * r] + 32 * k;
+        m = rl[2 * r + 1] - c0 < 32 ? rl[2 * r + 1] - c0 : 32;
+      };
+      int r = 0, k = part;
+      settle(r, k);
+      int bi = 0;
+      if (r < nr) {
+        int c0, m;
+        chunk(r, k, c0, m);
+        stage(c0, m, 0);
+      }
+#pragma unroll 1
+      while (r < nr) {
+        int c0, m;
+        chunk(r, k, c0, m);
+        int rn = r, kn = k + kFpParts;
+        settle(rn, kn);
+        // the next chunk's copies run while this one is summed
+        if (rn < nr) {
+          int n0, nm;
+          chunk(rn, kn, n0, nm);
+          stage(n0, nm, bi ^ 1);
+          cp_async_wait_group<1>();
+        } else {
+          cp_async_wait_group<0>();
+        }
+        __syncwarp();
+        const float4 *rows = wbuf + bi * kFpBufV, *pos = rows + 32 * kFpRowV;
+        const float *nw = reinterpret_cast<const float *>(pos + 32);
+#pragma unroll 1
+        for (int j = 0; j < m; ++j) {
+          const float4 q4 = pos[j];
+          const float dx = q4.x - p4.x, dy = q4.y - p4.y, dz = q4.z - p4.z;
+          const float d2 = dx * dx + dy * dy + dz * dz;
+          const bool acc_t = mine && c0 + j != i && d2 <= r2 && d2 != 0.f && nw[j] >= 0.f;
+          if (!__any_sync(0xffffffffu, acc_t)) continue;
+          const float w = acc_t ? rsqrtf(d2) : 0.f;
+          kk += acc_t ? 1 : 0;
+          const float4 *rj = rows + kFpRowV * j;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 v = rj[q];
+            acc[4 * q + 0] += w * v.x;
+            acc[4 * q + 1] += w * v.y;
+            acc[4 * q + 2] += w * v.z;
+            acc[4 * q + 3] += w * v.w;
+          }
+          acc[32] += w * rj[8].x;
+        }
+        __syncwarp();  // this buffer is refilled two chunks on
+        r = rn, k = kn, bi ^= 1;
+      }
     }
     // the parts' sums meet in the staging buffers ([bin][lane], then counts)
     float *cb = reinterpret_cast<float *>(wbuf);
 #pragma unroll
     for (int b = 0; b < kD; ++b) cb[b * 32 + lane] = acc[b];
     cb[kD * 32 + lane] = __int_as_float(kk);
-    __syncthreads();
+    window_sync(wslot);
     if (part == 0 && in) {
       kk = 0;
 #pragma unroll
       for (int b = 0; b < kD; ++b) acc[b] = 0.f;
       for (int pp = 0; pp < kFpParts; ++pp) {
-        const float *ob = reinterpret_cast<const float *>(fp_smem + (size_t)(wslot * kFpParts + pp) * 2 * kFpBufV);
+        const float *ob = reinterpret_cast<const float *>(fp_smem + (size_t)(wslot * kFpParts + pp) * kFpWarpV);
 #pragma unroll
         for (int b = 0; b < kD; ++b) acc[b] += ob[b * 32 + lane];
         kk += __float_as_int(ob[kD * 32 + lane]);
@@ -395,7 +438,7 @@ __global__ void __launch_bounds__(kFpThreads, 3) k_fpfh(const float4 *__restrict
 #pragma unroll
       for (int b = kD; b < kDS; ++b) row[b] = 0.f;
     }
-    __syncthreads();  // the buffers are reused by the next window
+    window_sync(wslot);  // the buffers are reused by the next window
   }
 }
 
