@@ -194,3 +194,24 @@ def test_tc_register_pair_identical(ctx, precision):
     assert np.array_equal(r16.T, r32.T)
     assert r16.inliers == r32.inliers and r16.survivors == r32.survivors
     assert r16.match_fallbacks >= 0
+
+
+@gpu
+@pytest.mark.parametrize("tile", [1, 2])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_tc_tile_shapes_equal_fp32(tile, precision):
+    """Both tile shapes (128 or 256 queries per unit) return the FP32
+    matcher's indices and distance bits, with ragged query units and database
+    tiles, an odd number of 128-row tiles and a single row."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1801_01572_gb300 as lsr
+    with lsr.Context(0, match_tile=tile) as c:
+        for nP, nQ in [(1, 1), (255, 129), (257, 257), (130, 385), (1000, 3001), (3000, 1000)]:
+            rng = np.random.default_rng(nP + 17 * nQ + 1000 * tile)
+            A, B = fpfh_like(nP, rng), fpfh_like(nQ, rng)
+            nn32, d32, _ = c.stage_match(A, B, precision=0)
+            nn, d, _ = c.stage_match(A, B, precision=precision)
+            assert np.array_equal(nn, nn32), (nP, nQ)
+            assert np.array_equal(d.view(np.uint32), d32.view(np.uint32)), (nP, nQ)
