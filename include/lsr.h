@@ -305,9 +305,9 @@ LSR_API int lsr_stage_consensus(lsr_ctx *ctx, const float *P, int64_t nP, const 
  *    on cuda_stream (NULL: the legacy default stream), and the call
  *    synchronises that stream before returning;
  *  - the first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it: make that first call before any
- *    stream capture; the cached address does not survive a reset of the
- *    device (cudaDeviceReset), after which the call must not be used;
+ *    (cudaGetSymbolAddress) and caches it; the cached address does not
+ *    survive a reset of the device (cudaDeviceReset), after which the call
+ *    must not be used;
  *  - every call on a device shares the array, which keeps the previous call's
  *    contents (the call clears what must start at zero): calls that overlap
  *    on the GPU (other streams, other host threads) race and must not be

@@ -14,8 +14,9 @@
 // cannot use the array's name as a device address: on the first call on each
 // device the entry point asks the runtime for the array's device address
 // (cudaGetSymbolAddress, with that device current) and caches it; every later
-// call on that device reuses the cached address. Because that first call
-// performs this set-up, it should be made before any stream capture begins.
+// call on that device reuses the cached address. The cached address does not
+// survive a reset of the device. Every call synchronises its stream before
+// returning.
 #include <cuda_runtime.h>
 #include <string.h>
 
