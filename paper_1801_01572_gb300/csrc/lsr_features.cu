@@ -155,15 +155,24 @@ __device__ __forceinline__ bool pair_bins(float3 p, float3 np, float3 q, float3 
 // per-bin column sums avoid bank conflicts), and into t's counts H (n x 36
 // ints, bins then the pair count in column 33) by atomic adds. p's own sums
 // are added to H at the end of its warp; k_spfh_finish divides. Counts are
-// integers, so the result does not depend on the order of the adds.
+// integers, so the result does not depend on the order of the adds. The
+// lanes test 32 candidates at a time against r; those within it are queued in
+// shared memory and their pair features evaluated 32 at a time, a lane each,
+// so that the feature arithmetic runs on full warps.
 __global__ void __launch_bounds__(kThreads) k_spfh(const float4 *__restrict__ X, const float4 *__restrict__ N, int n,
                                                    const GridParams *gfp, const int *__restrict__ start, float r2,
                                                    int *__restrict__ H) {
   __shared__ int hist[kWarps][kD * 33];
+  // candidates within r, queued until 32 can be evaluated at once (a lane
+  // each), so that the pair features run on full warps
+  __shared__ int qt_s[kWarps][64];
+  __shared__ float qd_s[kWarps][64];
   const GridParams g = *gfp;
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   int warp = (blockIdx.x * kThreads + threadIdx.x) >> 5, nwarps = (gridDim.x * kThreads) >> 5;
   int *h = hist[wl];
+  int *qt = qt_s[wl];
+  float *qd = qd_s[wl];
   for (int i = warp; i < n; i += nwarps) {
     for (int b = 0; b < kD; ++b) h[b * 33 + lane] = 0;
     float3 p = f3(X[i]);
@@ -171,37 +180,72 @@ __global__ void __launch_bounds__(kThreads) k_spfh(const float4 *__restrict__ X,
     int kk = 0;
     if (np4.w >= 0.f) {
       float3 np = f3(np4);
+      // the pair (p, t) for the queued candidate of this lane (m lanes)
+      auto evaluate = [&](int m) {
+        if (lane >= m) return;
+        const int t = qt[lane];
+        const float d2 = qd[lane];
+        const float4 q4 = X[t];
+        const float4 nq4 = N[t];
+        if (nq4.w < 0.f) return;
+        const float dx = q4.x - p.x, dy = q4.y - p.y, dz = q4.z - p.z;
+        int ba, bp, bt;
+        bool tie = false;
+        const bool ok = pair_bins(p, np, f3(q4), f3(nq4), d2, ba, bp, bt, &tie);
+        if (ok) {
+          h[ba * 33 + lane] += 1;
+          h[(kNB + bp) * 33 + lane] += 1;
+          h[(2 * kNB + bt) * 33 + lane] += 1;
+          ++kk;
+        }
+        int *ht = H + (size_t)t * kDS;
+        if (tie) {
+          // t's own view of the pair
+          const float qx = -dx, qy = -dy, qz = -dz;
+          if (!pair_bins(f3(q4), f3(nq4), p, np, qx * qx + qy * qy + qz * qz, ba, bp, bt)) return;
+        } else if (!ok) {
+          return;
+        }
+        atomicAdd(ht + ba, 1);
+        atomicAdd(ht + kNB + bp, 1);
+        atomicAdd(ht + 2 * kNB + bt, 1);
+        atomicAdd(ht + kD, 1);
+      };
+      int cnt = 0;  // queued candidates (the same on every lane)
       grid_ranges(g, start, p.x, p.y, p.z, [&](int b, int e) {
-        for (int t = (b > i + 1 ? b : i + 1) + lane; t < e; t += 32) {
-          float4 q4 = X[t];
-          float dx = q4.x - p.x, dy = q4.y - p.y, dz = q4.z - p.z;
-          float d2 = dx * dx + dy * dy + dz * dz;
-          if (d2 > r2 || d2 == 0.f) continue;
-          float4 nq4 = N[t];
-          if (nq4.w < 0.f) continue;
-          int ba, bp, bt;
-          bool tie = false;
-          const bool ok = pair_bins(p, np, f3(q4), f3(nq4), d2, ba, bp, bt, &tie);
-          if (ok) {
-            h[ba * 33 + lane] += 1;
-            h[(kNB + bp) * 33 + lane] += 1;
-            h[(2 * kNB + bt) * 33 + lane] += 1;
-            ++kk;
+        for (int t0 = b > i + 1 ? b : i + 1; t0 < e; t0 += 32) {
+          const int t = t0 + lane;
+          bool in = t < e;
+          float d2 = 0.f;
+          if (in) {
+            const float4 q4 = X[t];
+            const float dx = q4.x - p.x, dy = q4.y - p.y, dz = q4.z - p.z;
+            d2 = dx * dx + dy * dy + dz * dz;
+            in = !(d2 > r2 || d2 == 0.f);
           }
-          int *ht = H + (size_t)t * kDS;
-          if (tie) {
-            // t's own view of the pair
-            const float qx = -dx, qy = -dy, qz = -dz;
-            if (!pair_bins(f3(q4), f3(nq4), p, np, qx * qx + qy * qy + qz * qz, ba, bp, bt)) continue;
-          } else if (!ok) {
-            continue;
+          const unsigned m = __ballot_sync(0xffffffffu, in);
+          if (in) {
+            const int k = cnt + __popc(m & ((1u << lane) - 1u));
+            qt[k] = t;
+            qd[k] = d2;
           }
-          atomicAdd(ht + ba, 1);
-          atomicAdd(ht + kNB + bp, 1);
-          atomicAdd(ht + 2 * kNB + bt, 1);
-          atomicAdd(ht + kD, 1);
+          cnt += __popc(m);
+          if (cnt >= 32) {
+            __syncwarp();
+            evaluate(32);
+            __syncwarp();
+            // move the rest (fewer than 32) to the front
+            if (lane < cnt - 32) {
+              qt[lane] = qt[32 + lane];
+              qd[lane] = qd[32 + lane];
+            }
+            cnt -= 32;
+            __syncwarp();
+          }
         }
       });
+      __syncwarp();
+      evaluate(cnt);
     }
     kk = warp_sum(kk);
     __syncwarp();
