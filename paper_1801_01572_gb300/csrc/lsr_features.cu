@@ -153,7 +153,7 @@ __device__ __forceinline__ bool pair_bins(float3 p, float3 np, float3 q, float3 
 // p's private per-lane column of a per-warp [bin][lane] histogram in shared
 // memory (row stride 33 words, so both the lane-private updates and the
 // per-bin column sums avoid bank conflicts), and into t's counts H (n x 36
-// ints, bins then the pair count in column 33) by atomic adds. p's own sums
+// ints, the 33 bins) by atomic adds. p's own sums
 // are added to H at the end of its warp; k_spfh_finish divides. Counts are
 // integers, so the result does not depend on the order of the adds. The
 // lanes test 32 candidates at a time against r; those within it are queued in
@@ -177,7 +177,6 @@ __global__ void __launch_bounds__(kThreads) k_spfh(const float4 *__restrict__ X,
     for (int b = 0; b < kD; ++b) h[b * 33 + lane] = 0;
     float3 p = f3(X[i]);
     float4 np4 = N[i];
-    int kk = 0;
     if (np4.w >= 0.f) {
       float3 np = f3(np4);
       // the pair (p, t) for the queued candidate of this lane (m lanes)
@@ -196,7 +195,6 @@ __global__ void __launch_bounds__(kThreads) k_spfh(const float4 *__restrict__ X,
           h[ba * 33 + lane] += 1;
           h[(kNB + bp) * 33 + lane] += 1;
           h[(2 * kNB + bt) * 33 + lane] += 1;
-          ++kk;
         }
         int *ht = H + (size_t)t * kDS;
         if (tie) {
@@ -209,7 +207,6 @@ __global__ void __launch_bounds__(kThreads) k_spfh(const float4 *__restrict__ X,
         atomicAdd(ht + ba, 1);
         atomicAdd(ht + kNB + bp, 1);
         atomicAdd(ht + 2 * kNB + bt, 1);
-        atomicAdd(ht + kD, 1);
       };
       int cnt = 0;  // queued candidates (the same on every lane)
       grid_ranges(g, start, p.x, p.y, p.z, [&](int b, int e) {
@@ -247,7 +244,6 @@ __global__ void __launch_bounds__(kThreads) k_spfh(const float4 *__restrict__ X,
       __syncwarp();
       evaluate(cnt);
     }
-    kk = warp_sum(kk);
     __syncwarp();
     int *hi = H + (size_t)i * kDS;
     int c = 0;
@@ -257,19 +253,21 @@ __global__ void __launch_bounds__(kThreads) k_spfh(const float4 *__restrict__ X,
       int c2 = 0;
       for (int l = 0; l < 32; ++l) c2 += h[32 * 33 + l];
       if (c2) atomicAdd(hi + 32, c2);
-      if (kk) atomicAdd(hi + kD, kk);
     }
     __syncwarp();
   }
 }
 
 // S = H / (pair count), one thread per (point, column); zeros in the padding;
-// kout (optional): the pair counts.
+// kout (optional): the pair counts. Every counted pair adds one to each of
+// the three sub-histograms, so the count is the sum of the first one.
 __global__ void k_spfh_finish(const int *__restrict__ H, int n, float *__restrict__ S, int *__restrict__ kout) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * kDS) return;
   const int i = (int)(t / kDS), b = (int)(t - (int64_t)i * kDS);
-  const int kk = H[(size_t)i * kDS + kD];
+  int kk = 0;
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) kk += H[(size_t)i * kDS + k];
   const float inv = kk > 0 ? 1.f / (float)kk : 0.f;
   S[t] = b < kD ? (float)H[t] * inv : 0.f;
   if (b == 0 && kout) kout[i] = kk;
@@ -280,7 +278,6 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
