@@ -64,6 +64,9 @@ __device__ void sym3_eigen(const float a[6], float w[3], float v[3][3]) {
 // Normal of each point: PCA of the points within r (inclusive, self included),
 // accumulated about the query point (one pass), eigenvector of the smallest
 // eigenvalue, turned toward the viewpoint; fewer than 3 points: invalid.
+// A warp walks the neighbourhoods of 32 points one after another (the lanes
+// over each point's candidates); lane k keeps point k's sums, and the 32
+// eigen-decompositions then run at once, one per lane.
 __global__ void __launch_bounds__(kThreads) k_normals(const float4 *__restrict__ X, int n, const GridParams *gnp,
                                                       const int *__restrict__ start, const float4 *__restrict__ Xn,
                                                       float r2, float3 vp, float4 *__restrict__ N,
@@ -71,46 +74,59 @@ __global__ void __launch_bounds__(kThreads) k_normals(const float4 *__restrict__
   const GridParams g = *gnp;
   int lane = threadIdx.x & 31;
   int warp = (blockIdx.x * kThreads + threadIdx.x) >> 5, nwarps = (gridDim.x * kThreads) >> 5;
-  for (int i = warp; i < n; i += nwarps) {
-    float3 p = f3(X[i]);
-    int k = 0;
-    float s[3] = {0, 0, 0}, ss[6] = {0, 0, 0, 0, 0, 0};
-    grid_ranges(g, start, p.x, p.y, p.z, [&](int b, int e) {
-      for (int t = b + lane; t < e; t += 32) {
-        float4 q = Xn[t];
-        float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
-        if (dx * dx + dy * dy + dz * dz <= r2) {
-          ++k;
-          s[0] += dx, s[1] += dy, s[2] += dz;
-          ss[0] += dx * dx, ss[1] += dx * dy, ss[2] += dx * dz;
-          ss[3] += dy * dy, ss[4] += dy * dz, ss[5] += dz * dz;
+  // this warp's points: base + k * nwarps for k = 0..31
+  for (int base = warp; base < n; base += 32 * nwarps) {
+    int mk = 0;
+    float ms[3] = {0, 0, 0}, mss[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < 32; ++j) {
+      const int i = base + j * nwarps;
+      if (i >= n) break;
+      float3 p = f3(X[i]);
+      int k = 0;
+      float s[3] = {0, 0, 0}, ss[6] = {0, 0, 0, 0, 0, 0};
+      grid_ranges(g, start, p.x, p.y, p.z, [&](int b, int e) {
+        for (int t = b + lane; t < e; t += 32) {
+          float4 q = Xn[t];
+          float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+          if (dx * dx + dy * dy + dz * dz <= r2) {
+            ++k;
+            s[0] += dx, s[1] += dy, s[2] += dz;
+            ss[0] += dx * dx, ss[1] += dx * dy, ss[2] += dx * dz;
+            ss[3] += dy * dy, ss[4] += dy * dz, ss[5] += dz * dz;
+          }
         }
+      });
+      k = warp_sum(k);
+      for (int d = 0; d < 3; ++d) s[d] = warp_sum(s[d]);
+      for (int d = 0; d < 6; ++d) ss[d] = warp_sum(ss[d]);
+      if (lane == j) {
+        mk = k;
+        for (int d = 0; d < 3; ++d) ms[d] = s[d];
+        for (int d = 0; d < 6; ++d) mss[d] = ss[d];
       }
-    });
-    k = warp_sum(k);
-    for (int d = 0; d < 3; ++d) s[d] = warp_sum(s[d]);
-    for (int d = 0; d < 6; ++d) ss[d] = warp_sum(ss[d]);
-    if (lane == 0) {
-      float4 out = make_float4(0.f, 0.f, 0.f, -1.f);
-      if (k >= 3) {
-        float ik = 1.f / (float)k;
-        float m[3] = {s[0] * ik, s[1] * ik, s[2] * ik};
-        float C[6] = {ss[0] * ik - m[0] * m[0], ss[1] * ik - m[0] * m[1], ss[2] * ik - m[0] * m[2],
-                      ss[3] * ik - m[1] * m[1], ss[4] * ik - m[1] * m[2], ss[5] * ik - m[2] * m[2]};
-        float w[3], V[3][3];
-        sym3_eigen(C, w, V);
-        int j = 0;
-        if (w[1] < w[j]) j = 1;
-        if (w[2] < w[j]) j = 2;
-        float3 nrm = make_float3(V[0][j], V[1][j], V[2][j]);
-        float3 tv = make_float3(vp.x - p.x, vp.y - p.y, vp.z - p.z);
-        if (dot3(nrm, tv) < 0.f) nrm = make_float3(-nrm.x, -nrm.y, -nrm.z);
-        float sum = w[0] + w[1] + w[2];
-        out = make_float4(nrm.x, nrm.y, nrm.z, sum > 0.f ? fmaxf(w[j], 0.f) / sum : 0.f);
-      }
-      N[i] = out;
-      if (count) count[i] = k;
     }
+    const int i = base + lane * nwarps;
+    if (i >= n) continue;
+    const float3 p = f3(X[i]);
+    float4 out = make_float4(0.f, 0.f, 0.f, -1.f);
+    if (mk >= 3) {
+      float ik = 1.f / (float)mk;
+      float m[3] = {ms[0] * ik, ms[1] * ik, ms[2] * ik};
+      float C[6] = {mss[0] * ik - m[0] * m[0], mss[1] * ik - m[0] * m[1], mss[2] * ik - m[0] * m[2],
+                    mss[3] * ik - m[1] * m[1], mss[4] * ik - m[1] * m[2], mss[5] * ik - m[2] * m[2]};
+      float w[3], V[3][3];
+      sym3_eigen(C, w, V);
+      int jm = 0;
+      if (w[1] < w[jm]) jm = 1;
+      if (w[2] < w[jm]) jm = 2;
+      float3 nrm = make_float3(V[0][jm], V[1][jm], V[2][jm]);
+      float3 tv = make_float3(vp.x - p.x, vp.y - p.y, vp.z - p.z);
+      if (dot3(nrm, tv) < 0.f) nrm = make_float3(-nrm.x, -nrm.y, -nrm.z);
+      float sum = w[0] + w[1] + w[2];
+      out = make_float4(nrm.x, nrm.y, nrm.z, sum > 0.f ? fmaxf(w[jm], 0.f) / sum : 0.f);
+    }
+    N[i] = out;
+    if (count) count[i] = mk;
   }
 }
 
@@ -492,7 +508,10 @@ inline int blocks_for_warps(int n) {
 
 cudaError_t launch_normals(const float4 *X, int n, const GridParams *gn, const int *start_n, const float4 *Xn, float r,
                            float3 vp, float4 *N, int *count, cudaStream_t s) {
-  LSR_LAUNCH(k_normals<<<blocks_for_warps(n), kThreads, 0, s>>>(X, n, gn, start_n, Xn, r * r, vp, N, count));
+  // about 32 points a warp (the eigen-decompositions run a lane each)
+  const int64_t nb = lsr_div_up(lsr_div_up(n > 0 ? n : 1, 32), kWarps);
+  LSR_LAUNCH(k_normals<<<(int)(nb < kSms * 64 ? nb : kSms * 64), kThreads, 0, s>>>(X, n, gn, start_n, Xn, r * r, vp, N,
+                                                                                   count));
   return cudaGetLastError();
 }
 
